@@ -1,0 +1,275 @@
+"""FP64 CPU oracle for the phase-field fracture operator (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package.  It shares no code with the CUDA library: the
+compiled part (``pff_oracle.cpp``) has its own basis, kinematics, constitutive
+update (matrix functions + dual numbers), element matrices and CSR assembly;
+the Python part below adds what the paper states as textbook linear algebra:
+sparse products, the Chebyshev iteration and direct solves.
+
+Functions and the passages they follow:
+
+* ``basis``            -- GLL / Gauss points and 1D Lagrange matrices (Sec. 4, B_I, B_xi).
+* ``pointwise``        -- Box 1 + Sec. 3 pointwise update and its tangent (App. B, C by
+                          dual numbers).
+* ``assemble``         -- Eq. matrix-free-residual-compact / matrix-free-jacobian as a
+                          global residual and an assembled CSR Jacobian (Dirichlet rows
+                          and columns replaced by the identity).
+* ``sample_rows``      -- the same quantities for selected rows of large meshes.
+* ``prolongation``     -- p-prolongation P[f, c] = coarse basis at the fine nodes; R = P^T.
+* ``coarse_operator``  -- Galerkin product P^T A P (equal to rediscretisation at the fine
+                          Gauss points).
+* ``chebyshev``        -- textbook Chebyshev iteration on D^-1 A (Saad, Alg. 12.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pff_oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (FP64, no FMA contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+               "-o", _LIB + ".tmp", _SRC]
+        subprocess.check_call(cmd)
+        os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        u8p = ctypes.POINTER(ctypes.c_uint8)
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        L.orc_basis.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
+        L.orc_lagrange_eval.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.orc_pointwise.argtypes = [ctypes.c_int, dp, dp, u8p, dp, ctypes.c_int, dp,
+                                    dp, dp, dp, dp, u8p, dp]
+        L.orc_logm1p.argtypes = [dp, dp]
+        L.orc_expm.argtypes = [dp, dp]
+        L.orc_assemble.argtypes = [ip, dp, dp, ctypes.c_int, dp, dp, dp, u8p, u8p, dp,
+                                   ctypes.c_int, dp, dp, u8p, dp]
+        L.orc_assemble.restype = ctypes.c_void_p
+        L.orc_csr_nnz.argtypes = [ctypes.c_void_p]
+        L.orc_csr_nnz.restype = ctypes.c_longlong
+        L.orc_csr_get.argtypes = [ctypes.c_void_p, llp, llp, dp]
+        L.orc_csr_free.argtypes = [ctypes.c_void_p]
+        L.orc_sample_rows.argtypes = [ip, dp, dp, ctypes.c_int, dp, dp, dp, u8p, u8p, dp, dp,
+                                      ctypes.c_int, llp, dp, dp, dp, dp]
+        L.orc_prolong_coo.argtypes = [ip, ctypes.c_int, ctypes.c_int, llp, llp, dp]
+        L.orc_prolong_coo.restype = ctypes.c_longlong
+        L.orc_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a, t=ctypes.c_double):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _u8(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# ---------------------------------------------------------------------------
+def basis(p: int, Q: int):
+    """GLL nodes xg[P], Gauss nodes xq[Q] and weights wq[Q], and the 1D Lagrange
+    value / derivative matrices B[Q,P], D[Q,P] at the Gauss points."""
+    P = p + 1
+    xg, xq, wq = np.zeros(P), np.zeros(Q), np.zeros(Q)
+    B, D = np.zeros((Q, P)), np.zeros((Q, P))
+    lib().orc_basis(p, Q, _p(xg), _p(xq), _p(wq), _p(B), _p(D))
+    return xg, xq, wq, B, D
+
+
+def lagrange(p: int, t):
+    t = _f64(np.atleast_1d(t))
+    L = np.zeros((len(t), p + 1))
+    dL = np.zeros((len(t), p + 1))
+    lib().orc_lagrange_eval(p, len(t), _p(t), _p(L), _p(dL))
+    return L, dL
+
+
+def logm1p(X):
+    X = _f64(X).reshape(3, 3)
+    out = np.zeros((3, 3))
+    lib().orc_logm1p(_p(X), _p(out))
+    return out
+
+
+def expm(A):
+    A = _f64(A).reshape(3, 3)
+    out = np.zeros((3, 3))
+    lib().orc_expm(_p(A), _p(out))
+    return out
+
+
+def pointwise(inputs, hist, phase, phases, glob, tangent: bool = True, commit: bool = True):
+    """Pointwise update at n points.  inputs [n,13] = (grad u row-major, phi,
+    grad phi); hist [n,15] point-major; phase uint8 [n].  Returns a dict with
+    f0 [n,4], f1 [n,4,3], D [n,16,16], hist_new [n,15], flags, psi_plus,
+    margin_yield, margin_hist, theta."""
+    inputs = _f64(inputs)
+    n = inputs.shape[0]
+    hist = _f64(hist)
+    phase = _u8(phase)
+    phases = _f64(phases)
+    glob = _f64(glob)
+    f0 = np.zeros((n, 4))
+    f1 = np.zeros((n, 12))
+    D = np.zeros((n, 16, 16)) if tangent else None
+    hn = np.zeros((n, 15)) if commit else None
+    flags = np.zeros(n, dtype=np.uint8)
+    aux = np.zeros((n, 4))
+    lib().orc_pointwise(n, _p(inputs), _p(hist), _p(phase, ctypes.c_uint8), _p(phases), len(phases),
+                        _p(glob), _p(f0), _p(f1), _p(D), _p(hn), _p(flags, ctypes.c_uint8), _p(aux))
+    return dict(f0=f0, f1=f1.reshape(n, 4, 3), D=D, hist_new=hn, flags=flags,
+                psi_plus=aux[:, 0], margin_yield=aux[:, 1], margin_hist=aux[:, 2], theta=aux[:, 3])
+
+
+def _mesh_args(mesh):
+    dims = np.ascontiguousarray(mesh.dims, dtype=np.int32)
+    h = _f64(mesh.h)
+    return dims, h
+
+
+def assemble(w, z=None, hist=None, matrix: bool = True, mask="workload", dvals="workload"):
+    """Residual, trial history, flags and (optionally) the assembled CSR Jacobian
+    of workload ``w`` (see ``paper_2607_21150_gb300.inputs.Workload``)."""
+    import scipy.sparse as sp
+
+    m = w.mesh
+    z = _f64(w.z if z is None else z)
+    hist = _f64(w.hist if hist is None else hist)
+    mask = w.mask if isinstance(mask, str) else mask
+    dvals = w.dvals if isinstance(dvals, str) else dvals
+    mask = _u8(mask)
+    dvals = None if dvals is None else _f64(dvals)
+    dims, h = _mesh_args(m)
+    r = np.zeros(4 * m.nn)
+    hn = np.zeros((15, m.nq))
+    flags = np.zeros(m.nq, dtype=np.uint8)
+    margins = np.zeros((m.nq, 3))
+    L = lib()
+    handle = L.orc_assemble(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(w.phases)),
+                            len(w.phases), _p(_f64(w.glob)), _p(z), _p(hist),
+                            _p(_u8(w.phase), ctypes.c_uint8), _p(mask, ctypes.c_uint8), _p(dvals),
+                            1 if matrix else 0, _p(r), _p(hn), _p(flags, ctypes.c_uint8), _p(margins))
+    out = dict(r=r.reshape(4, m.nn), hist_new=hn, flags=flags, margins=margins)
+    if matrix:
+        nnz = L.orc_csr_nnz(handle)
+        nd = 4 * m.nn
+        indptr = np.zeros(nd + 1, dtype=np.int64)
+        indices = np.zeros(nnz, dtype=np.int64)
+        data = np.zeros(nnz)
+        L.orc_csr_get(handle, _p(indptr, ctypes.c_longlong), _p(indices, ctypes.c_longlong), _p(data))
+        L.orc_csr_free(handle)
+        out["K"] = sp.csr_matrix((data, indices, indptr), shape=(nd, nd))
+    return out
+
+
+def sample_rows(w, dofs, x, z=None, hist=None):
+    """For global DoFs ``dofs``: residual, (J x), (J^T x) and diag(J) entries."""
+    m = w.mesh
+    dofs = np.ascontiguousarray(dofs, dtype=np.int64)
+    ns = len(dofs)
+    z = _f64(w.z if z is None else z)
+    hist = _f64(w.hist if hist is None else hist)
+    x = _f64(x)
+    dims, h = _mesh_args(m)
+    r, jx, jtx, dg = np.zeros(ns), np.zeros(ns), np.zeros(ns), np.zeros(ns)
+    lib().orc_sample_rows(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(w.phases)),
+                          len(w.phases), _p(_f64(w.glob)), _p(z), _p(hist),
+                          _p(_u8(w.phase), ctypes.c_uint8), _p(_u8(w.mask), ctypes.c_uint8),
+                          _p(None if w.dvals is None else _f64(w.dvals)), _p(x), ns,
+                          _p(dofs, ctypes.c_longlong), _p(r), _p(jx), _p(jtx), _p(dg))
+    return dict(r=r, jx=jx, jtx=jtx, diag=dg)
+
+
+def prolongation(mesh, pc: int, pf: int | None = None):
+    """Sparse p-prolongation P (4 n_f x 4 n_c) from order pc to order pf (default
+    mesh.p) on the element grid of ``mesh``: coarse Lagrange basis at fine nodes."""
+    import scipy.sparse as sp
+
+    pf = mesh.p if pf is None else pf
+    dims = np.ascontiguousarray(mesh.dims, dtype=np.int32)
+    L = lib()
+    ip = dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    n = L.orc_prolong_coo(ip, pc, pf, None, None, None)
+    rows = np.zeros(n, dtype=np.int64)
+    cols = np.zeros(n, dtype=np.int64)
+    vals = np.zeros(n)
+    L.orc_prolong_coo(ip, pc, pf, _p(rows, ctypes.c_longlong), _p(cols, ctypes.c_longlong), _p(vals))
+    nf = (pf * mesh.nx + 1) * (pf * mesh.ny + 1) * (pf * mesh.nz + 1)
+    nc = (pc * mesh.nx + 1) * (pc * mesh.ny + 1) * (pc * mesh.nz + 1)
+    P1 = sp.csr_matrix((vals, (rows, cols)), shape=(nf, nc))
+    return sp.block_diag([P1] * 4, format="csr")
+
+
+def masked_prolongation(P, mask_f, mask_c):
+    """P with the rows of fine Dirichlet DoFs and columns of coarse Dirichlet
+    DoFs removed: diag(1 - m_f) P diag(1 - m_c)."""
+    import scipy.sparse as sp
+
+    mf = 1.0 - np.asarray(mask_f, dtype=np.float64).ravel()
+    mc = 1.0 - np.asarray(mask_c, dtype=np.float64).ravel()
+    return (sp.diags(mf) @ P @ sp.diags(mc)).tocsr()
+
+
+def coarse_operator(K_f, P, mask_c=None):
+    """Galerkin coarse operator P^T K_f P, Dirichlet DoFs of the coarse level
+    set to the identity (P must already be masked)."""
+    import scipy.sparse as sp
+
+    Kc = (P.T @ K_f @ P).tocsr()
+    if mask_c is not None:
+        mc = np.asarray(mask_c, dtype=bool).ravel()
+        keep = sp.diags((~mc).astype(np.float64))
+        Kc = (keep @ Kc @ keep + sp.diags(mc.astype(np.float64))).tocsr()
+    return Kc
+
+
+def chebyshev(A, diag, b, x0, degree: int, lmin: float, lmax: float):
+    """Chebyshev iteration for A x = b preconditioned by D = diag(diag) on the
+    eigenvalue interval [lmin, lmax] of D^-1 A (Saad, Iterative Methods for
+    Sparse Linear Systems, Alg. 12.1): ``degree`` matrix-vector products, the
+    error is multiplied by T_k((theta - D^-1 A)/delta) / T_k(theta/delta)."""
+    theta = 0.5 * (lmax + lmin)
+    delta = 0.5 * (lmax - lmin)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = (b - A @ x) / diag
+    d = r / theta
+    for k in range(degree):
+        x = x + d
+        if k == degree - 1:
+            break
+        r = r - (A @ d) / diag
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * r
+        rho = rho_new
+    return x

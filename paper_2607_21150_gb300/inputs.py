@@ -1,0 +1,486 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the oracle.
+
+This module holds NO arithmetic of the method: it only draws random numbers,
+lays out a structured box mesh, places particles and writes parameter tables.
+Everything it returns is plain numpy data that both sides consume.
+
+Workloads (units mm, MPa, s):
+
+* ``cube``     -- unit cube, 4^3 Q2 elements, homogeneous matrix material
+                  (Hooke + Maxwell + perfectly plastic Prandtl, Table 2,
+                  Example 3 column), AT2, random nodal fields, zero history.
+* ``cube_b``   -- the same mesh with a seeded random committed history so that
+                  both yield states and both history states occur.
+* ``tension_q4``   -- Q4, 16^3 elements, two-phase particle/matrix
+                  microstructure (spheres, lognormal radii, volume fraction
+                  0.6), uniaxial tension, AT1, Example 3 parameters.
+* ``notched_q3``   -- Q3, 48x48x144 elements, notched bar (aspect 1:1:3).
+* ``adjoint_q2``   -- Q2, 24^3 elements, tension, AT2.
+* ``compress_q4``  -- Q4, 64^3 elements (~67.9 M DoF), volume fraction 0.7,
+                  uniaxial compression with frictionless platens, AT2,
+                  Example 2 parameters.
+
+The paper's own microstructures (microstructpy seed lists, Gmsh meshes) are not
+available; these generators stand in for them with the same statistics.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ---------------------------------------------------------------------------
+# Material parameters (Table 2), converted to mm / MPa / s.
+# Phase parameter vector layout (12 doubles):
+#   Gc, l0, E_inf, nu_inf, hasMaxwell, E1, nu1, eta_d, hasPrandtl, E2, nu2, sigma0
+# Global parameter vector (5 doubles): AT (1|2), eta (residual stiffness),
+#   zeta (damage viscosity), dt, s_phi.
+# ---------------------------------------------------------------------------
+GPA = 1.0e3  # MPa per GPa
+
+EX3_PARTICLE = dict(Gc=8.0, l0=0.005, E0=400 * GPA, nu0=0.25)
+EX3_MATRIX = dict(Gc=0.8, l0=0.005, E0=1.0 * GPA, nu0=0.3,
+                  maxwell=(1.0 * GPA, 0.3, 0.01 * GPA),
+                  prandtl=(198 * GPA, 0.30, 500.0))
+EX2_PARTICLE = dict(Gc=0.1, l0=0.01, E0=10 * GPA, nu0=0.3)
+EX2_MATRIX = dict(Gc=0.01, l0=0.01, E0=1.0 * GPA, nu0=0.4,
+                  maxwell=(1.0 * GPA, 0.4, 0.1 * GPA))
+
+
+def phase_vector(d: dict) -> np.ndarray:
+    """Pack one phase's parameters into the 12-double layout above."""
+    v = np.zeros(12)
+    v[0], v[1], v[2], v[3] = d["Gc"], d["l0"], d["E0"], d["nu0"]
+    if "maxwell" in d:
+        v[4] = 1.0
+        v[5], v[6], v[7] = d["maxwell"]
+    if "prandtl" in d:
+        v[8] = 1.0
+        v[9], v[10], v[11] = d["prandtl"]
+    return v
+
+
+def c0_of(at: int) -> float:
+    """Normalisation constant of the AT1 (8/3) / AT2 (2) crack density."""
+    return 8.0 / 3.0 if at == 1 else 2.0
+
+
+def s_phi_of(matrix: dict, at: int) -> float:
+    """Global phase-field residual scale E c0 / (2 l0 Gc) of the matrix phase."""
+    return matrix["E0"] * c0_of(at) / (2.0 * matrix["l0"] * matrix["Gc"])
+
+
+def glob_vector(at: int, eta: float, zeta: float, dt: float, s_phi: float) -> np.ndarray:
+    return np.array([float(at), eta, zeta, dt, s_phi])
+
+
+# ---------------------------------------------------------------------------
+# Structured box mesh
+# ---------------------------------------------------------------------------
+@dataclass
+class Mesh:
+    nx: int
+    ny: int
+    nz: int
+    p: int
+    Q: int
+    L: tuple  # side lengths (Lx, Ly, Lz)
+
+    @property
+    def h(self):
+        return (self.L[0] / self.nx, self.L[1] / self.ny, self.L[2] / self.nz)
+
+    @property
+    def dims(self):
+        return np.array([self.nx, self.ny, self.nz, self.p, self.Q], dtype=np.int32)
+
+    @property
+    def nnx(self):
+        return self.p * self.nx + 1
+
+    @property
+    def nny(self):
+        return self.p * self.ny + 1
+
+    @property
+    def nnz(self):
+        return self.p * self.nz + 1
+
+    @property
+    def nn(self):
+        return self.nnx * self.nny * self.nnz
+
+    @property
+    def nel(self):
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nq(self):
+        return self.nel * self.Q ** 3
+
+    @property
+    def ndof(self):
+        return 4 * self.nn
+
+
+def gll_points(p: int) -> np.ndarray:
+    """Gauss-Lobatto-Legendre points on [-1, 1] (numpy's Legendre roots)."""
+    if p == 1:
+        return np.array([-1.0, 1.0])
+    inner = np.polynomial.legendre.Legendre.basis(p).deriv().roots()
+    return np.concatenate([[-1.0], np.sort(inner.real), [1.0]])
+
+
+def gauss_points(Q: int) -> np.ndarray:
+    return np.polynomial.legendre.leggauss(Q)[0]
+
+
+def node_coords(m: Mesh) -> np.ndarray:
+    """Reference coordinates of every node, shape [nn, 3] (node id = I + nnx (J + nny K))."""
+    xs = []
+    g = gll_points(m.p)
+    for d, (n, Ld) in enumerate(zip((m.nx, m.ny, m.nz), m.L)):
+        h = Ld / n
+        pts = np.empty(m.p * n + 1)
+        for e in range(n):
+            pts[m.p * e: m.p * e + m.p + 1] = e * h + (g + 1.0) * 0.5 * h
+        xs.append(pts)
+    X, Y, Z = np.meshgrid(xs[0], xs[1], xs[2], indexing="ij")
+    # node id = I + nnx*(J + nny*K): flatten with K slowest, I fastest
+    return np.stack([X.transpose(2, 1, 0).ravel(), Y.transpose(2, 1, 0).ravel(),
+                     Z.transpose(2, 1, 0).ravel()], axis=1)
+
+
+def qpoint_coords(m: Mesh) -> np.ndarray:
+    """Reference coordinates of every Gauss point, shape [nq, 3] (q = e Q^3 + i + Q (j + Q k))."""
+    g = gauss_points(m.Q)
+    hx, hy, hz = m.h
+    ex = np.arange(m.nx)
+    ey = np.arange(m.ny)
+    ez = np.arange(m.nz)
+    # element-major, then k, j, i (i fastest)
+    EZ, EY, EX, K, J, I = np.meshgrid(ez, ey, ex, np.arange(m.Q), np.arange(m.Q), np.arange(m.Q), indexing="ij")
+    x = EX * hx + (g[I] + 1) * 0.5 * hx
+    y = EY * hy + (g[J] + 1) * 0.5 * hy
+    z = EZ * hz + (g[K] + 1) * 0.5 * hz
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+# ---------------------------------------------------------------------------
+# Microstructure: seeded spheres, lognormal radii, force-biased relaxation
+# ---------------------------------------------------------------------------
+@dataclass
+class Spheres:
+    centers: np.ndarray
+    radii: np.ndarray
+    max_overlap: float
+    sweeps: int
+
+
+def place_spheres(seed: int, mean: float, sd: float, vf: float, max_sweeps: int = 2000) -> Spheres:
+    """Spheres in the unit cube (periodic), radii lognormal(mean, sd), until their
+    summed volume reaches ``vf``; overlaps pushed apart pairwise until the largest
+    relative overlap is below 1e-3 or ``max_sweeps`` is reached."""
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    s2 = math.log(1.0 + (sd / mean) ** 2)
+    mu = math.log(mean) - 0.5 * s2
+    radii = []
+    vol = 0.0
+    while vol < vf:
+        r = float(rng.lognormal(mu, math.sqrt(s2)))
+        r = min(r, 0.45)
+        radii.append(r)
+        vol += 4.0 / 3.0 * math.pi * r ** 3
+    radii = np.array(sorted(radii, reverse=True))
+    centers = rng.random((len(radii), 3))
+    rmax = radii.max()
+    worst = 0.0
+    sweep = 0
+    for sweep in range(1, max_sweeps + 1):
+        tree = cKDTree(centers, boxsize=1.0)
+        pairs = tree.query_pairs(2.0 * rmax, output_type="ndarray")
+        if len(pairs) == 0:
+            worst = 0.0
+            break
+        d = centers[pairs[:, 1]] - centers[pairs[:, 0]]
+        d -= np.round(d)
+        dist = np.linalg.norm(d, axis=1)
+        rs = radii[pairs[:, 0]] + radii[pairs[:, 1]]
+        ov = rs - dist
+        sel = ov > 0
+        if not np.any(sel):
+            worst = 0.0
+            break
+        worst = float(np.max(ov[sel] / rs[sel]))
+        if worst < 1e-3:
+            break
+        pr, d, dist, ov = pairs[sel], d[sel], np.maximum(dist[sel], 1e-12), ov[sel]
+        push = (0.5 * ov / dist)[:, None] * d
+        np.add.at(centers, pr[:, 0], -push)
+        np.add.at(centers, pr[:, 1], push)
+        centers %= 1.0
+    return Spheres(centers, radii, worst, sweep)
+
+
+def phase_map(points_unit: np.ndarray, sph: Spheres, chunk: int = 1 << 20) -> np.ndarray:
+    """uint8 phase per point: 1 inside any (periodic) sphere = particle, 0 = matrix.
+    ``points_unit`` are coordinates scaled to the unit cube."""
+    from scipy.spatial import cKDTree
+
+    tree = cKDTree(sph.centers, boxsize=1.0)
+    rmax = sph.radii.max()
+    out = np.zeros(len(points_unit), dtype=np.uint8)
+    pts = np.mod(points_unit, 1.0)
+    for s in range(0, len(pts), chunk):
+        p = pts[s:s + chunk]
+        near = tree.query_ball_point(p, rmax)
+        for i, lst in enumerate(near):
+            if not lst:
+                continue
+            d = sph.centers[lst] - p[i]
+            d -= np.round(d)
+            if np.any(np.einsum("ij,ij->i", d, d) < sph.radii[lst] ** 2):
+                out[s + i] = 1
+    return out
+
+
+def phase_map_fast(m: Mesh, sph: Spheres, scale: np.ndarray) -> np.ndarray:
+    """Phase per Gauss point by rasterising each sphere's bounding box on the
+    structured grid of Gauss points (same result as ``phase_map``)."""
+    g = gauss_points(m.Q)
+    h = np.array(m.h)
+    n = np.array([m.nx, m.ny, m.nz])
+    # 1D Gauss coordinates along each axis, in unit-cube coordinates
+    axes = []
+    for d in range(3):
+        e = np.arange(n[d])[:, None]
+        axes.append(((e * h[d] + (g[None, :] + 1) * 0.5 * h[d]) / scale[d]).ravel())
+    nqx, nqy, nqz = len(axes[0]), len(axes[1]), len(axes[2])
+    grid = np.zeros((nqz, nqy, nqx), dtype=np.uint8)
+    for c, r in zip(sph.centers, sph.radii):
+        for sx in (-1, 0, 1):
+            for sy in (-1, 0, 1):
+                for sz in (-1, 0, 1):
+                    cc = c + np.array([sx, sy, sz])
+                    lo = cc - r
+                    hi = cc + r
+                    if np.any(hi < 0) or np.any(lo > 1):
+                        continue
+                    ix = np.nonzero((axes[0] >= lo[0]) & (axes[0] <= hi[0]))[0]
+                    iy = np.nonzero((axes[1] >= lo[1]) & (axes[1] <= hi[1]))[0]
+                    iz = np.nonzero((axes[2] >= lo[2]) & (axes[2] <= hi[2]))[0]
+                    if len(ix) == 0 or len(iy) == 0 or len(iz) == 0:
+                        continue
+                    dx = (axes[0][ix] - cc[0]) ** 2
+                    dy = (axes[1][iy] - cc[1]) ** 2
+                    dz = (axes[2][iz] - cc[2]) ** 2
+                    inside = (dz[:, None, None] + dy[None, :, None] + dx[None, None, :]) < r * r
+                    sub = grid[np.ix_(iz, iy, ix)]
+                    grid[np.ix_(iz, iy, ix)] = sub | inside.astype(np.uint8)
+    # reorder from the (z,y,x) Gauss grid to element-major q = e Q^3 + i + Q (j + Q k)
+    Q = m.Q
+    g6 = grid.reshape(m.nz, Q, m.ny, Q, m.nx, Q)  # ez, k, ey, j, ex, i
+    return np.ascontiguousarray(g6.transpose(0, 2, 4, 1, 3, 5)).ravel()
+
+
+# ---------------------------------------------------------------------------
+# Dirichlet data
+# ---------------------------------------------------------------------------
+def dirichlet_tension(m: Mesh, delta: float):
+    """Bottom face z = 0 clamped; top face z = Lz: u_x = u_y = 0, u_z = delta."""
+    mask = np.zeros((4, m.nnz, m.nny, m.nnx), dtype=np.uint8)
+    vals = np.zeros((4, m.nnz, m.nny, m.nnx))
+    mask[0:3, 0] = 1
+    mask[0:3, -1] = 1
+    vals[2, -1] = delta
+    return mask.reshape(4, -1), vals.reshape(4, -1)
+
+
+def dirichlet_compression(m: Mesh, delta: float):
+    """Frictionless platens: u_z = 0 at z = 0, u_z = -delta at z = Lz, u_x = 0 on
+    x = 0, u_y = 0 on y = 0."""
+    mask = np.zeros((4, m.nnz, m.nny, m.nnx), dtype=np.uint8)
+    vals = np.zeros((4, m.nnz, m.nny, m.nnx))
+    mask[2, 0] = 1
+    mask[2, -1] = 1
+    vals[2, -1] = -delta
+    mask[0, :, :, 0] = 1
+    mask[1, :, 0, :] = 1
+    return mask.reshape(4, -1), vals.reshape(4, -1)
+
+
+def top_face_mask(m: Mesh) -> np.ndarray:
+    """uint8 [4][nn] selecting the u_z DoFs of the top face (reaction force)."""
+    mask = np.zeros((4, m.nnz, m.nny, m.nnx), dtype=np.uint8)
+    mask[2, -1] = 1
+    return mask.reshape(4, -1)
+
+
+# ---------------------------------------------------------------------------
+# Random fields and histories
+# ---------------------------------------------------------------------------
+def random_state(m: Mesh, seed: int = 0, u_amp: float = 1e-3, phi_max: float = 0.3) -> np.ndarray:
+    """Nodal z [4][nn]: u ~ U[-u_amp, u_amp] (mm), phi ~ U[0, phi_max]; PCG64(seed),
+    drawn in the order u_x, u_y, u_z, phi over nodes in lexicographic order."""
+    rng = np.random.default_rng(seed)
+    z = np.empty((4, m.nn))
+    for f in range(3):
+        z[f] = rng.uniform(-u_amp, u_amp, m.nn)
+    z[3] = rng.uniform(0.0, phi_max, m.nn)
+    return z
+
+
+def random_vector(n: int, seed: int = 1) -> np.ndarray:
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+
+
+def zero_history(nq: int, H0: float = 0.0) -> np.ndarray:
+    """Committed history [15][nq]: C_M = C_P = I (Voigt), eps_p = 0, H = H0, phi_n = 0."""
+    h = np.zeros((15, nq))
+    h[0:3] = 1.0
+    h[6:9] = 1.0
+    h[13] = H0
+    return h
+
+
+def _sym_from_voigt(v):
+    A = np.empty(v.shape[:-1] + (3, 3))
+    A[..., 0, 0], A[..., 1, 1], A[..., 2, 2] = v[..., 0], v[..., 1], v[..., 2]
+    A[..., 1, 2] = A[..., 2, 1] = v[..., 3]
+    A[..., 0, 2] = A[..., 2, 0] = v[..., 4]
+    A[..., 0, 1] = A[..., 1, 0] = v[..., 5]
+    return A
+
+
+def random_history(nq: int, seed: int = 2, c_amp: float = 0.05, ep_max: float = 0.01,
+                   H_max: float = 1.0, phi_n_max: float = 0.3) -> np.ndarray:
+    """Committed history [15][nq] with isochoric C_M, C_P = exp(S), S symmetric
+    traceless with |S|_F <= c_amp, eps_p ~ U[0, ep_max], H ~ U[0, H_max],
+    phi_n ~ U[0, phi_n_max]."""
+    rng = np.random.default_rng(seed)
+    h = np.zeros((15, nq))
+    for off in (0, 6):
+        v = rng.uniform(-1.0, 1.0, (nq, 6))
+        S = _sym_from_voigt(v)
+        tr = np.trace(S, axis1=1, axis2=2)
+        S -= tr[:, None, None] / 3.0 * np.eye(3)
+        nrm = np.linalg.norm(S, axis=(1, 2))
+        S *= (c_amp * rng.uniform(0.0, 1.0, nq) / np.maximum(nrm, 1e-300))[:, None, None]
+        w, V = np.linalg.eigh(S)
+        C = np.einsum("nij,nj,nkj->nik", V, np.exp(w), V)
+        h[off + 0], h[off + 1], h[off + 2] = C[:, 0, 0], C[:, 1, 1], C[:, 2, 2]
+        h[off + 3], h[off + 4], h[off + 5] = C[:, 1, 2], C[:, 0, 2], C[:, 0, 1]
+    h[12] = rng.uniform(0.0, ep_max, nq)
+    h[13] = rng.uniform(0.0, H_max, nq)
+    h[14] = rng.uniform(0.0, phi_n_max, nq)
+    return h
+
+
+# ---------------------------------------------------------------------------
+# Workload definitions
+# ---------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    phases: np.ndarray            # [nphase][12]
+    glob: np.ndarray              # [5]
+    phase: np.ndarray             # uint8 [nq]
+    z: np.ndarray                 # [4][nn] state
+    hist: np.ndarray              # [15][nq]
+    mask: np.ndarray | None = None
+    dvals: np.ndarray | None = None
+    meta: dict = field(default_factory=dict)
+
+
+def cube(nx: int = 4, p: int = 2, seed_state: int = 0, hist_seed: int | None = None,
+         H_max: float = 1.0, u_amp: float = 1e-3) -> Workload:
+    """Homogeneous unit cube (Table 2, Example 3 matrix), AT2, dt = 0.01 s,
+    eta = 1e-3, zeta = 1e-2 MPa s, no Dirichlet conditions."""
+    m = Mesh(nx, nx, nx, p, p + 1, (1.0, 1.0, 1.0))
+    at = 2
+    glob = glob_vector(at, 1e-3, 1e-2, 0.01, s_phi_of(EX3_MATRIX, at))
+    phases = np.stack([phase_vector(EX3_MATRIX)])
+    phase = np.zeros(m.nq, dtype=np.uint8)
+    z = random_state(m, seed_state, u_amp=u_amp)
+    hist = zero_history(m.nq) if hist_seed is None else random_history(m.nq, hist_seed, H_max=H_max)
+    return Workload("cube" if hist_seed is None else "cube_b", m, phases, glob, phase, z, hist)
+
+
+def two_phase_box(nx, ny, nz, p, L, sph_mean, sph_sd, vf, seed, at, example, bc, delta,
+                  dt, eta=1e-3, zeta=1e-2, notch=False) -> Workload:
+    m = Mesh(nx, ny, nz, p, p + 1, L)
+    if example == 3:
+        matrix, particle = EX3_MATRIX, EX3_PARTICLE
+    else:
+        matrix, particle = EX2_MATRIX, EX2_PARTICLE
+    phases = np.stack([phase_vector(matrix), phase_vector(particle)])
+    glob = glob_vector(at, eta, zeta, dt, s_phi_of(matrix, at))
+    sph = place_spheres(seed, sph_mean, sph_sd, vf)
+    scale = np.array(L) / max(L)
+    phase = phase_map_fast(m, sph, np.array([max(L)] * 3))
+    H0 = np.zeros(m.nq)
+    if at == 1:  # AT1 threshold psi_c = 3 Gc / (16 l0) per phase
+        for ph_id, d in ((0, matrix), (1, particle)):
+            H0[phase == ph_id] = 3.0 * d["Gc"] / (16.0 * d["l0"])
+    hist = zero_history(m.nq)
+    hist[13] = H0
+    z = np.zeros((4, m.nn))
+    if notch:
+        xq = qpoint_coords(m)
+        sel = (xq[:, 0] < 0.2 * L[0]) & (np.abs(xq[:, 2] - 0.5 * L[2]) < 0.01 * L[2])
+        hist[13, sel] = 1e4 * hist[13, sel]
+        X = node_coords(m)
+        nsel = (X[:, 0] < 0.2 * L[0]) & (np.abs(X[:, 2] - 0.5 * L[2]) < 0.01 * L[2])
+        z[3, nsel] = 1.0
+    mask, dvals = (dirichlet_tension if bc == "tension" else dirichlet_compression)(m, delta)
+    z[mask.astype(bool)] = dvals[mask.astype(bool)]
+    meta = dict(spheres=len(sph.radii), max_overlap=sph.max_overlap, sweeps=sph.sweeps,
+                vf_points=float(phase.mean()), scale=scale.tolist())
+    return Workload("box", m, phases, glob, phase, z, hist, mask, dvals, meta)
+
+
+def tension_q4(n: int = 16, seed: int = 0) -> Workload:
+    """Q4, n^3 elements on L = 0.16 mm (h = 2 l0), spheres mean 0.06 L / sd 0.02 L,
+    vf 0.6, tension at 0.4 /s, AT1, Example 3; 10 steps to 2 % strain."""
+    L = 0.16 * n / 16.0
+    strain_per_step = 0.002
+    dt = strain_per_step / 0.4
+    w = two_phase_box(n, n, n, 4, (L, L, L), 0.06, 0.02, 0.6, seed, 1, 3, "tension",
+                      strain_per_step * L, dt)
+    w.name = "tension_q4"
+    w.meta.update(steps=10, strain_per_step=strain_per_step)
+    return w
+
+
+def notched_q3(n: int = 48, seed: int = 0) -> Workload:
+    L = (0.01 * n, 0.01 * n, 0.03 * n)
+    strain_per_step = 0.001
+    w = two_phase_box(n, n, 3 * n, 3, L, 0.06, 0.02, 0.6, seed, 1, 3, "tension",
+                      strain_per_step * L[2], strain_per_step / 0.4, notch=True)
+    w.name = "notched_q3"
+    w.meta.update(steps=40, strain_per_step=strain_per_step)
+    return w
+
+
+def adjoint_q2(n: int = 24, seed: int = 0) -> Workload:
+    L = 0.01 * n
+    strain_per_step = 0.001
+    w = two_phase_box(n, n, n, 2, (L, L, L), 0.06, 0.02, 0.6, seed, 2, 3, "tension",
+                      strain_per_step * L, strain_per_step / 0.4)
+    w.name = "adjoint_q2"
+    w.meta.update(steps=20, strain_per_step=strain_per_step)
+    return w
+
+
+def compress_q4(n: int = 64, seed: int = 0) -> Workload:
+    L = 0.01 * n
+    strain_per_step = 0.001
+    w = two_phase_box(n, n, n, 4, (L, L, L), 0.04, 0.015, 0.7, seed, 2, 2, "compression",
+                      strain_per_step * L, strain_per_step / 0.05, eta=1e-2)
+    w.name = "compress_q4"
+    w.meta.update(steps=30, strain_per_step=strain_per_step)
+    return w

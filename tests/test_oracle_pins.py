@@ -1,0 +1,445 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Each test states the passage or the closed form it checks.  None of them
+re-types the oracle's own formula: they use textbook values, library routines
+(scipy matrix functions, numpy polynomials), closed-form solutions, exact
+discrete identities, finite differences, or an independent restatement of
+the paper's Appendix B/C closed forms (tests/appendix_tangent.py).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from paper_2607_21150_gb300 import inputs
+import appendix_tangent as app
+
+
+# --------------------------------------------------------------------------- basis
+def test_gll_gauss_textbook(orc):
+    xg, xq, wq, B, D = orc.basis(2, 3)
+    assert np.allclose(xg, [-1, 0, 1], atol=1e-15)
+    assert np.allclose(xq, [-np.sqrt(3 / 5), 0, np.sqrt(3 / 5)], atol=1e-15)
+    assert np.allclose(wq, [5 / 9, 8 / 9, 5 / 9], atol=1e-15)
+    xg4, *_ = orc.basis(4, 5)
+    assert np.allclose(xg4, [-1, -np.sqrt(3 / 7), 0, np.sqrt(3 / 7), 1], atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_basis_partition_and_exactness(orc, p):
+    Q = p + 1
+    xg, xq, wq, B, D = orc.basis(p, Q)
+    assert np.allclose(B.sum(1), 1.0, atol=1e-14)          # partition of unity
+    assert np.allclose(D.sum(1), 0.0, atol=1e-13)
+    for k in range(2 * Q):                                  # Gauss exact to degree 2Q-1
+        exact = (1 - (-1) ** (k + 1)) / (k + 1)
+        assert abs(np.dot(wq, xq ** k) - exact) < 1e-14
+    # B and D reproduce polynomials of degree p and their derivatives
+    for k in range(p + 1):
+        assert np.allclose(B @ xg ** k, xq ** k, atol=1e-13)
+        assert np.allclose(D @ xg ** k, k * xq ** max(k - 1, 0) * (k > 0), atol=1e-12)
+
+
+# --------------------------------------------------------------------------- matrix functions
+def _spd_perturbation(rng, amp):
+    A = rng.standard_normal((3, 3))
+    X = amp * (A + A.T) / 2
+    return X
+
+
+@pytest.mark.parametrize("amp", [1e-8, 1e-3, 0.1, 0.5, 1.5])
+def test_logm_matches_scipy(orc, amp):
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        X = _spd_perturbation(rng, amp)
+        if np.linalg.eigvalsh(np.eye(3) + X).min() <= 0.05:
+            continue
+        L = orc.logm1p(X)
+        ref = sla.logm(np.eye(3) + X).real
+        assert np.linalg.norm(L - ref) <= 1e-13 * max(1.0, np.linalg.norm(ref)) + 1e-15 * amp
+        # small arguments: relative accuracy against the eigen formula with log1p
+        w, V = np.linalg.eigh(X)
+        ref2 = V @ np.diag(np.log1p(w)) @ V.T
+        assert np.linalg.norm(L - ref2) <= 1e-13 * np.linalg.norm(ref2)
+
+
+def test_expm_matches_scipy(orc):
+    rng = np.random.default_rng(6)
+    for amp in (1e-6, 0.1, 1.0, 3.0):
+        A = _spd_perturbation(rng, amp)
+        assert np.allclose(orc.expm(A), sla.expm(A), rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- pointwise closed forms
+def _inp(G, phi=0.0, gphi=(0, 0, 0)):
+    v = np.zeros(13)
+    v[:9] = np.asarray(G).ravel()
+    v[9] = phi
+    v[10:] = gphi
+    return v
+
+
+def _glob(at=2, eta=0.0, zeta=0.0, dt=0.01, s_phi=1.0):
+    return np.array([at, eta, zeta, dt, s_phi], dtype=float)
+
+
+def _phase(E0=1000.0, nu0=0.3, maxwell=None, prandtl=None, Gc=0.8, l0=0.005):
+    d = dict(Gc=Gc, l0=l0, E0=E0, nu0=nu0)
+    if maxwell:
+        d["maxwell"] = maxwell
+    if prandtl:
+        d["prandtl"] = prandtl
+    return inputs.phase_vector(d)
+
+
+def _hist(n=1, H=0.0):
+    return inputs.zero_history(n, H).T.copy()
+
+
+def test_uniaxial_hooke_closed_form(orc):
+    """F = diag(lam,1,1): tau11 = (4/3) mu ln(lam) + kappa ln(lam), tau22 = -(2/3) mu ln + kappa ln."""
+    E, nu = 1000.0, 0.3
+    mu, kap = E / (2 * (1 + nu)), E / (3 * (1 - 2 * nu))
+    for lam in (1.01, 0.97, 1.5):
+        G = np.diag([lam - 1, 0, 0])
+        out = orc.pointwise(_inp(G)[None], _hist(), np.zeros(1, np.uint8), _phase(E, nu)[None], _glob())
+        P = out["f1"][0, :3]
+        tau = P @ np.diag([lam, 1, 1])                    # tau = P F^T
+        ln = np.log(lam)
+        assert np.isclose(tau[0, 0], 4 / 3 * mu * ln + kap * ln, rtol=1e-13)
+        assert np.isclose(tau[1, 1], -2 / 3 * mu * ln + kap * ln, rtol=1e-13)
+        assert abs(tau[0, 1]) < 1e-12 * abs(tau[0, 0])
+
+
+def test_maxwell_ramp_hold_recursion(orc):
+    """Exact discrete recursion of the Maxwell branch under fixed principal axes:
+    eps_d^e_{n+1} = (eps_d^e_n + d eps_d)/(1 + mu dt/eta_d) (Box 1, closed form);
+    plus C_in^-1 after commit = diag(exp(2 (eps^e_i - eps_i)))."""
+    E1, nu1, etad, dt = 1000.0, 0.3, 10.0, 0.01
+    mu = E1 / (2 * (1 + nu1))
+    ph = _phase(1e-15, 0.3, maxwell=(E1, nu1, etad))
+    hist = _hist()
+    lams = list(np.linspace(1.0, 1.02, 6)[1:]) + [1.02] * 5
+    epsd_e = 0.0   # deviatoric elastic strain, 11 component
+    prev_ln = 0.0
+    c = mu * dt / etad
+    for lam in lams:
+        ln = np.log(lam)
+        epsd_e = (epsd_e + (2 / 3) * (ln - prev_ln)) / (1 + c)
+        prev_ln = ln
+        G = np.diag([lam - 1, 0, 0])
+        out = orc.pointwise(_inp(G)[None], hist, np.zeros(1, np.uint8), ph[None], _glob(eta=0.0, dt=dt))
+        tau = out["f1"][0, :3] @ np.diag([lam, 1, 1])
+        kap1 = E1 / (3 * (1 - 2 * nu1))
+        taud11 = tau[0, 0] - np.trace(tau) / 3
+        assert np.isclose(taud11, 2 * mu * epsd_e, rtol=1e-11, atol=1e-12)
+        hist = out["hist_new"].copy()
+        # committed C_M = diag(exp(2(eps^e - eps)))
+        eps = np.array([ln, 0, 0])
+        epse = np.array([epsd_e, -epsd_e / 2, -epsd_e / 2]) + ln / 3
+        assert np.allclose(hist[0, 0:3], np.exp(2 * (epse - eps)), rtol=1e-13)
+        assert np.allclose(hist[0, 3:6], 0.0, atol=1e-15)
+
+
+def test_prandtl_perfect_closed_form(orc):
+    """q_tr = 2 mu |ln lam|; yield iff 2 g mu |ln lam| > sigma0; at yield the von Mises
+    stress of the degraded deviator equals sigma0 and d(tau_d,degr)/dphi = 0
+    (Eqs. degraded-perfect-plastic-stress, prandtl-degraded-dtau-dphi)."""
+    E2, nu2, s0 = 198000.0, 0.3, 500.0
+    mu = E2 / (2 * (1 + nu2))
+    ph = _phase(1e-9, 0.3, prandtl=(E2, nu2, s0))
+    for lam, phi in ((1.001, 0.0), (1.01, 0.0), (1.01, 0.5), (0.99, 0.2)):
+        g = (1 - phi) ** 2 + 1e-3
+        G = np.diag([lam - 1, 0, 0])
+        out = orc.pointwise(_inp(G, phi)[None], _hist(), np.zeros(1, np.uint8), ph[None], _glob(eta=1e-3))
+        should_yield = 2 * g * mu * abs(np.log(lam)) > s0
+        assert bool(out["flags"][0] & 1) == should_yield
+        tau = out["f1"][0, :3] @ np.diag([lam, 1, 1])
+        td = tau - np.trace(tau) / 3 * np.eye(3)
+        vm = np.sqrt(1.5) * np.linalg.norm(td)
+        if should_yield:
+            assert np.isclose(vm, s0, rtol=1e-12)
+            # phi column of the tangent: deviatoric part vanishes
+            dP = out["D"][0, 4:13, 3].reshape(3, 3)
+            dtau = dP @ np.diag([lam, 1, 1])
+            dtd = dtau - np.trace(dtau) / 3 * np.eye(3)
+            assert np.linalg.norm(dtd) < 1e-9 * s0
+            # Delta gamma = (g q - sigma0) / (3 g mu)
+            dgam = (2 * g * mu * abs(np.log(lam)) - s0) / (3 * g * mu)
+            assert np.isclose(out["hist_new"][0, 12], dgam, rtol=1e-12)
+        else:
+            assert np.isclose(vm, g * 2 * mu * abs(np.log(lam)), rtol=1e-12)
+
+
+def test_small_strain_limit(orc):
+    """|grad u| ~ 1e-7: tau = g(2 mu dev sym H + kappa tr H I) + O(|H|^2)."""
+    rng = np.random.default_rng(7)
+    E, nu = 1000.0, 0.3
+    mu, kap = E / (2 * (1 + nu)), E / (3 * (1 - 2 * nu))
+    for _ in range(5):
+        H = 1e-7 * rng.standard_normal((3, 3))
+        out = orc.pointwise(_inp(H)[None], _hist(), np.zeros(1, np.uint8), _phase(E, nu)[None], _glob())
+        tau = out["f1"][0, :3] @ (np.eye(3) + H).T
+        eps = 0.5 * (H + H.T)
+        ref = 2 * mu * (eps - np.trace(eps) / 3 * np.eye(3)) + kap * np.trace(eps) * np.eye(3)
+        if np.trace(H) < 0:
+            pass  # g = 1 with eta = 0 and phi = 0: both branches of the split agree
+        assert np.linalg.norm(tau - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_rigid_rotation_objectivity(orc):
+    """u = (R - I) X with C = I: tau = 0; and tau(RF) = R tau(F) R^T."""
+    rng = np.random.default_rng(8)
+    ph = inputs.phase_vector(inputs.EX3_MATRIX)
+    R = sla.expm(np.array([[0, -0.3, 0.2], [0.3, 0, -0.1], [-0.2, 0.1, 0]]))
+    out = orc.pointwise(_inp(R - np.eye(3))[None], _hist(), np.zeros(1, np.uint8), ph[None], _glob(eta=1e-3))
+    assert np.linalg.norm(out["f1"][0, :3]) < 1e-10
+    hist = inputs.random_history(1, 3).T.copy()
+    for _ in range(3):
+        F = np.eye(3) + 0.02 * rng.standard_normal((3, 3))
+        o1 = orc.pointwise(_inp(F - np.eye(3), 0.1)[None], hist, np.zeros(1, np.uint8), ph[None], _glob(eta=1e-3))
+        o2 = orc.pointwise(_inp(R @ F - np.eye(3), 0.1)[None], hist, np.zeros(1, np.uint8), ph[None], _glob(eta=1e-3))
+        t1 = o1["f1"][0, :3] @ F.T
+        t2 = o2["f1"][0, :3] @ (R @ F).T
+        assert np.linalg.norm(t2 - R @ t1 @ R.T) <= 1e-12 * np.linalg.norm(t1)
+        assert np.isclose(o1["f0"][0, 3], o2["f0"][0, 3], rtol=1e-12)
+
+
+def test_at1_threshold_stationary(orc):
+    """AT1: with H = psi_c = 3 Gc / (16 l0), u = 0, phi = 0 the local residual L vanishes
+    (the energy threshold of Sec. 3)."""
+    ph = _phase()
+    Gc, l0 = ph[0], ph[1]
+    psi_c = 3 * Gc / (16 * l0)
+    out = orc.pointwise(_inp(np.zeros((3, 3)))[None], _hist(H=psi_c), np.zeros(1, np.uint8), ph[None],
+                        _glob(at=1, eta=0.0))
+    assert abs(out["f0"][0, 3]) < 1e-12 * psi_c
+
+
+def test_tangent_matches_appendix_bc(orc):
+    """Dual-number tangent vs the closed forms of Appendices B and C at random points
+    (distinct eigenvalues), every branch state and both signs of the volumetric strain."""
+    rng = np.random.default_rng(11)
+    ph_m = inputs.phase_vector(inputs.EX3_MATRIX)
+    ph_m2 = inputs.phase_vector(inputs.EX2_MATRIX)
+    ph_p = inputs.phase_vector(inputs.EX3_PARTICLE)
+    seen = set()
+    for ph in (ph_m, ph_m2, ph_p):
+        for at in (1, 2):
+            glob = np.array([at, 1e-3, 1e-2, 0.01, 1234.5])
+            for trial in range(12):
+                amp = [1e-3, 1e-2, 5e-2][trial % 3]
+                inp = np.zeros(13)
+                inp[:9] = amp * rng.standard_normal(9)
+                inp[9] = rng.uniform(0, 0.9)
+                inp[10:] = rng.standard_normal(3)
+                hist = inputs.random_history(1, 100 + trial, H_max=[0.0, 1.0, 1e3][trial % 3]).T[0]
+                out = orc.pointwise(inp[None], hist[None], np.zeros(1, np.uint8), ph[None], glob)
+                D = out["D"][0]
+                Dref = app.tangent16(inp, hist, ph, glob)
+                err = np.abs(D - Dref).max() / np.abs(Dref).max()
+                assert err < 1e-10, (err, trial)
+                seen.add((int(out["flags"][0]) & 7))
+    assert len(seen) >= 5  # several combinations of yield / active / tension
+
+
+# --------------------------------------------------------------------------- assembled operator
+def _affine_state(m, A, phi0):
+    X = inputs.node_coords(m)
+    z = np.zeros((4, m.nn))
+    z[:3] = (X @ A.T).T
+    z[3] = phi0
+    return z
+
+
+def _gll_integrals(p):
+    xg = inputs.gll_points(p)
+    ints = []
+    for a in range(p + 1):
+        others = np.delete(xg, a)
+        poly = np.poly1d(np.poly(others)) / np.prod(xg[a] - others)
+        ip = np.polyint(poly)
+        ints.append(ip(1) - ip(-1))
+    return np.array(ints)
+
+
+def test_patch_test_affine(orc):
+    """u = A X gives constant F and tau: interior u-residual = 0 and the phi-residual is
+    s_phi L int N_a (Eq. matrix-free-residual-compact with constant integrands)."""
+    w = inputs.cube(nx=3, p=2)
+    w.phases = np.stack([_phase(1000.0, 0.3)])          # Hooke-only: closed-form L
+    m = w.mesh
+    A = np.array([[2e-3, 1e-3, 0], [0, -1e-3, 5e-4], [3e-4, 0, 1.5e-3]])
+    phi0 = 0.2
+    w.z = _affine_state(m, A, phi0)
+    w.hist = inputs.zero_history(m.nq)
+    out = orc.assemble(w, matrix=False)
+    r = out["r"].reshape(4, m.nnz, m.nny, m.nnx)
+    interior = r[:3, 1:-1, 1:-1, 1:-1]
+    bnd = np.abs(r[:3]).max()
+    assert np.abs(interior).max() <= 1e-13 * bnd
+    # phi residual = s_phi L * int N_a, int N_a = product of 1D GLL-Lagrange integrals
+    I1 = _gll_integrals(m.p) * m.h[0] / 2
+    Ia = np.zeros(m.nnx)
+    for e in range(m.nx):
+        Ia[m.p * e: m.p * e + m.p + 1] += I1
+    intN = Ia[None, None, :] * Ia[None, :, None] * Ia[:, None, None]
+    # closed-form L for the Hooke branch with F = I + A (scipy logm)
+    F = np.eye(3) + A
+    eps = 0.5 * sla.logm(F @ F.T).real
+    E, nu = 1000.0, 0.3
+    mu, kap = E / (2 * (1 + nu)), E / (3 * (1 - 2 * nu))
+    th = np.log(np.linalg.det(F))
+    ed = eps - np.trace(eps) / 3 * np.eye(3)
+    psip = mu * np.sum(ed * ed) + (0.5 * kap * th ** 2 if th >= 0 else 0.0)
+    at, eta, zeta, dt, s_phi = w.glob
+    Gc, l0 = 0.8, 0.005
+    L = -2 * (1 - phi0) * psip + Gc / (2 * l0) * 2 * phi0 + zeta * phi0 / dt
+    assert np.allclose(r[3], s_phi * L * intN, rtol=1e-12)
+
+
+def test_self_equilibrium(orc):
+    """Without Dirichlet data: sum_a r_u,a = 0 and sum_a x_a x r_u,a = 0 (tau symmetric)."""
+    w = inputs.cube(nx=3, p=2, hist_seed=4, H_max=50.0)
+    out = orc.assemble(w, matrix=False)
+    m = w.mesh
+    ru = out["r"][:3]
+    scale = np.abs(ru).max()
+    assert np.abs(ru.sum(axis=1)).max() <= 1e-12 * scale * np.sqrt(m.nn)
+    x = inputs.node_coords(m).T + w.z[:3]
+    mom = np.cross(x.T, ru.T).sum(axis=0)
+    assert np.abs(mom).max() <= 1e-12 * scale * np.sqrt(m.nn)
+
+
+def test_fd_of_residual(orc):
+    """Assembled Jacobian vs central differences of the residual (step 1e-6 |z|)."""
+    w = inputs.cube(nx=2, p=2, hist_seed=2, H_max=80.0)
+    out = orc.assemble(w, matrix=True)
+    K = out["K"]
+    v = inputs.random_vector(w.mesh.ndof, 1)
+    eps = 1e-6 * np.linalg.norm(w.z) / np.linalg.norm(v)
+    zp = w.z + eps * v.reshape(4, -1)
+    zm = w.z - eps * v.reshape(4, -1)
+    op = orc.assemble(w, z=zp, matrix=False)
+    om = orc.assemble(w, z=zm, matrix=False)
+    assert np.array_equal(op["flags"], out["flags"]) and np.array_equal(om["flags"], out["flags"])
+    fd = (op["r"] - om["r"]).ravel() / (2 * eps)
+    Kv = K @ v
+    assert np.linalg.norm(Kv - fd) <= 1e-7 * np.linalg.norm(Kv)
+
+
+def test_elastic_block_symmetric(orc):
+    """K_uu (phi frozen) is symmetric for every branch: the algorithmic stress derives from
+    an incremental potential and the reference-frame tangent is its Hessian."""
+    w = inputs.cube(nx=2, p=2, hist_seed=3, H_max=10.0)
+    K = orc.assemble(w)["K"]
+    nu = 3 * w.mesh.nn
+    Kuu = K[:nu, :nu].toarray()
+    assert np.abs(Kuu - Kuu.T).max() <= 1e-11 * np.abs(Kuu).max()
+
+
+def _crack_bar(orc, at, ne, p):
+    """1D crack profile: u = 0, phi = 1 on x = 0, natural at x = Lx."""
+    l0 = 0.005
+    Lx = 8 * l0
+    m = inputs.Mesh(ne, 1, 1, p, p + 1, (Lx, l0, l0))
+    ph = _phase(1000.0, 0.3, Gc=0.8, l0=l0)
+    glob = np.array([at, 0.0, 0.0, 0.01, 1.0])
+    H0 = 3 * 0.8 / (16 * l0) if at == 1 else 0.0
+    hist = inputs.zero_history(m.nq, H0)
+    mask = np.zeros((4, m.nnz, m.nny, m.nnx), np.uint8)
+    mask[:3] = 1
+    mask[3, :, :, 0] = 1
+    dv = np.zeros((4, m.nnz, m.nny, m.nnx))
+    dv[3, :, :, 0] = 1.0
+    w = inputs.Workload("bar", m, ph[None], glob, np.zeros(m.nq, np.uint8), np.zeros((4, m.nn)), hist,
+                        mask.reshape(4, -1), dv.reshape(4, -1))
+    z = np.zeros(4 * m.nn)
+    for _ in range(2):  # linear in phi: one Newton step converges, the second checks it
+        out = orc.assemble(w, z=z.reshape(4, -1))
+        import scipy.sparse.linalg as spla
+        dz = spla.spsolve(out["K"].tocsc(), out["r"].ravel())
+        z = z - dz
+    X = inputs.node_coords(m)[:, 0]
+    k = 1 / l0 if at == 2 else 1 / (np.sqrt(2) * l0)
+    exact = np.cosh(k * (Lx - X)) / np.cosh(k * Lx)
+    return np.abs(z.reshape(4, -1)[3] - exact).max()
+
+
+@pytest.mark.parametrize("at", [1, 2])
+def test_crack_profile_1d(orc, at):
+    """AT2: phi = exp(-|x|/l0) (cosh form on a finite bar); AT1 with H0 = psi_c:
+    exp(-|x|/(sqrt 2 l0)).  Error falls like h^(p+1)."""
+    e1 = _crack_bar(orc, at, 8, 2)
+    e2 = _crack_bar(orc, at, 16, 2)
+    assert e1 < 1e-2
+    rate = np.log2(e1 / e2)
+    assert rate > 2.5, (e1, e2, rate)
+
+
+# --------------------------------------------------------------------------- multigrid pieces
+def test_prolongation_reproduces_coarse_polynomials(orc):
+    m = inputs.Mesh(3, 2, 2, 4, 5, (1.0, 1.0, 1.0))
+    for pc in (1, 2):
+        P = orc.prolongation(m, pc)
+        mc = inputs.Mesh(3, 2, 2, pc, 5, (1.0, 1.0, 1.0))
+        Xc = inputs.node_coords(mc)
+        Xf = inputs.node_coords(m)
+        f = lambda X: (1 + X[:, 0] ** pc - 2 * X[:, 1] ** pc + 0.5 * X[:, 2] * X[:, 0] ** (pc - 1)
+                       + X[:, 0] * X[:, 1] * X[:, 2] ** (pc - 1))
+        zc = np.concatenate([f(Xc)] * 4)
+        zf = P @ zc
+        assert np.allclose(zf, np.concatenate([f(Xf)] * 4), atol=1e-13)
+
+
+def test_galerkin_equals_rediscretisation(orc):
+    """R9: the coarse operator P^T K_f P equals the order-pc operator built at the fine
+    Gauss points (same state), which is how the GPU levels are defined."""
+    mf = inputs.Mesh(2, 2, 2, 4, 5, (1.0, 1.0, 1.0))
+    mc = inputs.Mesh(2, 2, 2, 2, 5, (1.0, 1.0, 1.0))
+    P = orc.prolongation(mf, 2)
+    rng = np.random.default_rng(3)
+    zc = np.concatenate([rng.uniform(-1e-3, 1e-3, 3 * mc.nn), rng.uniform(0, 0.3, mc.nn)])
+    zf = P @ zc
+    ph = inputs.phase_vector(inputs.EX3_MATRIX)
+    glob = np.array([2, 1e-3, 1e-2, 0.01, 1000.0])
+    hist = inputs.random_history(mf.nq, 9, H_max=30.0)
+    phase = np.zeros(mf.nq, np.uint8)
+    wf = inputs.Workload("f", mf, ph[None], glob, phase, zf.reshape(4, -1), hist)
+    wc = inputs.Workload("c", mc, ph[None], glob, phase, zc.reshape(4, -1), hist)
+    Kf = orc.assemble(wf)["K"]
+    Kc = orc.assemble(wc)["K"]
+    G = (P.T @ Kf @ P).toarray()
+    assert np.abs(G - Kc.toarray()).max() <= 1e-11 * np.abs(G).max()
+
+
+def test_chebyshev_polynomial(orc):
+    """On a diagonal operator the Chebyshev iteration multiplies each error component by
+    T_k((lmax + lmin - 2 lam)/(lmax - lmin)) / T_k((lmax + lmin)/(lmax - lmin))."""
+    import scipy.sparse as sp
+    from numpy.polynomial import chebyshev as C
+
+    lam = np.linspace(0.05, 1.2, 40)
+    A = sp.diags(lam)
+    b = np.zeros(40)
+    x0 = np.ones(40)
+    lmin, lmax = 0.1, 1.1
+    for k in (1, 2, 3, 5):
+        x = orc.chebyshev(A, np.ones(40), b, x0, k, lmin, lmax)
+        Tk = C.Chebyshev.basis(k)
+        ref = Tk((lmax + lmin - 2 * lam) / (lmax - lmin)) / Tk((lmax + lmin) / (lmax - lmin))
+        assert np.allclose(x, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_golden_table2_parameters():
+    """Table 2 values as printed, against the input module's tables (tests/golden)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "table2.json")))
+    gpa = 1e3
+    ex3 = g["example3"]
+    assert inputs.EX3_PARTICLE["Gc"] == ex3["particle"]["Gc_kJ_m2"]
+    assert inputs.EX3_PARTICLE["E0"] == ex3["particle"]["E_inf_GPa"] * gpa
+    assert inputs.EX3_MATRIX["prandtl"] == (ex3["matrix"]["E2_GPa"] * gpa, ex3["matrix"]["nu2"],
+                                            ex3["matrix"]["sigma0_MPa"])
+    assert inputs.EX3_MATRIX["maxwell"][2] == ex3["matrix"]["eta_d_GPa_s"] * gpa
+    assert inputs.EX2_MATRIX["maxwell"][2] == g["example2"]["matrix"]["eta_d_GPa_s"][0] * gpa
