@@ -1,0 +1,195 @@
+/*
+ * libpff -- C ABI of the GB300 matrix-free phase-field fracture operator.
+ *
+ * Method: "Matrix-free phase-field modeling of fracture in micromechanical
+ * testing simulations of inelastic materials".  Peric-Dettmer rheology
+ * (Hooke, Maxwell and perfectly plastic Prandtl branches on Hencky strains,
+ * Sec. 2, Box 1) in series with a phase-field fracture element (Sec. 3),
+ * monolithic 4-field residual and Jacobian evaluated matrix-free on
+ * tensor-product Q_p hexahedra (Sec. 4), with the p-multigrid pieces
+ * (matrix-free diagonal, Chebyshev-Jacobi smoothing, p-prolongation and
+ * restriction) that the paper's solver uses (Sec. 5).
+ *
+ * Conventions
+ *   - Units: mm, MPa, s.
+ *   - Mesh: structured box of nx*ny*nz affine hexahedra of size hx*hy*hz, order
+ *     p (P = p + 1 Gauss-Lobatto-Legendre nodes per direction), Q Gauss points
+ *     per direction (Q = p_fine + 1 on every multigrid level).
+ *     Node (I,J,K) has id I + nnx*(J + nny*K), nnx = p*nx + 1, nny = p*ny + 1.
+ *     Element e = ex + nx*(ey + ny*ez); its local node (a,b,c) is node
+ *     (p*ex + a, p*ey + b, p*ez + c).
+ *   - Vectors: structure of arrays [4][N_n] (u_x, u_y, u_z, phi), FP64
+ *     (PFF_F64) or FP32 (PFF_F32) as the call states.
+ *   - Quadrature point q = e*Q^3 + i + Q*(j + Q*k) (Gauss points ascending).
+ *   - History, structure of arrays [15][N_q] of FP64: words 0-5 C_in^-1 of the
+ *     Maxwell branch, 6-11 C_in^-1 of the Prandtl branch (Voigt order 11, 22,
+ *     33, 23, 13, 12), 12 accumulated plastic strain, 13 history field H,
+ *     14 phase field at the last converged step (phi_n).
+ *   - Flags, one uint8 per quadrature point: bit0 Prandtl branch yielded,
+ *     bit1 history field active (psi+ > H_n), bit2 theta = ln J >= 0.
+ *   - Dirichlet mask: uint8 [4][N_n], 1 = prescribed.
+ *
+ * Memory and streams
+ *   Every array argument is a DEVICE pointer owned by the caller unless stated
+ *   otherwise; handles own the device buffers they allocate (history, stored
+ *   linearisation, work space) and free them in pff_destroy_*.  `stream` is a
+ *   cudaStream_t passed as void*; calls are asynchronous on it.  Kernel-side
+ *   failures (eigen sweeps not converged, det F <= 0, non-finite values) set a
+ *   status word that pff_get_status reads back.
+ *
+ * Errors
+ *   Every call returns PFF_OK (0) or a negative PFF_ERR_* code; the message of
+ *   the last failing call on this thread is available from
+ *   pff_last_error_message().  No exception crosses the ABI.
+ */
+#ifndef PFF_H
+#define PFF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFF_OK 0
+#define PFF_ERR_INVALID -1   /* bad argument or handle */
+#define PFF_ERR_CUDA -2      /* CUDA runtime error (launch, copy, allocation) */
+#define PFF_ERR_DEVICE -3    /* kernel status word set (see pff_get_status) */
+#define PFF_ERR_UNSUPPORTED -4
+
+/* kernel status bits returned by pff_get_status */
+#define PFF_STATUS_EIGEN 1       /* Jacobi eigen sweeps hit their cap (20) */
+#define PFF_STATUS_DETF 2        /* det F <= 0 at some quadrature point */
+#define PFF_STATUS_NONFINITE 4   /* non-finite residual integrand */
+#define PFF_STATUS_PHASE 8       /* phase id >= nphase (phase 0 used) */
+
+typedef enum { PFF_F64 = 0, PFF_F32 = 1 } pff_prec;
+
+typedef struct pff_ctx pff_ctx;
+typedef struct pff_basis pff_basis;
+typedef struct pff_restr pff_restr;
+typedef struct pff_op pff_op;
+typedef struct pff_level pff_level;
+
+/* Material and global parameters (Table 2; Sec. 3, 3.1).  phase_params holds
+ * nphase rows of 12 doubles:
+ *   Gc, l0, E_inf, nu_inf, hasMaxwell, E1, nu1, eta_d, hasPrandtl, E2, nu2, sigma0
+ * (eta_d may be +inf).  at = 1 (AT1, c0 = 8/3) or 2 (AT2, c0 = 2); eta =
+ * residual stiffness of g = (1 - phi)^2 + eta (Eq. degr-funct); zeta = damage
+ * viscosity (Sec. 3.1); dt = time step; s_phi = phase-field residual scale
+ * (Eq. damage-residual-scaling).  Host memory; copied. */
+typedef struct {
+  int nphase;
+  const double* phase_params;
+  int at;
+  double eta;
+  double zeta;
+  double dt;
+  double s_phi;
+} pff_problem;
+
+/* Affine box: nx*ny*nz elements of size hx*hy*hz. */
+typedef struct {
+  int nx, ny, nz;
+  double hx, hy, hz;
+} pff_box;
+
+const char* pff_last_error_message(void);
+int pff_version(void);
+
+/* Context: parameters of the constitutive model (host data, copied). */
+int pff_create_context(pff_ctx** ctx, const pff_problem* problem);
+int pff_destroy_context(pff_ctx* ctx);
+
+/* Basis: GLL(p+1) nodes, Gauss(q) points and weights, 1D interpolation B[q][p+1]
+ * and collocated derivative D[q][q] (Sec. 4, B_I and B_xi).  1 <= p, p+1 <= q <= 5.
+ * pff_basis_get copies the 1D tables to host arrays (any may be NULL):
+ * xg[p+1], xq[q], wq[q], B[q*(p+1)], Dc[q*q]. */
+int pff_create_basis(pff_ctx* ctx, int p, int q, pff_basis** basis);
+int pff_basis_get(const pff_basis* basis, double* xg, double* xq, double* wq, double* B, double* Dc);
+int pff_destroy_basis(pff_basis* basis);
+
+/* Element restriction E (Sec. 4): the structured box map, or explicit offsets
+ * (device int32 [nel][(p+1)^3] of node ids, borrowed: must stay valid while
+ * operators built on it are used).  nnodes = nodes per field. */
+int pff_create_restriction(pff_ctx* ctx, const pff_box* box, int p, const int32_t* offsets_or_null,
+                           int64_t nnodes, pff_restr** restr);
+int pff_destroy_restriction(pff_restr* restr);
+
+/* Fine-level operator: allocates the quadrature-point state (committed and
+ * trial history, phase ids, flags), the FP64 stored linearisation
+ * (67 words per point) and the residual work space. */
+int pff_create_operator(pff_ctx* ctx, pff_basis* fine, pff_restr* restr, pff_op** op);
+int pff_destroy_operator(pff_op* op);
+/* Also keep an FP32 copy of the stored linearisation (written by pff_residual),
+ * needed by PFF_F32 applies. */
+int pff_op_enable_f32(pff_op* op, int enable);
+int64_t pff_op_num_qpoints(const pff_op* op);
+int64_t pff_op_num_nodes(const pff_op* op);
+
+/* Quadrature-point state: phase ids (uint8 [N_q]) and committed history
+ * (FP64 [15][N_q]); device pointers, copied. */
+int pff_set_qpoint_state(pff_op* op, const uint8_t* phase, const double* hist_committed, void* stream);
+/* Dirichlet data of the fine level: mask uint8 [4][N_n] and values FP64
+ * [4][N_n] (device, copied; values may be NULL = zero; mask NULL = none). */
+int pff_set_dirichlet(pff_op* op, const uint8_t* mask, const double* values, void* stream);
+
+/* Residual R(z) (Eq. matrix-free-residual-compact), FP64: r = internal
+ * residual on free DoFs, r = z - ubar on Dirichlet DoFs.  Also writes the
+ * trial history (Box 1 step 4), the flags, and the stored linearisation used
+ * by every Jacobian action until the next call. */
+int pff_residual(pff_op* op, const double* z, double* r, void* stream);
+
+/* Multigrid level built on the fine operator's quadrature points (coarse
+ * Lagrange basis of order p_level evaluated at the fine Gauss points, sharing
+ * the fine stored linearisation, i.e. the Galerkin operator P^T A P).
+ * p_level = the fine order gives the fine operator itself. */
+int pff_create_level(pff_op* fine, int p_level, pff_level** level);
+int pff_destroy_level(pff_level* level);
+int64_t pff_level_num_nodes(const pff_level* level);
+/* Dirichlet mask of this level (uint8 [4][N_n(level)], device, copied; NULL = none).
+ * The fine level created with p_level = fine order uses the operator's mask. */
+int pff_level_set_mask(pff_level* level, const uint8_t* mask, void* stream);
+
+/* Jacobian action y = J x (Eq. matrix-free-jacobian) with Dirichlet rows and
+ * columns replaced by the identity: y = (I-M) J (I-M) x + M x.  x, y are
+ * [4][N_n(level)] of the given precision. */
+int pff_jacobian_apply(pff_level* level, pff_prec prec, const void* x, void* y, void* stream);
+/* Transposed action y = J^T x (same Dirichlet treatment). */
+int pff_jacobian_transpose_apply(pff_level* level, pff_prec prec, const void* x, void* y, void* stream);
+/* Diagonal of J (1 on Dirichlet DoFs). */
+int pff_assemble_diagonal(pff_level* level, pff_prec prec, void* diag, void* stream);
+
+/* p-transfer between a coarse level and the next finer one (same element
+ * grid): prolongation x_f = P x_c with P[f, c] = coarse Lagrange basis at the
+ * fine GLL node, rows of fine Dirichlet DoFs and columns of coarse Dirichlet
+ * DoFs removed; restriction r_c = P^T r_f. */
+int pff_prolong(pff_level* coarse, pff_level* fine, pff_prec prec, const void* xc, void* xf, void* stream);
+int pff_restrict(pff_level* coarse, pff_level* fine, pff_prec prec, const void* rf, void* rc, void* stream);
+
+/* Chebyshev smoothing of J x = b preconditioned by diag (Saad, Alg. 12.1)
+ * on the eigenvalue interval [lmin, lmax] of D^-1 J: `degree` Jacobian
+ * actions; x updated in place.  work: 3 vectors [3][4][N_n] of the given
+ * precision (caller-owned scratch). */
+int pff_chebyshev_smooth(pff_level* level, pff_prec prec, int degree, double lmin, double lmax,
+                         const void* diag, const void* b, void* x, void* work, void* stream);
+
+/* Accept the trial history written by the last pff_residual (Box 1 step 4,
+ * C_in^-1 = F^-1 exp(2 eps_e) F^-T; eps_p += dgamma; H = max(H_n, psi+);
+ * phi_n = phi). */
+int pff_commit_history(pff_op* op, void* stream);
+/* Copies of the per-point data (device destinations). which = 0 committed, 1 trial. */
+int pff_get_history(pff_op* op, int which, double* hist, void* stream);
+int pff_get_flags(pff_op* op, uint8_t* flags, void* stream);
+/* Copy of the stored linearisation in the canonical point order: out[67][N_q]
+ * (device FP64); for tests and diagnostics. */
+int pff_get_linearization(pff_op* op, double* out, void* stream);
+
+/* Synchronises `stream`, returns the kernel status bits accumulated since the
+ * last call in *status and clears them. */
+int pff_get_status(pff_op* op, void* stream, int* status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFF_H */

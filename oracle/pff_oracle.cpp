@@ -307,7 +307,7 @@ void pointwise(const T G[3][3], const T& phi, const T gphi[3], const double* his
   T psid = T(0.0);
   double kap_tot = 0.0;
   out.flags = 0;
-  out.margin_yield = 0.0;
+  out.margin_yield = INFINITY;  // no yield decision without a Prandtl branch
   double dgam_v = 0.0;
   M3<double> epsE_M = zero3<double>(), epsE_P = zero3<double>();
 

@@ -1,0 +1,657 @@
+// C ABI of libpff: handles, parameter derivation, kernel launches.
+#include "../../include/pff.h"
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pff_internal.h"
+
+using namespace pff;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define PFF_CK(call)                                                                             \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) return fail(PFF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define PFF_REQUIRE(cond, msg)                          \
+  do {                                                  \
+    if (!(cond)) return fail(PFF_ERR_INVALID, (msg));   \
+  } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename T>
+int upload(const std::vector<double>& h, T** d) {
+  std::vector<T> tmp(h.begin(), h.end());
+  PFF_CK(cudaMalloc((void**)d, sizeof(T) * (tmp.empty() ? 1 : tmp.size())));
+  if (!tmp.empty()) PFF_CK(cudaMemcpy(*d, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice));
+  return PFF_OK;
+}
+
+}  // namespace
+
+struct pff_ctx {
+  int nphase;
+  PhaseDev phase[kMaxPhase];
+  GlobDev glob;
+};
+
+struct pff_basis {
+  int p, q;
+  std::vector<double> xg, xq, wq, B, Dc, Dt;
+};
+
+struct pff_restr {
+  pff_box box;
+  int p;
+  const int32_t* offsets;
+  int64_t nn;
+};
+
+struct Tables {  // per-level device copies of the 1D matrices, both precisions
+  double *B64 = nullptr, *Dc64 = nullptr, *Dt64 = nullptr;
+  float *B32 = nullptr, *Dc32 = nullptr, *Dt32 = nullptr;
+};
+
+struct pff_op {
+  pff_ctx* ctx;
+  int p, Q;
+  pff_box box;
+  MeshDev mesh;
+  long long nq, nel;
+  Geom geom;
+  Tables tab;
+  double* hist_c = nullptr;
+  double* hist_t = nullptr;
+  uint8_t* phase = nullptr;
+  uint8_t* flags = nullptr;
+  double* lin64 = nullptr;
+  float* lin32 = nullptr;
+  long long lin_len = 0;
+  double* io = nullptr;
+  uint8_t* mask = nullptr;
+  double* dvals = nullptr;
+  int* status = nullptr;
+  int f32 = 0;
+};
+
+struct pff_level {
+  pff_op* op;
+  int p;
+  MeshDev mesh;
+  Tables tab;
+  uint8_t* mask = nullptr;   // owned copy (coarse levels) ; fine level uses op->mask
+  bool is_fine = false;
+  // prolongation table towards the finer level with order I_pf
+  int I_pf = -1;
+  double* I64 = nullptr;
+  float* I32 = nullptr;
+};
+
+namespace {
+
+long long stride_of(int Q) { return (long long)Q * Q * Q * elems_per_block(Q); }
+
+int make_tables(int p, int Q, Tables& t) {
+  std::vector<double> xg(p + 1), xq(Q), wq(Q);
+  gll_nodes(p, xg.data());
+  gauss_rule(Q, xq.data(), wq.data());
+  int P = p + 1;
+  std::vector<double> B(Q * P), Dt(Q * P), Dc(Q * Q);
+  for (int i = 0; i < Q; ++i)
+    for (int a = 0; a < P; ++a) {
+      B[i * P + a] = lagrange(xg.data(), P, a, xq[i]);
+      Dt[i * P + a] = lagrange_deriv(xg.data(), P, a, xq[i]);
+    }
+  for (int i = 0; i < Q; ++i)
+    for (int k = 0; k < Q; ++k) Dc[i * Q + k] = lagrange_deriv(xq.data(), Q, k, xq[i]);
+  int rc;
+  if ((rc = upload(B, &t.B64))) return rc;
+  if ((rc = upload(B, &t.B32))) return rc;
+  if ((rc = upload(Dc, &t.Dc64))) return rc;
+  if ((rc = upload(Dc, &t.Dc32))) return rc;
+  if ((rc = upload(Dt, &t.Dt64))) return rc;
+  if ((rc = upload(Dt, &t.Dt32))) return rc;
+  return PFF_OK;
+}
+
+void free_tables(Tables& t) {
+  cudaFree(t.B64); cudaFree(t.Dc64); cudaFree(t.Dt64);
+  cudaFree(t.B32); cudaFree(t.Dc32); cudaFree(t.Dt32);
+  t = Tables();
+}
+
+MeshDev mesh_for(const pff_box& b, int p, const int32_t* offsets) {
+  MeshDev m;
+  m.nel = b.nx * b.ny * b.nz;
+  m.nx = b.nx; m.ny = b.ny; m.nz = b.nz;
+  m.p = p;
+  m.nnx = p * b.nx + 1;
+  m.nny = p * b.ny + 1;
+  m.nn = (long long)m.nnx * m.nny * (p * b.nz + 1);
+  m.offsets = offsets;
+  return m;
+}
+
+template <typename T>
+cudaError_t elem_dispatch(int Q, int P, int mode, const ElemArgs<T>& a, cudaStream_t st) {
+  switch (Q) {
+    case 2: return launch_elem_q2<T>(P, mode, a, st);
+    case 3: return launch_elem_q3<T>(P, mode, a, st);
+    case 4: return launch_elem_q4<T>(P, mode, a, st);
+    case 5: return launch_elem_q5<T>(P, mode, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+template <typename T>
+cudaError_t diag_dispatch(int Q, int P, const ElemArgs<T>& a, cudaStream_t st) {
+  switch (Q) {
+    case 2: return launch_diag_q2<T>(P, a, st);
+    case 3: return launch_diag_q3<T>(P, a, st);
+    case 4: return launch_diag_q4<T>(P, a, st);
+    case 5: return launch_diag_q5<T>(P, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T> const T* tabB(const Tables& t);
+template <> const double* tabB<double>(const Tables& t) { return t.B64; }
+template <> const float* tabB<float>(const Tables& t) { return t.B32; }
+template <typename T> const T* tabDc(const Tables& t);
+template <> const double* tabDc<double>(const Tables& t) { return t.Dc64; }
+template <> const float* tabDc<float>(const Tables& t) { return t.Dc32; }
+template <typename T> const T* tabDt(const Tables& t);
+template <> const double* tabDt<double>(const Tables& t) { return t.Dt64; }
+template <> const float* tabDt<float>(const Tables& t) { return t.Dt32; }
+template <typename T> const T* linOf(const pff_op* op);
+template <> const double* linOf<double>(const pff_op* op) { return op->lin64; }
+template <> const float* linOf<float>(const pff_op* op) { return op->lin32; }
+
+const uint8_t* level_mask(const pff_level* L) { return L->is_fine ? L->op->mask : L->mask; }
+
+template <typename T>
+ElemArgs<T> level_args(const pff_level* L) {
+  ElemArgs<T> a;
+  std::memset(&a, 0, sizeof(a));
+  a.mesh = L->mesh;
+  a.mask = level_mask(L);
+  a.B = tabB<T>(L->tab);
+  a.Dc = tabDc<T>(L->tab);
+  a.Dt = tabDt<T>(L->tab);
+  a.lin = linOf<T>(L->op);
+  a.nq = L->op->nq;
+  for (int d = 0; d < 3; ++d) a.s[d] = L->op->geom.s[d];
+  return a;
+}
+
+template <typename T>
+int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st) {
+  pff_op* op = L->op;
+  PFF_REQUIRE(linOf<T>(op) != nullptr, "FP32 apply needs pff_op_enable_f32 before pff_residual");
+  PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
+  ElemArgs<T> a = level_args<T>(L);
+  a.x = x;
+  a.y = y;
+  long long stride = stride_of(op->Q);
+  const T* lin = a.lin;
+  a.linP = lin + (transpose ? kWC : kWP) * stride;
+  a.linC = lin + (transpose ? kWP : kWC) * stride;
+  a.transpose = transpose;
+  PFF_CK(elem_dispatch<T>(op->Q, L->p + 1, kApply, a, st));
+  return PFF_OK;
+}
+
+template <typename T>
+int diag_t(pff_level* L, T* diag, cudaStream_t st) {
+  pff_op* op = L->op;
+  PFF_REQUIRE(linOf<T>(op) != nullptr, "FP32 diagonal needs pff_op_enable_f32 before pff_residual");
+  PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, diag, nullptr, nullptr, level_mask(L), 4 * L->mesh.nn, 2, st));
+  ElemArgs<T> a = level_args<T>(L);
+  a.y = diag;
+  PFF_CK(diag_dispatch<T>(op->Q, L->p + 1, a, st));
+  return PFF_OK;
+}
+
+int ensure_prolong_table(pff_level* c, pff_level* f) {
+  if (c->I_pf == f->p) return PFF_OK;
+  cudaFree(c->I64); cudaFree(c->I32);
+  c->I64 = nullptr; c->I32 = nullptr;
+  int pc = c->p, pf = f->p;
+  std::vector<double> xc(pc + 1), xf(pf + 1);
+  gll_nodes(pc, xc.data());
+  gll_nodes(pf, xf.data());
+  std::vector<double> I((pf + 1) * (pc + 1));
+  for (int a = 0; a <= pf; ++a)
+    for (int b = 0; b <= pc; ++b) I[a * (pc + 1) + b] = lagrange(xc.data(), pc + 1, b, xf[a]);
+  int rc;
+  if ((rc = upload(I, &c->I64))) return rc;
+  if ((rc = upload(I, &c->I32))) return rc;
+  c->I_pf = pf;
+  return PFF_OK;
+}
+
+}  // namespace
+
+template <typename T>
+static int cheb_t(pff_level* L, int degree, double lmin, double lmax, const T* diag, const T* b, T* x, T* work,
+                  cudaStream_t st) {
+  const long long n = 4 * L->mesh.nn;
+  T* r = work;
+  T* d = work + n;
+  T* Ad = work + 2 * n;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  int rc = apply_t<T>(L, x, Ad, 0, st);
+  if (rc) return rc;
+  PFF_CK(launch_cheb_init<T>(n, b, Ad, diag, r, d, 1.0 / theta, st));
+  for (int k = 0; k < degree; ++k) {
+    if (k == degree - 1) {
+      PFF_CK(launch_cheb_step<T>(n, x, d, r, Ad, diag, 0.0, 0.0, 1, st));
+      break;
+    }
+    rc = apply_t<T>(L, d, Ad, 0, st);
+    if (rc) return rc;
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    PFF_CK(launch_cheb_step<T>(n, x, d, r, Ad, diag, rho_new * rho, 2.0 * rho_new / delta, 0, st));
+    rho = rho_new;
+  }
+  return PFF_OK;
+}
+
+extern "C" {
+
+const char* pff_last_error_message(void) { return g_err.c_str(); }
+int pff_version(void) { return 1; }
+
+int pff_create_context(pff_ctx** out, const pff_problem* pr) {
+  PFF_REQUIRE(out && pr, "pff_create_context: null argument");
+  PFF_REQUIRE(pr->nphase >= 1 && pr->nphase <= kMaxPhase, "pff_create_context: 1 <= nphase <= 8");
+  PFF_REQUIRE(pr->at == 1 || pr->at == 2, "pff_create_context: at must be 1 (AT1) or 2 (AT2)");
+  PFF_REQUIRE(pr->dt > 0.0, "pff_create_context: dt must be positive");
+  PFF_REQUIRE(pr->phase_params != nullptr, "pff_create_context: phase_params is null");
+  pff_ctx* c = new (std::nothrow) pff_ctx();
+  if (!c) return fail(PFF_ERR_INVALID, "out of host memory");
+  c->nphase = pr->nphase;
+  const double c0 = (pr->at == 1) ? 8.0 / 3.0 : 2.0;
+  for (int i = 0; i < pr->nphase; ++i) {
+    const double* v = pr->phase_params + 12 * i;
+    PhaseDev& ph = c->phase[i];
+    std::memset(&ph, 0, sizeof(ph));
+    const double E[3] = {v[2], v[5], v[9]};
+    const double nu[3] = {v[3], v[6], v[10]};
+    ph.has[0] = 1;
+    ph.has[1] = v[4] != 0.0;
+    ph.has[2] = v[8] != 0.0;
+    ph.kap_tot = 0.0;
+    for (int b = 0; b < 3; ++b) {
+      if (!ph.has[b]) continue;
+      if (!(E[b] > 0.0) || !(nu[b] > -1.0 && nu[b] < 0.5)) {
+        delete c;
+        return fail(PFF_ERR_INVALID, "pff_create_context: branch moduli must satisfy E > 0, -1 < nu < 0.5");
+      }
+      ph.mu[b] = E[b] / (2.0 * (1.0 + nu[b]));
+      ph.kap[b] = E[b] / (3.0 * (1.0 - 2.0 * nu[b]));
+      ph.kap_tot += ph.kap[b];
+    }
+    ph.cmax = (ph.has[1] && std::isfinite(v[7])) ? ph.mu[1] * pr->dt / v[7] : 0.0;
+    ph.sig0 = v[11];
+    ph.gc_c0l0 = v[0] / (c0 * v[1]);
+    ph.kphi = pr->s_phi * 2.0 * v[0] * v[1] / c0;
+  }
+  c->glob.at = pr->at;
+  c->glob.eta = pr->eta;
+  c->glob.zeta = pr->zeta;
+  c->glob.dt = pr->dt;
+  c->glob.s_phi = pr->s_phi;
+  *out = c;
+  return PFF_OK;
+}
+
+int pff_destroy_context(pff_ctx* ctx) {
+  delete ctx;
+  return PFF_OK;
+}
+
+int pff_create_basis(pff_ctx* ctx, int p, int q, pff_basis** out) {
+  PFF_REQUIRE(ctx && out, "pff_create_basis: null argument");
+  PFF_REQUIRE(p >= 1 && q >= p + 1 && q <= kMaxQ, "pff_create_basis: need 1 <= p and p + 1 <= q <= 5");
+  pff_basis* b = new pff_basis();
+  b->p = p; b->q = q;
+  int P = p + 1;
+  b->xg.resize(P); b->xq.resize(q); b->wq.resize(q);
+  gll_nodes(p, b->xg.data());
+  gauss_rule(q, b->xq.data(), b->wq.data());
+  b->B.resize(q * P); b->Dt.resize(q * P); b->Dc.resize(q * q);
+  for (int i = 0; i < q; ++i) {
+    for (int a = 0; a < P; ++a) {
+      b->B[i * P + a] = lagrange(b->xg.data(), P, a, b->xq[i]);
+      b->Dt[i * P + a] = lagrange_deriv(b->xg.data(), P, a, b->xq[i]);
+    }
+    for (int k = 0; k < q; ++k) b->Dc[i * q + k] = lagrange_deriv(b->xq.data(), q, k, b->xq[i]);
+  }
+  *out = b;
+  return PFF_OK;
+}
+
+int pff_basis_get(const pff_basis* b, double* xg, double* xq, double* wq, double* B, double* Dc) {
+  PFF_REQUIRE(b, "pff_basis_get: null basis");
+  if (xg) std::memcpy(xg, b->xg.data(), sizeof(double) * b->xg.size());
+  if (xq) std::memcpy(xq, b->xq.data(), sizeof(double) * b->xq.size());
+  if (wq) std::memcpy(wq, b->wq.data(), sizeof(double) * b->wq.size());
+  if (B) std::memcpy(B, b->B.data(), sizeof(double) * b->B.size());
+  if (Dc) std::memcpy(Dc, b->Dc.data(), sizeof(double) * b->Dc.size());
+  return PFF_OK;
+}
+
+int pff_destroy_basis(pff_basis* b) {
+  delete b;
+  return PFF_OK;
+}
+
+int pff_create_restriction(pff_ctx* ctx, const pff_box* box, int p, const int32_t* offsets, int64_t nnodes,
+                           pff_restr** out) {
+  PFF_REQUIRE(ctx && box && out, "pff_create_restriction: null argument");
+  PFF_REQUIRE(box->nx >= 1 && box->ny >= 1 && box->nz >= 1, "pff_create_restriction: empty element grid");
+  PFF_REQUIRE(box->hx > 0 && box->hy > 0 && box->hz > 0, "pff_create_restriction: element sizes must be positive");
+  PFF_REQUIRE(p >= 1 && p + 1 <= kMaxQ, "pff_create_restriction: 1 <= p <= 4");
+  long long nn_box = (long long)(p * box->nx + 1) * (p * box->ny + 1) * (p * box->nz + 1);
+  PFF_REQUIRE(offsets || nnodes == nn_box, "pff_create_restriction: nnodes does not match the structured box");
+  PFF_REQUIRE(nnodes > 0 && nnodes < (1LL << 40), "pff_create_restriction: nnodes out of range");
+  pff_restr* r = new pff_restr();
+  r->box = *box;
+  r->p = p;
+  r->offsets = offsets;
+  r->nn = nnodes;
+  *out = r;
+  return PFF_OK;
+}
+
+int pff_destroy_restriction(pff_restr* r) {
+  delete r;
+  return PFF_OK;
+}
+
+int pff_create_operator(pff_ctx* ctx, pff_basis* fine, pff_restr* restr, pff_op** out) {
+  PFF_REQUIRE(ctx && fine && restr && out, "pff_create_operator: null argument");
+  PFF_REQUIRE(fine->p == restr->p, "pff_create_operator: basis and restriction orders differ");
+  pff_op* op = new pff_op();
+  op->ctx = ctx;
+  op->p = fine->p;
+  op->Q = fine->q;
+  op->box = restr->box;
+  op->mesh = mesh_for(restr->box, fine->p, restr->offsets);
+  op->mesh.nn = restr->nn;
+  op->nel = op->mesh.nel;
+  op->nq = op->nel * (long long)op->Q * op->Q * op->Q;
+  op->geom.s[0] = 2.0 / restr->box.hx;
+  op->geom.s[1] = 2.0 / restr->box.hy;
+  op->geom.s[2] = 2.0 / restr->box.hz;
+  op->geom.detJ = restr->box.hx * restr->box.hy * restr->box.hz / 8.0;
+  for (int i = 0; i < kMaxQ; ++i) op->geom.wq[i] = (i < op->Q) ? fine->wq[i] : 0.0;
+  int EB = elems_per_block(op->Q);
+  long long nblk = (op->nel + EB - 1) / EB;
+  op->lin_len = nblk * kLinWords * stride_of(op->Q);
+  int rc = make_tables(op->p, op->Q, op->tab);
+  if (rc) { delete op; return rc; }
+  cudaError_t e = cudaSuccess;
+  e = cudaMalloc((void**)&op->hist_c, sizeof(double) * 15 * op->nq);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&op->hist_t, sizeof(double) * 15 * op->nq);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&op->phase, op->nq);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&op->flags, op->nq);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&op->lin64, sizeof(double) * op->lin_len);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&op->io, sizeof(double) * 13 * op->nq);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&op->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(op->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(op->phase, 0, op->nq);
+  if (e == cudaSuccess) e = cudaMemset(op->lin64, 0, sizeof(double) * op->lin_len);
+  if (e != cudaSuccess) {
+    pff_destroy_operator(op);
+    return fail(PFF_ERR_CUDA, std::string("pff_create_operator: ") + cudaGetErrorString(e));
+  }
+  *out = op;
+  return PFF_OK;
+}
+
+int pff_destroy_operator(pff_op* op) {
+  if (!op) return PFF_OK;
+  cudaFree(op->hist_c); cudaFree(op->hist_t); cudaFree(op->phase); cudaFree(op->flags);
+  cudaFree(op->lin64); cudaFree(op->lin32); cudaFree(op->io); cudaFree(op->mask);
+  cudaFree(op->dvals); cudaFree(op->status);
+  free_tables(op->tab);
+  delete op;
+  return PFF_OK;
+}
+
+int pff_op_enable_f32(pff_op* op, int enable) {
+  PFF_REQUIRE(op, "pff_op_enable_f32: null operator");
+  if (enable && !op->lin32) {
+    PFF_CK(cudaMalloc((void**)&op->lin32, sizeof(float) * op->lin_len));
+    PFF_CK(cudaMemset(op->lin32, 0, sizeof(float) * op->lin_len));
+  }
+  if (!enable && op->lin32) {
+    cudaFree(op->lin32);
+    op->lin32 = nullptr;
+  }
+  op->f32 = enable ? 1 : 0;
+  return PFF_OK;
+}
+
+int64_t pff_op_num_qpoints(const pff_op* op) { return op ? op->nq : -1; }
+int64_t pff_op_num_nodes(const pff_op* op) { return op ? op->mesh.nn : -1; }
+
+int pff_set_qpoint_state(pff_op* op, const uint8_t* phase, const double* hist, void* stream) {
+  PFF_REQUIRE(op && phase && hist, "pff_set_qpoint_state: null argument");
+  PFF_CK(cudaMemcpyAsync(op->phase, phase, op->nq, cudaMemcpyDeviceToDevice, S(stream)));
+  PFF_CK(cudaMemcpyAsync(op->hist_c, hist, sizeof(double) * 15 * op->nq, cudaMemcpyDeviceToDevice, S(stream)));
+  return PFF_OK;
+}
+
+int pff_set_dirichlet(pff_op* op, const uint8_t* mask, const double* values, void* stream) {
+  PFF_REQUIRE(op, "pff_set_dirichlet: null operator");
+  long long n = 4 * op->mesh.nn;
+  if (!mask) {
+    cudaFree(op->mask); op->mask = nullptr;
+    cudaFree(op->dvals); op->dvals = nullptr;
+    return PFF_OK;
+  }
+  if (!op->mask) PFF_CK(cudaMalloc((void**)&op->mask, n));
+  PFF_CK(cudaMemcpyAsync(op->mask, mask, n, cudaMemcpyDeviceToDevice, S(stream)));
+  if (values) {
+    if (!op->dvals) PFF_CK(cudaMalloc((void**)&op->dvals, sizeof(double) * n));
+    PFF_CK(cudaMemcpyAsync(op->dvals, values, sizeof(double) * n, cudaMemcpyDeviceToDevice, S(stream)));
+  } else if (op->dvals) {
+    PFF_CK(cudaMemsetAsync(op->dvals, 0, sizeof(double) * n, S(stream)));
+  }
+  return PFF_OK;
+}
+
+int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
+  PFF_REQUIRE(op && z && r, "pff_residual: null argument");
+  cudaStream_t st = S(stream);
+  const long long n = 4 * op->mesh.nn;
+  PFF_CK(launch_init_masked(0, r, z, op->dvals, op->mask, n, 1, st));
+  ElemArgs<double> a;
+  std::memset(&a, 0, sizeof(a));
+  a.mesh = op->mesh;
+  a.x = z;
+  a.mask = nullptr;
+  a.B = op->tab.B64;
+  a.Dc = op->tab.Dc64;
+  a.Dt = op->tab.Dt64;
+  a.scratch = op->io;
+  a.nq = op->nq;
+  for (int d = 0; d < 3; ++d) a.s[d] = op->geom.s[d];
+  PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kEval, a, st));
+  PointArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  for (int i = 0; i < op->ctx->nphase; ++i) pa.phase[i] = op->ctx->phase[i];
+  pa.glob = op->ctx->glob;
+  pa.geom = op->geom;
+  pa.Q = op->Q;
+  pa.nphase = op->ctx->nphase;
+  pa.nq = op->nq;
+  pa.nel = op->nel;
+  pa.io = op->io;
+  pa.hist = op->hist_c;
+  pa.hist_trial = op->hist_t;
+  pa.phase_id = op->phase;
+  pa.flags = op->flags;
+  pa.lin = op->lin64;
+  pa.status = op->status;
+  pa.want_tangent = 1;
+  PFF_CK(launch_pointwise(pa, st));
+  a.y = r;
+  a.mask = op->mask;
+  PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
+  if (op->f32 && op->lin32) PFF_CK(launch_to_f32(op->lin64, op->lin32, op->lin_len, st));
+  return PFF_OK;
+}
+
+int pff_create_level(pff_op* fine, int p, pff_level** out) {
+  PFF_REQUIRE(fine && out, "pff_create_level: null argument");
+  PFF_REQUIRE(p >= 1 && p <= fine->p, "pff_create_level: 1 <= p_level <= fine order");
+  PFF_REQUIRE(p == fine->p || fine->mesh.offsets == nullptr,
+              "pff_create_level: coarse levels need the structured restriction");
+  pff_level* L = new pff_level();
+  L->op = fine;
+  L->p = p;
+  L->is_fine = (p == fine->p);
+  L->mesh = L->is_fine ? fine->mesh : mesh_for(fine->box, p, nullptr);
+  int rc = make_tables(p, fine->Q, L->tab);
+  if (rc) { delete L; return rc; }
+  *out = L;
+  return PFF_OK;
+}
+
+int pff_destroy_level(pff_level* L) {
+  if (!L) return PFF_OK;
+  free_tables(L->tab);
+  cudaFree(L->mask);
+  cudaFree(L->I64); cudaFree(L->I32);
+  delete L;
+  return PFF_OK;
+}
+
+int64_t pff_level_num_nodes(const pff_level* L) { return L ? L->mesh.nn : -1; }
+
+int pff_level_set_mask(pff_level* L, const uint8_t* mask, void* stream) {
+  PFF_REQUIRE(L, "pff_level_set_mask: null level");
+  PFF_REQUIRE(!L->is_fine, "pff_level_set_mask: the fine level uses pff_set_dirichlet");
+  long long n = 4 * L->mesh.nn;
+  if (!mask) { cudaFree(L->mask); L->mask = nullptr; return PFF_OK; }
+  if (!L->mask) PFF_CK(cudaMalloc((void**)&L->mask, n));
+  PFF_CK(cudaMemcpyAsync(L->mask, mask, n, cudaMemcpyDeviceToDevice, S(stream)));
+  return PFF_OK;
+}
+
+int pff_jacobian_apply(pff_level* L, pff_prec prec, const void* x, void* y, void* stream) {
+  PFF_REQUIRE(L && x && y, "pff_jacobian_apply: null argument");
+  if (prec == PFF_F64) return apply_t<double>(L, (const double*)x, (double*)y, 0, S(stream));
+  if (prec == PFF_F32) return apply_t<float>(L, (const float*)x, (float*)y, 0, S(stream));
+  return fail(PFF_ERR_INVALID, "pff_jacobian_apply: unknown precision");
+}
+
+int pff_jacobian_transpose_apply(pff_level* L, pff_prec prec, const void* x, void* y, void* stream) {
+  PFF_REQUIRE(L && x && y, "pff_jacobian_transpose_apply: null argument");
+  if (prec == PFF_F64) return apply_t<double>(L, (const double*)x, (double*)y, 1, S(stream));
+  if (prec == PFF_F32) return apply_t<float>(L, (const float*)x, (float*)y, 1, S(stream));
+  return fail(PFF_ERR_INVALID, "pff_jacobian_transpose_apply: unknown precision");
+}
+
+int pff_assemble_diagonal(pff_level* L, pff_prec prec, void* diag, void* stream) {
+  PFF_REQUIRE(L && diag, "pff_assemble_diagonal: null argument");
+  if (prec == PFF_F64) return diag_t<double>(L, (double*)diag, S(stream));
+  if (prec == PFF_F32) return diag_t<float>(L, (float*)diag, S(stream));
+  return fail(PFF_ERR_INVALID, "pff_assemble_diagonal: unknown precision");
+}
+
+int pff_prolong(pff_level* c, pff_level* f, pff_prec prec, const void* xc, void* xf, void* stream) {
+  PFF_REQUIRE(c && f && xc && xf, "pff_prolong: null argument");
+  PFF_REQUIRE(c->op == f->op && c->p < f->p, "pff_prolong: levels must share the operator, coarse p < fine p");
+  PFF_REQUIRE(f->mesh.offsets == nullptr, "pff_prolong: structured restriction required");
+  int rc = ensure_prolong_table(c, f);
+  if (rc) return rc;
+  const uint8_t* mc = level_mask(c);
+  const uint8_t* mf = level_mask(f);
+  if (prec == PFF_F64) PFF_CK(launch_prolong<double>(c->mesh, f->mesh, c->I64, (const double*)xc, (double*)xf, mc, mf, S(stream)));
+  else if (prec == PFF_F32) PFF_CK(launch_prolong<float>(c->mesh, f->mesh, c->I32, (const float*)xc, (float*)xf, mc, mf, S(stream)));
+  else return fail(PFF_ERR_INVALID, "pff_prolong: unknown precision");
+  return PFF_OK;
+}
+
+int pff_restrict(pff_level* c, pff_level* f, pff_prec prec, const void* rf, void* rc_, void* stream) {
+  PFF_REQUIRE(c && f && rf && rc_, "pff_restrict: null argument");
+  PFF_REQUIRE(c->op == f->op && c->p < f->p, "pff_restrict: levels must share the operator, coarse p < fine p");
+  PFF_REQUIRE(f->mesh.offsets == nullptr, "pff_restrict: structured restriction required");
+  int rc = ensure_prolong_table(c, f);
+  if (rc) return rc;
+  const uint8_t* mc = level_mask(c);
+  const uint8_t* mf = level_mask(f);
+  if (prec == PFF_F64) PFF_CK(launch_restrict<double>(c->mesh, f->mesh, c->I64, (const double*)rf, (double*)rc_, mc, mf, S(stream)));
+  else if (prec == PFF_F32) PFF_CK(launch_restrict<float>(c->mesh, f->mesh, c->I32, (const float*)rf, (float*)rc_, mc, mf, S(stream)));
+  else return fail(PFF_ERR_INVALID, "pff_restrict: unknown precision");
+  return PFF_OK;
+}
+
+int pff_chebyshev_smooth(pff_level* L, pff_prec prec, int degree, double lmin, double lmax, const void* diag,
+                         const void* b, void* x, void* work, void* stream) {
+  PFF_REQUIRE(L && diag && b && x && work, "pff_chebyshev_smooth: null argument");
+  PFF_REQUIRE(degree >= 1 && degree <= 64, "pff_chebyshev_smooth: 1 <= degree <= 64");
+  PFF_REQUIRE(lmax > lmin && lmin > 0.0, "pff_chebyshev_smooth: need 0 < lmin < lmax");
+  if (prec == PFF_F64)
+    return cheb_t<double>(L, degree, lmin, lmax, (const double*)diag, (const double*)b, (double*)x, (double*)work, S(stream));
+  if (prec == PFF_F32)
+    return cheb_t<float>(L, degree, lmin, lmax, (const float*)diag, (const float*)b, (float*)x, (float*)work, S(stream));
+  return fail(PFF_ERR_INVALID, "pff_chebyshev_smooth: unknown precision");
+}
+
+int pff_commit_history(pff_op* op, void* stream) {
+  PFF_REQUIRE(op, "pff_commit_history: null operator");
+  PFF_CK(cudaMemcpyAsync(op->hist_c, op->hist_t, sizeof(double) * 15 * op->nq, cudaMemcpyDeviceToDevice, S(stream)));
+  return PFF_OK;
+}
+
+int pff_get_history(pff_op* op, int which, double* hist, void* stream) {
+  PFF_REQUIRE(op && hist && (which == 0 || which == 1), "pff_get_history: bad argument");
+  PFF_CK(cudaMemcpyAsync(hist, which ? op->hist_t : op->hist_c, sizeof(double) * 15 * op->nq,
+                         cudaMemcpyDeviceToDevice, S(stream)));
+  return PFF_OK;
+}
+
+int pff_get_flags(pff_op* op, uint8_t* flags, void* stream) {
+  PFF_REQUIRE(op && flags, "pff_get_flags: null argument");
+  PFF_CK(cudaMemcpyAsync(flags, op->flags, op->nq, cudaMemcpyDeviceToDevice, S(stream)));
+  return PFF_OK;
+}
+
+int pff_get_linearization(pff_op* op, double* out, void* stream) {
+  PFF_REQUIRE(op && out, "pff_get_linearization: null argument");
+  PFF_CK(launch_untile(op->lin64, out, op->nq, op->Q, S(stream)));
+  return PFF_OK;
+}
+
+int pff_get_status(pff_op* op, void* stream, int* status) {
+  PFF_REQUIRE(op && status, "pff_get_status: null argument");
+  PFF_CK(cudaStreamSynchronize(S(stream)));
+  int h = 0;
+  PFF_CK(cudaMemcpy(&h, op->status, sizeof(int), cudaMemcpyDeviceToHost));
+  PFF_CK(cudaMemset(op->status, 0, sizeof(int)));
+  *status = h;
+  return PFF_OK;
+}
+
+}  // extern "C"

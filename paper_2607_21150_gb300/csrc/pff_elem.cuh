@@ -1,0 +1,472 @@
+// Element kernels of the matrix-free operator (Sec. 4):
+//   y = P^T sum_el E^T [B_I; B_xi]^T W Lambda f_hat(...) [B_I; B_xi] E P x
+//
+// One thread block handles EB = 256 / Q^2 consecutive elements with Q*Q threads
+// per element; thread (i, j) of an element owns the column of quadrature
+// points (i, j, 0..Q-1).  The tensor contractions are sum-factorised through
+// shared memory one direction at a time; gradients at the Gauss points use
+// the collocated derivative D_c (exact because p <= Q - 1).  The pointwise
+// linearisation is read from a tiled layout so that every load of a block is
+// one contiguous run: word w of slice k of block b sits at
+//   b * 67 * Q^3 * EB + w * Q^3 * EB + k * Q^2 * EB + threadIdx.x.
+#pragma once
+#include "pff_internal.h"
+
+namespace pff {
+
+template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+template <int P, int Q>
+__device__ __forceinline__ long long node_of(const MeshDev& m, int e, int a, int b, int c) {
+  if (m.offsets) return m.offsets[(long long)e * (P * P * P) + a + P * (b + P * c)];
+  int ex = e % m.nx;
+  int t = e / m.nx;
+  int ey = t % m.ny;
+  int ez = t / m.ny;
+  return (long long)(m.p * ex + a) + (long long)m.nnx * ((long long)(m.p * ey + b) + (long long)m.nny * (m.p * ez + c));
+}
+
+// Shared-memory layout per element: two ping-pong buffers of 4 fields x Q^3
+// values and a slice buffer of 8 x Q^2 values (x- and y-derivative outputs of
+// the four fields at one k).
+template <int Q> __host__ __device__ constexpr int elem_smem_words() { return 8 * Q * Q * Q + 8 * Q * Q; }
+template <int P, int Q> __host__ __device__ constexpr int mat_smem_words() { return 3 * Q * P + Q * Q; }
+
+template <int P, int Q, typename T>
+struct ElemSmem {
+  T* bufA;  // [4][Q^3]
+  T* bufB;  // [4][Q^3]
+  T* slice; // [8][Q^2]
+  const T* B;
+  const T* Dc;
+  const T* Dt;
+};
+
+// Forward: gather x into bufA, interpolate to Gauss points into bufB.
+template <int P, int Q, typename T>
+__device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, Q, T>& s, int e, bool valid, int ij) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
+  const long long nn = a.mesh.nn;
+  for (int idx = ij; idx < P3; idx += Q2) {
+    int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);
+    long long n = valid ? node_of<P, Q>(a.mesh, e, aa, bb, cc) : 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      T v = T(0);
+      if (valid) {
+        long long g = f * nn + n;
+        v = ldg(a.x + g);
+        if (a.mask && a.mask[g]) v = T(0);
+      }
+      s.bufA[f * Q3 + idx] = v;
+    }
+  }
+  __syncthreads();
+  // x: [c][b][a] -> [c][b][i]
+  for (int idx = ij; idx < P * P * Q; idx += Q2) {
+    int i = idx % Q, r = idx / Q;  // r = b + P c
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T* in = s.bufA + f * Q3 + r * P;
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) acc += s.B[i * P + k] * in[k];
+      s.bufB[f * Q3 + idx] = acc;
+    }
+  }
+  __syncthreads();
+  // y: [c][b][i] -> [c][j][i]
+  for (int idx = ij; idx < P * Q * Q; idx += Q2) {
+    int i = idx % Q, j = (idx / Q) % Q, c = idx / Q2;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T* in = s.bufB + f * Q3 + c * (P * Q) + i;
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < P; ++k) acc += s.B[j * P + k] * in[k * Q];
+      s.bufA[f * Q3 + idx] = acc;
+    }
+  }
+  __syncthreads();
+  // z: [c][j][i] -> [k][j][i]
+  {
+    const int i = ij % Q, j = ij / Q;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      T col[P];
+#pragma unroll
+      for (int c = 0; c < P; ++c) col[c] = s.bufA[f * Q3 + c * Q2 + j * Q + i];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) {
+        T acc = T(0);
+#pragma unroll
+        for (int c = 0; c < P; ++c) acc += s.B[k * P + c] * col[c];
+        s.bufB[f * Q3 + k * Q2 + j * Q + i] = acc;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Parent-frame gradients of the four fields at point (i, j, k) from bufB.
+template <int P, int Q, typename T>
+__device__ __forceinline__ void grad_at(const ElemSmem<P, Q, T>& s, int i, int j, int k, T g[4][3], T& phi) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const T* V = s.bufB + f * Q3;
+    T gx = T(0), gy = T(0), gz = T(0);
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      gx += s.Dc[i * Q + m] * V[k * Q2 + j * Q + m];
+      gy += s.Dc[j * Q + m] * V[k * Q2 + m * Q + i];
+      gz += s.Dc[k * Q + m] * V[m * Q2 + j * Q + i];
+    }
+    g[f][0] = gx; g[f][1] = gy; g[f][2] = gz;
+  }
+  phi = s.bufB[3 * Q3 + k * Q2 + j * Q + i];
+}
+
+// Backward: from accumulated column values Y[f][k] (transposed derivative
+// already applied) to nodal element values, then scatter-add.
+template <int P, int Q, typename T>
+__device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P, Q, T>& s, int e, bool valid, int ij,
+                                         T Y[4][Q]) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
+  const int i = ij % Q, j = ij / Q;
+  // z (registers): [k][j][i] -> [c][j][i]
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      T acc = T(0);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) acc += s.B[k * P + c] * Y[f][k];
+      s.bufA[f * Q3 + c * Q2 + j * Q + i] = acc;
+    }
+  __syncthreads();
+  // y: [c][j][i] -> [c][b][i]
+  for (int idx = ij; idx < P * P * Q; idx += Q2) {
+    int ii = idx % Q, bb = (idx / Q) % P, c = idx / (P * Q);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T* in = s.bufA + f * Q3 + c * Q2 + ii;
+      T acc = T(0);
+#pragma unroll
+      for (int jj = 0; jj < Q; ++jj) acc += s.B[jj * P + bb] * in[jj * Q];
+      s.bufB[f * Q3 + idx] = acc;
+    }
+  }
+  __syncthreads();
+  // x: [c][b][i] -> [c][b][a]
+  for (int idx = ij; idx < P3; idx += Q2) {
+    int aa = idx % P, r = idx / P;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T* in = s.bufB + f * Q3 + r * Q;
+      T acc = T(0);
+#pragma unroll
+      for (int ii = 0; ii < Q; ++ii) acc += s.B[ii * P + aa] * in[ii];
+      s.bufA[f * Q3 + idx] = acc;
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  const long long nn = a.mesh.nn;
+  for (int idx = ij; idx < P3; idx += Q2) {
+    int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);
+    long long n = node_of<P, Q>(a.mesh, e, aa, bb, cc);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      long long g = f * nn + n;
+      if (a.mask && a.mask[g]) continue;
+      atomicAdd(a.y + g, s.bufA[f * Q3 + idx]);
+    }
+  }
+}
+
+// Pointwise linear map of the Jacobian with the stored words (already scaled
+// by the quadrature weight and the parent-to-reference factors).
+template <typename T>
+__device__ __forceinline__ void jac_point(const T* lin, const T* linP, const T* linC, long long stride,
+                                          const T g[4][3], T phi, T o[4][3], T& o0) {
+  T gu[9];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) gu[3 * f + al] = g[f][al];
+  T ou[9];
+#pragma unroll
+  for (int m = 0; m < 9; ++m) ou[m] = ldg(linP + m * stride) * phi;
+  // symmetric 9x9 block
+#pragma unroll
+  for (int m = 0; m < 9; ++m) {
+#pragma unroll
+    for (int n = m; n < 9; ++n) {
+      T A = ldg(lin + (long long)sym9(m, n) * stride);
+      ou[m] += A * gu[n];
+      if (n != m) ou[n] += A * gu[m];
+    }
+  }
+  T s0 = ldg(lin + kWD * stride) * phi;
+#pragma unroll
+  for (int m = 0; m < 9; ++m) s0 += ldg(linC + m * stride) * gu[m];
+  o0 = s0;
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) o[f][al] = ou[3 * f + al];
+#pragma unroll
+  for (int al = 0; al < 3; ++al) o[3][al] = ldg(lin + (kWK + al) * stride) * g[3][al];
+}
+
+template <int P, int Q, typename T, int MODE>
+__global__ void __launch_bounds__(Q * Q * elems_per_block(Q))
+k_elem(const ElemArgs<T> a) {
+  constexpr int EB = elems_per_block(Q);
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int t = threadIdx.x;
+  const int el = t / Q2, ij = t % Q2;
+  const int i = ij % Q, j = ij / Q;
+  const int e = blockIdx.x * EB + el;
+  const bool valid = e < a.mesh.nel;
+
+  T* mats = sm;
+  T* Bs = mats;
+  T* Dcs = Bs + Q * P;
+  for (int idx = t; idx < Q * P; idx += blockDim.x) Bs[idx] = a.B[idx];
+  for (int idx = t; idx < Q * Q; idx += blockDim.x) Dcs[idx] = a.Dc[idx];
+  T* base = sm + mat_smem_words<P, Q>() + el * elem_smem_words<Q>();
+  ElemSmem<P, Q, T> s{base, base + 4 * Q3, base + 8 * Q3, Bs, Dcs, nullptr};
+  __syncthreads();
+
+  if constexpr (MODE == kApply || MODE == kEval) forward<P, Q, T>(a, s, e, valid, ij);
+
+  if constexpr (MODE == kEval) {
+    if (valid) {
+#pragma unroll 1
+      for (int k = 0; k < Q; ++k) {
+        T g[4][3], phi;
+        grad_at<P, Q, T>(s, i, j, k, g, phi);
+        long long q = (long long)e * Q3 + k * Q2 + j * Q + i;
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+          for (int al = 0; al < 3; ++al) a.scratch[(3 * f + al) * a.nq + q] = (double)g[f][al] * a.s[al];
+        a.scratch[9 * a.nq + q] = (double)phi;
+#pragma unroll
+        for (int al = 0; al < 3; ++al) a.scratch[(10 + al) * a.nq + q] = (double)g[3][al] * a.s[al];
+      }
+    }
+    return;
+  }
+
+  T Y[4][Q];
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int k = 0; k < Q; ++k) Y[f][k] = T(0);
+
+  const long long blk_words = (long long)kLinWords * Q3 * EB;
+  const long long stride = (long long)Q3 * EB;
+#pragma unroll
+  for (int k = 0; k < Q; ++k) {
+    T o[4][3], o0 = T(0);
+    if constexpr (MODE == kApply) {
+      T g[4][3], phi;
+      grad_at<P, Q, T>(s, i, j, k, g, phi);
+      if (valid) {
+        long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
+        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, g, phi, o, o0);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = T(0);
+      }
+    } else {  // kBack: integrands from the pointwise kernel
+      if (valid) {
+        long long q = (long long)e * Q3 + k * Q2 + j * Q + i;
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+          for (int al = 0; al < 3; ++al) o[f][al] = (T)a.scratch[(3 * f + al) * a.nq + q];
+        o0 = (T)a.scratch[9 * a.nq + q];
+#pragma unroll
+        for (int al = 0; al < 3; ++al) o[3][al] = (T)a.scratch[(10 + al) * a.nq + q];
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = T(0);
+      }
+    }
+    // transposed z-derivative (own column) and the value term
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+      for (int kk = 0; kk < Q; ++kk) Y[f][kk] += s.Dc[k * Q + kk] * o[f][2];
+    Y[3][k] += o0;
+    // x- and y-derivative outputs of this slice through shared memory
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      s.slice[(2 * f) * Q2 + ij] = o[f][0];
+      s.slice[(2 * f + 1) * Q2 + ij] = o[f][1];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < Q; ++m) {
+        acc += s.Dc[m * Q + i] * s.slice[(2 * f) * Q2 + j * Q + m];
+        acc += s.Dc[m * Q + j] * s.slice[(2 * f + 1) * Q2 + m * Q + i];
+      }
+      Y[f][k] += acc;
+    }
+    __syncthreads();
+  }
+  backward<P, Q, T>(a, s, e, valid, ij, Y);
+}
+
+// Diagonal of the element operators: for each field f and node a,
+//   sum_q sum_{alpha,beta} D_{f alpha, f beta}(q) d_alpha N_a d_beta N_a
+// (+ the value term of the phase field), sum-factorised per (alpha, beta)
+// pair with the 1D products B*B, B*D, D*D.
+template <int P, int Q, typename T>
+__global__ void __launch_bounds__(Q * Q * elems_per_block(Q))
+k_diag(const ElemArgs<T> a) {
+  constexpr int EB = elems_per_block(Q);
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int t = threadIdx.x;
+  const int el = t / Q2, ij = t % Q2;
+  const int i = ij % Q, j = ij / Q;
+  const int e = blockIdx.x * EB + el;
+  const bool valid = e < a.mesh.nel;
+  T* M = sm;  // [3][Q][P]: BB, BD, DD
+  for (int idx = t; idx < Q * P; idx += blockDim.x) {
+    T b = a.B[idx], d = a.Dt[idx];
+    M[idx] = b * b;
+    M[Q * P + idx] = b * d;
+    M[2 * Q * P + idx] = d * d;
+  }
+  T* base = sm + mat_smem_words<P, Q>() + el * elem_smem_words<Q>();
+  T* bufA = base;           // Q^3
+  T* bufB = base + Q3;      // Q^3
+  T* acc = base + 2 * Q3;   // [4][P3]
+  for (int idx = ij; idx < 4 * P3; idx += Q2) acc[idx] = T(0);
+  __syncthreads();
+  const long long blk_words = (long long)kLinWords * Q3 * EB;
+  const long long stride = (long long)Q3 * EB;
+  // term list: (field, word, dim-kinds mask, weight)
+  // u fields: pairs alpha <= beta; phase field: value term and 3 gradient terms
+#pragma unroll 1
+  for (int term = 0; term < 22; ++term) {
+    int f, word, kx, ky, kz;
+    T wgt = T(1);
+    if (term < 18) {
+      f = term / 6;
+      int pr = term % 6;
+      const int al_of[6] = {0, 1, 2, 0, 0, 1};
+      const int be_of[6] = {0, 1, 2, 1, 2, 2};
+      int al = al_of[pr], be = be_of[pr];
+      word = sym9(3 * f + al, 3 * f + be);
+      if (al != be) wgt = T(2);
+      int kd[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) kd[d] = (d == al) + (d == be);  // 0: BB, 1: BD, 2: DD
+      kx = kd[0]; ky = kd[1]; kz = kd[2];
+    } else {
+      f = 3;
+      if (term == 18) { word = kWD; kx = ky = kz = 0; }
+      else {
+        int al = term - 19;
+        word = kWK + al;
+        kx = (al == 0) ? 2 : 0; ky = (al == 1) ? 2 : 0; kz = (al == 2) ? 2 : 0;
+      }
+    }
+    const T* Mx = M + kx * Q * P;
+    const T* My = M + ky * Q * P;
+    const T* Mz = M + kz * Q * P;
+    // coefficients on the column (i, j, :) -> z contraction in registers
+    T col[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      long long off = blockIdx.x * blk_words + (long long)word * stride + (long long)k * Q2 * EB + t;
+      col[k] = valid ? ldg(a.lin + off) * wgt : T(0);
+    }
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      T s = T(0);
+#pragma unroll
+      for (int k = 0; k < Q; ++k) s += Mz[k * P + c] * col[k];
+      bufA[c * Q2 + j * Q + i] = s;
+    }
+    __syncthreads();
+    for (int idx = ij; idx < P * P * Q; idx += Q2) {
+      int ii = idx % Q, bb = (idx / Q) % P, c = idx / (P * Q);
+      T s = T(0);
+#pragma unroll
+      for (int jj = 0; jj < Q; ++jj) s += My[jj * P + bb] * bufA[c * Q2 + jj * Q + ii];
+      bufB[idx] = s;
+    }
+    __syncthreads();
+    for (int idx = ij; idx < P3; idx += Q2) {
+      int aa = idx % P, r = idx / P;
+      T s = T(0);
+#pragma unroll
+      for (int ii = 0; ii < Q; ++ii) s += Mx[ii * P + aa] * bufB[r * Q + ii];
+      acc[f * P3 + idx] += s;
+    }
+    __syncthreads();
+  }
+  if (!valid) return;
+  const long long nn = a.mesh.nn;
+  for (int idx = ij; idx < P3; idx += Q2) {
+    int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);
+    long long n = node_of<P, Q>(a.mesh, e, aa, bb, cc);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      long long g = f * nn + n;
+      if (a.mask && a.mask[g]) continue;
+      atomicAdd(a.y + g, acc[f * P3 + idx]);
+    }
+  }
+}
+
+template <int P, int Q, typename T>
+cudaError_t launch_elem_pq(int mode, const ElemArgs<T>& a, cudaStream_t st) {
+  constexpr int EB = elems_per_block(Q);
+  int nblk = (a.mesh.nel + EB - 1) / EB;
+  if (nblk == 0) return cudaSuccess;
+  size_t smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words<Q>());
+  dim3 block(Q * Q * EB);
+  if (mode == kApply) {
+    auto k = k_elem<P, Q, T, kApply>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nblk, block, smem, st>>>(a);
+  } else if (mode == kEval) {
+    auto k = k_elem<P, Q, T, kEval>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nblk, block, smem, st>>>(a);
+  } else {
+    auto k = k_elem<P, Q, T, kBack>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nblk, block, smem, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int P, int Q, typename T>
+cudaError_t launch_diag_pq(const ElemArgs<T>& a, cudaStream_t st) {
+  constexpr int EB = elems_per_block(Q);
+  int nblk = (a.mesh.nel + EB - 1) / EB;
+  if (nblk == 0) return cudaSuccess;
+  size_t smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words<Q>());
+  auto k = k_diag<P, Q, T>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<nblk, Q * Q * EB, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace pff

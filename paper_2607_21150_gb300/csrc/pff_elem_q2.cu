@@ -1,0 +1,25 @@
+// Element kernels for Q = 2 Gauss points per direction, every P <= Q, FP64 and FP32.
+#include "pff_elem.cuh"
+
+namespace pff {
+
+template <typename T>
+cudaError_t launch_elem_q2(int P, int mode, const ElemArgs<T>& a, cudaStream_t st) {
+  switch (P) {
+    case 2: return launch_elem_pq<2, 2, T>(mode, a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t launch_diag_q2(int P, const ElemArgs<T>& a, cudaStream_t st) {
+  switch (P) {
+    case 2: return launch_diag_pq<2, 2, T>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_elem_q2<double>(int, int, const ElemArgs<double>&, cudaStream_t);
+template cudaError_t launch_elem_q2<float>(int, int, const ElemArgs<float>&, cudaStream_t);
+template cudaError_t launch_diag_q2<double>(int, const ElemArgs<double>&, cudaStream_t);
+template cudaError_t launch_diag_q2<float>(int, const ElemArgs<float>&, cudaStream_t);
+
+}  // namespace pff

@@ -1,0 +1,130 @@
+// Internal declarations of the CUDA library (not part of the public C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pff {
+
+constexpr int kMaxPhase = 8;
+constexpr int kMaxQ = 5;          // quadrature points per direction (Q <= p_fine + 1 <= 5)
+constexpr int kLinWords = 67;     // stored pointwise linearisation words per quadrature point
+// word layout: [0,45) upper triangle of the 9x9 block dP/dF (row-major, m <= n,
+// m = 3 i + A), [45,54) dP/dphi, [54,63) d(s_phi L)/dF, [63] d(s_phi L)/dphi,
+// [64,67) diagonal coefficients of the phase-gradient term.
+constexpr int kWA = 0, kWP = 45, kWC = 54, kWD = 63, kWK = 64;
+
+// Elements handled by one thread block of the element kernels: Q*Q threads per element.
+__host__ __device__ constexpr int elems_per_block(int Q) { return 256 / (Q * Q); }
+
+__host__ __device__ constexpr int sym9(int m, int n) {  // m <= n
+  return m * 9 - (m * (m - 1)) / 2 + (n - m);
+}
+
+// Per-phase material constants for the pointwise update (host-derived).
+struct PhaseDev {
+  double mu[3], kap[3];   // branch 0 Hooke, 1 Maxwell, 2 Prandtl
+  int has[3];
+  double cmax;            // Maxwell: mu dt / eta_d (0 when eta_d = +inf)
+  double sig0;            // Prandtl perfect-plastic yield stress
+  double kap_tot;
+  double gc_c0l0;         // Gc / (c0 l0)
+  double kphi;            // s_phi * 2 Gc l0 / c0
+};
+
+struct GlobDev {
+  int at;                 // 1 = AT1, 2 = AT2
+  double eta, zeta, dt, s_phi;
+};
+
+// Geometry of the affine box elements.
+struct Geom {
+  double s[3];            // d xi / d X per direction = 2 / h
+  double detJ;            // h_x h_y h_z / 8
+  double wq[kMaxQ];       // 1D Gauss weights
+};
+
+// Mesh / restriction description shared by the element kernels.
+struct MeshDev {
+  int nel, nx, ny, nz;    // element grid
+  int p;                  // order of this level (P = p + 1 nodes per direction)
+  int nnx, nny;           // node grid sizes in x and y
+  long long nn;           // nodes per field
+  const int32_t* offsets; // optional explicit element -> node map [nel][P^3]
+};
+
+struct PointArgs {
+  PhaseDev phase[kMaxPhase];
+  GlobDev glob;
+  Geom geom;
+  int Q;
+  int nphase;
+  long long nq;
+  long long nel;
+  double* io;             // [13][nq] inputs in, residual integrands out
+  const double* hist;     // [15][nq] committed history
+  double* hist_trial;     // [15][nq]
+  const uint8_t* phase_id;// [nq]
+  uint8_t* flags;         // [nq]
+  double* lin;            // tiled stored linearisation (FP64)
+  int* status;            // device status word (bit0 eigen sweeps, bit1 J <= 0, bit2 non-finite, bit3 phase id)
+  int want_tangent;
+};
+
+// Element-kernel launches (pff_elem*.cu).  T = double or float.
+enum ElemMode { kApply = 0, kEval = 1, kBack = 2 };
+
+template <typename T>
+struct ElemArgs {
+  MeshDev mesh;
+  const T* x;             // [4][nn] input (apply) / unused
+  T* y;                   // [4][nn] output (scatter-add)
+  const uint8_t* mask;    // [4][nn] Dirichlet mask or nullptr
+  const T* B;             // [Q][P] interpolation to Gauss points
+  const T* Dc;            // [Q][Q] collocated derivative at Gauss points
+  const T* Dt;            // [Q][P] derivative of the basis at Gauss points (diagonal)
+  const T* lin;           // tiled stored linearisation (apply / diagonal)
+  const T* linP;          // words multiplying dphi in the u rows (dP/dphi or, transposed, dL/dF)
+  const T* linC;          // words multiplying grad u in the phi row
+  double* scratch;        // [13][nq] (eval / back)
+  double s[3];            // d xi / d X (eval)
+  long long nq;
+  int transpose;
+};
+
+// One translation unit per quadrature size Q (pff_elem_q<Q>.cu); each covers
+// every basis size P <= Q in both precisions.
+#define PFF_DECLARE_ELEM_Q(QQ)                                                                  \
+  template <typename T> cudaError_t launch_elem_q##QQ(int P, int mode, const ElemArgs<T>& a, cudaStream_t st); \
+  template <typename T> cudaError_t launch_diag_q##QQ(int P, const ElemArgs<T>& a, cudaStream_t st);
+PFF_DECLARE_ELEM_Q(2)
+PFF_DECLARE_ELEM_Q(3)
+PFF_DECLARE_ELEM_Q(4)
+PFF_DECLARE_ELEM_Q(5)
+
+cudaError_t launch_pointwise(const PointArgs& a, cudaStream_t st);
+
+// Vector / transfer kernels (pff_vec.cu)
+cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
+                               const uint8_t* mask, long long n, int mode, cudaStream_t st);
+cudaError_t launch_to_f32(const double* a, float* b, long long n, cudaStream_t st);
+cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st);
+template <typename T>
+cudaError_t launch_prolong(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* xc, T* xf,
+                           const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st);
+template <typename T>
+cudaError_t launch_restrict(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* rf, T* rc,
+                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cheb_init(long long n, const T* b, const T* Ax, const T* diag, T* r, T* d,
+                             double inv_theta, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cheb_step(long long n, T* x, T* d, T* r, const T* Ad, const T* diag,
+                             double c_d, double c_r, int last, cudaStream_t st);
+
+// Host basis data (pff_basis.cpp)
+void gll_nodes(int p, double* x);
+void gauss_rule(int Q, double* x, double* w);
+double lagrange(const double* nodes, int n, int a, double t);
+double lagrange_deriv(const double* nodes, int n, int a, double t);
+
+}  // namespace pff

@@ -1,0 +1,377 @@
+// Pointwise Peric-Dettmer update with the series fracture element, one thread
+// per quadrature point, FP64.
+//
+// Principal-stress format (Appendix A): every branch k spectrally decomposes
+// X_k = b_k^tr - I = F (C_k - I) F^T + (F F^T - I) (Eq. inelasticity-be-update),
+// takes eps_i = log1p(x_i) / 2 (the log1p form of Sec. 2.2), corrects the
+// deviatoric principal strains with the branch factor a_k (Box 1 step 2 and
+// Eq. principal-directions-format-1 with the degraded mu and q_tr of Sec. 3),
+// and rebuilds tau_d,k = N diag(2 mu a eps_d) N^T.  The volumetric strain
+// theta = ln J is shared by all branches and decides the Amor split
+// (Eqs. linear-Psi-plus, linear-degraded-stress).
+//
+// The consistent tangent follows Appendix B (d b = ell b + b ell^T with
+// ell = dF F^-1, d eps_i = d b_i / (2 b_i), Box A1 per branch, Eq.
+// hencky-stress-linearization) with the eigenvector term written as the
+// divided difference (tau_i - tau_j)/(b_i - b_j) = mu a log1p(x)/(x b_j),
+// x = (b_i - b_j)/b_j, which is exact at distinct eigenvalues and smooth where
+// they coincide; and Appendix C for the phase-field coupling
+// (Eqs. linear-degraded-stress-linearization, maxwell-dtau-dphi,
+// prandtl-dtau-dphi, linearized-local-damage-residual,
+// history-field-linearization, energy-displacement-linearization,
+// maxwell-energy-dphi, prandtl-energy-dphi).  The reference-frame tangent
+// dP = (d tau_degr - tau_degr ell^T) F^-T is evaluated column by column for the
+// nine unit directions of F and for phi, scaled by the quadrature weight and
+// the parent-to-reference factors and stored in the tiled 67-word layout.
+#include <cmath>
+
+#include "pff_internal.h"
+
+namespace pff {
+
+static __device__ __forceinline__ void vo_idx(int v, int& r, int& c) {
+  const int I[6] = {0, 1, 2, 1, 0, 0};
+  const int J[6] = {0, 1, 2, 2, 2, 1};
+  r = I[v]; c = J[v];
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (in place).
+// On exit w = eigenvalues, V columns = eigenvectors.  Returns 0 when the
+// off-diagonal part vanished within the sweep cap.
+static __device__ int jacobi3(double A[3][3], double V[3][3], double w[3]) {
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) V[r][c] = (r == c) ? 1.0 : 0.0;
+  int ok = 0;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-36 * dia || off < 1e-300) { ok = 1; break; }
+    for (int pr = 0; pr < 3; ++pr) {
+      const int p = (pr == 2) ? 1 : 0;
+      const int q = (pr == 0) ? 1 : 2;
+      double apq = A[p][q];
+      if (apq == 0.0) continue;
+      double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+      double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      double c = 1.0 / sqrt(t * t + 1.0);
+      double s = t * c;
+      double tau = s / (1.0 + c);
+      A[p][p] -= t * apq;
+      A[q][q] += t * apq;
+      A[p][q] = A[q][p] = 0.0;
+      const int r = 3 - p - q;
+      double arp = A[r][p], arq = A[r][q];
+      A[r][p] = A[p][r] = arp - s * (arq + tau * arp);
+      A[r][q] = A[q][r] = arq + s * (arp - tau * arq);
+      for (int k = 0; k < 3; ++k) {
+        double vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = vkp - s * (vkq + tau * vkp);
+        V[k][q] = vkq + s * (vkp - tau * vkq);
+      }
+    }
+  }
+  w[0] = A[0][0]; w[1] = A[1][1]; w[2] = A[2][2];
+  return ok;
+}
+
+// (ln b_p - ln b_q) / (b_p - b_q) from the eigenvalues x = b - 1.
+static __device__ __forceinline__ double log_ratio(double xp, double xq) {
+  double bq = 1.0 + xq;
+  double y = (xp - xq) / bq;
+  double l1;
+  if (fabs(y) < 1e-4) l1 = 1.0 - y * (0.5 - y * (1.0 / 3.0 - 0.25 * y));
+  else l1 = log1p(y) / y;
+  return l1 / bq;
+}
+
+__global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= a.nq) return;
+  const int Q = a.Q, Q2 = Q * Q, Q3 = Q2 * Q;
+  const long long nq = a.nq;
+  const int lq = (int)(q % Q3);
+  const int qi = lq % Q, qj = (lq / Q) % Q, qk = lq / Q2;
+  const long long e = q / Q3;
+  const double wdet = a.geom.wq[qi] * a.geom.wq[qj] * a.geom.wq[qk] * a.geom.detJ;
+  const double* sg = a.geom.s;
+
+  double Hm[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) Hm[r][c] = a.io[(3 * r + c) * nq + q];
+  const double phi = a.io[9 * nq + q];
+  double gphi[3] = {a.io[10 * nq + q], a.io[11 * nq + q], a.io[12 * nq + q]};
+  int status = 0;
+  int pid = a.phase_id[q];
+  if (pid >= a.nphase) {
+    status |= 8;
+    pid = 0;
+  }
+  const PhaseDev ph = a.phase[pid];
+  const GlobDev gl = a.glob;
+
+  // kinematics
+  double F[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) F[r][c] = Hm[r][c] + (r == c ? 1.0 : 0.0);
+  const double trH = Hm[0][0] + Hm[1][1] + Hm[2][2];
+  double trHH = 0.0;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) trHH += Hm[r][c] * Hm[c][r];
+  const double detH = Hm[0][0] * (Hm[1][1] * Hm[2][2] - Hm[1][2] * Hm[2][1]) -
+                      Hm[0][1] * (Hm[1][0] * Hm[2][2] - Hm[1][2] * Hm[2][0]) +
+                      Hm[0][2] * (Hm[1][0] * Hm[2][1] - Hm[1][1] * Hm[2][0]);
+  const double Jm1 = trH + 0.5 * (trH * trH - trHH) + detH;
+  if (!(Jm1 > -1.0)) status |= 2;
+  const double theta = log1p(Jm1);
+  const double J = 1.0 + Jm1;
+  double Fi[3][3];
+  Fi[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) / J;
+  Fi[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) / J;
+  Fi[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) / J;
+  Fi[1][0] = (F[1][2] * F[2][0] - F[1][0] * F[2][2]) / J;
+  Fi[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) / J;
+  Fi[1][2] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) / J;
+  Fi[2][0] = (F[1][0] * F[2][1] - F[1][1] * F[2][0]) / J;
+  Fi[2][1] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) / J;
+  Fi[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) / J;
+  double GG[3][3];  // F F^T - I
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      double s = Hm[r][c] + Hm[c][r];
+      for (int k = 0; k < 3; ++k) s += Hm[r][k] * Hm[c][k];
+      GG[r][c] = s;
+    }
+
+  // degradation g = (1 - phi)^2 + eta (Eq. degr-funct)
+  const double omp = 1.0 - phi;
+  const double g = omp * omp + gl.eta;
+  const double gp = -2.0 * omp;
+
+  double taud[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double psid = 0.0;
+  double dtau[10][6];
+  double dpsi[10];
+  for (int d = 0; d < 10; ++d) {
+    dpsi[d] = 0.0;
+    for (int v = 0; v < 6; ++v) dtau[d][v] = 0.0;
+  }
+  uint8_t flag = 0;
+  double dgam = 0.0;
+  double hist_new[12];
+  for (int v = 0; v < 12; ++v) hist_new[v] = a.hist[v * nq + q];
+
+  for (int br = 0; br < 3; ++br) {
+    if (!ph.has[br]) continue;
+    const double mu = ph.mu[br];
+    double X[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) X[r][c] = GG[r][c];
+    if (br > 0) {
+      const int off = (br == 1) ? 0 : 6;
+      double M[3][3];
+      for (int v = 0; v < 6; ++v) {
+        int r, c;
+        vo_idx(v, r, c);
+        double m = a.hist[(off + v) * nq + q] - (v < 3 ? 1.0 : 0.0);
+        M[r][c] = m; M[c][r] = m;
+      }
+      double FM[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) FM[r][c] = F[r][0] * M[0][c] + F[r][1] * M[1][c] + F[r][2] * M[2][c];
+      for (int r = 0; r < 3; ++r)
+        for (int c = r; c < 3; ++c) {
+          double s = FM[r][0] * F[c][0] + FM[r][1] * F[c][1] + FM[r][2] * F[c][2];
+          X[r][c] += s;
+          if (c != r) X[c][r] += s;
+        }
+    }
+    double N[3][3], x[3];
+    if (!jacobi3(X, N, x)) status |= 1;
+    double eps[3], ed[3];
+    for (int p = 0; p < 3; ++p) eps[p] = 0.5 * log1p(x[p]);
+    const double tr = eps[0] + eps[1] + eps[2];
+    for (int p = 0; p < 3; ++p) ed[p] = eps[p] - tr / 3.0;
+    const double s2 = ed[0] * ed[0] + ed[1] * ed[1] + ed[2] * ed[2];
+    double af = 1.0, da_dphi = 0.0;
+    bool plastic = false;
+    if (br == 1) {
+      af = 1.0 / (1.0 + ph.cmax * g);
+      da_dphi = -af * af * ph.cmax * gp;
+    } else if (br == 2) {
+      const double qtr = 2.0 * mu * sqrt(1.5 * s2);
+      const double f = g * qtr - ph.sig0;
+      if (f > 0.0) {
+        af = ph.sig0 / (g * qtr);
+        da_dphi = -af * gp / g;
+        plastic = true;
+        flag |= 1;
+        dgam = f / (3.0 * g * mu);
+      }
+    }
+    double ti[3];
+    for (int p = 0; p < 3; ++p) ti[p] = 2.0 * mu * af * ed[p];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) taud[r][c] += N[r][0] * ti[0] * N[c][0] + N[r][1] * ti[1] * N[c][1] + N[r][2] * ti[2] * N[c][2];
+    psid += mu * af * af * s2;
+
+    if (br > 0) {  // trial history: C = F^-1 N diag(exp(2 eps_e)) N^T F^-T
+      double ee[3];
+      for (int p = 0; p < 3; ++p) ee[p] = exp(2.0 * (af * ed[p] + theta / 3.0));
+      double W[3][3];  // F^-1 N
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) W[r][c] = Fi[r][0] * N[0][c] + Fi[r][1] * N[1][c] + Fi[r][2] * N[2][c];
+      const int off = (br == 1) ? 0 : 6;
+      for (int v = 0; v < 6; ++v) {
+        int r, c;
+        vo_idx(v, r, c);
+        hist_new[off + v] = W[r][0] * ee[0] * W[c][0] + W[r][1] * ee[1] * W[c][1] + W[r][2] * ee[2] * W[c][2];
+      }
+    }
+
+    if (a.want_tangent) {
+      double V[3][3];  // F^-1 N : ell_hat for ell = e_a (x) F^-T e_B is N[a][p] V[B][q]
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) V[r][c] = Fi[r][0] * N[0][c] + Fi[r][1] * N[1][c] + Fi[r][2] * N[2][c];
+      const double rho01 = log_ratio(x[0], x[1]);
+      const double rho02 = log_ratio(x[0], x[2]);
+      const double rho12 = log_ratio(x[1], x[2]);
+      const double b[3] = {1.0 + x[0], 1.0 + x[1], 1.0 + x[2]};
+      for (int d = 0; d < 10; ++d) {
+        double lh[3][3];
+        double dphi = 0.0;
+        if (d < 9) {
+          const int aa = d / 3, BB = d % 3;
+          for (int p = 0; p < 3; ++p)
+            for (int r = 0; r < 3; ++r) lh[p][r] = N[aa][p] * V[BB][r];
+        } else {
+          for (int p = 0; p < 3; ++p)
+            for (int r = 0; r < 3; ++r) lh[p][r] = 0.0;
+          dphi = 1.0;
+        }
+        const double trl = lh[0][0] + lh[1][1] + lh[2][2];
+        double ded[3], edde = 0.0;
+        for (int p = 0; p < 3; ++p) {
+          ded[p] = lh[p][p] - trl / 3.0;
+          edde += ed[p] * lh[p][p];
+        }
+        double da = dphi * da_dphi;
+        if (plastic) da -= af * edde / s2;
+        double dh[3][3];
+        for (int p = 0; p < 3; ++p) dh[p][p] = 2.0 * mu * (af * ded[p] + da * ed[p]);
+        dh[0][1] = dh[1][0] = mu * af * rho01 * (lh[0][1] * b[1] + b[0] * lh[1][0]);
+        dh[0][2] = dh[2][0] = mu * af * rho02 * (lh[0][2] * b[2] + b[0] * lh[2][0]);
+        dh[1][2] = dh[2][1] = mu * af * rho12 * (lh[1][2] * b[2] + b[1] * lh[2][1]);
+        for (int v = 0; v < 6; ++v) {
+          int r, c;
+          vo_idx(v, r, c);
+          double s = 0.0;
+          for (int p = 0; p < 3; ++p)
+            for (int t = 0; t < 3; ++t) s += N[r][p] * dh[p][t] * N[c][t];
+          dtau[d][v] += s;
+        }
+        dpsi[d] += 2.0 * mu * af * af * edde + 2.0 * mu * af * s2 * da;
+      }
+    }
+  }
+
+  // volumetric part and the Amor split
+  const double tv = ph.kap_tot * theta;
+  const double psiv = 0.5 * ph.kap_tot * theta * theta;
+  const bool tens = theta >= 0.0;
+  double tdeg[3][3];
+  double psip;
+  if (tens) {
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) tdeg[r][c] = g * (taud[r][c] + (r == c ? tv : 0.0));
+    psip = psid + psiv;
+    flag |= 4;
+  } else {
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) tdeg[r][c] = g * taud[r][c] + (r == c ? tv : 0.0);
+    psip = psid;
+  }
+  const double Hn = a.hist[13 * nq + q];
+  const bool active = psip > Hn;
+  if (active) flag |= 2;
+  const double Hh = active ? psip : Hn;
+  const double alphap = (gl.at == 1) ? 1.0 : 2.0 * phi;
+  const double phin = a.hist[14 * nq + q];
+  const double L = gp * Hh + ph.gc_c0l0 * alphap + gl.zeta * (phi - phin) / gl.dt;
+
+  // residual integrands, parent frame with the weight folded in
+  double Pm[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int A = 0; A < 3; ++A) Pm[r][A] = tdeg[r][0] * Fi[A][0] + tdeg[r][1] * Fi[A][1] + tdeg[r][2] * Fi[A][2];
+  double outv[13];
+  for (int r = 0; r < 3; ++r)
+    for (int A = 0; A < 3; ++A) outv[3 * r + A] = wdet * sg[A] * Pm[r][A];
+  outv[9] = wdet * gl.s_phi * L;
+  for (int A = 0; A < 3; ++A) outv[10 + A] = wdet * sg[A] * ph.kphi * gphi[A];
+  for (int v = 0; v < 13; ++v) {
+    if (!isfinite(outv[v])) status |= 4;
+    a.io[v * nq + q] = outv[v];
+  }
+
+  // trial history and flags
+  for (int v = 0; v < 12; ++v) a.hist_trial[v * nq + q] = hist_new[v];
+  a.hist_trial[12 * nq + q] = a.hist[12 * nq + q] + dgam;
+  a.hist_trial[13 * nq + q] = Hh;
+  a.hist_trial[14 * nq + q] = phi;
+  a.flags[q] = flag;
+
+  if (a.want_tangent) {
+    const int EB = elems_per_block(Q);
+    const long long stride = (long long)Q3 * EB;
+    const long long blk = e / EB;
+    const int el = (int)(e % EB);
+    double* lin = a.lin + blk * (long long)kLinWords * stride + (long long)qk * Q2 * EB + el * Q2 + qj * Q + qi;
+    const double app = (gl.at == 1) ? 0.0 : 2.0;
+    const double cL = 2.0 * Hh + ph.gc_c0l0 * app + gl.zeta / gl.dt;
+    for (int d = 0; d < 10; ++d) {
+      const double dphi = (d == 9) ? 1.0 : 0.0;
+      const int aa = (d < 9) ? d / 3 : 0, BB = (d < 9) ? d % 3 : 0;
+      const double trl = (d < 9) ? Fi[BB][aa] : 0.0;
+      const double dtv = ph.kap_tot * trl;
+      double M[3][3];
+      double dpsip;
+      for (int v = 0; v < 6; ++v) {
+        int r, c;
+        vo_idx(v, r, c);
+        double val;
+        if (tens) val = g * dtau[d][v] + gp * dphi * taud[r][c] + (r == c ? g * dtv + gp * dphi * tv : 0.0);
+        else val = g * dtau[d][v] + gp * dphi * taud[r][c] + (r == c ? dtv : 0.0);
+        M[r][c] = val; M[c][r] = val;
+      }
+      dpsip = tens ? dpsi[d] + ph.kap_tot * theta * trl : dpsi[d];
+      if (d < 9) {  // geometric term: - tau_degr ell^T, (tau ell^T)_{i aa} = (tau F^-T e_BB)_i
+        for (int r = 0; r < 3; ++r) M[r][aa] -= tdeg[r][0] * Fi[BB][0] + tdeg[r][1] * Fi[BB][1] + tdeg[r][2] * Fi[BB][2];
+      }
+      double dP[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int A = 0; A < 3; ++A) dP[r][A] = M[r][0] * Fi[A][0] + M[r][1] * Fi[A][1] + M[r][2] * Fi[A][2];
+      const double dL = cL * dphi + gp * (active ? dpsip : 0.0);
+      if (d < 9) {
+        const int n = 3 * aa + BB;
+        for (int m = 0; m <= n; ++m) {
+          const int r = m / 3, A = m % 3;
+          lin[(long long)(kWA + sym9(m, n)) * stride] = wdet * sg[A] * sg[BB] * dP[r][A];
+        }
+        lin[(long long)(kWC + n) * stride] = wdet * sg[BB] * gl.s_phi * dL;
+      } else {
+        for (int m = 0; m < 9; ++m) lin[(long long)(kWP + m) * stride] = wdet * sg[m % 3] * dP[m / 3][m % 3];
+        lin[(long long)kWD * stride] = wdet * gl.s_phi * dL;
+      }
+    }
+    for (int A = 0; A < 3; ++A) lin[(long long)(kWK + A) * stride] = wdet * sg[A] * sg[A] * ph.kphi;
+  }
+  if (status) atomicOr(a.status, status);
+}
+
+cudaError_t launch_pointwise(const PointArgs& a, cudaStream_t st) {
+  if (a.nq == 0) return cudaSuccess;
+  long long nb = (a.nq + 127) / 128;
+  k_pointwise<<<(unsigned)nb, 128, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace pff

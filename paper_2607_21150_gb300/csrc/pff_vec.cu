@@ -1,0 +1,239 @@
+// Vector kernels: Dirichlet initialisation, precision conversion, the
+// p-multigrid transfer operators and the Chebyshev smoother updates.
+#include "pff_internal.h"
+
+namespace pff {
+
+constexpr int kVecThreads = 256;
+
+static unsigned grid_for(long long n) {
+  long long b = (n + kVecThreads - 1) / kVecThreads;
+  if (b > 152LL * 64) b = 152LL * 64;  // grid-stride beyond 64 blocks per SM
+  return (unsigned)(b > 0 ? b : 1);
+}
+
+// mode 0: y = mask ? x : 0      (Jacobian action: identity rows of Dirichlet DoFs)
+// mode 1: y = mask ? x - u : 0  (residual: z - ubar on Dirichlet DoFs)
+// mode 2: y = mask ? 1 : 0      (diagonal)
+template <typename T>
+__global__ void k_init_masked(T* __restrict__ y, const T* __restrict__ x, const double* __restrict__ ubar,
+                              const uint8_t* __restrict__ mask, long long n, int mode) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    bool m = mask && mask[i];
+    T v = T(0);
+    if (m) {
+      if (mode == 0) v = x[i];
+      else if (mode == 1) v = x[i] - (ubar ? (T)ubar[i] : T(0));
+      else v = T(1);
+    }
+    y[i] = v;
+  }
+}
+
+cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar, const uint8_t* mask,
+                               long long n, int mode, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  if (prec == 0)
+    k_init_masked<double><<<grid_for(n), kVecThreads, 0, st>>>((double*)y, (const double*)x, ubar, mask, n, mode);
+  else
+    k_init_masked<float><<<grid_for(n), kVecThreads, 0, st>>>((float*)y, (const float*)x, ubar, mask, n, mode);
+  return cudaGetLastError();
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+cudaError_t launch_to_f32(const double* a, float* b, long long n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_to_f32<<<grid_for(n), kVecThreads, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+// Prolongation x_f = P x_c, P[f, c] = coarse Lagrange basis at the fine GLL
+// node (I1[a][b], a fine, b coarse, per direction).  One thread per fine node;
+// the owning element is any element whose closure holds the node (the coarse
+// space is continuous, so every choice gives the same value).
+template <typename T>
+__global__ void k_prolong(MeshDev mc, MeshDev mf, const T* __restrict__ I1, const T* __restrict__ xc,
+                          T* __restrict__ xf, const uint8_t* __restrict__ maskc, const uint8_t* __restrict__ maskf) {
+  const int Pc = mc.p + 1, Pf = mf.p + 1;
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= mf.nn) return;
+  const int I = (int)(n % mf.nnx);
+  const int J = (int)((n / mf.nnx) % mf.nny);
+  const int K = (int)(n / ((long long)mf.nnx * mf.nny));
+  const int idx[3] = {I, J, K};
+  const int ne[3] = {mf.nx, mf.ny, mf.nz};
+  int el[3], loc[3];
+  for (int d = 0; d < 3; ++d) {
+    int e = idx[d] / mf.p;
+    if (e >= ne[d]) e = ne[d] - 1;
+    el[d] = e;
+    loc[d] = idx[d] - mf.p * e;
+  }
+  for (int f = 0; f < 4; ++f) {
+    long long gf = f * mf.nn + n;
+    if (maskf && maskf[gf]) { xf[gf] = T(0); continue; }
+    T s = T(0);
+    for (int c = 0; c < Pc; ++c) {
+      T wz = I1[loc[2] * Pc + c];
+      for (int b = 0; b < Pc; ++b) {
+        T wyz = wz * I1[loc[1] * Pc + b];
+        for (int a = 0; a < Pc; ++a) {
+          long long nc = (long long)(mc.p * el[0] + a) + (long long)mc.nnx * ((long long)(mc.p * el[1] + b) + (long long)mc.nny * (mc.p * el[2] + c));
+          long long gc = f * mc.nn + nc;
+          if (maskc && maskc[gc]) continue;
+          s += wyz * I1[loc[0] * Pc + a] * xc[gc];
+        }
+      }
+    }
+    xf[gf] = s;
+  }
+  (void)Pf;
+}
+
+template <typename T>
+cudaError_t launch_prolong(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* xc, T* xf,
+                           const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
+  if (mf.nn == 0) return cudaSuccess;
+  unsigned nb = (unsigned)((mf.nn + 255) / 256);
+  k_prolong<T><<<nb, 256, 0, st>>>(mc, mf, I1, xc, xf, maskc, maskf);
+  return cudaGetLastError();
+}
+
+// Restriction r_c = P^T r_f, element by element: every element adds
+// I1^T-weighted fine residuals divided by the fine node's multiplicity (the
+// number of elements sharing it), which sums to exactly P^T r_f.  One thread
+// per (element, coarse local node).
+template <typename T>
+__global__ void k_restrict(MeshDev mc, MeshDev mf, const T* __restrict__ I1, const T* __restrict__ rf,
+                           T* __restrict__ rc, const uint8_t* __restrict__ maskc, const uint8_t* __restrict__ maskf) {
+  const int Pc = mc.p + 1, Pf = mf.p + 1;
+  const int Pc3 = Pc * Pc * Pc;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= (long long)mc.nel * Pc3) return;
+  const int e = (int)(tid / Pc3);
+  const int lb = (int)(tid % Pc3);
+  const int b0 = lb % Pc, b1 = (lb / Pc) % Pc, b2 = lb / (Pc * Pc);
+  const int ex = e % mf.nx, ey = (e / mf.nx) % mf.ny, ez = e / (mf.nx * mf.ny);
+  const long long nc = (long long)(mc.p * ex + b0) + (long long)mc.nnx * ((long long)(mc.p * ey + b1) + (long long)mc.nny * (mc.p * ez + b2));
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (int c = 0; c < Pf; ++c) {
+    const int K = mf.p * ez + c;
+    const T mz = (c == 0 && ez > 0) || (c == mf.p && ez < mf.nz - 1) ? T(0.5) : T(1);
+    const T wz = I1[c * Pc + b2] * mz;
+    for (int b = 0; b < Pf; ++b) {
+      const int J = mf.p * ey + b;
+      const T my = (b == 0 && ey > 0) || (b == mf.p && ey < mf.ny - 1) ? T(0.5) : T(1);
+      const T wyz = wz * I1[b * Pc + b1] * my;
+      for (int a = 0; a < Pf; ++a) {
+        const int I = mf.p * ex + a;
+        const T mx = (a == 0 && ex > 0) || (a == mf.p && ex < mf.nx - 1) ? T(0.5) : T(1);
+        const T w = wyz * I1[a * Pc + b0] * mx;
+        const long long nf = I + (long long)mf.nnx * (J + (long long)mf.nny * K);
+        for (int f = 0; f < 4; ++f) {
+          long long gf = f * mf.nn + nf;
+          if (maskf && maskf[gf]) continue;
+          acc[f] += w * rf[gf];
+        }
+      }
+    }
+  }
+  for (int f = 0; f < 4; ++f) {
+    long long gc = f * mc.nn + nc;
+    if (maskc && maskc[gc]) continue;
+    atomicAdd(rc + gc, acc[f]);
+  }
+}
+
+template <typename T>
+cudaError_t launch_restrict(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* rf, T* rc,
+                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
+  long long n = (long long)mc.nel * (mc.p + 1) * (mc.p + 1) * (mc.p + 1);
+  cudaError_t err = cudaMemsetAsync(rc, 0, sizeof(T) * 4 * mc.nn, st);
+  if (err != cudaSuccess) return err;
+  if (n == 0) return cudaSuccess;
+  k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mc, mf, I1, rf, rc, maskc, maskf);
+  return cudaGetLastError();
+}
+
+// Chebyshev iteration (Saad, Alg. 12.1) on D^-1 A:
+//   init:  r = D^-1 (b - A x),  d = r / theta
+//   step:  x += d;  r -= D^-1 A d;  d = c_d d + c_r r      (c_d = rho_k+1 rho_k, c_r = 2 rho_k+1 / delta)
+//   last:  x += d
+template <typename T>
+__global__ void k_cheb_init(long long n, const T* __restrict__ b, const T* __restrict__ Ax, const T* __restrict__ diag,
+                            T* __restrict__ r, T* __restrict__ d, T inv_theta) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T ri = (b[i] - Ax[i]) / diag[i];
+    r[i] = ri;
+    d[i] = ri * inv_theta;
+  }
+}
+template <typename T>
+__global__ void k_cheb_step(long long n, T* __restrict__ x, T* __restrict__ d, T* __restrict__ r,
+                            const T* __restrict__ Ad, const T* __restrict__ diag, T c_d, T c_r, int last) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    T di = d[i];
+    x[i] += di;
+    if (!last) {
+      T ri = r[i] - Ad[i] / diag[i];
+      r[i] = ri;
+      d[i] = c_d * di + c_r * ri;
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_cheb_init(long long n, const T* b, const T* Ax, const T* diag, T* r, T* d, double inv_theta,
+                             cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_cheb_init<T><<<grid_for(n), kVecThreads, 0, st>>>(n, b, Ax, diag, r, d, (T)inv_theta);
+  return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_cheb_step(long long n, T* x, T* d, T* r, const T* Ad, const T* diag, double c_d, double c_r,
+                             int last, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_cheb_step<T><<<grid_for(n), kVecThreads, 0, st>>>(n, x, d, r, Ad, diag, (T)c_d, (T)c_r, last);
+  return cudaGetLastError();
+}
+
+
+// Stored linearisation from the tiled layout to the canonical order [67][N_q].
+__global__ void k_untile(const double* __restrict__ lin, double* __restrict__ out, long long nq, int Q) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int Q2 = Q * Q, Q3 = Q2 * Q, EB = elems_per_block(Q);
+  const long long e = q / Q3;
+  const int lq = (int)(q % Q3);
+  const int i = lq % Q, j = (lq / Q) % Q, k = lq / Q2;
+  const long long stride = (long long)Q3 * EB;
+  const long long base = (e / EB) * kLinWords * stride + (long long)k * Q2 * EB + (e % EB) * Q2 + j * Q + i;
+  for (int w = 0; w < kLinWords; ++w) out[w * nq + q] = lin[base + w * stride];
+}
+cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  k_untile<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(lin, out, nq, Q);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_prolong<double>(const MeshDev&, const MeshDev&, const double*, const double*, double*,
+                                            const uint8_t*, const uint8_t*, cudaStream_t);
+template cudaError_t launch_prolong<float>(const MeshDev&, const MeshDev&, const float*, const float*, float*,
+                                           const uint8_t*, const uint8_t*, cudaStream_t);
+template cudaError_t launch_restrict<double>(const MeshDev&, const MeshDev&, const double*, const double*, double*,
+                                             const uint8_t*, const uint8_t*, cudaStream_t);
+template cudaError_t launch_restrict<float>(const MeshDev&, const MeshDev&, const float*, const float*, float*,
+                                            const uint8_t*, const uint8_t*, cudaStream_t);
+template cudaError_t launch_cheb_init<double>(long long, const double*, const double*, const double*, double*, double*,
+                                              double, cudaStream_t);
+template cudaError_t launch_cheb_init<float>(long long, const float*, const float*, const float*, float*, float*,
+                                             double, cudaStream_t);
+template cudaError_t launch_cheb_step<double>(long long, double*, double*, double*, const double*, const double*,
+                                              double, double, int, cudaStream_t);
+template cudaError_t launch_cheb_step<float>(long long, float*, float*, float*, const float*, const float*, double,
+                                             double, int, cudaStream_t);
+
+}  // namespace pff

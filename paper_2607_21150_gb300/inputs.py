@@ -484,3 +484,48 @@ def compress_q4(n: int = 64, seed: int = 0) -> Workload:
     w.name = "compress_q4"
     w.meta.update(steps=30, strain_per_step=strain_per_step)
     return w
+
+
+def coarsen_mask(m: Mesh, mask: np.ndarray, pc: int) -> np.ndarray:
+    """Dirichlet mask of the order-pc level on the same element grid, for masks
+    that are constant on each boundary class (face, edge, corner, interior):
+    a coarse node is prescribed iff the fine nodes of its class are."""
+    mf = np.asarray(mask, dtype=np.uint8).reshape(4, m.nnz, m.nny, m.nnx)
+    sizes_f = (m.nnx, m.nny, m.nnz)
+    sizes_c = (pc * m.nx + 1, pc * m.ny + 1, pc * m.nz + 1)
+
+    def cls(n):
+        c = np.ones(n, dtype=np.int64)
+        c[0] = 0
+        c[-1] = 2
+        return c
+
+    out = np.zeros((4, sizes_c[2], sizes_c[1], sizes_c[0]), dtype=np.uint8)
+    cf = [cls(s) for s in sizes_f]
+    cc = [cls(s) for s in sizes_c]
+    for f in range(4):
+        table = np.zeros((3, 3, 3), dtype=np.uint8)
+        for kz in range(3):
+            for ky in range(3):
+                for kx in range(3):
+                    sel = mf[f][np.ix_(cf[2] == kz, cf[1] == ky, cf[0] == kx)]
+                    if sel.size:
+                        if sel.min() != sel.max():
+                            raise ValueError("mask is not constant on a boundary class")
+                        table[kz, ky, kx] = sel.flat[0]
+        out[f] = table[np.ix_(cc[2], cc[1], cc[0])]
+    return out.reshape(4, -1)
+
+
+def element_offsets(m: Mesh) -> np.ndarray:
+    """Explicit element -> node map int32 [nel][P^3] of the structured box (for
+    exercising the general restriction)."""
+    P = m.p + 1
+    e = np.arange(m.nel)
+    ex, ey, ez = e % m.nx, (e // m.nx) % m.ny, e // (m.nx * m.ny)
+    a = np.arange(P)
+    C, B, A = np.meshgrid(a, a, a, indexing="ij")
+    I = m.p * ex[:, None] + A.ravel()[None, :]
+    J = m.p * ey[:, None] + B.ravel()[None, :]
+    K = m.p * ez[:, None] + C.ravel()[None, :]
+    return (I + m.nnx * (J + m.nny * K)).astype(np.int32)

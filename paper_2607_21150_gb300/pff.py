@@ -1,0 +1,276 @@
+"""Thin ctypes binding of libpff (include/pff.h): same names, argument
+marshalling only.  Every computation runs in the CUDA library; if the library
+is missing this module raises instead of falling back to anything else.
+
+Pointer arguments accept torch tensors (their ``data_ptr()``), plain integers
+or ``None``; streams accept a ``torch.cuda.Stream``, an integer handle or
+``None`` (the current torch stream)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PFF_F64 = 0
+PFF_F32 = 1
+STATUS_EIGEN, STATUS_DETF, STATUS_NONFINITE = 1, 2, 4
+
+_lib = None
+
+
+class PffError(RuntimeError):
+    pass
+
+
+class pff_problem(ctypes.Structure):
+    _fields_ = [("nphase", ctypes.c_int), ("phase_params", ctypes.POINTER(ctypes.c_double)),
+                ("at", ctypes.c_int), ("eta", ctypes.c_double), ("zeta", ctypes.c_double),
+                ("dt", ctypes.c_double), ("s_phi", ctypes.c_double)]
+
+
+class pff_box(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double)]
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_I64 = ctypes.c_int64
+
+_SIGS = {
+    "pff_last_error_message": ([], ctypes.c_char_p),
+    "pff_version": ([], _I),
+    "pff_create_context": ([ctypes.POINTER(_VP), ctypes.POINTER(pff_problem)], _I),
+    "pff_destroy_context": ([_VP], _I),
+    "pff_create_basis": ([_VP, _I, _I, ctypes.POINTER(_VP)], _I),
+    "pff_basis_get": ([_VP, _VP, _VP, _VP, _VP, _VP], _I),
+    "pff_destroy_basis": ([_VP], _I),
+    "pff_create_restriction": ([_VP, ctypes.POINTER(pff_box), _I, _VP, _I64, ctypes.POINTER(_VP)], _I),
+    "pff_destroy_restriction": ([_VP], _I),
+    "pff_create_operator": ([_VP, _VP, _VP, ctypes.POINTER(_VP)], _I),
+    "pff_destroy_operator": ([_VP], _I),
+    "pff_op_enable_f32": ([_VP, _I], _I),
+    "pff_op_num_qpoints": ([_VP], _I64),
+    "pff_op_num_nodes": ([_VP], _I64),
+    "pff_set_qpoint_state": ([_VP, _VP, _VP, _VP], _I),
+    "pff_set_dirichlet": ([_VP, _VP, _VP, _VP], _I),
+    "pff_residual": ([_VP, _VP, _VP, _VP], _I),
+    "pff_create_level": ([_VP, _I, ctypes.POINTER(_VP)], _I),
+    "pff_destroy_level": ([_VP], _I),
+    "pff_level_num_nodes": ([_VP], _I64),
+    "pff_level_set_mask": ([_VP, _VP, _VP], _I),
+    "pff_jacobian_apply": ([_VP, _I, _VP, _VP, _VP], _I),
+    "pff_jacobian_transpose_apply": ([_VP, _I, _VP, _VP, _VP], _I),
+    "pff_assemble_diagonal": ([_VP, _I, _VP, _VP], _I),
+    "pff_prolong": ([_VP, _VP, _I, _VP, _VP, _VP], _I),
+    "pff_restrict": ([_VP, _VP, _I, _VP, _VP, _VP], _I),
+    "pff_chebyshev_smooth": ([_VP, _I, _I, _D, _D, _VP, _VP, _VP, _VP, _VP], _I),
+    "pff_commit_history": ([_VP, _VP], _I),
+    "pff_get_history": ([_VP, _I, _VP, _VP], _I),
+    "pff_get_flags": ([_VP, _VP, _VP], _I),
+    "pff_get_linearization": ([_VP, _VP, _VP], _I),
+    "pff_get_status": ([_VP, _VP, ctypes.POINTER(_I)], _I),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libpff.so (built in-tree by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise PffError(f"libpff.so is not built ({path}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, ctypes.c_void_p):
+        return x.value
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(rc, name):
+    if rc != 0:
+        msg = lib().pff_last_error_message()
+        raise PffError(f"{name} failed ({rc}): {msg.decode() if msg else ''}")
+
+
+def _call(name, *args):
+    rc = getattr(lib(), name)(*args)
+    _check(rc, name)
+
+
+# ---------------------------------------------------------------- handles
+def pff_create_context(phase_params, at, eta, zeta, dt, s_phi):
+    import numpy as np
+    pp = np.ascontiguousarray(phase_params, dtype=np.float64).reshape(-1, 12)
+    pr = pff_problem(len(pp), pp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(at), float(eta),
+                     float(zeta), float(dt), float(s_phi))
+    h = _VP()
+    _call("pff_create_context", ctypes.byref(h), ctypes.byref(pr))
+    return h
+
+
+def pff_destroy_context(ctx):
+    _call("pff_destroy_context", ctx)
+
+
+def pff_create_basis(ctx, p, q):
+    h = _VP()
+    _call("pff_create_basis", ctx, int(p), int(q), ctypes.byref(h))
+    return h
+
+
+def pff_basis_get(basis, p, q):
+    import numpy as np
+    P = p + 1
+    xg, xq, wq = np.zeros(P), np.zeros(q), np.zeros(q)
+    B, Dc = np.zeros((q, P)), np.zeros((q, q))
+    _call("pff_basis_get", basis, xg.ctypes.data, xq.ctypes.data, wq.ctypes.data, B.ctypes.data, Dc.ctypes.data)
+    return xg, xq, wq, B, Dc
+
+
+def pff_destroy_basis(basis):
+    _call("pff_destroy_basis", basis)
+
+
+def pff_create_restriction(ctx, box, p, offsets, nnodes):
+    """box = (nx, ny, nz, hx, hy, hz)."""
+    b = pff_box(int(box[0]), int(box[1]), int(box[2]), float(box[3]), float(box[4]), float(box[5]))
+    h = _VP()
+    _call("pff_create_restriction", ctx, ctypes.byref(b), int(p), _ptr(offsets), int(nnodes), ctypes.byref(h))
+    return h
+
+
+def pff_destroy_restriction(r):
+    _call("pff_destroy_restriction", r)
+
+
+def pff_create_operator(ctx, basis, restr):
+    h = _VP()
+    _call("pff_create_operator", ctx, basis, restr, ctypes.byref(h))
+    return h
+
+
+def pff_destroy_operator(op):
+    _call("pff_destroy_operator", op)
+
+
+def pff_op_enable_f32(op, enable=True):
+    _call("pff_op_enable_f32", op, 1 if enable else 0)
+
+
+def pff_op_num_qpoints(op):
+    return int(lib().pff_op_num_qpoints(op))
+
+
+def pff_op_num_nodes(op):
+    return int(lib().pff_op_num_nodes(op))
+
+
+def pff_set_qpoint_state(op, phase, hist, stream=None):
+    _call("pff_set_qpoint_state", op, _ptr(phase), _ptr(hist), _stream(stream))
+
+
+def pff_set_dirichlet(op, mask, values, stream=None):
+    _call("pff_set_dirichlet", op, _ptr(mask), _ptr(values), _stream(stream))
+
+
+def pff_residual(op, z, r, stream=None):
+    _call("pff_residual", op, _ptr(z), _ptr(r), _stream(stream))
+
+
+def pff_create_level(op, p):
+    h = _VP()
+    _call("pff_create_level", op, int(p), ctypes.byref(h))
+    return h
+
+
+def pff_destroy_level(level):
+    _call("pff_destroy_level", level)
+
+
+def pff_level_num_nodes(level):
+    return int(lib().pff_level_num_nodes(level))
+
+
+def pff_level_set_mask(level, mask, stream=None):
+    _call("pff_level_set_mask", level, _ptr(mask), _stream(stream))
+
+
+def pff_jacobian_apply(level, prec, x, y, stream=None):
+    _call("pff_jacobian_apply", level, int(prec), _ptr(x), _ptr(y), _stream(stream))
+
+
+def pff_jacobian_transpose_apply(level, prec, x, y, stream=None):
+    _call("pff_jacobian_transpose_apply", level, int(prec), _ptr(x), _ptr(y), _stream(stream))
+
+
+def pff_assemble_diagonal(level, prec, diag, stream=None):
+    _call("pff_assemble_diagonal", level, int(prec), _ptr(diag), _stream(stream))
+
+
+def pff_prolong(coarse, fine, prec, xc, xf, stream=None):
+    _call("pff_prolong", coarse, fine, int(prec), _ptr(xc), _ptr(xf), _stream(stream))
+
+
+def pff_restrict(coarse, fine, prec, rf, rc, stream=None):
+    _call("pff_restrict", coarse, fine, int(prec), _ptr(rf), _ptr(rc), _stream(stream))
+
+
+def pff_chebyshev_smooth(level, prec, degree, lmin, lmax, diag, b, x, work, stream=None):
+    _call("pff_chebyshev_smooth", level, int(prec), int(degree), float(lmin), float(lmax), _ptr(diag), _ptr(b),
+          _ptr(x), _ptr(work), _stream(stream))
+
+
+def pff_commit_history(op, stream=None):
+    _call("pff_commit_history", op, _stream(stream))
+
+
+def pff_get_history(op, which, hist, stream=None):
+    _call("pff_get_history", op, int(which), _ptr(hist), _stream(stream))
+
+
+def pff_get_flags(op, flags, stream=None):
+    _call("pff_get_flags", op, _ptr(flags), _stream(stream))
+
+
+def pff_get_linearization(op, out, stream=None):
+    _call("pff_get_linearization", op, _ptr(out), _stream(stream))
+
+
+def pff_get_status(op, stream=None):
+    st = _I()
+    _call("pff_get_status", op, _stream(stream), ctypes.byref(st))
+    return int(st.value)

@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every entry point include/pff.h declares;
+host-only calls (argument checks, basis tables) work without a GPU."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpff():
+    from paper_2607_21150_gb300 import build, pff
+    build.build()
+    return pff.lib()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "pff.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pff_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_symbols_exported(libpff):
+    from paper_2607_21150_gb300 import build, pff
+    names = header_functions()
+    assert len(names) >= 30
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (pff_[a-z0-9_]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert sorted(pff.declared_symbols()) == names  # the binding covers the header exactly
+
+
+def test_argument_errors_without_gpu(libpff):
+    from paper_2607_21150_gb300 import inputs, pff
+    with pytest.raises(pff.PffError, match="nphase"):
+        pff.pff_create_context(np.zeros((0, 12)), 2, 1e-3, 1e-2, 0.01, 1.0)
+    with pytest.raises(pff.PffError, match="at must be"):
+        pff.pff_create_context(inputs.phase_vector(inputs.EX3_MATRIX)[None], 3, 1e-3, 1e-2, 0.01, 1.0)
+    ctx = pff.pff_create_context(inputs.phase_vector(inputs.EX3_MATRIX)[None], 2, 1e-3, 1e-2, 0.01, 1.0)
+    with pytest.raises(pff.PffError, match="p \\+ 1 <= q"):
+        pff.pff_create_basis(ctx, 4, 4)
+    with pytest.raises(pff.PffError, match="nnodes"):
+        pff.pff_create_restriction(ctx, (2, 2, 2, 0.1, 0.1, 0.1), 2, None, 7)
+    pff.pff_destroy_context(ctx)
+
+
+@pytest.mark.parametrize("p,q", [(1, 2), (2, 3), (3, 4), (4, 5), (2, 5), (1, 5)])
+def test_library_basis_tables_match_oracle(libpff, orc, p, q):
+    from paper_2607_21150_gb300 import inputs, pff
+    ctx = pff.pff_create_context(inputs.phase_vector(inputs.EX3_MATRIX)[None], 2, 1e-3, 1e-2, 0.01, 1.0)
+    b = pff.pff_create_basis(ctx, p, q)
+    xg, xq, wq, B, Dc = pff.pff_basis_get(b, p, q)
+    oxg, oxq, owq, oB, oD = orc.basis(p, q)
+    assert np.abs(xg - oxg).max() < 1e-15
+    assert np.abs(xq - oxq).max() < 1e-15 and np.abs(wq - owq).max() < 1e-15
+    assert np.abs(B - oB).max() < 1e-14
+    assert np.abs(Dc @ B - oD).max() < 1e-12
+    pff.pff_destroy_basis(b)
+    pff.pff_destroy_context(ctx)

@@ -1,0 +1,260 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerance (FP64): relative L2 error <= 1e-12 for the residual, the Jacobian
+action and its transpose, the diagonal, the transfers and the Chebyshev
+smoother; flags bit-exact at every point whose decision margin exceeds 1e-10
+(relative); trial history <= 1e-12 relative.  FP32 level applies are compared
+with the FP64 ones at the FP32 rounding level (<= 2e-5 relative L2).
+"""
+import numpy as np
+import pytest
+
+from paper_2607_21150_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2607_21150_gb300.session import Session  # noqa: E402
+from paper_2607_21150_gb300 import pff  # noqa: E402
+
+TOL = 1e-12
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def _flags_agree(gpu_flags, ref, margins, eps=1e-10):
+    safe = (np.abs(margins[:, 0]) > eps) & (np.abs(margins[:, 1]) > eps) & (np.abs(margins[:, 2]) > eps)
+    assert safe.mean() > 0.99
+    assert np.array_equal(gpu_flags[safe], ref[safe])
+
+
+def _two_phase(nx, ny, nz, p, seed, mask=True, at=2):
+    """Small two-phase box with random state and history, tension Dirichlet data."""
+    m = inputs.Mesh(nx, ny, nz, p, p + 1, (0.01 * nx, 0.01 * ny, 0.01 * nz))
+    rng = np.random.default_rng(seed)
+    phases = np.stack([inputs.phase_vector(inputs.EX3_MATRIX), inputs.phase_vector(inputs.EX3_PARTICLE)])
+    glob = inputs.glob_vector(at, 1e-3, 1e-2, 0.005, inputs.s_phi_of(inputs.EX3_MATRIX, at))
+    phase = (rng.random(m.nq) < 0.4).astype(np.uint8)
+    z = inputs.random_state(m, seed, u_amp=2e-4, phi_max=0.6)
+    hist = inputs.random_history(m.nq, seed + 1, H_max=3000.0)
+    mk = dv = None
+    if mask:
+        mk, dv = inputs.dirichlet_tension(m, 1e-4)
+        z[mk.astype(bool)] = dv[mk.astype(bool)] + rng.uniform(-1e-5, 1e-5, mk.sum())
+    return inputs.Workload("box", m, phases, glob, phase, z, hist, mk, dv)
+
+
+CASES = {
+    "cube_q2": lambda: inputs.cube(),
+    "cube_b_q2": lambda: inputs.cube(hist_seed=2, H_max=80.0),
+    "box_q4_ragged": lambda: _two_phase(3, 2, 2, 4, 5),      # 12 elements: 2 blocks of 10, ragged
+    "box_q3_ragged": lambda: _two_phase(3, 3, 2, 3, 7, at=1),  # 18 elements: blocks of 16
+    "box_q1": lambda: _two_phase(5, 4, 4, 1, 9),              # 80 elements: blocks of 64
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request, orc):
+    w = CASES[request.param]()
+    ref = orc.assemble(w)
+    s = Session(w)
+    r = s.residual(w.z)
+    torch.cuda.synchronize()
+    return request.param, w, ref, s, r
+
+
+def test_residual(case):
+    name, w, ref, s, r = case
+    assert s.status() == 0
+    assert rel(np_(r), ref["r"]) <= TOL, name
+
+
+def test_flags_and_trial_history(case):
+    name, w, ref, s, r = case
+    _flags_agree(np_(s.flags()), ref["flags"], ref["margins"])
+    h = np_(s.history(1))
+    assert rel(h, ref["hist_new"]) <= TOL, name
+    s.commit()
+    assert rel(np_(s.history(0)), ref["hist_new"]) <= TOL
+
+
+def test_jacobian_apply(case):
+    name, w, ref, s, r = case
+    v = inputs.random_vector(w.mesh.ndof, 1)
+    x = torch.from_numpy(v).cuda()
+    y = s.apply(x)
+    assert rel(np_(y), ref["K"] @ v) <= TOL, name
+    yt = s.apply(x, transpose=True)
+    assert rel(np_(yt), ref["K"].T @ v) <= TOL, name
+
+
+def test_diagonal(case):
+    name, w, ref, s, r = case
+    d = s.diag()
+    assert rel(np_(d), ref["K"].diagonal()) <= TOL, name
+
+
+def test_offsets_restriction_matches_structured(orc):
+    w = _two_phase(3, 2, 2, 4, 11)
+    a = Session(w)
+    b = Session(w, offsets=True)
+    ra, rb = a.residual(w.z), b.residual(w.z)
+    v = torch.from_numpy(inputs.random_vector(w.mesh.ndof, 3)).cuda()
+    assert rel(np_(rb), np_(ra)) <= 1e-14
+    assert rel(np_(b.apply(v)), np_(a.apply(v))) <= 1e-14
+
+
+def test_fp32_apply_close_to_fp64(orc):
+    w = _two_phase(3, 2, 2, 4, 13)
+    s = Session(w, f32=True)
+    s.residual(w.z)
+    v = inputs.random_vector(w.mesh.ndof, 4)
+    y64 = np_(s.apply(torch.from_numpy(v).cuda()))
+    y32 = np_(s.apply(torch.from_numpy(v.astype(np.float32)).cuda(), prec=pff.PFF_F32))
+    assert rel(y32, y64) <= 2e-5
+
+
+@pytest.mark.parametrize("pf,levels", [(4, (2, 1)), (2, (1,)), (3, (1,))])
+def test_multigrid_levels(orc, pf, levels):
+    """Level operator = P^T K_f P (R9); transfers = oracle P with Dirichlet rows/cols
+    removed; level diagonal = diag(P^T K_f P)."""
+    w = _two_phase(2, 3, 2, pf, 17 + pf)
+    ref = orc.assemble(w)
+    s = Session(w, levels=levels)
+    s.residual(w.z)
+    Kf = ref["K"]
+    for pc in levels:
+        P = orc.prolongation(w.mesh, pc)
+        mc = inputs.coarsen_mask(w.mesh, w.mask, pc)
+        Pm = orc.masked_prolongation(P, w.mask, mc)
+        Kc = orc.coarse_operator(Kf, Pm, mc)
+        nc = Pm.shape[1]
+        xc = inputs.random_vector(nc, 21)
+        yc = np_(s.apply(torch.from_numpy(xc).cuda(), p=pc))
+        assert rel(yc, Kc @ xc) <= TOL, pc
+        ytc = np_(s.apply(torch.from_numpy(xc).cuda(), p=pc, transpose=True))
+        assert rel(ytc, Kc.T @ xc) <= TOL, pc
+        assert rel(np_(s.diag(pc)), Kc.diagonal()) <= TOL, pc
+        # transfers to the finest level
+        xf = np_(s.prolong(torch.from_numpy(xc).cuda(), pc, pf))
+        assert rel(xf, Pm @ xc) <= 1e-14
+        rf = inputs.random_vector(Pm.shape[0], 22)
+        rc = np_(s.restrict(torch.from_numpy(rf).cuda(), pc, pf))
+        assert rel(rc, Pm.T @ rf) <= 1e-14
+    if len(levels) == 2:  # level-to-level transfer 2 -> 1
+        P21 = orc.prolongation(inputs.Mesh(2, 3, 2, 2, pf + 1, w.mesh.L), 1, 2)
+        m2 = inputs.coarsen_mask(w.mesh, w.mask, 2)
+        m1 = inputs.coarsen_mask(w.mesh, w.mask, 1)
+        P21m = orc.masked_prolongation(P21, m2, m1)
+        x1 = inputs.random_vector(P21m.shape[1], 23)
+        x2 = np_(s.prolong(torch.from_numpy(x1).cuda(), 1, 2))
+        assert rel(x2, P21m @ x1) <= 1e-14
+
+
+def test_chebyshev_smoother(orc):
+    w = _two_phase(3, 2, 2, 4, 31)
+    ref = orc.assemble(w)
+    s = Session(w)
+    s.residual(w.z)
+    K = ref["K"]
+    dg = K.diagonal()
+    b = inputs.random_vector(w.mesh.ndof, 5)
+    x0 = inputs.random_vector(w.mesh.ndof, 6) * 1e-3
+    for degree in (1, 3, 4):
+        xr = orc.chebyshev(K, dg, b, x0, degree, 0.1, 1.9)
+        x = torch.from_numpy(x0.copy()).cuda()
+        s.chebyshev(torch.from_numpy(b).cuda(), x, s.diag(), degree, 0.1, 1.9)
+        assert rel(np_(x), xr) <= TOL, degree
+
+
+def test_linearization_vs_oracle_tangent(orc):
+    """Stored 67 words = the oracle's dual-number tangent scaled by w detJ and the
+    parent factors (a direct check of Appendix B/C on the GPU)."""
+    w = inputs.cube(nx=2, hist_seed=2, H_max=80.0)
+    s = Session(w)
+    s.residual(w.z)
+    lin = np_(s.linearization())
+    # oracle pointwise inputs at the Gauss points of the GPU's own interpolation
+    m = w.mesh
+    xg, xq, wq, B, D = orc.basis(m.p, m.Q)
+    P = m.p + 1
+    h = np.array(m.h)
+    sc = 2.0 / h
+    detJ = np.prod(h) / 8
+    nodes = inputs.element_offsets(m)
+    inp = np.zeros((m.nq, 13))
+    wdet = np.zeros(m.nq)
+    for e in range(m.nel):
+        ze = w.z[:, nodes[e]].reshape(4, P, P, P)  # [f][c][b][a]
+        for k in range(m.Q):
+            for j in range(m.Q):
+                for i in range(m.Q):
+                    q = e * m.Q ** 3 + i + m.Q * (j + m.Q * k)
+                    Bi, Bj, Bk = B[i], B[j], B[k]
+                    Di, Dj, Dk = D[i], D[j], D[k]
+                    for f in range(4):
+                        zf = ze[f]
+                        gx = np.einsum("c,b,a,cba->", Bk, Bj, Di, zf) * sc[0]
+                        gy = np.einsum("c,b,a,cba->", Bk, Dj, Bi, zf) * sc[1]
+                        gz = np.einsum("c,b,a,cba->", Dk, Bj, Bi, zf) * sc[2]
+                        if f < 3:
+                            inp[q, 3 * f:3 * f + 3] = gx, gy, gz
+                        else:
+                            inp[q, 10:13] = gx, gy, gz
+                            inp[q, 9] = np.einsum("c,b,a,cba->", Bk, Bj, Bi, zf)
+                    wdet[q] = wq[i] * wq[j] * wq[k] * detJ
+    out = orc.pointwise(inp, w.hist.T.copy(), w.phase, w.phases, w.glob)
+    Dh = out["D"]
+    # rebuild the 67 words from the oracle tangent
+    ref = np.zeros((67, m.nq))
+    k = 0
+    for mm in range(9):
+        for nn in range(mm, 9):
+            ref[k] = wdet * sc[mm % 3] * sc[nn % 3] * Dh[:, 4 + mm, 4 + nn]
+            k += 1
+    for mm in range(9):
+        ref[45 + mm] = wdet * sc[mm % 3] * Dh[:, 4 + mm, 3]
+        ref[54 + mm] = wdet * sc[mm % 3] * Dh[:, 3, 4 + mm]
+    ref[63] = wdet * Dh[:, 3, 3]
+    for a in range(3):
+        ref[64 + a] = wdet * sc[a] ** 2 * Dh[:, 13 + a, 13 + a]
+    for blk, sl in (("A", slice(0, 45)), ("P", slice(45, 54)), ("C", slice(54, 63)), ("D", slice(63, 64)),
+                    ("K", slice(64, 67))):
+        assert rel(lin[sl], ref[sl]) <= 1e-11, blk
+
+
+def test_full_size_tension_q4_sampled_rows(orc):
+    """16^3 Q4 two-phase tension workload (1.1 M DoF) at full size: residual,
+    J x, J^T x and diag(J) at sampled rows against the oracle's element rows."""
+    w = inputs.tension_q4()
+    rng = np.random.default_rng(3)
+    w.z = w.z + 0.0
+    w.z[:3] += rng.uniform(-2e-4, 2e-4, (3, w.mesh.nn))
+    w.z[3] = rng.uniform(0, 0.4, w.mesh.nn)
+    mk = w.mask.astype(bool)
+    w.z[mk] = w.dvals[mk]
+    w.hist = inputs.random_history(w.mesh.nq, 4, H_max=400.0)
+    w.hist[13] = np.maximum(w.hist[13], inputs.zero_history(1)[13, 0])
+    s = Session(w)
+    r = np_(s.residual(w.z))
+    x = inputs.random_vector(w.mesh.ndof, 8)
+    xt = torch.from_numpy(x).cuda()
+    jx, jtx, dg = np_(s.apply(xt)), np_(s.apply(xt, transpose=True)), np_(s.diag())
+    dofs = np.sort(rng.choice(w.mesh.ndof, 48, replace=False))
+    dofs = np.concatenate([dofs, [0, w.mesh.ndof - 1, 3 * w.mesh.nn + w.mesh.nn // 2]])
+    ref = orc.sample_rows(w, dofs, x)
+    for key, g in (("r", r), ("jx", jx), ("jtx", jtx), ("diag", dg)):
+        err = np.abs(g[dofs] - ref[key]) / np.maximum(np.abs(ref[key]), 1e-300)
+        scale = np.abs(ref[key]).max()
+        assert np.all(np.abs(g[dofs] - ref[key]) <= 1e-11 * scale + 1e-12 * np.abs(ref[key])), (key, err.max())
