@@ -1,0 +1,344 @@
+"""Benchmark of the matrix-free phase-field fracture operator on GB300.
+
+Default workload: the Q4 compression microstructure (64^3 elements, 67.9 M
+DoF, particle volume fraction 0.7, lognormal radii mean 0.04 / sd 0.015,
+frictionless platens, Example 2 parameters, AT2), synthetic seeded state.
+One timed step = one FP64 Jacobian action y = J x over the whole mesh (the
+hottest call of the Newton-Krylov solve), inputs resident in HBM; the FP32
+level action (p-multigrid smoother precision) and the residual are timed
+beside it.  value = whole-job FP64 apply throughput in GDoF/s.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config compress_q4|tension_q4]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Q4 Jacobian-apply GDoF/s & %HBM roofline; Newton step time FP64 vs mixed p-MG"
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x max SM clock
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def make_workload(name: str, seed: int = 0):
+    from paper_2607_21150_gb300 import inputs
+    w = getattr(inputs, name)()
+    rng = np.random.default_rng(seed + 100)
+    m = w.mesh
+    h = min(m.h) / m.p
+    w.z = np.zeros((4, m.nn))
+    w.z[:3] = rng.uniform(-1e-3 * h, 1e-3 * h, (3, m.nn))
+    w.z[3] = rng.uniform(0.0, 0.3, m.nn)
+    mk = w.mask.astype(bool)
+    w.z[mk] = w.dvals[mk]
+    w.hist[13] = np.maximum(w.hist[13], rng.uniform(0.0, 2e-3, m.nq))
+    return w
+
+
+def apply_counts(P: int, Q: int):
+    """Algorithmic FP64/FP32 flops of one element of the fused Jacobian action:
+    per field 2 (P^3 Q + P^2 Q^2 + P Q^3) + 6 Q^4 MACs of sum-factorised basis work
+    (collocated gradient), plus 103 MACs of the stored-tangent map per point."""
+    basis = 4 * (2 * (P ** 3 * Q + P ** 2 * Q ** 2 + P * Q ** 3) + 6 * Q ** 4)
+    point = 103 * Q ** 3
+    return 2 * (basis + point)
+
+
+class ClockSampler:
+    def __init__(self, period_ms=200):
+        self.samples = []
+        self.proc = None
+        self.period = period_ms
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", str(self.period)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 8 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 8 and s[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            if len(s) > 8:
+                for k, nm in enumerate(names):
+                    if s[5 + k].lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# --------------------------------------------------------------------------- CPU oracle
+def oracle_sample(seconds_budget: float = 20.0):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of the
+    Q4 workload: a 4x4x4-element sub-box of the same material/state recipe.
+    Times the CSR assembly (element matrices by full quadrature) once and the
+    CSR SpMV (the oracle's Jacobian action) repeatedly."""
+    import oracle
+    from paper_2607_21150_gb300 import inputs
+    oracle.build()
+    n = 4
+    w = inputs.compress_q4(n=n)
+    rng = np.random.default_rng(7)
+    m = w.mesh
+    h = min(m.h) / m.p
+    w.z = np.zeros((4, m.nn))
+    w.z[:3] = rng.uniform(-1e-3 * h, 1e-3 * h, (3, m.nn))
+    w.z[3] = rng.uniform(0.0, 0.3, m.nn)
+    mk = w.mask.astype(bool)
+    w.z[mk] = w.dvals[mk]
+    t0 = time.perf_counter()
+    out = oracle.assemble(w)
+    t_asm = time.perf_counter() - t0
+    K = out["K"]
+    x = inputs.random_vector(m.ndof, 1)
+    y_ref = K @ x
+    assert np.linalg.norm(oracle.spmv(K, x) - y_ref) <= 1e-12 * np.linalg.norm(y_ref)
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.spmv(K, x)
+        reps += 1
+        if time.perf_counter() - t0 > min(5.0, seconds_budget):
+            break
+    t_spmv = (time.perf_counter() - t0) / reps
+    return dict(ndof=m.ndof, nel=m.nel, t_assemble=t_asm, t_spmv=t_spmv, threads=oracle.num_threads(),
+                gdofs=m.ndof / t_spmv / 1e9, gdofs_incl_assembly=m.ndof / (t_spmv + t_asm) / 1e9)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2607_21150_gb300 import inputs
+    oracle.build()
+    w = inputs.compress_q4(n=4)
+    m = w.mesh
+    rng = np.random.default_rng(7)
+    h = min(m.h) / m.p
+    w.z = np.zeros((4, m.nn))
+    w.z[:3] = rng.uniform(-1e-3 * h, 1e-3 * h, (3, m.nn))
+    w.z[3] = rng.uniform(0.0, 0.3, m.nn)
+    x = inputs.random_vector(m.ndof, 1)
+    K = oracle.assemble(w)["K"]
+    for _ in range(args.warmup):
+        oracle.spmv(K, x)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spmv(K, x)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = m.ndof / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "compress_q4 sub-box 4x4x4 Q4 elements (oracle CSR SpMV)", "ndof": m.ndof},
+            "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "4x4x4-element Q4 sub-box of the compression workload; CSR SpMV of the "
+                                       "oracle's assembled Jacobian"},
+            "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2607_21150_gb300 import pff
+    from paper_2607_21150_gb300.session import Session
+
+    w = make_workload(args.config, seed=rank)
+    m = w.mesh
+    s = Session(w, f32=True)
+    stream = torch.cuda.current_stream()
+    z = torch.from_numpy(w.z.ravel()).cuda()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    # residual (stores the linearisation used by every action), timed separately
+    s.residual(z)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    r = s.residual(z)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    t_res = t0.elapsed_time(t1)
+    status = s.status()
+    ndof = m.ndof
+    L = s.levels[m.p]
+    x64 = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, ndof)).cuda()
+    y64 = torch.empty_like(x64)
+    x32 = x64.float()
+    y32 = torch.empty_like(x32)
+
+    def apply64():
+        pff.pff_jacobian_apply(L, pff.PFF_F64, x64, y64, stream)
+
+    def apply32():
+        pff.pff_jacobian_apply(L, pff.PFF_F32, x32, y32, stream)
+
+    def timed(fn, K, W):
+        for _ in range(W):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - wall0
+        per = [a.elapsed_time(b) for a, b in evs]
+        return sum(per), per, wall
+
+    with ClockSampler() as clk:
+        tot64, per64, wall64 = timed(apply64, args.steps, args.warmup)
+    tot32, per32, _ = timed(apply32, args.steps, args.warmup)
+    # dominant kernel alone (the fused element kernel, without the y-init kernel)
+    y64.zero_()
+    ker = []
+    for _ in range(max(3, args.steps)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        apply64()
+        b.record(stream)
+        ker.append((a, b))
+    torch.cuda.synchronize()
+
+    # end to end through the C ABI with host buffers: pinned x -> device, apply, y -> pinned host
+    xh = x64.cpu().pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x64)
+    yd = torch.empty_like(x64)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        pff.pff_jacobian_apply(L, pff.PFF_F64, xd, yd, stream)
+        yh.copy_(yd, non_blocking=True)
+
+    tot_e2e, _, _ = timed(e2e_step, args.steps, 1)
+
+    # max over ranks
+    tmax = torch.tensor([tot64], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tot64 = float(tmax.item())
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    P, Q = m.p + 1, m.Q
+    flops_el = apply_counts(P, Q)
+    t_apply = tot64 / args.steps / 1e3
+    value = world * ndof * args.steps / (tot64 / 1e3) / 1e9
+    achieved_flops = flops_el * m.nel / t_apply / 1e12
+    hbm_peak, src = peaks()
+    bytes64 = 8 * ndof * 2 + ndof + 67 * 8 * m.nq
+    bytes32 = 4 * ndof * 2 + ndof + 67 * 4 * m.nq
+    t32 = tot32 / args.steps / 1e3
+    cpu = oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot64 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.config}: Q{m.p} {m.nx}x{m.ny}x{m.nz} elements, {ndof} DoF, "
+                               f"{m.nq} quadrature points", "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (stored linearisation %.1f GB)" % (67 * 8 * m.nq / 1e9),
+                   "microstructure": w.meta},
+        "roofline": {"bound": "alu", "achieved": achieved_flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved_flops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (unit count measured by an FMA-chain probe)",
+                     "hbm_frac": bytes64 / t_apply / 1e9 / hbm_peak, "hbm_peak_gbs": hbm_peak,
+                     "hbm_peak_source": src},
+        "fp32_level_apply": {"gdofs": ndof / t32 / 1e9, "ms": t32 * 1e3,
+                             "achieved_gbs": bytes32 / t32 / 1e9, "hbm_frac": bytes32 / t32 / 1e9 / hbm_peak,
+                             "bound": "hbm", "peak_gbs": hbm_peak, "peak_source": src},
+        "residual_ms": t_res, "kernel_status": status,
+        "e2e": {"value": world * ndof * args.steps / (tot_e2e / 1e3) / 1e9, "unit": "GDoF/s",
+                "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
+        "gpu_launches": 2 * args.steps,
+        "cpu_baseline": {"value": cpu["gdofs"], "unit": "GDoF/s", "cores": cpu["threads"], "kind": "oracle",
+                         "sample": f"{cpu['nel']}-element Q4 sub-box ({cpu['ndof']} DoF) of the same workload; "
+                                   f"CSR SpMV of the oracle's assembled Jacobian "
+                                   f"(assembly {cpu['t_assemble']:.2f} s not included)"},
+        "clocks": clk.summary(),
+        "wall_s_timed": wall64,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--config", default="compress_q4", choices=["compress_q4", "tension_q4"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -72,6 +72,7 @@ def lib():
         L.orc_prolong_coo.argtypes = [ip, ctypes.c_int, ctypes.c_int, llp, llp, dp]
         L.orc_prolong_coo.restype = ctypes.c_longlong
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_csr_spmv.argtypes = [ctypes.c_longlong, llp, llp, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -92,6 +93,18 @@ def _u8(a):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def spmv(K, x):
+    """y = K x with the oracle's OpenMP CSR loop (K from ``assemble``)."""
+    indptr = np.ascontiguousarray(K.indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(K.indices, dtype=np.int64)
+    data = _f64(K.data)
+    x = _f64(x)
+    y = np.zeros(K.shape[0])
+    lib().orc_csr_spmv(K.shape[0], _p(indptr, ctypes.c_longlong), _p(indices, ctypes.c_longlong), _p(data),
+                       _p(x), _p(y))
+    return y
 
 
 # ---------------------------------------------------------------------------

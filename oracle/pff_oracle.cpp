@@ -989,6 +989,19 @@ long long orc_prolong_coo(const int* dims, int pc, int pf, long long* rows, long
   return cnt;
 }
 
+// y = A x for a CSR matrix (plain row loop, OpenMP over rows): the oracle's
+// Jacobian action once the Jacobian is assembled.
+int orc_csr_spmv(long long nrows, const long long* indptr, const long long* indices, const double* data,
+                 const double* x, double* y) {
+#pragma omp parallel for schedule(static)
+  for (long long i = 0; i < nrows; ++i) {
+    double s = 0.0;
+    for (long long k = indptr[i]; k < indptr[i + 1]; ++k) s += data[k] * x[indices[k]];
+    y[i] = s;
+  }
+  return 0;
+}
+
 int orc_num_threads() {
 #ifdef _OPENMP
   return omp_get_max_threads();

@@ -178,7 +178,7 @@ class Spheres:
     sweeps: int
 
 
-def place_spheres(seed: int, mean: float, sd: float, vf: float, max_sweeps: int = 2000) -> Spheres:
+def place_spheres(seed: int, mean: float, sd: float, vf: float, max_sweeps: int = 300) -> Spheres:
     """Spheres in the unit cube (periodic), radii lognormal(mean, sd), until their
     summed volume reaches ``vf``; overlaps pushed apart pairwise until the largest
     relative overlap is below 1e-3 or ``max_sweeps`` is reached."""
