@@ -174,6 +174,21 @@ int pff_restrict(pff_level* coarse, pff_level* fine, pff_prec prec, const void* 
 int pff_chebyshev_smooth(pff_level* level, pff_prec prec, int degree, double lmin, double lmax,
                          const void* diag, const void* b, void* x, void* work, void* stream);
 
+/* The same smoother without caller-provided work space, for callers that may not
+ * allocate device memory where they smooth (memory owned by another allocator or
+ * a budget fixed at start-up; loops where cudaMalloc/cudaFree would synchronise
+ * the device).  The paper has no counterpart: it is an interface convenience.
+ * The three work vectors come from one array compiled into the library (up to
+ * 4*N_n(level) = 2 097 152 entries per vector, 48 MiB, held by every GPU that
+ * loads the library until exit); larger levels are rejected with
+ * PFF_ERR_INVALID and a message.  Allocates nothing.  The first call on each
+ * device looks up the array's device address (with that device current) and
+ * should come before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (different streams, no ordering) race; the leftover
+ * contents of earlier calls are never read. */
+int pff_chebyshev_smooth_noalloc(pff_level* level, pff_prec prec, int degree, double lmin, double lmax,
+                                 const void* diag, const void* b, void* x, void* stream);
+
 /* Accept the trial history written by the last pff_residual (Box 1 step 4,
  * C_in^-1 = F^-1 exp(2 eps_e) F^-T; eps_p += dgamma; H = max(H_n, psi+);
  * phi_n = phi). */

@@ -272,6 +272,10 @@ static int cheb_t(pff_level* L, int degree, double lmin, double lmax, const T* d
   return PFF_OK;
 }
 
+namespace pff {
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace pff
+
 extern "C" {
 
 const char* pff_last_error_message(void) { return g_err.c_str(); }

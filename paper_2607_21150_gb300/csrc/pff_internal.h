@@ -121,6 +121,9 @@ template <typename T>
 cudaError_t launch_cheb_step(long long n, T* x, T* d, T* r, const T* Ad, const T* diag,
                              double c_d, double c_r, int last, cudaStream_t st);
 
+// Records the message returned by pff_last_error_message and returns code (pff_abi.cpp).
+int set_last_error(int code, const char* msg);
+
 // Host basis data (pff_basis.cpp)
 void gll_nodes(int p, double* x);
 void gauss_rule(int Q, double* x, double* w);

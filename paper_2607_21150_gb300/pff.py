@@ -67,6 +67,7 @@ _SIGS = {
     "pff_prolong": ([_VP, _VP, _I, _VP, _VP, _VP], _I),
     "pff_restrict": ([_VP, _VP, _I, _VP, _VP, _VP], _I),
     "pff_chebyshev_smooth": ([_VP, _I, _I, _D, _D, _VP, _VP, _VP, _VP, _VP], _I),
+    "pff_chebyshev_smooth_noalloc": ([_VP, _I, _I, _D, _D, _VP, _VP, _VP, _VP], _I),
     "pff_commit_history": ([_VP, _VP], _I),
     "pff_get_history": ([_VP, _I, _VP, _VP], _I),
     "pff_get_flags": ([_VP, _VP, _VP], _I),
@@ -252,6 +253,12 @@ def pff_restrict(coarse, fine, prec, rf, rc, stream=None):
 def pff_chebyshev_smooth(level, prec, degree, lmin, lmax, diag, b, x, work, stream=None):
     _call("pff_chebyshev_smooth", level, int(prec), int(degree), float(lmin), float(lmax), _ptr(diag), _ptr(b),
           _ptr(x), _ptr(work), _stream(stream))
+
+
+def pff_chebyshev_smooth_noalloc(level, prec, degree, lmin, lmax, diag, b, x, stream=None):
+    """Chebyshev smoothing with the library's built-in work space (no allocation)."""
+    _call("pff_chebyshev_smooth_noalloc", level, int(prec), int(degree), float(lmin), float(lmax), _ptr(diag),
+          _ptr(b), _ptr(x), _stream(stream))
 
 
 def pff_commit_history(op, stream=None):
