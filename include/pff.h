@@ -189,6 +189,70 @@ int pff_chebyshev_smooth(pff_level* level, pff_prec prec, int degree, double lmi
 int pff_chebyshev_smooth_noalloc(pff_level* level, pff_prec prec, int degree, double lmin, double lmax,
                                  const void* diag, const void* b, void* x, void* stream);
 
+/* ----------------------------------------------------------------------------
+ * Newton-Krylov solver with p-multigrid preconditioning (Sec. 5: Newton, GMRES
+ * with adaptive classical Gram-Schmidt refinement, p-multigrid with Chebyshev
+ * smoothing; the paper's AMG coarse solve is replaced by Chebyshev-Jacobi on the
+ * assembled order-1 Galerkin operator).  Outer iterations, Krylov vectors and
+ * inner products are FP64; with mixed = 1 the level operators and smoothers run
+ * in FP32 (stored tangent copied by pff_op_enable_f32), the coarsest assembled
+ * solve stays FP64.
+ * ------------------------------------------------------------------------- */
+typedef struct pff_solver pff_solver;
+
+typedef struct {
+  int mixed;            /* 1: FP32 multigrid levels and smoothers; 0: all FP64 */
+  int cheb_degree;      /* Chebyshev degree of pre- and post-smoothing */
+  double cheb_lo;       /* smoothing interval [cheb_lo, cheb_hi] * lambda_max(D^-1 J) */
+  double cheb_hi;
+  int coarse_degree;    /* Chebyshev degree of the coarsest-level solve */
+  double coarse_lo;     /* coarse interval [coarse_lo, cheb_hi] * lambda_max */
+  int power_iters;      /* power iterations estimating lambda_max per level */
+  int krylov_restart;   /* FGMRES restart length, 1..60 */
+  int krylov_maxit;     /* iterations per linear solve */
+  double krylov_rtol;   /* relative tolerance of each linear solve */
+  int newton_maxit;     /* Newton iterations per call */
+  double newton_rtol;   /* stop when ||r|| <= newton_rtol * ||r_0|| */
+} pff_solver_params;
+
+typedef struct {
+  int newton_iterations;
+  int krylov_iterations;    /* summed over the Newton iterations */
+  int converged;
+  int status;               /* kernel status bits of a failed residual */
+  double res0, res;         /* ||r|| at the first and the last residual */
+  double last_krylov_relres;
+  double t_residual, t_setup, t_krylov;  /* seconds, host clock around synchronised phases */
+  double res_history[64];   /* ||r|| per Newton iteration */
+} pff_newton_stats;
+
+/* Fills the defaults: mixed 1, Chebyshev(3) on [0.1, 1.1] lambda_max, coarse
+ * Chebyshev(16) on [0.02, 1.1], 10 power iterations, FGMRES(30) to 1e-3 with at
+ * most 200 iterations, Newton to 1e-8 in at most 20 iterations. */
+int pff_solver_default_params(pff_solver_params* params);
+/* levels[0] = the fine level of op (pff_create_level with the fine order), then
+ * coarser levels with decreasing order; if the last has order 1 its operator is
+ * assembled (27-point stencil, 4x4 blocks, FP64).  Allocates the level vectors,
+ * the FGMRES basis ((restart + 1) + restart fine vectors) and work space. */
+int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const pff_solver_params* params,
+                      pff_solver** solver);
+int pff_destroy_solver(pff_solver* solver);
+/* Diagonals, coarse assembly and lambda_max estimates for the current stored
+ * linearisation (call after pff_residual).  Synchronises the stream. */
+int pff_solver_setup(pff_solver* solver, void* stream);
+/* lambda_max of D^-1 J estimated for a level by the last setup. */
+int pff_solver_level_lambda(const pff_solver* solver, int level, double* lmax);
+/* One V-cycle z = M^-1 r on FP64 fine vectors. */
+int pff_solver_vcycle(pff_solver* solver, const double* r, double* z, void* stream);
+/* y = A_c x with the assembled coarse operator (FP64 coarse vectors). */
+int pff_solver_coarse_apply(pff_solver* solver, const double* x, double* y, void* stream);
+/* FGMRES solve J x = b (x starts at 0); returns iterations and ||b - J x|| / ||b||. */
+int pff_solver_krylov(pff_solver* solver, const double* b, double* x, double rtol, int maxit, int* iters,
+                      double* relres, void* stream);
+/* Newton iterations on z (FP64 [4][N_n], Dirichlet values already imposed):
+ * residual, setup, FGMRES to krylov_rtol, z -= dz, until newton_rtol. */
+int pff_newton_solve(pff_solver* solver, double* z, pff_newton_stats* stats, void* stream);
+
 /* Accept the trial history written by the last pff_residual (Box 1 step 4,
  * C_in^-1 = F^-1 exp(2 eps_e) F^-T; eps_p += dgamma; H = max(H_n, psi+);
  * phi_n = phi). */

@@ -286,3 +286,40 @@ def chebyshev(A, diag, b, x0, degree: int, lmin: float, lmax: float):
         d = rho_new * rho * d + (2.0 * rho_new / delta) * r
         rho = rho_new
     return x
+
+
+def vcycle(Ks, Ps, diags, lmaxs, r, degree=3, lo=0.1, hi=1.1, coarse_degree=16, coarse_lo=0.02):
+    """Textbook p-multigrid V-cycle z = M^-1 r: on every level but the coarsest,
+    Chebyshev(degree) pre-smoothing from 0 on [lo, hi] lambda_max, residual,
+    restriction R = P^T, recursion, prolongation, Chebyshev post-smoothing; on the
+    coarsest level Chebyshev(coarse_degree) from 0 on [coarse_lo, hi] lambda_max.
+    Ks[l]: level matrices (fine first), Ps[l]: prolongation from level l+1 to l."""
+
+    def cycle(l, b):
+        K, d, lm = Ks[l], diags[l], lmaxs[l]
+        x0 = np.zeros_like(b)
+        if l == len(Ks) - 1:
+            return chebyshev(K, d, b, x0, coarse_degree, coarse_lo * lm, hi * lm)
+        x = chebyshev(K, d, b, x0, degree, lo * lm, hi * lm)
+        rc = Ps[l].T @ (b - K @ x)
+        x = x + Ps[l] @ cycle(l + 1, rc)
+        return chebyshev(K, d, b, x, degree, lo * lm, hi * lm)
+
+    return cycle(0, np.asarray(r, dtype=np.float64))
+
+
+def newton(w, rtol=1e-12, maxit=20):
+    """Newton's method on the assembled system with direct linear solves; returns
+    the converged nodal state and the residual-norm history."""
+    import scipy.sparse.linalg as spla
+
+    z = np.array(w.z, dtype=np.float64).ravel()
+    hist = []
+    for _ in range(maxit + 1):
+        out = assemble(w, z=z.reshape(4, -1))
+        r = out["r"].ravel()
+        hist.append(float(np.linalg.norm(r)))
+        if hist[-1] <= rtol * hist[0] or hist[-1] == 0.0:
+            break
+        z = z - spla.spsolve(out["K"].tocsc(), r)
+    return z.reshape(4, -1), hist, out

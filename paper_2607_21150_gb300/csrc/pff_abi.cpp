@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "pff_internal.h"
+#include "pff_handles.h"
 
 using namespace pff;
 
@@ -42,64 +43,6 @@ int upload(const std::vector<double>& h, T** d) {
 }
 
 }  // namespace
-
-struct pff_ctx {
-  int nphase;
-  PhaseDev phase[kMaxPhase];
-  GlobDev glob;
-};
-
-struct pff_basis {
-  int p, q;
-  std::vector<double> xg, xq, wq, B, Dc, Dt;
-};
-
-struct pff_restr {
-  pff_box box;
-  int p;
-  const int32_t* offsets;
-  int64_t nn;
-};
-
-struct Tables {  // per-level device copies of the 1D matrices, both precisions
-  double *B64 = nullptr, *Dc64 = nullptr, *Dt64 = nullptr;
-  float *B32 = nullptr, *Dc32 = nullptr, *Dt32 = nullptr;
-};
-
-struct pff_op {
-  pff_ctx* ctx;
-  int p, Q;
-  pff_box box;
-  MeshDev mesh;
-  long long nq, nel;
-  Geom geom;
-  Tables tab;
-  double* hist_c = nullptr;
-  double* hist_t = nullptr;
-  uint8_t* phase = nullptr;
-  uint8_t* flags = nullptr;
-  double* lin64 = nullptr;
-  float* lin32 = nullptr;
-  long long lin_len = 0;
-  double* io = nullptr;
-  uint8_t* mask = nullptr;
-  double* dvals = nullptr;
-  int* status = nullptr;
-  int f32 = 0;
-};
-
-struct pff_level {
-  pff_op* op;
-  int p;
-  MeshDev mesh;
-  Tables tab;
-  uint8_t* mask = nullptr;   // owned copy (coarse levels) ; fine level uses op->mask
-  bool is_fine = false;
-  // prolongation table towards the finer level with order I_pf
-  int I_pf = -1;
-  double* I64 = nullptr;
-  float* I32 = nullptr;
-};
 
 namespace {
 

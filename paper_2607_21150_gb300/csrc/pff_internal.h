@@ -121,6 +121,29 @@ template <typename T>
 cudaError_t launch_cheb_step(long long n, T* x, T* d, T* r, const T* Ad, const T* diag,
                              double c_d, double c_r, int last, cudaStream_t st);
 
+
+// Krylov vectors and the assembled coarse operator (pff_krylov.cu)
+constexpr int kReduceBlocks = 152 * 4;
+// out[j] = V_j . w for j < k (vectors V_j at stride ldv), FP64 accumulation in a
+// fixed order; partial needs k * kReduceBlocks doubles.
+template <typename TV, typename T>
+cudaError_t launch_mdot(const TV* V, long long ldv, int k, const T* w, long long n, double* partial, double* out,
+                        cudaStream_t st);
+cudaError_t launch_maxpy(double* w, const double* V, long long ldv, int k, const double* h, double sign, long long n,
+                         cudaStream_t st);
+template <typename T>
+cudaError_t launch_axpby(T* y, const T* x, double a, double b, long long n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bminus(T* y, const T* b, long long n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_dscale(T* y, const T* x, const T* d, long long n, cudaStream_t st);
+cudaError_t launch_d2f(float* y, const double* x, long long n, cudaStream_t st);
+cudaError_t launch_f2d(double* y, const float* x, long long n, cudaStream_t st);
+cudaError_t launch_q1_assemble(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
+                               const uint8_t* maskc, double* A, cudaStream_t st);
+cudaError_t launch_q1_spmv(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st);
+
 // Records the message returned by pff_last_error_message and returns code (pff_abi.cpp).
 int set_last_error(int code, const char* msg);
 

@@ -1,0 +1,509 @@
+// Newton-Krylov solver with p-multigrid preconditioning (Sec. 5: Newton,
+// GMRES with adaptive classical Gram-Schmidt refinement, p-multigrid with
+// Chebyshev smoothing), host-driven, every vector operation a device kernel.
+//
+// * Outer: Newton on the FP64 residual; each linear solve is FGMRES(m), FP64,
+//   right-preconditioned by one V-cycle (flexible because the coarse solve and
+//   the mixed-precision cycle are not exactly linear in FP64).
+// * V-cycle: Chebyshev(k) pre- and post-smoothing on D^-1 J of every
+//   matrix-free level (FP64, or FP32 in the mixed variant), p-restriction /
+//   prolongation between levels, and on an order-1 coarsest level an FP64
+//   Chebyshev-Jacobi solve with the assembled Q1 Galerkin operator.
+// * Eigenvalue bounds: lambda_max of D^-1 J per level by power iteration from a
+//   fixed seeded vector; smoothing interval [lo, hi] * lambda_max.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pff_handles.h"
+
+using namespace pff;
+
+namespace {
+
+int sfail(int code, const std::string& msg) { return set_last_error(code, msg.c_str()); }
+
+#define S_CK(call)                                                                                   \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return sfail(PFF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define S_RC(call)            \
+  do {                        \
+    int r_ = (call);          \
+    if (r_ != PFF_OK) return r_; \
+  } while (0)
+
+struct LevelWork {
+  pff_level* L = nullptr;
+  int p = 0;
+  int prec = PFF_F64;
+  size_t esz = 8;
+  long long n = 0;
+  void *diag = nullptr, *b = nullptr, *x = nullptr, *tmp = nullptr, *work = nullptr;
+  double lmax = 1.0;
+};
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+struct pff_solver {
+  pff_op* op = nullptr;
+  pff_solver_params prm;
+  std::vector<LevelWork> lv;
+  bool assembled = false;
+  double *A = nullptr, *cdiag = nullptr, *cb = nullptr, *cx = nullptr, *cwork = nullptr;
+  double clmax = 1.0;
+  long long n = 0;
+  double *V = nullptr, *Z = nullptr, *r = nullptr, *dz = nullptr;
+  double *partial = nullptr, *dots = nullptr, *hdev = nullptr;
+  double* pw64 = nullptr;  // power-iteration start vector (FP64, fine size)
+  float* pw32 = nullptr;
+};
+
+namespace {
+
+int dev_dots(pff_solver* s, const double* V, long long ldv, int k, const double* w, long long n, double* host,
+             cudaStream_t st) {
+  S_CK((launch_mdot<double, double>(V, ldv, k, w, n, s->partial, s->dots, st)));
+  S_CK(cudaMemcpyAsync(host, s->dots, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  S_CK(cudaStreamSynchronize(st));
+  return PFF_OK;
+}
+
+int norm_level(pff_solver* s, const LevelWork& w, const void* v, double* out, cudaStream_t st) {
+  if (w.prec == PFF_F64) S_CK((launch_mdot<double, double>((const double*)v, 0, 1, (const double*)v, w.n, s->partial, s->dots, st)));
+  else S_CK((launch_mdot<float, float>((const float*)v, 0, 1, (const float*)v, w.n, s->partial, s->dots, st)));
+  double h = 0.0;
+  S_CK(cudaMemcpyAsync(&h, s->dots, sizeof(double), cudaMemcpyDeviceToHost, st));
+  S_CK(cudaStreamSynchronize(st));
+  *out = std::sqrt(h);
+  return PFF_OK;
+}
+
+int axpby_level(const LevelWork& w, void* y, const void* x, double a, double b, cudaStream_t st) {
+  if (w.prec == PFF_F64) S_CK(launch_axpby<double>((double*)y, (const double*)x, a, b, w.n, st));
+  else S_CK(launch_axpby<float>((float*)y, (const float*)x, a, b, w.n, st));
+  return PFF_OK;
+}
+
+int coarse_cheb(pff_solver* s, cudaStream_t st) {
+  // FP64 Chebyshev-Jacobi on the assembled coarse operator, from x = 0.
+  LevelWork& c = s->lv.back();
+  const MeshDev& mc = c.L->mesh;
+  const long long n = c.n;
+  double* r = s->cwork;
+  double* d = s->cwork + n;
+  double* Ad = s->cwork + 2 * n;
+  if (c.prec == PFF_F64) S_CK(cudaMemcpyAsync(s->cb, c.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_f2d(s->cb, (const float*)c.b, n, st));
+  S_CK(cudaMemsetAsync(s->cx, 0, sizeof(double) * n, st));
+  const double lmax = s->clmax * s->prm.cheb_hi, lmin = s->clmax * s->prm.coarse_lo;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  S_CK(cudaMemsetAsync(Ad, 0, sizeof(double) * n, st));
+  S_CK(launch_cheb_init<double>(n, s->cb, Ad, s->cdiag, r, d, 1.0 / theta, st));
+  const int deg = s->prm.coarse_degree;
+  for (int k = 0; k < deg; ++k) {
+    if (k == deg - 1) {
+      S_CK(launch_cheb_step<double>(n, s->cx, d, r, Ad, s->cdiag, 0.0, 0.0, 1, st));
+      break;
+    }
+    S_CK(launch_q1_spmv(mc, s->A, d, Ad, st));
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    S_CK(launch_cheb_step<double>(n, s->cx, d, r, Ad, s->cdiag, rho_new * rho, 2.0 * rho_new / delta, 0, st));
+    rho = rho_new;
+  }
+  if (c.prec == PFF_F64) S_CK(cudaMemcpyAsync(c.x, s->cx, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_d2f((float*)c.x, s->cx, n, st));
+  return PFF_OK;
+}
+
+int vcycle(pff_solver* s, int l, cudaStream_t st) {
+  LevelWork& w = s->lv[l];
+  const bool coarsest = (l + 1 == (int)s->lv.size());
+  if (coarsest && s->assembled) return coarse_cheb(s, st);
+  S_CK(cudaMemsetAsync(w.x, 0, w.esz * w.n, st));
+  const int deg = coarsest ? s->prm.coarse_degree : s->prm.cheb_degree;
+  const double lo = coarsest ? s->prm.coarse_lo : s->prm.cheb_lo;
+  S_RC(pff_chebyshev_smooth(w.L, (pff_prec)w.prec, deg, lo * w.lmax, s->prm.cheb_hi * w.lmax, w.diag, w.b, w.x,
+                            w.work, st));
+  if (coarsest) return PFF_OK;
+  // residual, restriction, coarse correction, prolongation
+  S_RC(pff_jacobian_apply(w.L, (pff_prec)w.prec, w.x, w.tmp, st));
+  if (w.prec == PFF_F64) S_CK(launch_bminus<double>((double*)w.tmp, (const double*)w.b, w.n, st));
+  else S_CK(launch_bminus<float>((float*)w.tmp, (const float*)w.b, w.n, st));
+  LevelWork& c = s->lv[l + 1];
+  S_RC(pff_restrict(c.L, w.L, (pff_prec)w.prec, w.tmp, c.b, st));
+  S_RC(vcycle(s, l + 1, st));
+  S_RC(pff_prolong(c.L, w.L, (pff_prec)w.prec, c.x, w.tmp, st));
+  S_RC(axpby_level(w, w.x, w.tmp, 1.0, 1.0, st));
+  S_RC(pff_chebyshev_smooth(w.L, (pff_prec)w.prec, s->prm.cheb_degree, s->prm.cheb_lo * w.lmax,
+                            s->prm.cheb_hi * w.lmax, w.diag, w.b, w.x, w.work, st));
+  return PFF_OK;
+}
+
+int power_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
+  // lambda_max of D^-1 J by power iteration from the seeded start vector.
+  void* v = w.x;
+  void* y = w.tmp;
+  if (w.prec == PFF_F64) S_CK(cudaMemcpyAsync(v, s->pw64, sizeof(double) * w.n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(cudaMemcpyAsync(v, s->pw32, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, st));
+  double nv;
+  S_RC(norm_level(s, w, v, &nv, st));
+  S_RC(axpby_level(w, v, v, 1.0 / nv, 0.0, st));
+  double lam = 1.0;
+  for (int it = 0; it < s->prm.power_iters; ++it) {
+    S_RC(pff_jacobian_apply(w.L, (pff_prec)w.prec, v, y, st));
+    if (w.prec == PFF_F64) S_CK(launch_dscale<double>((double*)y, (const double*)y, (const double*)w.diag, w.n, st));
+    else S_CK(launch_dscale<float>((float*)y, (const float*)y, (const float*)w.diag, w.n, st));
+    S_RC(norm_level(s, w, y, &lam, st));
+    if (!(lam > 0.0) || !std::isfinite(lam)) return sfail(PFF_ERR_DEVICE, "power iteration: non-finite eigenvalue estimate");
+    S_RC(axpby_level(w, v, y, 1.0 / lam, 0.0, st));
+  }
+  w.lmax = lam;
+  return PFF_OK;
+}
+
+int power_coarse(pff_solver* s, cudaStream_t st) {
+  LevelWork& c = s->lv.back();
+  const long long n = c.n;
+  double* v = s->cx;
+  double* y = s->cb;
+  S_CK(cudaMemcpyAsync(v, s->pw64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  double h;
+  S_RC(dev_dots(s, v, 0, 1, v, n, &h, st));
+  S_CK(launch_axpby<double>(v, v, 1.0 / std::sqrt(h), 0.0, n, st));
+  double lam = 1.0;
+  for (int it = 0; it < s->prm.power_iters; ++it) {
+    S_CK(launch_q1_spmv(c.L->mesh, s->A, v, y, st));
+    S_CK(launch_dscale<double>(y, y, s->cdiag, n, st));
+    S_RC(dev_dots(s, y, 0, 1, y, n, &h, st));
+    lam = std::sqrt(h);
+    if (!(lam > 0.0) || !std::isfinite(lam)) return sfail(PFF_ERR_DEVICE, "coarse power iteration failed");
+    S_CK(launch_axpby<double>(v, y, 1.0 / lam, 0.0, n, st));
+  }
+  s->clmax = lam;
+  return PFF_OK;
+}
+
+// FGMRES(m), right preconditioned (Saad, Alg. 9.6), FP64; classical
+// Gram-Schmidt with a second pass when the first one loses accuracy.
+int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+           cudaStream_t st) {
+  const long long n = s->n;
+  const int m = s->prm.krylov_restart;
+  pff_level* F = s->lv[0].L;
+  std::vector<double> H((m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), h(m + 2), y(m);
+  S_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+  double beta0 = -1.0, res = 0.0;
+  int total = 0;
+  bool first = true;
+  while (true) {
+    double* v0 = s->V;
+    if (first) {
+      S_CK(cudaMemcpyAsync(v0, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+      S_RC(pff_jacobian_apply(F, PFF_F64, x, v0, st));
+      S_CK(launch_bminus<double>(v0, b, n, st));
+    }
+    double bb;
+    S_RC(dev_dots(s, v0, 0, 1, v0, n, &bb, st));
+    double beta = std::sqrt(bb);
+    if (beta0 < 0) beta0 = beta;
+    if (beta == 0.0 || beta0 == 0.0) { res = 0.0; break; }
+    res = beta;
+    if (beta <= rtol * beta0 || total >= maxit) break;
+    S_CK(launch_axpby<double>(v0, v0, 1.0 / beta, 0.0, n, st));
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jend = 0;
+    for (int j = 0; j < m && total < maxit; ++j) {
+      double* vj = s->V + (long long)j * n;
+      double* zj = s->Z + (long long)j * n;
+      double* w = s->V + (long long)(j + 1) * n;
+      // z_j = M^-1 v_j (one V-cycle)
+      LevelWork& f = s->lv[0];
+      if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(f.b, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      else S_CK(launch_d2f((float*)f.b, vj, n, st));
+      S_RC(vcycle(s, 0, st));
+      if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(zj, f.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      else S_CK(launch_f2d(zj, (const float*)f.x, n, st));
+      // w = J z_j
+      S_RC(pff_jacobian_apply(F, PFF_F64, zj, w, st));
+      // Gram-Schmidt: h = V^T w, |w|^2 in the same pass (w is V_{j+1})
+      S_RC(dev_dots(s, s->V, n, j + 2, w, n, h.data(), st));
+      double ww = h[j + 1];
+      S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+      S_CK(launch_maxpy(w, s->V, n, j + 1, s->hdev, -1.0, n, st));
+      double hsq = 0.0;
+      for (int i = 0; i <= j; ++i) hsq += h[i] * h[i];
+      std::vector<double> hcol(h.begin(), h.begin() + j + 1);
+      // second pass: exact norm and the residual projection
+      S_RC(dev_dots(s, s->V, n, j + 2, w, n, h.data(), st));
+      double ww2 = h[j + 1];
+      double h2sq = 0.0;
+      for (int i = 0; i <= j; ++i) h2sq += h[i] * h[i];
+      if (h2sq > 1e-24 * ww2 || ww - hsq < 0.5 * ww) {
+        S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+        S_CK(launch_maxpy(w, s->V, n, j + 1, s->hdev, -1.0, n, st));
+        for (int i = 0; i <= j; ++i) hcol[i] += h[i];
+        ww2 = std::max(ww2 - h2sq, 0.0);
+      }
+      double hn = std::sqrt(ww2);
+      for (int i = 0; i <= j; ++i) H[i * m + j] = hcol[i];
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0.0) S_CK(launch_axpby<double>(w, w, 1.0 / hn, 0.0, n, st));
+      // Givens rotations
+      for (int i = 0; i < j; ++i) {
+        double a = H[i * m + j], c = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * c;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+      }
+      double a = H[j * m + j], c = H[(j + 1) * m + j];
+      double den = std::hypot(a, c);
+      cs[j] = den > 0 ? a / den : 1.0;
+      sn[j] = den > 0 ? c / den : 0.0;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++total;
+      jend = j + 1;
+      res = std::fabs(g[j + 1]);
+      if (res <= rtol * beta0 || hn == 0.0) break;
+    }
+    // x += Z y with H y = g (upper triangular)
+    for (int i = jend - 1; i >= 0; --i) {
+      double sum = g[i];
+      for (int k = i + 1; k < jend; ++k) sum -= H[i * m + k] * y[k];
+      y[i] = sum / H[i * m + i];
+    }
+    S_CK(cudaMemcpyAsync(s->hdev, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, st));
+    S_CK(launch_maxpy(x, s->Z, n, jend, s->hdev, 1.0, n, st));
+    S_CK(cudaStreamSynchronize(st));
+    first = false;
+    if (res <= rtol * beta0 || total >= maxit) break;
+  }
+  *iters = total;
+  *relres = beta0 > 0 ? res / beta0 : 0.0;
+  return PFF_OK;
+}
+
+int setup(pff_solver* s, cudaStream_t st) {
+  const int L = (int)s->lv.size();
+  for (int l = 0; l < L; ++l) {
+    LevelWork& w = s->lv[l];
+    if (l + 1 == L && s->assembled) continue;
+    S_RC(pff_assemble_diagonal(w.L, (pff_prec)w.prec, w.diag, st));
+  }
+  if (s->assembled) {
+    LevelWork& c = s->lv.back();
+    pff_op* op = s->op;
+    S_CK(launch_q1_assemble(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->A, st));
+    S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
+    S_RC(power_coarse(s, st));
+  }
+  for (int l = 0; l < L; ++l) {
+    if (l + 1 == L && s->assembled) continue;
+    S_RC(power_level(s, s->lv[l], st));
+  }
+  return PFF_OK;
+}
+
+void free_solver(pff_solver* s) {
+  for (auto& w : s->lv) {
+    cudaFree(w.diag); cudaFree(w.b); cudaFree(w.x); cudaFree(w.tmp); cudaFree(w.work);
+  }
+  cudaFree(s->A); cudaFree(s->cdiag); cudaFree(s->cb); cudaFree(s->cx); cudaFree(s->cwork);
+  cudaFree(s->V); cudaFree(s->Z); cudaFree(s->r); cudaFree(s->dz);
+  cudaFree(s->partial); cudaFree(s->dots); cudaFree(s->hdev);
+  cudaFree(s->pw64); cudaFree(s->pw32);
+}
+
+}  // namespace
+
+extern "C" {
+
+int pff_solver_default_params(pff_solver_params* p) {
+  if (!p) return sfail(PFF_ERR_INVALID, "pff_solver_default_params: null");
+  p->mixed = 1;
+  p->cheb_degree = 3;
+  p->cheb_lo = 0.1;
+  p->cheb_hi = 1.1;
+  p->coarse_degree = 16;
+  p->coarse_lo = 0.02;
+  p->power_iters = 10;
+  p->krylov_restart = 30;
+  p->krylov_maxit = 200;
+  p->krylov_rtol = 1e-3;
+  p->newton_maxit = 20;
+  p->newton_rtol = 1e-8;
+  return PFF_OK;
+}
+
+int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const pff_solver_params* prm,
+                      pff_solver** out) {
+  if (!op || !levels || !prm || !out || nlevels < 1) return sfail(PFF_ERR_INVALID, "pff_create_solver: bad argument");
+  if (prm->krylov_restart < 1 || prm->krylov_restart > 60) return sfail(PFF_ERR_INVALID, "pff_create_solver: 1 <= restart <= 60");
+  if (prm->cheb_degree < 1 || prm->coarse_degree < 1) return sfail(PFF_ERR_INVALID, "pff_create_solver: degrees >= 1");
+  if (!(prm->cheb_hi > prm->cheb_lo && prm->cheb_lo > 0 && prm->coarse_lo > 0 && prm->coarse_lo < prm->cheb_hi))
+    return sfail(PFF_ERR_INVALID, "pff_create_solver: need 0 < lo < hi");
+  if (levels[0]->op != op || !levels[0]->is_fine) return sfail(PFF_ERR_INVALID, "pff_create_solver: levels[0] must be the fine level of op");
+  for (int l = 1; l < nlevels; ++l)
+    if (levels[l]->op != op || levels[l]->p >= levels[l - 1]->p)
+      return sfail(PFF_ERR_INVALID, "pff_create_solver: levels must share op with decreasing order");
+  if (prm->mixed && !op->lin32) return sfail(PFF_ERR_INVALID, "pff_create_solver: mixed precision needs pff_op_enable_f32");
+  pff_solver* s = new pff_solver();
+  s->op = op;
+  s->prm = *prm;
+  s->n = 4 * op->mesh.nn;
+  s->assembled = (levels[nlevels - 1]->p == 1 && nlevels > 1);
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < nlevels; ++l) {
+    LevelWork w;
+    w.L = levels[l];
+    w.p = levels[l]->p;
+    w.prec = prm->mixed ? PFF_F32 : PFF_F64;
+    w.esz = (w.prec == PFF_F64) ? 8 : 4;
+    w.n = 4 * levels[l]->mesh.nn;
+    if (e == cudaSuccess) e = cudaMalloc(&w.diag, w.esz * w.n);
+    if (e == cudaSuccess) e = cudaMalloc(&w.b, w.esz * w.n);
+    if (e == cudaSuccess) e = cudaMalloc(&w.x, w.esz * w.n);
+    if (e == cudaSuccess) e = cudaMalloc(&w.tmp, w.esz * w.n);
+    if (e == cudaSuccess) e = cudaMalloc(&w.work, 3 * w.esz * w.n);
+    s->lv.push_back(w);
+  }
+  if (s->assembled) {
+    const long long nc = s->lv.back().n;
+    if (e == cudaSuccess) e = cudaMalloc(&s->A, sizeof(double) * 27 * 16 * (nc / 4));
+    if (e == cudaSuccess) e = cudaMalloc(&s->cdiag, sizeof(double) * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&s->cb, sizeof(double) * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&s->cx, sizeof(double) * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&s->cwork, sizeof(double) * 3 * nc);
+  }
+  const int m = prm->krylov_restart;
+  if (e == cudaSuccess) e = cudaMalloc(&s->V, sizeof(double) * (m + 1) * s->n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->Z, sizeof(double) * m * s->n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->r, sizeof(double) * s->n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->dz, sizeof(double) * s->n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->partial, sizeof(double) * 64 * kReduceBlocks);
+  if (e == cudaSuccess) e = cudaMalloc(&s->dots, sizeof(double) * 64);
+  if (e == cudaSuccess) e = cudaMalloc(&s->hdev, sizeof(double) * 64);
+  if (e == cudaSuccess) e = cudaMalloc(&s->pw64, sizeof(double) * s->n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->pw32, sizeof(float) * s->n);
+  if (e == cudaSuccess) {
+    // seeded start vector of the power iterations (xorshift64*, uniform in [0.5, 1.5))
+    std::vector<double> h(s->n);
+    std::vector<float> hf(s->n);
+    unsigned long long st = 0x9E3779B97F4A7C15ull;
+    for (long long i = 0; i < s->n; ++i) {
+      st ^= st >> 12; st ^= st << 25; st ^= st >> 27;
+      double u = (double)((st * 0x2545F4914F6CDD1Dull) >> 11) * (1.0 / 9007199254740992.0);
+      h[i] = 0.5 + u;
+      hf[i] = (float)h[i];
+    }
+    e = cudaMemcpy(s->pw64, h.data(), sizeof(double) * s->n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->pw32, hf.data(), sizeof(float) * s->n, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) {
+    free_solver(s);
+    delete s;
+    return sfail(PFF_ERR_CUDA, std::string("pff_create_solver: ") + cudaGetErrorString(e));
+  }
+  *out = s;
+  return PFF_OK;
+}
+
+int pff_destroy_solver(pff_solver* s) {
+  if (!s) return PFF_OK;
+  free_solver(s);
+  delete s;
+  return PFF_OK;
+}
+
+int pff_solver_setup(pff_solver* s, void* stream) {
+  if (!s) return sfail(PFF_ERR_INVALID, "pff_solver_setup: null solver");
+  return setup(s, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pff_solver_level_lambda(const pff_solver* s, int level, double* lmax) {
+  if (!s || !lmax || level < 0 || level >= (int)s->lv.size()) return sfail(PFF_ERR_INVALID, "pff_solver_level_lambda: bad argument");
+  *lmax = (level + 1 == (int)s->lv.size() && s->assembled) ? s->clmax : s->lv[level].lmax;
+  return PFF_OK;
+}
+
+int pff_solver_vcycle(pff_solver* s, const double* r, double* z, void* stream) {
+  if (!s || !r || !z) return sfail(PFF_ERR_INVALID, "pff_solver_vcycle: null argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  LevelWork& f = s->lv[0];
+  if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(f.b, r, sizeof(double) * f.n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_d2f((float*)f.b, r, f.n, st));
+  S_RC(vcycle(s, 0, st));
+  if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(z, f.x, sizeof(double) * f.n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_f2d(z, (const float*)f.x, f.n, st));
+  return PFF_OK;
+}
+
+int pff_solver_coarse_apply(pff_solver* s, const double* x, double* y, void* stream) {
+  if (!s || !x || !y || !s->assembled) return sfail(PFF_ERR_INVALID, "pff_solver_coarse_apply: needs an assembled coarse level");
+  S_CK(launch_q1_spmv(s->lv.back().L->mesh, s->A, x, y, reinterpret_cast<cudaStream_t>(stream)));
+  return PFF_OK;
+}
+
+int pff_solver_krylov(pff_solver* s, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+                      void* stream) {
+  if (!s || !b || !x || !iters || !relres) return sfail(PFF_ERR_INVALID, "pff_solver_krylov: null argument");
+  return fgmres(s, b, x, rtol, maxit, iters, relres, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int pff_newton_solve(pff_solver* s, double* z, pff_newton_stats* stats, void* stream) {
+  if (!s || !z || !stats) return sfail(PFF_ERR_INVALID, "pff_newton_solve: null argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  std::memset(stats, 0, sizeof(*stats));
+  const long long n = s->n;
+  double r0 = -1.0;
+  for (int it = 0;; ++it) {
+    double t0 = now();
+    S_RC(pff_residual(s->op, z, s->r, st));
+    int status = 0;
+    S_RC(pff_get_status(s->op, stream, &status));
+    if (status) {
+      stats->status = status;
+      return sfail(PFF_ERR_DEVICE, "pff_newton_solve: residual kernel status " + std::to_string(status));
+    }
+    double rr;
+    S_RC(dev_dots(s, s->r, 0, 1, s->r, n, &rr, st));
+    double rn = std::sqrt(rr);
+    stats->t_residual += now() - t0;
+    if (r0 < 0) r0 = rn;
+    if (it < 64) stats->res_history[it] = rn;
+    stats->res0 = r0;
+    stats->res = rn;
+    if (rn <= s->prm.newton_rtol * r0 || rn == 0.0) { stats->converged = 1; break; }
+    if (it >= s->prm.newton_maxit) break;
+    t0 = now();
+    S_RC(setup(s, st));
+    S_CK(cudaStreamSynchronize(st));
+    stats->t_setup += now() - t0;
+    t0 = now();
+    int its = 0;
+    double rel = 0.0;
+    S_RC(fgmres(s, s->r, s->dz, s->prm.krylov_rtol, s->prm.krylov_maxit, &its, &rel, st));
+    S_CK(launch_axpby<double>(z, s->dz, -1.0, 1.0, n, st));
+    S_CK(cudaStreamSynchronize(st));
+    stats->t_krylov += now() - t0;
+    stats->krylov_iterations += its;
+    stats->newton_iterations = it + 1;
+    stats->last_krylov_relres = rel;
+  }
+  return PFF_OK;
+}
+
+}  // extern "C"

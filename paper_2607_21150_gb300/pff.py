@@ -34,6 +34,26 @@ class pff_box(ctypes.Structure):
                 ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("hz", ctypes.c_double)]
 
 
+class pff_solver_params(ctypes.Structure):
+    _fields_ = [("mixed", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
+                ("cheb_hi", ctypes.c_double), ("coarse_degree", ctypes.c_int), ("coarse_lo", ctypes.c_double),
+                ("power_iters", ctypes.c_int), ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int),
+                ("krylov_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int), ("newton_rtol", ctypes.c_double)]
+
+
+class pff_newton_stats(ctypes.Structure):
+    _fields_ = [("newton_iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
+                ("converged", ctypes.c_int), ("status", ctypes.c_int), ("res0", ctypes.c_double),
+                ("res", ctypes.c_double), ("last_krylov_relres", ctypes.c_double),
+                ("t_residual", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_krylov", ctypes.c_double),
+                ("res_history", ctypes.c_double * 64)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "res_history"}
+        d["res_history"] = list(self.res_history[:max(1, self.newton_iterations + 1)])
+        return d
+
+
 _VP = ctypes.c_void_p
 _I = ctypes.c_int
 _D = ctypes.c_double
@@ -68,6 +88,15 @@ _SIGS = {
     "pff_restrict": ([_VP, _VP, _I, _VP, _VP, _VP], _I),
     "pff_chebyshev_smooth": ([_VP, _I, _I, _D, _D, _VP, _VP, _VP, _VP, _VP], _I),
     "pff_chebyshev_smooth_noalloc": ([_VP, _I, _I, _D, _D, _VP, _VP, _VP, _VP], _I),
+    "pff_solver_default_params": ([ctypes.POINTER(pff_solver_params)], _I),
+    "pff_create_solver": ([_VP, _I, ctypes.POINTER(_VP), ctypes.POINTER(pff_solver_params), ctypes.POINTER(_VP)], _I),
+    "pff_destroy_solver": ([_VP], _I),
+    "pff_solver_setup": ([_VP, _VP], _I),
+    "pff_solver_level_lambda": ([_VP, _I, ctypes.POINTER(_D)], _I),
+    "pff_solver_vcycle": ([_VP, _VP, _VP, _VP], _I),
+    "pff_solver_coarse_apply": ([_VP, _VP, _VP, _VP], _I),
+    "pff_solver_krylov": ([_VP, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP], _I),
+    "pff_newton_solve": ([_VP, _VP, ctypes.POINTER(pff_newton_stats), _VP], _I),
     "pff_commit_history": ([_VP, _VP], _I),
     "pff_get_history": ([_VP, _I, _VP, _VP], _I),
     "pff_get_flags": ([_VP, _VP, _VP], _I),
@@ -259,6 +288,57 @@ def pff_chebyshev_smooth_noalloc(level, prec, degree, lmin, lmax, diag, b, x, st
     """Chebyshev smoothing with the library's built-in work space (no allocation)."""
     _call("pff_chebyshev_smooth_noalloc", level, int(prec), int(degree), float(lmin), float(lmax), _ptr(diag),
           _ptr(b), _ptr(x), _stream(stream))
+
+
+def pff_solver_default_params(**overrides):
+    prm = pff_solver_params()
+    _call("pff_solver_default_params", ctypes.byref(prm))
+    for k, v in overrides.items():
+        setattr(prm, k, v)
+    return prm
+
+
+def pff_create_solver(op, levels, params):
+    arr = (_VP * len(levels))(*[lv.value if isinstance(lv, _VP) else lv for lv in levels])
+    h = _VP()
+    _call("pff_create_solver", op, len(levels), arr, ctypes.byref(params), ctypes.byref(h))
+    return h
+
+
+def pff_destroy_solver(solver):
+    _call("pff_destroy_solver", solver)
+
+
+def pff_solver_setup(solver, stream=None):
+    _call("pff_solver_setup", solver, _stream(stream))
+
+
+def pff_solver_level_lambda(solver, level):
+    v = _D()
+    _call("pff_solver_level_lambda", solver, int(level), ctypes.byref(v))
+    return float(v.value)
+
+
+def pff_solver_vcycle(solver, r, z, stream=None):
+    _call("pff_solver_vcycle", solver, _ptr(r), _ptr(z), _stream(stream))
+
+
+def pff_solver_coarse_apply(solver, x, y, stream=None):
+    _call("pff_solver_coarse_apply", solver, _ptr(x), _ptr(y), _stream(stream))
+
+
+def pff_solver_krylov(solver, b, x, rtol, maxit, stream=None):
+    it = _I()
+    rel = _D()
+    _call("pff_solver_krylov", solver, _ptr(b), _ptr(x), float(rtol), int(maxit), ctypes.byref(it),
+          ctypes.byref(rel), _stream(stream))
+    return int(it.value), float(rel.value)
+
+
+def pff_newton_solve(solver, z, stream=None):
+    st = pff_newton_stats()
+    _call("pff_newton_solve", solver, _ptr(z), ctypes.byref(st), _stream(stream))
+    return st.as_dict()
 
 
 def pff_commit_history(op, stream=None):

@@ -94,6 +94,14 @@ class Session:
         pff.pff_chebyshev_smooth(self.levels[p], prec, degree, lmin, lmax, diag, b, x, work, self.stream)
         return x
 
+    def solver(self, levels=None, **params):
+        """FGMRES / p-multigrid solver over the given level orders (fine first)."""
+        m = self.w.mesh
+        levels = [m.p] + sorted([p for p in self.levels if p != m.p], reverse=True) if levels is None else levels
+        prm = pff.pff_solver_default_params(**params)
+        handles = [self.levels[p] for p in levels]
+        return pff.pff_create_solver(self.op, handles, prm)
+
     def flags(self):
         f = torch.zeros(self.w.mesh.nq, dtype=torch.uint8, device=self.dev)
         pff.pff_get_flags(self.op, f, self.stream)
