@@ -148,6 +148,49 @@ def oracle_sample(seconds_budget: float = 20.0):
                 gdofs=m.ndof / t_spmv / 1e9, gdofs_incl_assembly=m.ndof / (t_spmv + t_asm) / 1e9)
 
 
+def newton_compare(name: str, steps: int = 1):
+    """Load steps from the unloaded state with FP64 p-MG and with mixed p-MG (FP32
+    levels and smoothers), both to ||r||/||r0|| <= 1e-8 with inner rtol 1e-3.
+    Returns per-variant timings (host clock around synchronised phases) and the
+    relative difference of the two converged fields."""
+    import torch
+    from paper_2607_21150_gb300 import inputs
+    from paper_2607_21150_gb300.driver import LoadStepper
+    out = {"workload": name, "load_steps": steps}
+    fields = {}
+    for label, mixed in (("mixed", True), ("fp64", False)):
+        w = getattr(inputs, name)()
+        lsp = LoadStepper(w, mixed=mixed, verbose=1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its = kr = 0
+        res = []
+        tr = ts = tk = 0.0
+        for k in range(1, steps + 1):
+            st = lsp.step(k)
+            its += st["newton_iterations"]
+            kr += st["krylov_iterations"]
+            tr += st["t_residual"]
+            ts += st["t_setup"]
+            tk += st["t_krylov"]
+            res.append(st["res_history"])
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        fields[label] = lsp.z.cpu().numpy()
+        out[label] = {"wall_s": wall, "newton_iterations": its, "krylov_iterations": kr,
+                      "ms_per_newton_iteration": 1e3 * wall / max(its, 1), "t_residual_s": tr, "t_setup_s": ts,
+                      "t_krylov_s": tk, "reaction": st["reaction"], "res_history": res[-1],
+                      "levels": lsp.levels}
+        print(json.dumps({"newton_variant": label, **out[label]}), file=sys.stderr, flush=True)
+        lsp.close()
+        del lsp
+        torch.cuda.empty_cache()
+    a, b = fields["fp64"], fields["mixed"]
+    out["field_rel_diff"] = float(np.linalg.norm(a - b) / np.linalg.norm(a))
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -293,6 +336,10 @@ def run_native(args):
     bytes64 = 8 * ndof * 2 + ndof + 67 * 8 * m.nq
     bytes32 = 4 * ndof * 2 + ndof + 67 * 4 * m.nq
     t32 = tot32 / args.steps / 1e3
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    newton = newton_compare(args.newton, args.newton_steps) if args.newton != "none" else None
     cpu = oracle_sample()
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -311,6 +358,7 @@ def run_native(args):
                              "achieved_gbs": bytes32 / t32 / 1e9, "hbm_frac": bytes32 / t32 / 1e9 / hbm_peak,
                              "bound": "hbm", "peak_gbs": hbm_peak, "peak_source": src},
         "residual_ms": t_res, "kernel_status": status,
+        "newton_step": newton,
         "e2e": {"value": world * ndof * args.steps / (tot_e2e / 1e3) / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
         "gpu_launches": 2 * args.steps,
@@ -334,6 +382,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default="compress_q4", choices=["compress_q4", "tension_q4"])
+    ap.add_argument("--newton", default="tension_q4", choices=["none", "tension_q4", "compress_q4", "notched_q3"],
+                    help="workload of the FP64-vs-mixed Newton comparison")
+    ap.add_argument("--newton-steps", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -140,6 +140,15 @@ int pff_set_dirichlet(pff_op* op, const uint8_t* mask, const double* values, voi
  * by every Jacobian action until the next call. */
 int pff_residual(pff_op* op, const double* z, double* r, void* stream);
 
+/* z = ubar on the Dirichlet DoFs set by pff_set_dirichlet (other entries kept). */
+int pff_apply_dirichlet(pff_op* op, double* z, void* stream);
+/* Reaction: sums, per field, of the internal force vector (Eq.
+ * matrix-free-residual-compact without Dirichlet rows) over the DoFs selected
+ * by sel (uint8 [4][N_n], device), for the state of the last pff_residual.
+ * out4 is a HOST array of 4 doubles; synchronises the stream.  Allocates its
+ * work vector on first use. */
+int pff_reaction(pff_op* op, const uint8_t* sel, double* out4, void* stream);
+
 /* Multigrid level built on the fine operator's quadrature points (coarse
  * Lagrange basis of order p_level evaluated at the fine Gauss points, sharing
  * the fine stored linearisation, i.e. the Galerkin operator P^T A P).
@@ -207,12 +216,17 @@ typedef struct {
   double cheb_hi;
   int coarse_degree;    /* Chebyshev degree of the coarsest-level solve */
   double coarse_lo;     /* coarse interval [coarse_lo, cheb_hi] * lambda_max */
-  int power_iters;      /* power iterations estimating lambda_max per level */
+  int power_iters;      /* Arnoldi steps estimating lambda_max(D^-1 J) per level (<= restart) */
   int krylov_restart;   /* FGMRES restart length, 1..60 */
   int krylov_maxit;     /* iterations per linear solve */
   double krylov_rtol;   /* relative tolerance of each linear solve */
   int newton_maxit;     /* Newton iterations per call */
   double newton_rtol;   /* stop when ||r|| <= newton_rtol * ||r_0|| */
+  int line_search_max;  /* step halvings of the backtracking line search (0 = full steps) */
+  int coarse_solver;    /* coarsest assembled level: 0 Chebyshev(coarse_degree), 1 Jacobi-GMRES */
+  double coarse_rtol;   /* Jacobi-GMRES relative tolerance on the coarsest level */
+  int coarse_maxit;     /* Jacobi-GMRES iterations per coarse solve */
+  int verbose;          /* 1: one line per Newton iteration on stderr */
 } pff_solver_params;
 
 typedef struct {
@@ -220,15 +234,19 @@ typedef struct {
   int krylov_iterations;    /* summed over the Newton iterations */
   int converged;
   int status;               /* kernel status bits of a failed residual */
+  int line_search_cuts;     /* step halvings taken by the line search */
+  int coarse_iterations;    /* coarsest-level Krylov iterations, summed */
   double res0, res;         /* ||r|| at the first and the last residual */
   double last_krylov_relres;
   double t_residual, t_setup, t_krylov;  /* seconds, host clock around synchronised phases */
   double res_history[64];   /* ||r|| per Newton iteration */
 } pff_newton_stats;
 
-/* Fills the defaults: mixed 1, Chebyshev(3) on [0.1, 1.1] lambda_max, coarse
- * Chebyshev(16) on [0.02, 1.1], 10 power iterations, FGMRES(30) to 1e-3 with at
- * most 200 iterations, Newton to 1e-8 in at most 20 iterations. */
+/* Fills the defaults: mixed 1, Chebyshev(3) on [0.1, 1.1] lambda_max, coarsest
+ * assembled level solved by Jacobi-GMRES to 1e-2 (at most 200 iterations;
+ * Chebyshev(16) on [0.02, 1.1] when coarse_solver = 0), 10 Arnoldi steps,
+ * FGMRES(30) to 1e-3 with at most 200 iterations, Newton to 1e-8 in at most 20
+ * iterations with up to 8 line-search halvings, quiet. */
 int pff_solver_default_params(pff_solver_params* params);
 /* levels[0] = the fine level of op (pff_create_level with the fine order), then
  * coarser levels with decreasing order; if the last has order 1 its operator is
@@ -240,7 +258,9 @@ int pff_destroy_solver(pff_solver* solver);
 /* Diagonals, coarse assembly and lambda_max estimates for the current stored
  * linearisation (call after pff_residual).  Synchronises the stream. */
 int pff_solver_setup(pff_solver* solver, void* stream);
-/* lambda_max of D^-1 J estimated for a level by the last setup. */
+/* lambda_max of D^-1 J estimated for a level by the last setup (spectral radius of
+ * the Hessenberg matrix of power_iters Arnoldi steps from a seeded random-sign
+ * vector; power iteration on the assembled coarsest level). */
 int pff_solver_level_lambda(const pff_solver* solver, int level, double* lmax);
 /* One V-cycle z = M^-1 r on FP64 fine vectors. */
 int pff_solver_vcycle(pff_solver* solver, const double* r, double* z, void* stream);
@@ -250,8 +270,13 @@ int pff_solver_coarse_apply(pff_solver* solver, const double* x, double* y, void
 int pff_solver_krylov(pff_solver* solver, const double* b, double* x, double rtol, int maxit, int* iters,
                       double* relres, void* stream);
 /* Newton iterations on z (FP64 [4][N_n], Dirichlet values already imposed):
- * residual, setup, FGMRES to krylov_rtol, z -= dz, until newton_rtol. */
+ * residual, setup, FGMRES to krylov_rtol, backtracking line search on z - alpha dz
+ * (a residual with det F <= 0 or non-finite values counts as a rejected step),
+ * until newton_rtol.  The last residual evaluated is at the returned z. */
 int pff_newton_solve(pff_solver* solver, double* z, pff_newton_stats* stats, void* stream);
+
+/* y = a x + b y on n entries of the given precision (device vectors). */
+int pff_vec_axpby(pff_prec prec, int64_t n, double a, const void* x, double b, void* y, void* stream);
 
 /* Accept the trial history written by the last pff_residual (Box 1 step 4,
  * C_in^-1 = F^-1 exp(2 eps_e) F^-T; eps_p += dgamma; H = max(H_n, psi+);

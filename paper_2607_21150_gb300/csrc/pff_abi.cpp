@@ -378,6 +378,7 @@ int pff_destroy_operator(pff_op* op) {
   cudaFree(op->hist_c); cudaFree(op->hist_t); cudaFree(op->phase); cudaFree(op->flags);
   cudaFree(op->lin64); cudaFree(op->lin32); cudaFree(op->io); cudaFree(op->mask);
   cudaFree(op->dvals); cudaFree(op->status);
+  cudaFree(op->fint); cudaFree(op->sums);
   free_tables(op->tab);
   delete op;
   return PFF_OK;
@@ -465,6 +466,36 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   a.mask = op->mask;
   PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
   if (op->f32 && op->lin32) PFF_CK(launch_to_f32(op->lin64, op->lin32, op->lin_len, st));
+  return PFF_OK;
+}
+
+int pff_apply_dirichlet(pff_op* op, double* z, void* stream) {
+  PFF_REQUIRE(op && z, "pff_apply_dirichlet: null argument");
+  PFF_CK(launch_apply_dirichlet(z, op->dvals, op->mask, 4 * op->mesh.nn, S(stream)));
+  return PFF_OK;
+}
+
+int pff_reaction(pff_op* op, const uint8_t* sel, double* out4, void* stream) {
+  PFF_REQUIRE(op && sel && out4, "pff_reaction: null argument");
+  cudaStream_t st = S(stream);
+  const long long n = 4 * op->mesh.nn;
+  if (!op->fint) PFF_CK(cudaMalloc((void**)&op->fint, sizeof(double) * n));
+  if (!op->sums) PFF_CK(cudaMalloc((void**)&op->sums, sizeof(double) * 4));
+  PFF_CK(cudaMemsetAsync(op->fint, 0, sizeof(double) * n, st));
+  ElemArgs<double> a;
+  std::memset(&a, 0, sizeof(a));
+  a.mesh = op->mesh;
+  a.y = op->fint;
+  a.mask = nullptr;
+  a.B = op->tab.B64;
+  a.Dc = op->tab.Dc64;
+  a.Dt = op->tab.Dt64;
+  a.scratch = op->io;
+  a.nq = op->nq;
+  PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
+  PFF_CK(launch_masked_field_sums(op->fint, sel, op->mesh.nn, op->sums, st));
+  PFF_CK(cudaMemcpyAsync(out4, op->sums, sizeof(double) * 4, cudaMemcpyDeviceToHost, st));
+  PFF_CK(cudaStreamSynchronize(st));
   return PFF_OK;
 }
 

@@ -54,6 +54,8 @@ struct pff_op {
   double* dvals = nullptr;
   int* status = nullptr;
   int f32 = 0;
+  double* fint = nullptr;     // internal force work vector of pff_reaction (allocated on first use)
+  double* sums = nullptr;     // 4 doubles
 };
 
 struct pff_level {

@@ -107,6 +107,8 @@ cudaError_t launch_pointwise(const PointArgs& a, cudaStream_t st);
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
 cudaError_t launch_to_f32(const double* a, float* b, long long n, cudaStream_t st);
+cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st);
+cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st);
 cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st);
 template <typename T>
 cudaError_t launch_prolong(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* xc, T* xf,

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -59,9 +60,11 @@ struct pff_solver {
   std::vector<LevelWork> lv;
   bool assembled = false;
   double *A = nullptr, *cdiag = nullptr, *cb = nullptr, *cx = nullptr, *cwork = nullptr;
+  double *cV = nullptr, *cZ = nullptr;  // coarse GMRES basis
+  long long coarse_iters = 0;
   double clmax = 1.0;
   long long n = 0;
-  double *V = nullptr, *Z = nullptr, *r = nullptr, *dz = nullptr;
+  double *V = nullptr, *Z = nullptr, *r = nullptr, *dz = nullptr, *zold = nullptr;
   double *partial = nullptr, *dots = nullptr, *hdev = nullptr;
   double* pw64 = nullptr;  // power-iteration start vector (FP64, fine size)
   float* pw32 = nullptr;
@@ -93,7 +96,10 @@ int axpby_level(const LevelWork& w, void* y, const void* x, double a, double b, 
   return PFF_OK;
 }
 
+int coarse_gmres(pff_solver* s, cudaStream_t st);
+
 int coarse_cheb(pff_solver* s, cudaStream_t st) {
+  if (s->prm.coarse_solver == 1) return coarse_gmres(s, st);
   // FP64 Chebyshev-Jacobi on the assembled coarse operator, from x = 0.
   LevelWork& c = s->lv.back();
   const MeshDev& mc = c.L->mesh;
@@ -149,24 +155,75 @@ int vcycle(pff_solver* s, int l, cudaStream_t st) {
   return PFF_OK;
 }
 
-int power_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
-  // lambda_max of D^-1 J by power iteration from the seeded start vector.
-  void* v = w.x;
-  void* y = w.tmp;
-  if (w.prec == PFF_F64) S_CK(cudaMemcpyAsync(v, s->pw64, sizeof(double) * w.n, cudaMemcpyDeviceToDevice, st));
-  else S_CK(cudaMemcpyAsync(v, s->pw32, sizeof(float) * w.n, cudaMemcpyDeviceToDevice, st));
-  double nv;
-  S_RC(norm_level(s, w, v, &nv, st));
-  S_RC(axpby_level(w, v, v, 1.0 / nv, 0.0, st));
-  double lam = 1.0;
-  for (int it = 0; it < s->prm.power_iters; ++it) {
-    S_RC(pff_jacobian_apply(w.L, (pff_prec)w.prec, v, y, st));
-    if (w.prec == PFF_F64) S_CK(launch_dscale<double>((double*)y, (const double*)y, (const double*)w.diag, w.n, st));
-    else S_CK(launch_dscale<float>((float*)y, (const float*)y, (const float*)w.diag, w.n, st));
-    S_RC(norm_level(s, w, y, &lam, st));
-    if (!(lam > 0.0) || !std::isfinite(lam)) return sfail(PFF_ERR_DEVICE, "power iteration: non-finite eigenvalue estimate");
-    S_RC(axpby_level(w, v, y, 1.0 / lam, 0.0, st));
+// Spectral radius of a small dense matrix (row-major k x k) by power iteration
+// on the host, with the growth rate averaged over the last iterations so that a
+// dominant complex pair is measured too.
+double small_spectral_radius(const std::vector<double>& H, int k) {
+  std::vector<double> v(k, 1.0), y(k);
+  for (int i = 0; i < k; ++i) v[i] = 1.0 + 0.01 * i;
+  double logsum = 0.0;
+  int counted = 0;
+  for (int it = 0; it < 2000; ++it) {
+    double nrm = 0.0;
+    for (int i = 0; i < k; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += H[i * k + j] * v[j];
+      y[i] = s;
+      nrm += s * s;
+    }
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) return 0.0;
+    for (int i = 0; i < k; ++i) v[i] = y[i] / nrm;
+    if (it >= 1000) { logsum += std::log(nrm); ++counted; }
   }
+  return std::exp(logsum / counted);
+}
+
+// lambda_max of D^-1 J for a level: k Arnoldi steps (Gram-Schmidt twice, FP64
+// basis in the FGMRES storage) from a seeded random-sign vector; the estimate is
+// the spectral radius of the k x k Hessenberg block (the survey's reading of the
+// eigenvalue bound of a Chebyshev smoother: a few Arnoldi/Lanczos steps).
+int arnoldi_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
+  const long long n = w.n;
+  const int k = std::min(s->prm.power_iters, s->prm.krylov_restart);
+  double* V = s->V;  // (restart + 1) fine vectors >= (k + 1) level vectors
+  S_CK(cudaMemcpyAsync(V, s->pw64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  double h0;
+  S_RC(dev_dots(s, V, 0, 1, V, n, &h0, st));
+  S_CK(launch_axpby<double>(V, V, 1.0 / std::sqrt(h0), 0.0, n, st));
+  std::vector<double> H((k + 1) * k, 0.0), h(k + 2);
+  int kk = k;
+  for (int j = 0; j < k; ++j) {
+    double* vj = V + (long long)j * n;
+    double* wv = V + (long long)(j + 1) * n;
+    if (w.prec == PFF_F64) {
+      S_RC(pff_jacobian_apply(w.L, PFF_F64, vj, wv, st));
+      S_CK(launch_dscale<double>(wv, wv, (const double*)w.diag, n, st));
+    } else {
+      S_CK(launch_d2f((float*)w.x, vj, n, st));
+      S_RC(pff_jacobian_apply(w.L, PFF_F32, w.x, w.tmp, st));
+      S_CK(launch_dscale<float>((float*)w.tmp, (const float*)w.tmp, (const float*)w.diag, n, st));
+      S_CK(launch_f2d(wv, (const float*)w.tmp, n, st));
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+      S_RC(dev_dots(s, V, n, j + 1, wv, n, h.data(), st));
+      S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
+      S_CK(launch_maxpy(wv, V, n, j + 1, s->hdev, -1.0, n, st));
+      for (int i = 0; i <= j; ++i) H[i * k + j] += h[i];
+    }
+    double ww;
+    S_RC(dev_dots(s, wv, 0, 1, wv, n, &ww, st));
+    const double hn = std::sqrt(ww);
+    if (!std::isfinite(hn)) return sfail(PFF_ERR_DEVICE, "Arnoldi eigenvalue estimate: non-finite vector");
+    H[(j + 1) * k + j] = hn;
+    if (hn <= 1e-14 * std::fabs(H[j * k + j]) + 1e-300) { kk = j + 1; break; }
+    S_CK(launch_axpby<double>(wv, wv, 1.0 / hn, 0.0, n, st));
+  }
+  std::vector<double> Hk(kk * kk);
+  for (int i = 0; i < kk; ++i)
+    for (int j = 0; j < kk; ++j) Hk[i * kk + j] = H[i * k + j];
+  const double lam = small_spectral_radius(Hk, kk);
+  if (!(lam > 0.0) || !std::isfinite(lam)) return sfail(PFF_ERR_DEVICE, "Arnoldi eigenvalue estimate failed");
   w.lmax = lam;
   return PFF_OK;
 }
@@ -193,24 +250,31 @@ int power_coarse(pff_solver* s, cudaStream_t st) {
   return PFF_OK;
 }
 
-// FGMRES(m), right preconditioned (Saad, Alg. 9.6), FP64; classical
-// Gram-Schmidt with a second pass when the first one loses accuracy.
-int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
-           cudaStream_t st) {
-  const long long n = s->n;
-  const int m = s->prm.krylov_restart;
-  pff_level* F = s->lv[0].L;
+// Flexible GMRES(m), right preconditioned (Saad, Alg. 9.6), FP64; classical
+// Gram-Schmidt with a second pass when the first one loses accuracy (the
+// adaptive CGS refinement of Sec. 5).  V: (m+1) n, Z: m n device doubles.
+struct Krylov {
+  long long n = 0;
+  int m = 0;
+  double *V = nullptr, *Z = nullptr;
+};
+
+template <typename ApplyA, typename ApplyM>
+int gmres_flex(pff_solver* s, const Krylov& kw, ApplyA&& applyA, ApplyM&& applyM, const double* b, double* x,
+               double rtol, int maxit, int* iters, double* relres, cudaStream_t st) {
+  const long long n = kw.n;
+  const int m = kw.m;
   std::vector<double> H((m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0), h(m + 2), y(m);
   S_CK(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
   double beta0 = -1.0, res = 0.0;
   int total = 0;
   bool first = true;
   while (true) {
-    double* v0 = s->V;
+    double* v0 = kw.V;
     if (first) {
       S_CK(cudaMemcpyAsync(v0, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     } else {
-      S_RC(pff_jacobian_apply(F, PFF_F64, x, v0, st));
+      S_RC(applyA(x, v0));
       S_CK(launch_bminus<double>(v0, b, n, st));
     }
     double bb;
@@ -225,34 +289,25 @@ int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, in
     g[0] = beta;
     int jend = 0;
     for (int j = 0; j < m && total < maxit; ++j) {
-      double* vj = s->V + (long long)j * n;
-      double* zj = s->Z + (long long)j * n;
-      double* w = s->V + (long long)(j + 1) * n;
-      // z_j = M^-1 v_j (one V-cycle)
-      LevelWork& f = s->lv[0];
-      if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(f.b, vj, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-      else S_CK(launch_d2f((float*)f.b, vj, n, st));
-      S_RC(vcycle(s, 0, st));
-      if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(zj, f.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-      else S_CK(launch_f2d(zj, (const float*)f.x, n, st));
-      // w = J z_j
-      S_RC(pff_jacobian_apply(F, PFF_F64, zj, w, st));
-      // Gram-Schmidt: h = V^T w, |w|^2 in the same pass (w is V_{j+1})
-      S_RC(dev_dots(s, s->V, n, j + 2, w, n, h.data(), st));
+      double* vj = kw.V + (long long)j * n;
+      double* zj = kw.Z + (long long)j * n;
+      double* w = kw.V + (long long)(j + 1) * n;
+      S_RC(applyM(vj, zj));
+      S_RC(applyA(zj, w));
+      S_RC(dev_dots(s, kw.V, n, j + 2, w, n, h.data(), st));
       double ww = h[j + 1];
       S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
-      S_CK(launch_maxpy(w, s->V, n, j + 1, s->hdev, -1.0, n, st));
+      S_CK(launch_maxpy(w, kw.V, n, j + 1, s->hdev, -1.0, n, st));
       double hsq = 0.0;
       for (int i = 0; i <= j; ++i) hsq += h[i] * h[i];
       std::vector<double> hcol(h.begin(), h.begin() + j + 1);
-      // second pass: exact norm and the residual projection
-      S_RC(dev_dots(s, s->V, n, j + 2, w, n, h.data(), st));
+      S_RC(dev_dots(s, kw.V, n, j + 2, w, n, h.data(), st));
       double ww2 = h[j + 1];
       double h2sq = 0.0;
       for (int i = 0; i <= j; ++i) h2sq += h[i] * h[i];
       if (h2sq > 1e-24 * ww2 || ww - hsq < 0.5 * ww) {
         S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
-        S_CK(launch_maxpy(w, s->V, n, j + 1, s->hdev, -1.0, n, st));
+        S_CK(launch_maxpy(w, kw.V, n, j + 1, s->hdev, -1.0, n, st));
         for (int i = 0; i <= j; ++i) hcol[i] += h[i];
         ww2 = std::max(ww2 - h2sq, 0.0);
       }
@@ -260,7 +315,6 @@ int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, in
       for (int i = 0; i <= j; ++i) H[i * m + j] = hcol[i];
       H[(j + 1) * m + j] = hn;
       if (hn > 0.0) S_CK(launch_axpby<double>(w, w, 1.0 / hn, 0.0, n, st));
-      // Givens rotations
       for (int i = 0; i < j; ++i) {
         double a = H[i * m + j], c = H[(i + 1) * m + j];
         H[i * m + j] = cs[i] * a + sn[i] * c;
@@ -279,20 +333,76 @@ int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, in
       res = std::fabs(g[j + 1]);
       if (res <= rtol * beta0 || hn == 0.0) break;
     }
-    // x += Z y with H y = g (upper triangular)
     for (int i = jend - 1; i >= 0; --i) {
       double sum = g[i];
       for (int k = i + 1; k < jend; ++k) sum -= H[i * m + k] * y[k];
       y[i] = sum / H[i * m + i];
     }
     S_CK(cudaMemcpyAsync(s->hdev, y.data(), sizeof(double) * jend, cudaMemcpyHostToDevice, st));
-    S_CK(launch_maxpy(x, s->Z, n, jend, s->hdev, 1.0, n, st));
+    S_CK(launch_maxpy(x, kw.Z, n, jend, s->hdev, 1.0, n, st));
     S_CK(cudaStreamSynchronize(st));
     first = false;
     if (res <= rtol * beta0 || total >= maxit) break;
   }
   *iters = total;
   *relres = beta0 > 0 ? res / beta0 : 0.0;
+  return PFF_OK;
+}
+
+int precondition(pff_solver* s, const double* v, double* z, cudaStream_t st);
+
+int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, int* iters, double* relres,
+           cudaStream_t st) {
+  pff_level* F = s->lv[0].L;
+  Krylov kw;
+  kw.n = s->n;
+  kw.m = s->prm.krylov_restart;
+  kw.V = s->V;
+  kw.Z = s->Z;
+  auto A = [&](const double* in, double* out) { return pff_jacobian_apply(F, PFF_F64, in, out, st); };
+  auto M = [&](const double* in, double* out) { return precondition(s, in, out, st); };
+  return gmres_flex(s, kw, A, M, b, x, rtol, maxit, iters, relres, st);
+}
+
+// z = M^-1 v on FP64 fine vectors: one V-cycle (FP32 levels in the mixed variant).
+int precondition(pff_solver* s, const double* v, double* z, cudaStream_t st) {
+  LevelWork& f = s->lv[0];
+  const long long n = s->n;
+  if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(f.b, v, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_d2f((float*)f.b, v, n, st));
+  S_RC(vcycle(s, 0, st));
+  if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(z, f.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_f2d(z, (const float*)f.x, n, st));
+  return PFF_OK;
+}
+
+// Coarsest level: Jacobi-preconditioned GMRES on the assembled FP64 operator to
+// coarse_rtol (at most coarse_maxit iterations), from x = 0.
+int coarse_gmres(pff_solver* s, cudaStream_t st) {
+  LevelWork& c = s->lv.back();
+  const MeshDev& mc = c.L->mesh;
+  const long long n = c.n;
+  if (c.prec == PFF_F64) S_CK(cudaMemcpyAsync(s->cb, c.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_f2d(s->cb, (const float*)c.b, n, st));
+  Krylov kw;
+  kw.n = n;
+  kw.m = s->prm.krylov_restart;
+  kw.V = s->cV;
+  kw.Z = s->cZ;
+  auto A = [&](const double* in, double* out) -> int {
+    S_CK(launch_q1_spmv(mc, s->A, in, out, st));
+    return PFF_OK;
+  };
+  auto M = [&](const double* in, double* out) -> int {
+    S_CK(launch_dscale<double>(out, in, s->cdiag, n, st));
+    return PFF_OK;
+  };
+  int its = 0;
+  double rel = 0.0;
+  S_RC(gmres_flex(s, kw, A, M, s->cb, s->cx, s->prm.coarse_rtol, s->prm.coarse_maxit, &its, &rel, st));
+  s->coarse_iters += its;
+  if (c.prec == PFF_F64) S_CK(cudaMemcpyAsync(c.x, s->cx, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  else S_CK(launch_d2f((float*)c.x, s->cx, n, st));
   return PFF_OK;
 }
 
@@ -308,11 +418,11 @@ int setup(pff_solver* s, cudaStream_t st) {
     pff_op* op = s->op;
     S_CK(launch_q1_assemble(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->A, st));
     S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
-    S_RC(power_coarse(s, st));
+    if (s->prm.coarse_solver == 0) S_RC(power_coarse(s, st));
   }
   for (int l = 0; l < L; ++l) {
     if (l + 1 == L && s->assembled) continue;
-    S_RC(power_level(s, s->lv[l], st));
+    S_RC(arnoldi_level(s, s->lv[l], st));
   }
   return PFF_OK;
 }
@@ -322,7 +432,8 @@ void free_solver(pff_solver* s) {
     cudaFree(w.diag); cudaFree(w.b); cudaFree(w.x); cudaFree(w.tmp); cudaFree(w.work);
   }
   cudaFree(s->A); cudaFree(s->cdiag); cudaFree(s->cb); cudaFree(s->cx); cudaFree(s->cwork);
-  cudaFree(s->V); cudaFree(s->Z); cudaFree(s->r); cudaFree(s->dz);
+  cudaFree(s->cV); cudaFree(s->cZ);
+  cudaFree(s->V); cudaFree(s->Z); cudaFree(s->r); cudaFree(s->dz); cudaFree(s->zold);
   cudaFree(s->partial); cudaFree(s->dots); cudaFree(s->hdev);
   cudaFree(s->pw64); cudaFree(s->pw32);
 }
@@ -345,6 +456,11 @@ int pff_solver_default_params(pff_solver_params* p) {
   p->krylov_rtol = 1e-3;
   p->newton_maxit = 20;
   p->newton_rtol = 1e-8;
+  p->line_search_max = 8;
+  p->coarse_solver = 1;
+  p->coarse_rtol = 1e-2;
+  p->coarse_maxit = 200;
+  p->verbose = 0;
   return PFF_OK;
 }
 
@@ -387,26 +503,29 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     if (e == cudaSuccess) e = cudaMalloc(&s->cb, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->cx, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->cwork, sizeof(double) * 3 * nc);
+    if (e == cudaSuccess && prm->coarse_solver == 1) e = cudaMalloc(&s->cV, sizeof(double) * (prm->krylov_restart + 1) * nc);
+    if (e == cudaSuccess && prm->coarse_solver == 1) e = cudaMalloc(&s->cZ, sizeof(double) * prm->krylov_restart * nc);
   }
   const int m = prm->krylov_restart;
   if (e == cudaSuccess) e = cudaMalloc(&s->V, sizeof(double) * (m + 1) * s->n);
   if (e == cudaSuccess) e = cudaMalloc(&s->Z, sizeof(double) * m * s->n);
   if (e == cudaSuccess) e = cudaMalloc(&s->r, sizeof(double) * s->n);
   if (e == cudaSuccess) e = cudaMalloc(&s->dz, sizeof(double) * s->n);
+  if (e == cudaSuccess) e = cudaMalloc(&s->zold, sizeof(double) * s->n);
   if (e == cudaSuccess) e = cudaMalloc(&s->partial, sizeof(double) * 64 * kReduceBlocks);
   if (e == cudaSuccess) e = cudaMalloc(&s->dots, sizeof(double) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&s->hdev, sizeof(double) * 64);
   if (e == cudaSuccess) e = cudaMalloc(&s->pw64, sizeof(double) * s->n);
   if (e == cudaSuccess) e = cudaMalloc(&s->pw32, sizeof(float) * s->n);
   if (e == cudaSuccess) {
-    // seeded start vector of the power iterations (xorshift64*, uniform in [0.5, 1.5))
+    // seeded start vector of the eigenvalue estimates (xorshift64*, random signs)
     std::vector<double> h(s->n);
     std::vector<float> hf(s->n);
     unsigned long long st = 0x9E3779B97F4A7C15ull;
     for (long long i = 0; i < s->n; ++i) {
       st ^= st >> 12; st ^= st << 25; st ^= st >> 27;
       double u = (double)((st * 0x2545F4914F6CDD1Dull) >> 11) * (1.0 / 9007199254740992.0);
-      h[i] = 0.5 + u;
+      h[i] = (u < 0.5) ? -1.0 : 1.0;
       hf[i] = (float)h[i];
     }
     e = cudaMemcpy(s->pw64, h.data(), sizeof(double) * s->n, cudaMemcpyHostToDevice);
@@ -418,6 +537,15 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     return sfail(PFF_ERR_CUDA, std::string("pff_create_solver: ") + cudaGetErrorString(e));
   }
   *out = s;
+  return PFF_OK;
+}
+
+int pff_vec_axpby(pff_prec prec, int64_t n, double a, const void* x, double b, void* y, void* stream) {
+  if (!x || !y || n < 0) return sfail(PFF_ERR_INVALID, "pff_vec_axpby: bad argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (prec == PFF_F64) S_CK(launch_axpby<double>((double*)y, (const double*)x, a, b, n, st));
+  else if (prec == PFF_F32) S_CK(launch_axpby<float>((float*)y, (const float*)x, a, b, n, st));
+  else return sfail(PFF_ERR_INVALID, "pff_vec_axpby: unknown precision");
   return PFF_OK;
 }
 
@@ -441,14 +569,7 @@ int pff_solver_level_lambda(const pff_solver* s, int level, double* lmax) {
 
 int pff_solver_vcycle(pff_solver* s, const double* r, double* z, void* stream) {
   if (!s || !r || !z) return sfail(PFF_ERR_INVALID, "pff_solver_vcycle: null argument");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  LevelWork& f = s->lv[0];
-  if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(f.b, r, sizeof(double) * f.n, cudaMemcpyDeviceToDevice, st));
-  else S_CK(launch_d2f((float*)f.b, r, f.n, st));
-  S_RC(vcycle(s, 0, st));
-  if (f.prec == PFF_F64) S_CK(cudaMemcpyAsync(z, f.x, sizeof(double) * f.n, cudaMemcpyDeviceToDevice, st));
-  else S_CK(launch_f2d(z, (const float*)f.x, f.n, st));
-  return PFF_OK;
+  return precondition(s, r, z, reinterpret_cast<cudaStream_t>(stream));
 }
 
 int pff_solver_coarse_apply(pff_solver* s, const double* x, double* y, void* stream) {
@@ -467,16 +588,19 @@ int pff_newton_solve(pff_solver* s, double* z, pff_newton_stats* stats, void* st
   if (!s || !z || !stats) return sfail(PFF_ERR_INVALID, "pff_newton_solve: null argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   std::memset(stats, 0, sizeof(*stats));
+  s->coarse_iters = 0;
   const long long n = s->n;
   double r0 = -1.0;
   for (int it = 0;; ++it) {
     double t0 = now();
-    S_RC(pff_residual(s->op, z, s->r, st));
-    int status = 0;
-    S_RC(pff_get_status(s->op, stream, &status));
-    if (status) {
-      stats->status = status;
-      return sfail(PFF_ERR_DEVICE, "pff_newton_solve: residual kernel status " + std::to_string(status));
+    if (it == 0 || s->prm.line_search_max == 0) {
+      S_RC(pff_residual(s->op, z, s->r, st));
+      int status = 0;
+      S_RC(pff_get_status(s->op, stream, &status));
+      if (status) {
+        stats->status = status;
+        return sfail(PFF_ERR_DEVICE, "pff_newton_solve: residual kernel status " + std::to_string(status));
+      }
     }
     double rr;
     S_RC(dev_dots(s, s->r, 0, 1, s->r, n, &rr, st));
@@ -496,12 +620,42 @@ int pff_newton_solve(pff_solver* s, double* z, pff_newton_stats* stats, void* st
     int its = 0;
     double rel = 0.0;
     S_RC(fgmres(s, s->r, s->dz, s->prm.krylov_rtol, s->prm.krylov_maxit, &its, &rel, st));
-    S_CK(launch_axpby<double>(z, s->dz, -1.0, 1.0, n, st));
     S_CK(cudaStreamSynchronize(st));
     stats->t_krylov += now() - t0;
     stats->krylov_iterations += its;
     stats->newton_iterations = it + 1;
     stats->last_krylov_relres = rel;
+    stats->coarse_iterations = (int)s->coarse_iters;
+    if (s->prm.verbose)
+      std::fprintf(stderr, "[pff newton] it %d |r| %.6e |r|/|r0| %.3e krylov %d (rel %.2e) coarse its %lld t_res %.3f t_setup %.3f t_krylov %.3f\n",
+                   it, rn, rn / r0, its, rel, s->coarse_iters, stats->t_residual, stats->t_setup, stats->t_krylov);
+    // backtracking line search (Sec. 5): accept z - alpha dz once the residual is
+    // finite, every det F > 0 and ||r|| <= (1 - 1e-4 alpha) ||r_prev||; halve alpha
+    // otherwise.  The residual of the accepted point is the next iteration's.
+    t0 = now();
+    S_CK(cudaMemcpyAsync(s->zold, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    double alpha = 1.0;
+    bool accepted = false;
+    for (int ls = 0; ls <= s->prm.line_search_max; ++ls) {
+      S_CK(cudaMemcpyAsync(z, s->zold, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      S_CK(launch_axpby<double>(z, s->dz, -alpha, 1.0, n, st));
+      if (s->prm.line_search_max == 0) { accepted = true; break; }
+      S_RC(pff_residual(s->op, z, s->r, st));
+      int lst = 0;
+      S_RC(pff_get_status(s->op, stream, &lst));
+      double r2 = 0.0;
+      if (!lst) S_RC(dev_dots(s, s->r, 0, 1, s->r, n, &r2, st));
+      const double rt = std::sqrt(r2);
+      if (!lst && std::isfinite(rt) && rt <= (1.0 - 1e-4 * alpha) * rn) { accepted = true; break; }
+      if (!lst && std::isfinite(rt) && ls == s->prm.line_search_max) { accepted = true; break; }
+      alpha *= 0.5;
+      stats->line_search_cuts += 1;
+    }
+    stats->t_residual += now() - t0;
+    if (!accepted) {
+      S_CK(cudaMemcpyAsync(z, s->zold, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      return sfail(PFF_ERR_DEVICE, "pff_newton_solve: line search found no admissible step");
+    }
   }
   return PFF_OK;
 }

@@ -219,6 +219,47 @@ cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, c
   return cudaGetLastError();
 }
 
+
+// z = ubar on Dirichlet DoFs (other entries untouched).
+__global__ void k_apply_dirichlet(double* __restrict__ z, const double* __restrict__ ubar,
+                                  const uint8_t* __restrict__ mask, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (mask[i]) z[i] = ubar ? ubar[i] : 0.0;
+}
+cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st) {
+  if (n == 0 || !mask) return cudaSuccess;
+  k_apply_dirichlet<<<grid_for(n), kVecThreads, 0, st>>>(z, ubar, mask, n);
+  return cudaGetLastError();
+}
+
+// out[f] += sum over nodes n with sel[f][n] of v[f][n] (FP64, per-block partial
+// sums combined with atomics).
+__global__ void k_masked_field_sums(const double* __restrict__ v, const uint8_t* __restrict__ sel, long long nn,
+                                    double* __restrict__ out) {
+  __shared__ double red[4][kVecThreads / 32];
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn; i += (long long)gridDim.x * blockDim.x)
+    for (int f = 0; f < 4; ++f)
+      if (sel[f * nn + i]) s[f] += v[f * nn + i];
+  for (int f = 0; f < 4; ++f) {
+    double t = s[f];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[f][threadIdx.x >> 5] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < kVecThreads / 32; ++w) t += red[threadIdx.x][w];
+    atomicAdd(out + threadIdx.x, t);
+  }
+}
+cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), st);
+  if (e != cudaSuccess || nn == 0) return e;
+  k_masked_field_sums<<<grid_for(nn), kVecThreads, 0, st>>>(v, sel, nn, out);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_prolong<double>(const MeshDev&, const MeshDev&, const double*, const double*, double*,
                                             const uint8_t*, const uint8_t*, cudaStream_t);
 template cudaError_t launch_prolong<float>(const MeshDev&, const MeshDev&, const float*, const float*, float*,

@@ -38,12 +38,16 @@ class pff_solver_params(ctypes.Structure):
     _fields_ = [("mixed", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("cheb_lo", ctypes.c_double),
                 ("cheb_hi", ctypes.c_double), ("coarse_degree", ctypes.c_int), ("coarse_lo", ctypes.c_double),
                 ("power_iters", ctypes.c_int), ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int),
-                ("krylov_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int), ("newton_rtol", ctypes.c_double)]
+                ("krylov_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int), ("newton_rtol", ctypes.c_double),
+                ("line_search_max", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_rtol", ctypes.c_double),
+                ("coarse_maxit", ctypes.c_int), ("verbose", ctypes.c_int)]
 
 
 class pff_newton_stats(ctypes.Structure):
     _fields_ = [("newton_iterations", ctypes.c_int), ("krylov_iterations", ctypes.c_int),
-                ("converged", ctypes.c_int), ("status", ctypes.c_int), ("res0", ctypes.c_double),
+                ("converged", ctypes.c_int), ("status", ctypes.c_int), ("line_search_cuts", ctypes.c_int),
+                ("coarse_iterations", ctypes.c_int),
+                ("res0", ctypes.c_double),
                 ("res", ctypes.c_double), ("last_krylov_relres", ctypes.c_double),
                 ("t_residual", ctypes.c_double), ("t_setup", ctypes.c_double), ("t_krylov", ctypes.c_double),
                 ("res_history", ctypes.c_double * 64)]
@@ -77,6 +81,8 @@ _SIGS = {
     "pff_set_qpoint_state": ([_VP, _VP, _VP, _VP], _I),
     "pff_set_dirichlet": ([_VP, _VP, _VP, _VP], _I),
     "pff_residual": ([_VP, _VP, _VP, _VP], _I),
+    "pff_apply_dirichlet": ([_VP, _VP, _VP], _I),
+    "pff_reaction": ([_VP, _VP, ctypes.POINTER(_D), _VP], _I),
     "pff_create_level": ([_VP, _I, ctypes.POINTER(_VP)], _I),
     "pff_destroy_level": ([_VP], _I),
     "pff_level_num_nodes": ([_VP], _I64),
@@ -97,6 +103,7 @@ _SIGS = {
     "pff_solver_coarse_apply": ([_VP, _VP, _VP, _VP], _I),
     "pff_solver_krylov": ([_VP, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP], _I),
     "pff_newton_solve": ([_VP, _VP, ctypes.POINTER(pff_newton_stats), _VP], _I),
+    "pff_vec_axpby": ([_I, _I64, _D, _VP, _D, _VP, _VP], _I),
     "pff_commit_history": ([_VP, _VP], _I),
     "pff_get_history": ([_VP, _I, _VP, _VP], _I),
     "pff_get_flags": ([_VP, _VP, _VP], _I),
@@ -241,6 +248,16 @@ def pff_residual(op, z, r, stream=None):
     _call("pff_residual", op, _ptr(z), _ptr(r), _stream(stream))
 
 
+def pff_apply_dirichlet(op, z, stream=None):
+    _call("pff_apply_dirichlet", op, _ptr(z), _stream(stream))
+
+
+def pff_reaction(op, sel, stream=None):
+    out = (_D * 4)()
+    _call("pff_reaction", op, _ptr(sel), out, _stream(stream))
+    return [float(v) for v in out]
+
+
 def pff_create_level(op, p):
     h = _VP()
     _call("pff_create_level", op, int(p), ctypes.byref(h))
@@ -339,6 +356,10 @@ def pff_newton_solve(solver, z, stream=None):
     st = pff_newton_stats()
     _call("pff_newton_solve", solver, _ptr(z), ctypes.byref(st), _stream(stream))
     return st.as_dict()
+
+
+def pff_vec_axpby(prec, n, a, x, b, y, stream=None):
+    _call("pff_vec_axpby", int(prec), int(n), float(a), _ptr(x), float(b), _ptr(y), _stream(stream))
 
 
 def pff_commit_history(op, stream=None):

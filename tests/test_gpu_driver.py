@@ -1,0 +1,79 @@
+"""Load stepping and the reaction force on the GPU vs the oracle.
+
+* pff_reaction = the oracle's internal force summed over the top-face u_z DoFs;
+* three load steps of the tension box (Newton to 1e-11, history committed after
+  every step) reproduce the oracle's trajectory (Newton with direct solves,
+  commit of its own trial history) to 1e-9 in the fields and the reactions.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_21150_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2607_21150_gb300 import pff  # noqa: E402
+from paper_2607_21150_gb300.driver import LoadStepper  # noqa: E402
+from paper_2607_21150_gb300.session import Session  # noqa: E402
+
+
+def _tension_box(at=2):
+    m = inputs.Mesh(2, 2, 3, 2, 3, (0.02, 0.02, 0.03))
+    rng = np.random.default_rng(5)
+    phases = np.stack([inputs.phase_vector(inputs.EX3_MATRIX), inputs.phase_vector(inputs.EX3_PARTICLE)])
+    glob = inputs.glob_vector(at, 1e-3, 1e-2, 0.002 / 0.4, inputs.s_phi_of(inputs.EX3_MATRIX, at))
+    phase = (rng.random(m.nq) < 0.3).astype(np.uint8)
+    mask, dv = inputs.dirichlet_tension(m, 0.002 * m.L[2])
+    hist = inputs.zero_history(m.nq)
+    if at == 1:
+        for pid, d in ((0, inputs.EX3_MATRIX), (1, inputs.EX3_PARTICLE)):
+            hist[13, phase == pid] = 3 * d["Gc"] / (16 * d["l0"])
+    return inputs.Workload("tension", m, phases, glob, phase, np.zeros((4, m.nn)), hist, mask, dv)
+
+
+def test_reaction_matches_oracle_internal_force(orc):
+    w = _tension_box()
+    rng = np.random.default_rng(2)
+    w.z = inputs.random_state(w.mesh, 3, u_amp=1e-4, phi_max=0.2)
+    s = Session(w)
+    s.residual(torch.from_numpy(w.z.ravel()).cuda())
+    top = inputs.top_face_mask(w.mesh)
+    got = pff.pff_reaction(s.op, torch.from_numpy(top.ravel()).cuda())
+    fint = orc.assemble(w, matrix=False, mask=None, dvals=None)["r"]
+    ref = [float(fint[f][top[f].astype(bool)].sum()) for f in range(4)]
+    assert abs(got[2] - ref[2]) <= 1e-12 * np.abs(fint).max() * top.sum()
+    assert got[0] == 0.0 and got[3] == 0.0
+
+
+@pytest.mark.parametrize("at", [1, 2])
+def test_load_steps_match_oracle(orc, at):
+    w = _tension_box(at)
+    lsp = LoadStepper(w, levels=[2, 1], mixed=False, newton_rtol=1e-11, krylov_rtol=1e-8)
+    # oracle trajectory
+    z = w.z.copy()
+    hist = w.hist.copy()
+    mk = w.mask.astype(bool)
+    top = inputs.top_face_mask(w.mesh).astype(bool)
+    for k in (1, 2, 3):
+        wk = inputs.Workload("t", w.mesh, w.phases, w.glob, w.phase, z, hist, w.mask, w.dvals * k)
+        z = z.copy()
+        z[mk] = (w.dvals * k)[mk]
+        wk.z = z
+        z, hres, out = orc.newton(wk, rtol=1e-13)
+        hist = out["hist_new"]
+        fint = orc.assemble(inputs.Workload("t", w.mesh, w.phases, w.glob, w.phase, z, wk.hist, None, None),
+                            matrix=False, mask=None, dvals=None)["r"]
+        react = float(fint[2][top[2]].sum())
+        st = lsp.step(k)
+        assert st["converged"] == 1
+        zg = lsp.z.cpu().numpy().reshape(4, -1)
+        assert np.linalg.norm(zg - z) <= 1e-9 * np.linalg.norm(z)
+        assert abs(st["reaction"] - react) <= 1e-8 * abs(react)
+        hg = lsp.s.history(0).cpu().numpy()
+        assert np.linalg.norm(hg - hist) <= 1e-9 * np.linalg.norm(hist)
+    assert lsp.history[-1]["reaction"] > lsp.history[0]["reaction"] > 0
+    lsp.close()
