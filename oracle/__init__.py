@@ -73,6 +73,9 @@ def lib():
         L.orc_prolong_coo.restype = ctypes.c_longlong
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_csr_spmv.argtypes = [ctypes.c_longlong, llp, llp, dp, dp, dp]
+        L.orc_point_partials.argtypes = [ctypes.c_int, dp, dp, u8p, dp, ctypes.c_int, dp, dp, dp]
+        L.orc_qpoint_inputs.argtypes = [ip, dp, dp, dp]
+        L.orc_apply_bt.argtypes = [ip, dp, dp, ctypes.c_int, dp]
         _lib = L
     return _lib
 
@@ -323,3 +326,113 @@ def newton(w, rtol=1e-12, maxit=20):
             break
         z = z - spla.spsolve(out["K"].tocsc(), r)
     return z.reshape(4, -1), hist, out
+
+
+# ---------------------------------------------------------------------------
+# Discrete adjoint of a load-step sequence (assembled transposes, direct solves)
+# ---------------------------------------------------------------------------
+# Parameter vector theta (12): for phase k in (0, 1) the six entries
+# E_inf, nu_inf, sigma0, eta_d, Gc, l0 at 6 k + (0..5).
+PARAM_SLOTS = (2, 3, 11, 7, 0, 1)   # positions in the 12-double phase row
+
+
+def set_params(phases, theta):
+    ph = np.array(phases, dtype=np.float64, copy=True)
+    th = np.asarray(theta, dtype=np.float64).reshape(-1, 6)
+    for k in range(min(len(ph), len(th))):
+        for j, slot in enumerate(PARAM_SLOTS):
+            ph[k, slot] = th[k, j]
+    return ph
+
+
+def get_params(phases):
+    return np.array([[p[s] for s in PARAM_SLOTS] for p in phases]).ravel()
+
+
+def point_partials(inputs, hist, phase, phases, glob):
+    """Values [n, 28] and partials [n, 28, 34] of (integrands, trial history) at n points."""
+    inputs = _f64(inputs)
+    n = inputs.shape[0]
+    vals = np.zeros((n, 28))
+    J = np.zeros((n, 28, 34))
+    lib().orc_point_partials(n, _p(inputs), _p(_f64(hist)), _p(_u8(phase), ctypes.c_uint8), _p(_f64(phases)),
+                             len(phases), _p(_f64(glob)), _p(vals), _p(J))
+    return vals, J
+
+
+def qpoint_inputs(mesh, y):
+    dims, h = _mesh_args(mesh)
+    out = np.zeros((mesh.nq, 14))
+    lib().orc_qpoint_inputs(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(y)), _p(out))
+    return out[:, :13], out[:, 13]
+
+
+def apply_bt(mesh, pseudo, weighted):
+    dims, h = _mesh_args(mesh)
+    out = np.zeros(4 * mesh.nn)
+    lib().orc_apply_bt(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(pseudo)),
+                       1 if weighted else 0, _p(out))
+    return out
+
+
+def load_steps(w, theta, nsteps, top, rtol=1e-13):
+    """Forward load steps: step n imposes n times the workload's Dirichlet values,
+    solves by Newton with direct solves and commits the trial history.  Returns
+    reactions [nsteps], states z_n and committed histories h_0..h_nsteps."""
+    import copy
+    ww = copy.copy(w)
+    ww.phases = set_params(w.phases, theta)
+    z = np.array(w.z, dtype=np.float64, copy=True)
+    hist = np.array(w.hist, dtype=np.float64, copy=True)
+    mk = w.mask.astype(bool)
+    zs, hs, F = [], [hist.copy()], []
+    for n in range(1, nsteps + 1):
+        ww.hist = hist
+        ww.dvals = w.dvals * n
+        z = z.copy()
+        z[mk] = ww.dvals[mk]
+        ww.z = z
+        z, _, out = newton(ww, rtol=rtol)
+        fint = assemble(ww, z=z, matrix=False, mask=None, dvals=None)["r"]
+        F.append(float(fint[top.astype(bool)].sum()))
+        zs.append(z.copy())
+        hist = out["hist_new"]
+        hs.append(hist.copy())
+    return np.array(F), zs, hs
+
+
+def adjoint_gradient(w, theta, nsteps, top, target):
+    """Gradient of L = sum_n (F_n - target_n)^2 with respect to theta by the
+    discrete adjoint: backward over the load steps, J_n^T lam = g with the
+    assembled CSR transpose, local partials by dual numbers."""
+    import copy
+    import scipy.sparse.linalg as spla
+    F, zs, hs = load_steps(w, theta, nsteps, top)
+    ww = copy.copy(w)
+    ww.phases = set_params(w.phases, theta)
+    m = w.mesh
+    mk = w.mask.astype(bool).ravel()
+    sel = top.astype(np.float64).ravel()
+    hbar = np.zeros((m.nq, 15))
+    gtheta = np.zeros(12)
+    for n in range(nsteps, 0, -1):
+        z, hprev = zs[n - 1], hs[n - 1]
+        ww.hist = hprev
+        ww.dvals = w.dvals * n
+        wF = 2.0 * (F[n - 1] - target[n - 1])
+        a, wq = qpoint_inputs(m, z)
+        _, Jp = point_partials(a, hprev.T.copy(), w.phase, ww.phases, w.glob)
+        K = assemble(ww, z=z, matrix=True)["K"]
+        Kint = assemble(ww, z=z, matrix=True, mask=None, dvals=None)["K"]
+        qa = np.einsum("qr,qrc->qc", hbar, Jp[:, 13:28, 0:13])
+        g = wF * (Kint.T @ sel) + apply_bt(m, qa, weighted=False)
+        g[mk] = 0.0
+        lam = spla.spsolve(K.T.tocsc(), g)
+        pv, _ = qpoint_inputs(m, (wF * sel - lam).reshape(4, -1))
+        p = pv * wq[:, None]
+        hb_new = np.einsum("qr,qrc->qc", p, Jp[:, 0:13, 13:28]) + np.einsum("qr,qrc->qc", hbar, Jp[:, 13:28, 13:28])
+        gq = np.einsum("qr,qrc->qc", p, Jp[:, 0:13, 28:34]) + np.einsum("qr,qrc->qc", hbar, Jp[:, 13:28, 28:34])
+        for k in range(len(w.phases)):
+            gtheta[6 * k:6 * k + 6] += gq[w.phase == k].sum(axis=0)
+        hbar = hb_new
+    return gtheta, F

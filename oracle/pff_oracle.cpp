@@ -247,11 +247,13 @@ M3<double> expm(const M3<double>& A) {
 // ----------------------------------------------------------------------------
 // Phase parameters, 12 doubles: Gc, l0, E_inf, nu_inf, hasM, E1, nu1, eta_d,
 // hasP, E2, nu2, sigma0  (units mm, MPa, s; eta_d = +inf allowed).
-struct Phase {
-  double Gc, l0, E0, nu0;
-  int hasM; double E1, nu1, eta;
-  int hasP; double E2, nu2, sig0;
+template <typename T>
+struct PhaseT {
+  T Gc, l0, E0, nu0;
+  int hasM; T E1, nu1, eta; bool eta_inf;
+  int hasP; T E2, nu2, sig0;
 };
+typedef PhaseT<double> Phase;
 // Global parameters, 5 doubles: AT (1 or 2), eta (residual stiffness),
 // zeta (damage viscosity), dt, s_phi.
 struct Glob { int at; double eta_res, zeta, dt, s_phi; };
@@ -259,9 +261,16 @@ struct Glob { int at; double eta_res, zeta, dt, s_phi; };
 static Phase read_phase(const double* p) {
   Phase ph;
   ph.Gc = p[0]; ph.l0 = p[1]; ph.E0 = p[2]; ph.nu0 = p[3];
-  ph.hasM = p[4] != 0.0; ph.E1 = p[5]; ph.nu1 = p[6]; ph.eta = p[7];
+  ph.hasM = p[4] != 0.0; ph.E1 = p[5]; ph.nu1 = p[6]; ph.eta = p[7]; ph.eta_inf = !std::isfinite(p[7]);
   ph.hasP = p[8] != 0.0; ph.E2 = p[9]; ph.nu2 = p[10]; ph.sig0 = p[11];
   return ph;
+}
+template <typename T> PhaseT<T> lift(const Phase& p) {
+  PhaseT<T> q;
+  q.Gc = T(p.Gc); q.l0 = T(p.l0); q.E0 = T(p.E0); q.nu0 = T(p.nu0);
+  q.hasM = p.hasM; q.E1 = T(p.E1); q.nu1 = T(p.nu1); q.eta = T(p.eta_inf ? 1.0 : p.eta); q.eta_inf = p.eta_inf;
+  q.hasP = p.hasP; q.E2 = T(p.E2); q.nu2 = T(p.nu2); q.sig0 = T(p.sig0);
+  return q;
 }
 static Glob read_glob(const double* g) {
   Glob gl; gl.at = (int)g[0]; gl.eta_res = g[1]; gl.zeta = g[2]; gl.dt = g[3]; gl.s_phi = g[4];
@@ -271,21 +280,40 @@ static Glob read_glob(const double* g) {
 static const int VOIGT_I[6] = {0, 1, 2, 1, 0, 0};
 static const int VOIGT_J[6] = {0, 1, 2, 2, 2, 1};
 
+// exp(A) by scaling and squaring of the Taylor series (term count and scaling
+// decided on primal values, so that dual parts follow the same expression).
+template <typename T> M3<T> expm_t(const M3<T>& A) {
+  double r = frob_val(A);
+  int s = 0;
+  while (r > 0.25) { r *= 0.5; ++s; }
+  M3<T> As = scale(A, std::ldexp(1.0, -s));
+  M3<T> S = eye3<T>(), term = eye3<T>();
+  for (int k = 1; k < 40; ++k) {
+    term = scale(mul(term, As), 1.0 / (double)k);
+    S = add(S, term);
+    if (frob_val(term) < 1e-22) break;
+  }
+  for (int i = 0; i < s; ++i) S = mul(S, S);
+  return S;
+}
+
 template <typename T>
 struct PointResult {
   T f0[4];
   T f1[4][3];
+  T hist_new[15];
   uint8_t flags;
   double psi_plus, margin_yield, margin_hist, theta;
-  double hist_new[15];
 };
 
 // Pointwise update at one quadrature point.  G = grad_X u (G[i][A] = du_i/dX_A),
-// phi, gphi = grad_X phi; hist = committed history (15 words); commit = also
-// produce the trial history of Box 1 step 4 (primal only).
+// phi, gphi = grad_X phi; hist = committed history (15 words); ph = the
+// point's phase parameters; commit = also produce the trial history of Box 1
+// step 4.  Every input may carry dual parts (history and parameters included),
+// so the same function gives the tangent and the adjoint's local partials.
 template <typename T>
-void pointwise(const T G[3][3], const T& phi, const T gphi[3], const double* hist,
-               const Phase& ph, const Glob& gl, bool commit, PointResult<T>& out) {
+void pointwise(const T G[3][3], const T& phi, const T gphi[3], const T* hist,
+               const PhaseT<T>& ph, const Glob& gl, bool commit, PointResult<T>& out) {
   M3<T> Gm;
   for (int i = 0; i < 3; ++i) for (int A = 0; A < 3; ++A) Gm.a[i][A] = G[i][A];
   M3<T> F = add(eye3<T>(), Gm);
@@ -305,29 +333,29 @@ void pointwise(const T G[3][3], const T& phi, const T gphi[3], const double* his
 
   M3<T> taud = zero3<T>();
   T psid = T(0.0);
-  double kap_tot = 0.0;
+  T kap_tot = T(0.0);
   out.flags = 0;
   out.margin_yield = INFINITY;  // no yield decision without a Prandtl branch
-  double dgam_v = 0.0;
-  M3<double> epsE_M = zero3<double>(), epsE_P = zero3<double>();
+  T dgam = T(0.0);
+  M3<T> epsE_M = zero3<T>(), epsE_P = zero3<T>();
 
   for (int br = 0; br < 3; ++br) {
-    double E, nu;
-    const double* Ch = nullptr;
+    T E, nu;
+    const T* Ch = nullptr;
     if (br == 0) { E = ph.E0; nu = ph.nu0; }
     else if (br == 1) { if (!ph.hasM) continue; E = ph.E1; nu = ph.nu1; Ch = hist + 0; }
     else { if (!ph.hasP) continue; E = ph.E2; nu = ph.nu2; Ch = hist + 6; }
-    double mu = E / (2.0 * (1.0 + nu));
-    double kap = E / (3.0 * (1.0 - 2.0 * nu));
-    kap_tot += kap;
+    T mu = E / (2.0 * (1.0 + nu));
+    T kap = E / (3.0 * (1.0 - 2.0 * nu));
+    kap_tot = kap_tot + kap;
     // Elastic predictor (Box 1 step 1): b_tr - I = F (C - I) F^T + (F F^T - I)
     M3<T> X = GGt;
     if (Ch) {
       M3<T> CmI;
       for (int v = 0; v < 6; ++v) {
-        double c = Ch[v] - (v < 3 ? 1.0 : 0.0);
-        CmI.a[VOIGT_I[v]][VOIGT_J[v]] = T(c);
-        CmI.a[VOIGT_J[v]][VOIGT_I[v]] = T(c);
+        T c = Ch[v] - (v < 3 ? 1.0 : 0.0);
+        CmI.a[VOIGT_I[v]][VOIGT_J[v]] = c;
+        CmI.a[VOIGT_J[v]][VOIGT_I[v]] = c;
       }
       X = add(X, mul(mul(F, CmI), transpose(F)));
     }
@@ -339,24 +367,22 @@ void pointwise(const T G[3][3], const T& phi, const T gphi[3], const double* his
     // Correction step (Box 1 step 2) with degradation inside the branch (Sec. 3)
     T a = T(1.0);
     if (br == 1) {
-      if (std::isfinite(ph.eta)) a = 1.0 / (1.0 + g * (mu * gl.dt / ph.eta));
+      if (!ph.eta_inf) a = 1.0 / (1.0 + g * (mu * gl.dt / ph.eta));
     } else if (br == 2) {
-      double qv = 2.0 * mu * std::sqrt(1.5 * val(s));
-      double fv = val(g) * qv - ph.sig0;  // degraded admissibility check
-      out.margin_yield = fv / ph.sig0;
+      double qv = 2.0 * val(mu) * std::sqrt(1.5 * val(s));
+      double fv = val(g) * qv - val(ph.sig0);  // degraded admissibility check
+      out.margin_yield = fv / val(ph.sig0);
       if (fv > 0.0) {
         T q = 2.0 * mu * sqrt(1.5 * s);
         a = ph.sig0 / (g * q);
-        dgam_v = fv / (3.0 * val(g) * mu);
+        dgam = (g * q - ph.sig0) / (3.0 * g * mu);
         out.flags |= 1;
       }
     }
     taud = add(taud, scale(Ed, 2.0 * mu * a));
     psid = psid + mu * a * a * s;
     if (commit && Ch) {
-      M3<double> e;
-      for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j)
-        e.a[i][j] = val(a) * val(Ed.a[i][j]) + (i == j ? val(theta) / 3.0 : 0.0);
+      M3<T> e = add(scale(Ed, a), scale(eye3<T>(), theta / 3.0));
       if (br == 1) epsE_M = e; else epsE_P = e;
     }
   }
@@ -375,17 +401,16 @@ void pointwise(const T G[3][3], const T& phi, const T gphi[3], const double* his
     taudeg = add(scale(taud, g), scale(eye3<T>(), tauv));
   }
   // Miehe history field (Sec. 3.3), strict activity (R4)
-  double Hn = hist[13];
-  bool active = val(psip) > Hn;
+  const T& Hn = hist[13];
+  bool active = val(psip) > val(Hn);
   if (active) out.flags |= 2;
-  T H = active ? psip : T(Hn);
-  double denom = std::max(std::fabs(Hn), std::fabs(val(psip)));
-  out.margin_hist = denom > 0 ? (val(psip) - Hn) / denom : 0.0;
+  T H = active ? psip : Hn;
+  double denom = std::max(std::fabs(val(Hn)), std::fabs(val(psip)));
+  out.margin_hist = denom > 0 ? (val(psip) - val(Hn)) / denom : 0.0;
   // local phase-field residual L (Eq. L-viscous)
   double c0 = (gl.at == 1) ? 8.0 / 3.0 : 2.0;
-  double Gc = ph.Gc, l0 = ph.l0;
   T alphap = (gl.at == 1) ? T(1.0) : 2.0 * phi;
-  T L = gp * H + (Gc / (c0 * l0)) * alphap + gl.zeta * (phi - hist[14]) / gl.dt;
+  T L = gp * H + (ph.Gc / (c0 * ph.l0)) * alphap + gl.zeta * (phi - hist[14]) / gl.dt;
   // integrands in the reference frame: P = tau_degr F^-T, s_phi L, s_phi k grad_X phi
   for (int i = 0; i < 3; ++i) out.f0[i] = T(0.0);
   out.f0[3] = gl.s_phi * L;
@@ -396,7 +421,7 @@ void pointwise(const T G[3][3], const T& phi, const T gphi[3], const double* his
       s = s + taudeg.a[i][2] * Finv.a[A][2];
       out.f1[i][A] = s;
     }
-  double kphi = gl.s_phi * 2.0 * Gc * l0 / c0;
+  T kphi = gl.s_phi * 2.0 * ph.Gc * ph.l0 / c0;
   for (int A = 0; A < 3; ++A) out.f1[3][A] = kphi * gphi[A];
   out.psi_plus = val(psip);
   out.theta = val(theta);
@@ -404,20 +429,18 @@ void pointwise(const T G[3][3], const T& phi, const T gphi[3], const double* his
   if (commit) {
     // Box 1 step 4: C_in^-1 = F^-1 exp(2 eps_e) F^-T, plus eps_p, H, phi_n
     for (int v = 0; v < 15; ++v) out.hist_new[v] = hist[v];
-    M3<double> Fi, FiT;
-    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) Fi.a[i][j] = val(Finv.a[i][j]);
-    FiT = transpose(Fi);
+    M3<T> FiT = transpose(Finv);
     if (ph.hasM) {
-      M3<double> C = mul(mul(Fi, expm(scale(epsE_M, 2.0))), FiT);
+      M3<T> C = mul(mul(Finv, expm_t(scale(epsE_M, 2.0))), FiT);
       for (int v = 0; v < 6; ++v) out.hist_new[v] = C.a[VOIGT_I[v]][VOIGT_J[v]];
     }
     if (ph.hasP) {
-      M3<double> C = mul(mul(Fi, expm(scale(epsE_P, 2.0))), FiT);
+      M3<T> C = mul(mul(Finv, expm_t(scale(epsE_P, 2.0))), FiT);
       for (int v = 0; v < 6; ++v) out.hist_new[6 + v] = C.a[VOIGT_I[v]][VOIGT_J[v]];
-      out.hist_new[12] = hist[12] + dgam_v;
+      out.hist_new[12] = hist[12] + dgam;
     }
-    out.hist_new[13] = active ? val(psip) : Hn;
-    out.hist_new[14] = val(phi);
+    out.hist_new[13] = H;
+    out.hist_new[14] = phi;
   }
 }
 
@@ -595,7 +618,9 @@ static void element_eval(const Problem& pr, long long e, double* re, double* Dh,
       phid.d[9] = 1.0;
       for (int A = 0; A < 3; ++A) { gphid[A] = D13(gphi[A]); gphid[A].d[10 + A] = 1.0; }
       PointResult<D13> pt;
-      pointwise<D13>(Gd, phid, gphid, hq, ph, pr.gl, false, pt);
+      D13 hqd[15];
+      for (int v = 0; v < 15; ++v) hqd[v] = D13(hq[v]);
+      pointwise<D13>(Gd, phid, gphid, hqd, lift<D13>(ph), pr.gl, false, pt);
       double* D = Dh + (size_t)q * 256;
       for (int i = 0; i < 256; ++i) D[i] = 0.0;
       // seed -> input column: grad u_iA -> 4+3i+A, phi -> 3, grad phi_A -> 13+A
@@ -742,7 +767,9 @@ int orc_pointwise(int n, const double* inputs, const double* hist, const uint8_t
       phid.d[9] = 1.0;
       for (int A = 0; A < 3; ++A) { gphid[A] = D13(gphi[A]); gphid[A].d[10 + A] = 1.0; }
       PointResult<D13> pt;
-      pointwise<D13>(Gd, phid, gphid, hist + 15 * (size_t)k, ph, gl, false, pt);
+      D13 hqd[15];
+      for (int v = 0; v < 15; ++v) hqd[v] = D13(hist[15 * (size_t)k + v]);
+      pointwise<D13>(Gd, phid, gphid, hqd, lift<D13>(ph), gl, false, pt);
       double* D = Dh + 256 * (size_t)k;
       for (int i = 0; i < 256; ++i) D[i] = 0.0;
       int colOf[13];
@@ -987,6 +1014,101 @@ long long orc_prolong_coo(const int* dims, int pc, int pf, long long* rows, long
     }
   }
   return cnt;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint building blocks
+// ---------------------------------------------------------------------------
+typedef Dual<34> D34;
+
+// Per point: values out_vals[n][28] = (P_iA (9), s_phi L, f1_phi (3), trial
+// history (15)) and partials out_J[n][28][34] with respect to (grad u (9), phi,
+// grad phi (3), committed history (15), own-phase parameters E_inf, nu_inf,
+// sigma0, eta_d, Gc, l0), all by dual numbers through the same pointwise code.
+int orc_point_partials(int n, const double* inputs, const double* hist, const uint8_t* phase,
+                       const double* phase_params, int nphase, const double* glob, double* out_vals,
+                       double* out_J) {
+  std::vector<Phase> phases;
+  for (int i = 0; i < nphase; ++i) phases.push_back(read_phase(phase_params + 12 * i));
+  Glob gl = read_glob(glob);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int k = 0; k < n; ++k) {
+    const double* in = inputs + 13 * (size_t)k;
+    D34 Gd[3][3], phid, gphid[3], hd[15];
+    for (int i = 0; i < 3; ++i) for (int A = 0; A < 3; ++A) { Gd[i][A] = D34(in[3 * i + A]); Gd[i][A].d[3 * i + A] = 1.0; }
+    phid = D34(in[9]); phid.d[9] = 1.0;
+    for (int A = 0; A < 3; ++A) { gphid[A] = D34(in[10 + A]); gphid[A].d[10 + A] = 1.0; }
+    for (int v = 0; v < 15; ++v) { hd[v] = D34(hist[15 * (size_t)k + v]); hd[v].d[13 + v] = 1.0; }
+    const Phase& ph = phases[phase[k]];
+    PhaseT<D34> pd = lift<D34>(ph);
+    pd.E0.d[28] = 1.0; pd.nu0.d[29] = 1.0;
+    if (ph.hasP) pd.sig0.d[30] = 1.0;
+    if (ph.hasM && !ph.eta_inf) pd.eta.d[31] = 1.0;
+    pd.Gc.d[32] = 1.0; pd.l0.d[33] = 1.0;
+    PointResult<D34> pt;
+    pointwise<D34>(Gd, phid, gphid, hd, pd, gl, true, pt);
+    const D34* outs[28];
+    for (int i = 0; i < 3; ++i) for (int A = 0; A < 3; ++A) outs[3 * i + A] = &pt.f1[i][A];
+    outs[9] = &pt.f0[3];
+    for (int A = 0; A < 3; ++A) outs[10 + A] = &pt.f1[3][A];
+    for (int v = 0; v < 15; ++v) outs[13 + v] = &pt.hist_new[v];
+    for (int r = 0; r < 28; ++r) {
+      out_vals[28 * (size_t)k + r] = outs[r]->v;
+      for (int c = 0; c < 34; ++c) out_J[(28 * (size_t)k + r) * 34 + c] = outs[r]->d[c];
+    }
+  }
+  return 0;
+}
+
+// Interpolation of a nodal field y [4][nn] to every quadrature point:
+// out[nq][14] = (grad_X y_u (9), y_phi, grad_X y_phi (3), w_q det J).
+int orc_qpoint_inputs(const int* dims, const double* h, const double* y, double* out) {
+  Mesh m = make_mesh(dims, h);
+  ElemBasis eb = elem_basis(m);
+  long long nel = (long long)m.nx * m.ny * m.nz;
+  int P3 = eb.P3, Q3 = eb.Q3;
+#pragma omp parallel for schedule(static)
+  for (long long e = 0; e < nel; ++e) {
+    std::vector<long long> nodes(P3);
+    elem_nodes(m, e, nodes.data());
+    for (int q = 0; q < Q3; ++q) {
+      double* o = out + 14 * (size_t)(e * Q3 + q);
+      for (int c = 0; c < 13; ++c) o[c] = 0.0;
+      for (int a = 0; a < P3; ++a) {
+        const double* dNa = &eb.dN[(q * P3 + a) * 3];
+        for (int i = 0; i < 3; ++i) for (int A = 0; A < 3; ++A) o[3 * i + A] += y[i * m.nn + nodes[a]] * dNa[A];
+        o[9] += y[3 * m.nn + nodes[a]] * eb.N[q * P3 + a];
+        for (int A = 0; A < 3; ++A) o[10 + A] += y[3 * m.nn + nodes[a]] * dNa[A];
+      }
+      o[13] = eb.wdet[q];
+    }
+  }
+  return 0;
+}
+
+// out [4][nn] = sum_q B_q^T pseudo_q (optionally times w_q det J): the
+// transpose of orc_qpoint_inputs, with pseudo[nq][13] in the same layout.
+int orc_apply_bt(const int* dims, const double* h, const double* pseudo, int weighted, double* out) {
+  Mesh m = make_mesh(dims, h);
+  ElemBasis eb = elem_basis(m);
+  long long nel = (long long)m.nx * m.ny * m.nz;
+  int P3 = eb.P3, Q3 = eb.Q3;
+  for (long long i = 0; i < 4 * m.nn; ++i) out[i] = 0.0;
+  std::vector<long long> nodes(P3);
+  for (long long e = 0; e < nel; ++e) {
+    elem_nodes(m, e, nodes.data());
+    for (int q = 0; q < Q3; ++q) {
+      const double* p = pseudo + 13 * (size_t)(e * Q3 + q);
+      double w = weighted ? eb.wdet[q] : 1.0;
+      for (int a = 0; a < P3; ++a) {
+        const double* dNa = &eb.dN[(q * P3 + a) * 3];
+        for (int i = 0; i < 3; ++i)
+          out[i * m.nn + nodes[a]] += w * (p[3 * i] * dNa[0] + p[3 * i + 1] * dNa[1] + p[3 * i + 2] * dNa[2]);
+        out[3 * m.nn + nodes[a]] += w * (p[9] * eb.N[q * P3 + a] + p[10] * dNa[0] + p[11] * dNa[1] + p[12] * dNa[2]);
+      }
+    }
+  }
+  return 0;
 }
 
 // y = A x for a CSR matrix (plain row loop, OpenMP over rows): the oracle's

@@ -44,6 +44,12 @@ EX3_MATRIX = dict(Gc=0.8, l0=0.005, E0=1.0 * GPA, nu0=0.3,
                   maxwell=(1.0 * GPA, 0.3, 0.01 * GPA),
                   prandtl=(198 * GPA, 0.30, 500.0))
 EX2_PARTICLE = dict(Gc=0.1, l0=0.01, E0=10 * GPA, nu0=0.3)
+# Adjoint workload: the Example 3 particle phase with a Maxwell (eta_d = 1 GPa s)
+# and a perfectly plastic Prandtl branch (sigma0 = 5 GPa, E2 = E_inf) so that
+# none of the twelve parameter gradients is structurally zero.
+EX3_PARTICLE_ADJ = dict(Gc=8.0, l0=0.005, E0=400 * GPA, nu0=0.25,
+                        maxwell=(400 * GPA, 0.25, 1.0 * GPA),
+                        prandtl=(400 * GPA, 0.25, 5000.0))
 EX2_MATRIX = dict(Gc=0.01, l0=0.01, E0=1.0 * GPA, nu0=0.4,
                   maxwell=(1.0 * GPA, 0.4, 0.1 * GPA))
 
@@ -413,7 +419,9 @@ def cube(nx: int = 4, p: int = 2, seed_state: int = 0, hist_seed: int | None = N
 def two_phase_box(nx, ny, nz, p, L, sph_mean, sph_sd, vf, seed, at, example, bc, delta,
                   dt, eta=1e-3, zeta=1e-2, notch=False) -> Workload:
     m = Mesh(nx, ny, nz, p, p + 1, L)
-    if example == 3:
+    if example == "3adj":
+        matrix, particle = EX3_MATRIX, EX3_PARTICLE_ADJ
+    elif example == 3:
         matrix, particle = EX3_MATRIX, EX3_PARTICLE
     else:
         matrix, particle = EX2_MATRIX, EX2_PARTICLE
@@ -469,7 +477,7 @@ def notched_q3(n: int = 48, seed: int = 0) -> Workload:
 def adjoint_q2(n: int = 24, seed: int = 0) -> Workload:
     L = 0.01 * n
     strain_per_step = 0.001
-    w = two_phase_box(n, n, n, 2, (L, L, L), 0.06, 0.02, 0.6, seed, 2, 3, "tension",
+    w = two_phase_box(n, n, n, 2, (L, L, L), 0.06, 0.02, 0.6, seed, 2, "3adj", "tension",
                       strain_per_step * L, strain_per_step / 0.4)
     w.name = "adjoint_q2"
     w.meta.update(steps=20, strain_per_step=strain_per_step)
@@ -529,3 +537,10 @@ def element_offsets(m: Mesh) -> np.ndarray:
     J = m.p * ey[:, None] + B.ravel()[None, :]
     K = m.p * ez[:, None] + C.ravel()[None, :]
     return (I + m.nnx * (J + m.nny * K)).astype(np.int32)
+
+
+def twin_target(theta, seed: int = 1, sigma: float = 0.1):
+    """Parameters of the twin experiment that generates the target reaction
+    curve: theta scaled by seeded lognormal factors (sigma 0.1)."""
+    rng = np.random.default_rng(seed)
+    return np.asarray(theta) * np.exp(rng.normal(0.0, sigma, len(theta)))
