@@ -275,6 +275,25 @@ int pff_solver_krylov(pff_solver* solver, const double* b, double* x, double rto
  * until newton_rtol.  The last residual evaluated is at the returned z. */
 int pff_newton_solve(pff_solver* solver, double* z, pff_newton_stats* stats, void* stream);
 
+/* One reverse step of the discrete adjoint of a load-step sequence (the paper
+ * derives no adjoint; this extends its linearisation, App. B/C, to the
+ * committed history and the phase parameters).  For step n with converged
+ * state z_n (device FP64 [4][N_n]) and committed history of the previous step
+ * hist_prev (device [15][N_q]), reaction F_n = sum of the internal force over
+ * the DoFs selected by sel (device uint8 [4][N_n]) and dL/dF_n = wF:
+ *   recompute the linearisation at (z_n, hist_prev) (the operator's committed
+ *   history becomes hist_prev), solve J_n^T lam = wF J_int^T sel +
+ *   (dPhi/dz)^T hbar_n (Dirichlet entries zero) by FGMRES to rtol with the
+ *   transposed p-multigrid cycle, then
+ *   hbar_prev = (wF sel - lam)^T dR/dh + hbar_n^T dPhi/dh   (device [15][N_q]) and
+ *   grad[6 k + j] += (wF sel - lam)^T dR/dtheta_kj + hbar_n^T dPhi/dtheta_kj
+ * with theta_k = (E_inf, nu_inf, sigma0, eta_d, Gc, l0) of phase k (grad: HOST
+ * array of 6 nphase doubles).  hbar_n = NULL means zero (last step).  Phi is the
+ * trial history map, R the residual.  Synchronises the stream. */
+int pff_adjoint_step(pff_solver* solver, const double* z, const double* hist_prev, const uint8_t* sel, double wF,
+                     const double* hbar_n, double* hbar_prev, double* grad, double rtol, int maxit, int* iters,
+                     void* stream);
+
 /* y = a x + b y on n entries of the given precision (device vectors). */
 int pff_vec_axpby(pff_prec prec, int64_t n, double a, const void* x, double b, void* y, void* stream);
 

@@ -255,6 +255,12 @@ int pff_create_context(pff_ctx** out, const pff_problem* pr) {
       ph.kap_tot += ph.kap[b];
     }
     ph.cmax = (ph.has[1] && std::isfinite(v[7])) ? ph.mu[1] * pr->dt / v[7] : 0.0;
+    ph.E0 = v[2];
+    ph.nu0 = v[3];
+    ph.eta_d = (ph.has[1] && std::isfinite(v[7])) ? v[7] : 0.0;
+    ph.Gc = v[0];
+    ph.l0 = v[1];
+    ph.c0 = c0;
     ph.sig0 = v[11];
     ph.gc_c0l0 = v[0] / (c0 * v[1]);
     ph.kphi = pr->s_phi * 2.0 * v[0] * v[1] / c0;

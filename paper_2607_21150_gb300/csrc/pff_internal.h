@@ -29,6 +29,8 @@ struct PhaseDev {
   double kap_tot;
   double gc_c0l0;         // Gc / (c0 l0)
   double kphi;            // s_phi * 2 Gc l0 / c0
+  // raw parameters (adjoint): Hooke E, nu; Maxwell eta_d (0 = infinite); Gc, l0; c0
+  double E0, nu0, eta_d, Gc, l0, c0;
 };
 
 struct GlobDev {
@@ -69,6 +71,28 @@ struct PointArgs {
   int* status;            // device status word (bit0 eigen sweeps, bit1 J <= 0, bit2 non-finite, bit3 phase id)
   int want_tangent;
 };
+
+// Adjoint of the pointwise update (pff_adjoint.cu).  Mode 0: qa = (dPhi/da)^T hbar
+// as parent-frame pseudo-integrands [13][nq]; mode 1: hbar_out = p^T df/dh +
+// hbar^T dPhi/dh [15][nq] and gtheta[phase*6 + j] += p^T df/dtheta_j +
+// hbar^T dPhi/dtheta_j (theta_j = E_inf, nu_inf, sigma0, eta_d, Gc, l0).
+struct AdjArgs {
+  PhaseDev phase[kMaxPhase];
+  GlobDev glob;
+  Geom geom;
+  int Q, nphase, mode;
+  long long nq;
+  const double* a_in;     // [13][nq] grad_X u, phi, grad_X phi
+  const double* hist;     // [15][nq] committed history of the step
+  const uint8_t* phase_id;
+  const double* p;        // [13][nq] interpolated adjoint (reference frame), mode 1
+  const double* hbar;     // [15][nq] adjoint of the trial history (may be null)
+  double* qa_out;         // mode 0
+  double* hbar_out;       // mode 1
+  double* gtheta;         // mode 1, [nphase][6]
+  int* status;
+};
+cudaError_t launch_adjoint_point(const AdjArgs& a, cudaStream_t st);
 
 // Element-kernel launches (pff_elem*.cu).  T = double or float.
 enum ElemMode { kApply = 0, kEval = 1, kBack = 2 };
@@ -145,6 +169,9 @@ cudaError_t launch_q1_assemble(const MeshDev& mc, int Q, const double* lin, cons
                                const uint8_t* maskc, double* A, cudaStream_t st);
 cudaError_t launch_q1_spmv(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st);
+cudaError_t launch_q1_spmv_t(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
+cudaError_t launch_sel_scale(double* y, const uint8_t* sel, double s, long long n, cudaStream_t st);
+cudaError_t launch_zero_masked(double* y, const uint8_t* mask, long long n, cudaStream_t st);
 
 // Records the message returned by pff_last_error_message and returns code (pff_abi.cpp).
 int set_last_error(int code, const char* msg);

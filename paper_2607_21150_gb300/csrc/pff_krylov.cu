@@ -265,6 +265,51 @@ __global__ void k_q1_spmv(MeshDev mc, const double* __restrict__ A, const double
   }
   for (int f = 0; f < 4; ++f) y[f * mc.nn + n] = acc[f];
 }
+// y = A^T x with the stencil storage: row (g, m) of A^T gathers the entries
+// A[(f, n), (g, m)] of the nodes n = m - offset(slot).
+__global__ void k_q1_spmv_t(MeshDev mc, const double* __restrict__ A, const double* __restrict__ x,
+                            double* __restrict__ y) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= mc.nn) return;
+  const int nnz_ = (int)(mc.nn / ((long long)mc.nnx * mc.nny));
+  const int I = (int)(m % mc.nnx), J = (int)((m / mc.nnx) % mc.nny), K = (int)(m / ((long long)mc.nnx * mc.nny));
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int slot = 0; slot < 27; ++slot) {
+    const int dx = slot % 3 - 1, dy = (slot / 3) % 3 - 1, dz = slot / 9 - 1;
+    const int I2 = I - dx, J2 = J - dy, K2 = K - dz;
+    if (I2 < 0 || J2 < 0 || K2 < 0 || I2 >= mc.nnx || J2 >= mc.nny || K2 >= nnz_) continue;
+    const long long n = I2 + (long long)mc.nnx * (J2 + (long long)mc.nny * K2);
+    double xv[4];
+    for (int f = 0; f < 4; ++f) xv[f] = x[f * mc.nn + n];
+    for (int f = 0; f < 4; ++f)
+      for (int g = 0; g < 4; ++g) acc[g] += A[(long long)(slot * 16 + f * 4 + g) * mc.nn + n] * xv[f];
+  }
+  for (int g = 0; g < 4; ++g) y[g * mc.nn + m] = acc[g];
+}
+cudaError_t launch_q1_spmv_t(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st) {
+  k_q1_spmv_t<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, x, y);
+  return cudaGetLastError();
+}
+
+// y = s * sel (uint8 selector to FP64), and zeroing of Dirichlet entries.
+__global__ void k_sel_scale(double* __restrict__ y, const uint8_t* __restrict__ sel, double s, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = sel[i] ? s : 0.0;
+}
+__global__ void k_zero_masked(double* __restrict__ y, const uint8_t* __restrict__ mask, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    if (mask[i]) y[i] = 0.0;
+}
+cudaError_t launch_sel_scale(double* y, const uint8_t* sel, double s, long long n, cudaStream_t st) {
+  k_sel_scale<<<kRedBlocks * 2, 256, 0, st>>>(y, sel, s, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_zero_masked(double* y, const uint8_t* mask, long long n, cudaStream_t st) {
+  if (!mask) return cudaSuccess;
+  k_zero_masked<<<kRedBlocks * 2, 256, 0, st>>>(y, mask, n);
+  return cudaGetLastError();
+}
+
 __global__ void k_q1_diag(MeshDev mc, const double* __restrict__ A, double* __restrict__ d) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= mc.nn) return;

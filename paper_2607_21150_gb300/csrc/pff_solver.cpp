@@ -68,6 +68,9 @@ struct pff_solver {
   double *partial = nullptr, *dots = nullptr, *hdev = nullptr;
   double* pw64 = nullptr;  // power-iteration start vector (FP64, fine size)
   float* pw32 = nullptr;
+  int transpose = 0;       // 1 while solving with J^T (adjoint)
+  // adjoint work space (allocated on the first pff_adjoint_step)
+  double *a_in = nullptr, *pbuf = nullptr, *qa = nullptr, *ag = nullptr, *alam = nullptr, *av = nullptr, *gth = nullptr;
 };
 
 namespace {
@@ -98,6 +101,50 @@ int axpby_level(const LevelWork& w, void* y, const void* x, double a, double b, 
 
 int coarse_gmres(pff_solver* s, cudaStream_t st);
 
+int level_apply(pff_solver* s, const LevelWork& w, const void* x, void* y, cudaStream_t st) {
+  if (s->transpose) return pff_jacobian_transpose_apply(w.L, (pff_prec)w.prec, x, y, st);
+  return pff_jacobian_apply(w.L, (pff_prec)w.prec, x, y, st);
+}
+
+// Chebyshev smoothing (Saad, Alg. 12.1) of J x = b or, in transposed mode,
+// J^T x = b (same eigenvalue bounds: D^-1 J^T and D^-1 J have the same spectrum).
+int cheb_level(pff_solver* s, LevelWork& w, int degree, double lmin, double lmax, cudaStream_t st) {
+  const long long n = w.n;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  char* base = (char*)w.work;
+  void* r = base;
+  void* d = base + w.esz * n;
+  void* Ad = base + 2 * w.esz * n;
+  S_RC(level_apply(s, w, w.x, Ad, st));
+  if (w.prec == PFF_F64)
+    S_CK(launch_cheb_init<double>(n, (const double*)w.b, (const double*)Ad, (const double*)w.diag, (double*)r, (double*)d, 1.0 / theta, st));
+  else
+    S_CK(launch_cheb_init<float>(n, (const float*)w.b, (const float*)Ad, (const float*)w.diag, (float*)r, (float*)d, 1.0 / theta, st));
+  for (int k = 0; k < degree; ++k) {
+    const bool last = (k == degree - 1);
+    double cd = 0.0, cr = 0.0;
+    if (!last) {
+      S_RC(level_apply(s, w, d, Ad, st));
+      const double rho_new = 1.0 / (2.0 * sigma - rho);
+      cd = rho_new * rho;
+      cr = 2.0 * rho_new / delta;
+      rho = rho_new;
+    }
+    if (w.prec == PFF_F64)
+      S_CK(launch_cheb_step<double>(n, (double*)w.x, (double*)d, (double*)r, (const double*)Ad, (const double*)w.diag, cd, cr, last, st));
+    else
+      S_CK(launch_cheb_step<float>(n, (float*)w.x, (float*)d, (float*)r, (const float*)Ad, (const float*)w.diag, cd, cr, last, st));
+  }
+  return PFF_OK;
+}
+
+int coarse_spmv(pff_solver* s, const MeshDev& mc, const double* x, double* y, cudaStream_t st) {
+  if (s->transpose) S_CK(launch_q1_spmv_t(mc, s->A, x, y, st));
+  else S_CK(launch_q1_spmv(mc, s->A, x, y, st));
+  return PFF_OK;
+}
+
 int coarse_cheb(pff_solver* s, cudaStream_t st) {
   if (s->prm.coarse_solver == 1) return coarse_gmres(s, st);
   // FP64 Chebyshev-Jacobi on the assembled coarse operator, from x = 0.
@@ -121,7 +168,7 @@ int coarse_cheb(pff_solver* s, cudaStream_t st) {
       S_CK(launch_cheb_step<double>(n, s->cx, d, r, Ad, s->cdiag, 0.0, 0.0, 1, st));
       break;
     }
-    S_CK(launch_q1_spmv(mc, s->A, d, Ad, st));
+    S_RC(coarse_spmv(s, mc, d, Ad, st));
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     S_CK(launch_cheb_step<double>(n, s->cx, d, r, Ad, s->cdiag, rho_new * rho, 2.0 * rho_new / delta, 0, st));
     rho = rho_new;
@@ -138,11 +185,10 @@ int vcycle(pff_solver* s, int l, cudaStream_t st) {
   S_CK(cudaMemsetAsync(w.x, 0, w.esz * w.n, st));
   const int deg = coarsest ? s->prm.coarse_degree : s->prm.cheb_degree;
   const double lo = coarsest ? s->prm.coarse_lo : s->prm.cheb_lo;
-  S_RC(pff_chebyshev_smooth(w.L, (pff_prec)w.prec, deg, lo * w.lmax, s->prm.cheb_hi * w.lmax, w.diag, w.b, w.x,
-                            w.work, st));
+  S_RC(cheb_level(s, w, deg, lo * w.lmax, s->prm.cheb_hi * w.lmax, st));
   if (coarsest) return PFF_OK;
   // residual, restriction, coarse correction, prolongation
-  S_RC(pff_jacobian_apply(w.L, (pff_prec)w.prec, w.x, w.tmp, st));
+  S_RC(level_apply(s, w, w.x, w.tmp, st));
   if (w.prec == PFF_F64) S_CK(launch_bminus<double>((double*)w.tmp, (const double*)w.b, w.n, st));
   else S_CK(launch_bminus<float>((float*)w.tmp, (const float*)w.b, w.n, st));
   LevelWork& c = s->lv[l + 1];
@@ -150,8 +196,7 @@ int vcycle(pff_solver* s, int l, cudaStream_t st) {
   S_RC(vcycle(s, l + 1, st));
   S_RC(pff_prolong(c.L, w.L, (pff_prec)w.prec, c.x, w.tmp, st));
   S_RC(axpby_level(w, w.x, w.tmp, 1.0, 1.0, st));
-  S_RC(pff_chebyshev_smooth(w.L, (pff_prec)w.prec, s->prm.cheb_degree, s->prm.cheb_lo * w.lmax,
-                            s->prm.cheb_hi * w.lmax, w.diag, w.b, w.x, w.work, st));
+  S_RC(cheb_level(s, w, s->prm.cheb_degree, s->prm.cheb_lo * w.lmax, s->prm.cheb_hi * w.lmax, st));
   return PFF_OK;
 }
 
@@ -359,7 +404,10 @@ int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, in
   kw.m = s->prm.krylov_restart;
   kw.V = s->V;
   kw.Z = s->Z;
-  auto A = [&](const double* in, double* out) { return pff_jacobian_apply(F, PFF_F64, in, out, st); };
+  auto A = [&](const double* in, double* out) {
+    if (s->transpose) return pff_jacobian_transpose_apply(F, PFF_F64, in, out, st);
+    return pff_jacobian_apply(F, PFF_F64, in, out, st);
+  };
   auto M = [&](const double* in, double* out) { return precondition(s, in, out, st); };
   return gmres_flex(s, kw, A, M, b, x, rtol, maxit, iters, relres, st);
 }
@@ -389,10 +437,7 @@ int coarse_gmres(pff_solver* s, cudaStream_t st) {
   kw.m = s->prm.krylov_restart;
   kw.V = s->cV;
   kw.Z = s->cZ;
-  auto A = [&](const double* in, double* out) -> int {
-    S_CK(launch_q1_spmv(mc, s->A, in, out, st));
-    return PFF_OK;
-  };
+  auto A = [&](const double* in, double* out) -> int { return coarse_spmv(s, mc, in, out, st); };
   auto M = [&](const double* in, double* out) -> int {
     S_CK(launch_dscale<double>(out, in, s->cdiag, n, st));
     return PFF_OK;
@@ -436,6 +481,8 @@ void free_solver(pff_solver* s) {
   cudaFree(s->V); cudaFree(s->Z); cudaFree(s->r); cudaFree(s->dz); cudaFree(s->zold);
   cudaFree(s->partial); cudaFree(s->dots); cudaFree(s->hdev);
   cudaFree(s->pw64); cudaFree(s->pw32);
+  cudaFree(s->a_in); cudaFree(s->pbuf); cudaFree(s->qa); cudaFree(s->ag); cudaFree(s->alam); cudaFree(s->av);
+  cudaFree(s->gth);
 }
 
 }  // namespace
@@ -661,3 +708,134 @@ int pff_newton_solve(pff_solver* s, double* z, pff_newton_stats* stats, void* st
 }
 
 }  // extern "C"
+
+namespace {
+
+template <typename T>
+cudaError_t elem_launch(int Q, int P, int mode, const ElemArgs<T>& a, cudaStream_t st) {
+  switch (Q) {
+    case 2: return launch_elem_q2<T>(P, mode, a, st);
+    case 3: return launch_elem_q3<T>(P, mode, a, st);
+    case 4: return launch_elem_q4<T>(P, mode, a, st);
+    case 5: return launch_elem_q5<T>(P, mode, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+ElemArgs<double> fine_args(pff_op* op) {
+  ElemArgs<double> a;
+  std::memset(&a, 0, sizeof(a));
+  a.mesh = op->mesh;
+  a.B = op->tab.B64;
+  a.Dc = op->tab.Dc64;
+  a.Dt = op->tab.Dt64;
+  a.lin = op->lin64;
+  a.nq = op->nq;
+  for (int d = 0; d < 3; ++d) a.s[d] = op->geom.s[d];
+  return a;
+}
+
+AdjArgs adj_args(pff_op* op) {
+  AdjArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int i = 0; i < op->ctx->nphase; ++i) a.phase[i] = op->ctx->phase[i];
+  a.glob = op->ctx->glob;
+  a.geom = op->geom;
+  a.Q = op->Q;
+  a.nphase = op->ctx->nphase;
+  a.nq = op->nq;
+  a.hist = op->hist_c;
+  a.phase_id = op->phase;
+  a.status = op->status;
+  return a;
+}
+
+}  // namespace
+
+extern "C" int pff_adjoint_step(pff_solver* s, const double* z, const double* hist_prev, const uint8_t* sel,
+                                double wF, const double* hbar_n, double* hbar_prev, double* grad, double rtol,
+                                int maxit, int* iters, void* stream) {
+  if (!s || !z || !hist_prev || !sel || !hbar_prev || !grad || !iters)
+    return sfail(PFF_ERR_INVALID, "pff_adjoint_step: null argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  pff_op* op = s->op;
+  const long long nq = op->nq, n = s->n;
+  cudaError_t e = cudaSuccess;
+  if (!s->a_in) {
+    if (e == cudaSuccess) e = cudaMalloc(&s->a_in, sizeof(double) * 13 * nq);
+    if (e == cudaSuccess) e = cudaMalloc(&s->pbuf, sizeof(double) * 13 * nq);
+    if (e == cudaSuccess) e = cudaMalloc(&s->qa, sizeof(double) * 13 * nq);
+    if (e == cudaSuccess) e = cudaMalloc(&s->ag, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->alam, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->av, sizeof(double) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&s->gth, sizeof(double) * kMaxPhase * 6);
+    if (e != cudaSuccess) return sfail(PFF_ERR_CUDA, std::string("pff_adjoint_step: ") + cudaGetErrorString(e));
+  }
+  // 1. linearisation at (z_n, h_{n-1}): recomputed from the checkpoint
+  S_CK(cudaMemcpyAsync(op->hist_c, hist_prev, sizeof(double) * 15 * nq, cudaMemcpyDeviceToDevice, st));
+  S_RC(pff_residual(op, z, s->r, st));
+  int status = 0;
+  S_RC(pff_get_status(op, stream, &status));
+  if (status) return sfail(PFF_ERR_DEVICE, "pff_adjoint_step: residual kernel status " + std::to_string(status));
+  S_RC(setup(s, st));
+  // point inputs a(q)
+  ElemArgs<double> ea = fine_args(op);
+  ea.x = z;
+  ea.scratch = s->a_in;
+  S_CK(elem_launch<double>(op->Q, op->p + 1, kEval, ea, st));
+  // 2. right-hand side g = wF J_int^T sel + B^T [(dPhi/da)^T hbar_n], zero on Dirichlet DoFs
+  S_CK(cudaMemsetAsync(s->ag, 0, sizeof(double) * n, st));
+  if (hbar_n) {
+    AdjArgs aa = adj_args(op);
+    aa.mode = 0;
+    aa.a_in = s->a_in;
+    aa.hbar = hbar_n;
+    aa.qa_out = s->qa;
+    S_CK(launch_adjoint_point(aa, st));
+    ElemArgs<double> eb = fine_args(op);
+    eb.y = s->ag;
+    eb.scratch = s->qa;
+    S_CK(elem_launch<double>(op->Q, op->p + 1, kBack, eb, st));
+  }
+  S_CK(launch_sel_scale(s->av, sel, wF, n, st));
+  {
+    ElemArgs<double> et = fine_args(op);
+    const long long stride = (long long)op->Q * op->Q * op->Q * elems_per_block(op->Q);
+    et.x = s->av;
+    et.y = s->ag;
+    et.linP = op->lin64 + kWC * stride;
+    et.linC = op->lin64 + kWP * stride;
+    et.transpose = 1;
+    S_CK(elem_launch<double>(op->Q, op->p + 1, kApply, et, st));
+  }
+  S_CK(launch_zero_masked(s->ag, op->mask, n, st));
+  // 3. adjoint solve J_n^T lam = g (Dirichlet rows/columns identity, g = 0 there)
+  s->transpose = 1;
+  double rel = 0.0;
+  int rc = fgmres(s, s->ag, s->alam, rtol, maxit, iters, &rel, st);
+  s->transpose = 0;
+  if (rc) return rc;
+  // 4. pull-back p = interpolation of (wF sel - lam) to the Gauss points
+  S_CK(launch_axpby<double>(s->av, s->alam, -1.0, 1.0, n, st));
+  ElemArgs<double> ep = fine_args(op);
+  ep.x = s->av;
+  ep.scratch = s->pbuf;
+  S_CK(elem_launch<double>(op->Q, op->p + 1, kEval, ep, st));
+  // 5. history adjoint of the previous step and parameter gradient
+  S_CK(cudaMemsetAsync(s->gth, 0, sizeof(double) * kMaxPhase * 6, st));
+  AdjArgs ab = adj_args(op);
+  ab.mode = 1;
+  ab.a_in = s->a_in;
+  ab.p = s->pbuf;
+  ab.hbar = hbar_n;
+  ab.hbar_out = hbar_prev;
+  ab.gtheta = s->gth;
+  S_CK(launch_adjoint_point(ab, st));
+  std::vector<double> h(kMaxPhase * 6);
+  S_CK(cudaMemcpyAsync(h.data(), s->gth, sizeof(double) * kMaxPhase * 6, cudaMemcpyDeviceToHost, st));
+  S_CK(cudaStreamSynchronize(st));
+  for (int i = 0; i < op->ctx->nphase * 6; ++i) grad[i] += h[i];
+  S_RC(pff_get_status(op, stream, &status));
+  if (status) return sfail(PFF_ERR_DEVICE, "pff_adjoint_step: adjoint kernel status " + std::to_string(status));
+  return PFF_OK;
+}

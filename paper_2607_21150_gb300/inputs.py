@@ -544,3 +544,21 @@ def twin_target(theta, seed: int = 1, sigma: float = 0.1):
     curve: theta scaled by seeded lognormal factors (sigma 0.1)."""
     rng = np.random.default_rng(seed)
     return np.asarray(theta) * np.exp(rng.normal(0.0, sigma, len(theta)))
+
+
+# Parameter vector theta of the adjoint (12 entries): for phase k in (0, 1) the six
+# entries E_inf, nu_inf, sigma0, eta_d, Gc, l0 at 6 k + (0..5).
+PARAM_SLOTS = (2, 3, 11, 7, 0, 1)   # their positions in the 12-double phase row
+
+
+def with_params(phases, theta):
+    ph = np.array(phases, dtype=np.float64, copy=True)
+    th = np.asarray(theta, dtype=np.float64).reshape(-1, 6)
+    for k in range(min(len(ph), len(th))):
+        for j, slot in enumerate(PARAM_SLOTS):
+            ph[k, slot] = th[k, j]
+    return ph
+
+
+def params_of(phases):
+    return np.array([[p[s] for s in PARAM_SLOTS] for p in phases]).ravel()

@@ -104,6 +104,7 @@ _SIGS = {
     "pff_solver_krylov": ([_VP, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP], _I),
     "pff_newton_solve": ([_VP, _VP, ctypes.POINTER(pff_newton_stats), _VP], _I),
     "pff_vec_axpby": ([_I, _I64, _D, _VP, _D, _VP, _VP], _I),
+    "pff_adjoint_step": ([_VP, _VP, _VP, _VP, _D, _VP, _VP, ctypes.POINTER(_D), _D, _I, ctypes.POINTER(_I), _VP], _I),
     "pff_commit_history": ([_VP, _VP], _I),
     "pff_get_history": ([_VP, _I, _VP, _VP], _I),
     "pff_get_flags": ([_VP, _VP, _VP], _I),
@@ -360,6 +361,17 @@ def pff_newton_solve(solver, z, stream=None):
 
 def pff_vec_axpby(prec, n, a, x, b, y, stream=None):
     _call("pff_vec_axpby", int(prec), int(n), float(a), _ptr(x), float(b), _ptr(y), _stream(stream))
+
+
+def pff_adjoint_step(solver, z, hist_prev, sel, wF, hbar_n, hbar_prev, grad, rtol=1e-10, maxit=400, stream=None):
+    """One reverse load step; grad (numpy float64 array of 6 nphase) is accumulated in place."""
+    import numpy as np
+    g = np.ascontiguousarray(grad, dtype=np.float64)
+    it = _I()
+    _call("pff_adjoint_step", solver, _ptr(z), _ptr(hist_prev), _ptr(sel), float(wF), _ptr(hbar_n), _ptr(hbar_prev),
+          g.ctypes.data_as(ctypes.POINTER(_D)), float(rtol), int(maxit), ctypes.byref(it), _stream(stream))
+    grad[:] = g
+    return int(it.value)
 
 
 def pff_commit_history(op, stream=None):

@@ -1,0 +1,81 @@
+"""Discrete adjoint on the GPU vs the oracle's assembled-transpose adjoint and
+central finite differences.
+
+Three load steps of a two-phase Q2 tension box (history carried between
+steps): the GPU reactions equal the oracle's (1e-9), the adjoint gradient of the
+reaction-curve misfit equals the oracle's (1e-7 relative per component) and
+central differences of the GPU loss (1e-6), and torch autograd through
+ReactionCurve returns the same gradient.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_21150_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2607_21150_gb300.adjoint import ReactionCurve, ReactionCurveRunner  # noqa: E402
+
+
+def _adjoint_box():
+    w = inputs.adjoint_q2(n=2)
+    w.mesh = inputs.Mesh(2, 2, 2, 2, 3, w.mesh.L)
+    return w
+
+
+@pytest.fixture(scope="module")
+def problem(orc):
+    w = _adjoint_box()
+    top = inputs.top_face_mask(w.mesh)
+    theta0 = inputs.params_of(w.phases)
+    nsteps = 3
+    target, _, _ = orc.load_steps(w, inputs.twin_target(theta0), nsteps, top)
+    g_ref, F_ref = orc.adjoint_gradient(w, theta0, nsteps, top, target)
+    runner = ReactionCurveRunner(w, nsteps, levels=[2, 1])
+    return w, theta0, nsteps, target, g_ref, F_ref, runner
+
+
+def test_reactions_match_oracle(problem):
+    w, theta0, nsteps, target, g_ref, F_ref, runner = problem
+    F = runner.forward(theta0)
+    assert np.allclose(F, F_ref, rtol=1e-9, atol=0)
+
+
+def test_adjoint_gradient_matches_oracle(problem):
+    w, theta0, nsteps, target, g_ref, F_ref, runner = problem
+    F = runner.forward(theta0)
+    g = runner.backward(2.0 * (F - target))
+    scale = np.abs(g_ref * theta0).max()
+    for i in range(12):
+        assert abs(g[i] - g_ref[i]) <= 1e-7 * abs(g_ref[i]) + 1e-11 * scale / abs(theta0[i]), (i, g[i], g_ref[i])
+
+
+def test_adjoint_gradient_matches_central_differences(problem):
+    w, theta0, nsteps, target, g_ref, F_ref, runner = problem
+    F = runner.forward(theta0)
+    g = runner.backward(2.0 * (F - target))
+    loss = lambda th: float(np.sum((runner.forward(th) - target) ** 2))
+    for i in (0, 1, 4, 5, 6, 7, 9, 10, 11):
+        h = 1e-5 * abs(theta0[i])
+        tp, tm = theta0.copy(), theta0.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (loss(tp) - loss(tm)) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-6 * abs(fd) + 1e-9 * np.abs(g * theta0).max() / abs(theta0[i]), (i, g[i], fd)
+
+
+def test_autograd_function(problem):
+    w, theta0, nsteps, target, g_ref, F_ref, runner = problem
+    theta = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
+    F = ReactionCurve.apply(theta, runner)
+    loss = ((F - torch.as_tensor(target)) ** 2).sum()
+    loss.backward()
+    scale = np.abs(g_ref * theta0).max()
+    g = theta.grad.numpy()
+    for i in range(12):
+        assert abs(g[i] - g_ref[i]) <= 1e-7 * abs(g_ref[i]) + 1e-11 * scale / abs(theta0[i])
+    runner.close()
