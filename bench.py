@@ -191,6 +191,41 @@ def newton_compare(name: str, steps: int = 1):
     return out
 
 
+def adjoint_timing(steps: int = 10, fd_check: bool = True):
+    """Gradient of the reaction-curve misfit (twin-experiment target) for the
+    adjoint workload: forward load steps with checkpoints, then the discrete
+    adjoint backward; plus one central difference of the loss as a check."""
+    import torch
+    from paper_2607_21150_gb300 import inputs
+    from paper_2607_21150_gb300.adjoint import ReactionCurveRunner
+    w = inputs.adjoint_q2()
+    theta0 = inputs.params_of(w.phases)
+    runner = ReactionCurveRunner(w, steps, newton_rtol=1e-10, krylov_rtol=1e-6, adjoint_rtol=1e-9)
+    target = runner.forward(inputs.twin_target(theta0))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    F = runner.forward(theta0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g = runner.backward(2.0 * (F - target))
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out = {"workload": f"adjoint_q2: Q2 {w.mesh.nx}^3 elements, {w.mesh.ndof} DoF, {steps} load steps, 12 parameters",
+           "forward_s": t1 - t0, "backward_s": t2 - t1, "adjoint_krylov_iterations": int(sum(runner.adjoint_iters)),
+           "loss": float(np.sum((F - target) ** 2)), "grad": g.tolist()}
+    if fd_check:
+        i = 4  # matrix Gc
+        h = 1e-5 * theta0[i]
+        tp, tm = theta0.copy(), theta0.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (np.sum((runner.forward(tp) - target) ** 2) - np.sum((runner.forward(tm) - target) ** 2)) / (2 * h)
+        out["fd_check"] = {"param": "Gc matrix", "adjoint": float(g[i]), "central_difference": float(fd),
+                           "rel_err": float(abs(g[i] - fd) / abs(fd))}
+    runner.close()
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -340,6 +375,7 @@ def run_native(args):
     del s
     torch.cuda.empty_cache()
     newton = newton_compare(args.newton, args.newton_steps) if args.newton != "none" else None
+    adjoint = adjoint_timing(args.adjoint_steps) if args.adjoint_steps > 0 else None
     cpu = oracle_sample()
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
@@ -359,6 +395,7 @@ def run_native(args):
                              "bound": "hbm", "peak_gbs": hbm_peak, "peak_source": src},
         "residual_ms": t_res, "kernel_status": status,
         "newton_step": newton,
+        "adjoint": adjoint,
         "e2e": {"value": world * ndof * args.steps / (tot_e2e / 1e3) / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
         "gpu_launches": 2 * args.steps,
@@ -385,6 +422,7 @@ def main():
     ap.add_argument("--newton", default="tension_q4", choices=["none", "tension_q4", "compress_q4", "notched_q3"],
                     help="workload of the FP64-vs-mixed Newton comparison")
     ap.add_argument("--newton-steps", type=int, default=1)
+    ap.add_argument("--adjoint-steps", type=int, default=10, help="load steps of the adjoint timing (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
