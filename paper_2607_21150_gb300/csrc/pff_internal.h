@@ -94,25 +94,42 @@ struct AdjArgs {
 };
 cudaError_t launch_adjoint_point(const AdjArgs& a, cudaStream_t st);
 
-// Element-kernel launches (pff_elem*.cu).  T = double or float.
+// Element-kernel launches (pff_elem*.cu).  T = double, float or df64.
 enum ElemMode { kApply = 0, kEval = 1, kBack = 2 };
+
+// Double-float value hi + lo (two FP32 words, about 48 significant bits); the
+// arithmetic lives in pff_df.cuh.
+struct df64 {
+  float hi, lo;
+};
+
+// Storage types of an element kernel computing in T: vectors V, stored
+// linearisation L, 1D basis matrices M.  The double-float kernel reads and
+// writes FP64 vectors, the stored linearisation as two FP32 planes (hi, then
+// lo at a fixed offset) and converts the FP64 basis matrices on entry.
+template <typename T> struct ElemTypes { using V = T; using L = T; using M = T; };
+template <> struct ElemTypes<df64> { using V = double; using L = float; using M = double; };
 
 template <typename T>
 struct ElemArgs {
+  using V = typename ElemTypes<T>::V;
+  using L = typename ElemTypes<T>::L;
+  using M = typename ElemTypes<T>::M;
   MeshDev mesh;
-  const T* x;             // [4][nn] input (apply) / unused
-  T* y;                   // [4][nn] output (scatter-add)
+  const V* x;             // [4][nn] input (apply) / unused
+  V* y;                   // [4][nn] output (scatter-add)
   const uint8_t* mask;    // [4][nn] Dirichlet mask or nullptr
-  const T* B;             // [Q][P] interpolation to Gauss points
-  const T* Dc;            // [Q][Q] collocated derivative at Gauss points
-  const T* Dt;            // [Q][P] derivative of the basis at Gauss points (diagonal)
-  const T* lin;           // tiled stored linearisation (apply / diagonal)
-  const T* linP;          // words multiplying dphi in the u rows (dP/dphi or, transposed, dL/dF)
-  const T* linC;          // words multiplying grad u in the phi row
+  const M* B;             // [Q][P] interpolation to Gauss points
+  const M* Dc;            // [Q][Q] collocated derivative at Gauss points
+  const M* Dt;            // [Q][P] derivative of the basis at Gauss points (diagonal)
+  const L* lin;           // tiled stored linearisation (apply / diagonal)
+  const L* linP;          // words multiplying dphi in the u rows (dP/dphi or, transposed, dL/dF)
+  const L* linC;          // words multiplying grad u in the phi row
   double* scratch;        // [13][nq] (eval / back)
   double s[3];            // d xi / d X (eval)
   long long nq;
   int transpose;
+  long long lo;           // df64: offset (in words) from the hi plane to the lo plane
 };
 
 // One translation unit per quadrature size Q (pff_elem_q<Q>.cu); each covers
@@ -131,6 +148,8 @@ cudaError_t launch_pointwise(const PointArgs& a, cudaStream_t st);
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
 cudaError_t launch_to_f32(const double* a, float* b, long long n, cudaStream_t st);
+// hi[i] = fl32(a[i]) and, when lo is not null, lo[i] = fl32(a[i] - hi[i]).
+cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long n, cudaStream_t st);
 cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st);
 cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st);
 cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st);
@@ -165,10 +184,12 @@ template <typename T>
 cudaError_t launch_dscale(T* y, const T* x, const T* d, long long n, cudaStream_t st);
 cudaError_t launch_d2f(float* y, const double* x, long long n, cudaStream_t st);
 cudaError_t launch_f2d(double* y, const float* x, long long n, cudaStream_t st);
-cudaError_t launch_q1_assemble(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
-                               const uint8_t* maskc, double* A, cudaStream_t st);
 cudaError_t launch_q1_spmv(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st);
+// Sum-factorised element matrices (Ke: [nel][32][32] work space) and a
+// deterministic gather into the stencil storage.
+cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
+                                  const uint8_t* maskc, double* Ke, double* A, cudaStream_t st);
 cudaError_t launch_q1_spmv_t(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_sel_scale(double* y, const uint8_t* sel, double s, long long n, cudaStream_t st);
 cudaError_t launch_zero_masked(double* y, const uint8_t* mask, long long n, cudaStream_t st);

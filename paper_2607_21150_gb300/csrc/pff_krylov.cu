@@ -9,23 +9,35 @@ constexpr int kRedBlocks = kReduceBlocks;
 
 // ---------------------------------------------------------------- reductions
 // partial[j * kRedBlocks + b] = block b's share of sum_i V_j[i] w[i], j < k.
-template <typename TV, typename T>
+// Vectors are taken in chunks of CH so that w is read once per chunk (long
+// vectors: HBM traffic k + k / CH instead of 2 k vectors); short vectors live
+// in L2 and take CH = 1, which keeps fewer registers and barriers per pass.
+template <typename TV, typename T, int CH>
 __global__ void __launch_bounds__(kRedThreads) k_mdot_partial(const TV* __restrict__ V, long long ldv, int k,
                                                               const T* __restrict__ w, long long n,
                                                               double* __restrict__ partial) {
-  __shared__ double red[kRedThreads / 32];
-  for (int j = 0; j < k; ++j) {
-    const TV* v = V + j * ldv;
-    double s = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-      s += (double)v[i] * (double)w[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      double t = (threadIdx.x < kRedThreads / 32) ? red[threadIdx.x] : 0.0;
+  __shared__ double red[CH][kRedThreads / 32];
+  for (int j0 = 0; j0 < k; j0 += CH) {
+    double s[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s[c] = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+      const double wi = (double)w[i];
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (j0 + c < k) s[c] += (double)V[(j0 + c) * ldv + i] * wi;
+    }
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      double t = s[c];
       for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if (threadIdx.x == 0) partial[j * kRedBlocks + blockIdx.x] = t;
+      if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < CH && j0 + (int)threadIdx.x < k) {
+      double t = 0.0;
+      for (int wp = 0; wp < kRedThreads / 32; ++wp) t += red[threadIdx.x][wp];
+      partial[(j0 + threadIdx.x) * kRedBlocks + blockIdx.x] = t;
     }
     __syncthreads();
   }
@@ -50,7 +62,10 @@ template <typename TV, typename T>
 cudaError_t launch_mdot(const TV* V, long long ldv, int k, const T* w, long long n, double* partial, double* out,
                         cudaStream_t st) {
   if (k <= 0) return cudaSuccess;
-  k_mdot_partial<TV, T><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, k, w, n, partial);
+  if (n >= (1LL << 22))
+    k_mdot_partial<TV, T, 8><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, k, w, n, partial);
+  else
+    k_mdot_partial<TV, T, 1><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, k, w, n, partial);
   k_mdot_final<<<k, 256, 0, st>>>(partial, k, out);
   return cudaGetLastError();
 }
@@ -145,107 +160,10 @@ cudaError_t launch_f2d(double* y, const float* x, long long n, cudaStream_t st) 
 // order 1 evaluated at the fine points, fine stored tangent): the exact
 // Galerkin operator of the p-hierarchy.  Storage: 27-point stencil with a 4x4
 // block per neighbour, A[(slot*16 + f*4 + g) * nn + node], slot = neighbour
-// offset (dx+1) + 3 (dy+1) + 9 (dz+1).  One thread block per element.
-//
-// Per point, with the 67 stored words W (already scaled by w det J and the
-// parent factors) and the parent gradients dN_alpha(a) of the 8 vertex functions:
-//   K[f a][g b] += sum_{alpha,beta} dN_alpha(a) W_A[f alpha][g beta] dN_beta(b)      (f, g < 3)
-//   K[f a][3 b] += sum_alpha dN_alpha(a) W_P[f alpha] N(b)
-//   K[3 a][g b] += N(a) sum_beta W_C[g beta] dN_beta(b)
-//   K[3 a][3 b] += W_D N(a) N(b) + sum_alpha W_K[alpha] dN_alpha(a) dN_alpha(b)
-constexpr int kAsmThreads = 128;
+// offset (dx+1) + 3 (dy+1) + 9 (dz+1); Dirichlet rows and columns are zero
+// with a unit diagonal.
 
-__global__ void __launch_bounds__(kAsmThreads)
-k_q1_assemble(MeshDev mc, int Q, const double* __restrict__ lin, const double* __restrict__ B1,
-              const double* __restrict__ D1, const uint8_t* __restrict__ maskc, double* __restrict__ A) {
-  __shared__ double W[kLinWords];
-  __shared__ double Nv[8], dN[3][8];
-  __shared__ double T[9][3][8];  // T[f alpha][g][b] = sum_beta W_A[f alpha][g beta] dN_beta(b)
-  const int e = blockIdx.x;
-  const int t = threadIdx.x;
-  const int EB = elems_per_block(Q);
-  const int Q2 = Q * Q, Q3 = Q2 * Q;
-  const long long stride = (long long)Q3 * EB;
-  const long long base = (long long)(e / EB) * kLinWords * stride + (e % EB) * Q2;
-  double acc[8];
-  for (int s = 0; s < 8; ++s) acc[s] = 0.0;
-  for (int q = 0; q < Q3; ++q) {
-    const int i = q % Q, j = (q / Q) % Q, k = q / Q2;
-    if (t < kLinWords) W[t] = lin[base + (long long)t * stride + (long long)k * Q2 * EB + j * Q + i];
-    if (t < 8) {
-      const int a0 = t & 1, a1 = (t >> 1) & 1, a2 = t >> 2;
-      const double bx = B1[i * 2 + a0], by = B1[j * 2 + a1], bz = B1[k * 2 + a2];
-      Nv[t] = bx * by * bz;
-      dN[0][t] = D1[i * 2 + a0] * by * bz;
-      dN[1][t] = bx * D1[j * 2 + a1] * bz;
-      dN[2][t] = bx * by * D1[k * 2 + a2];
-    }
-    __syncthreads();
-    for (int idx = t; idx < 9 * 3 * 8; idx += kAsmThreads) {
-      const int m = idx / 24, g = (idx / 8) % 3, b = idx % 8;
-      double s = 0.0;
-      for (int be = 0; be < 3; ++be) {
-        const int n = 3 * g + be;
-        s += W[kWA + (m <= n ? sym9(m, n) : sym9(n, m))] * dN[be][b];
-      }
-      T[m][g][b] = s;
-    }
-    __syncthreads();
-    for (int s = 0; s < 8; ++s) {
-      const int idx = t + s * kAsmThreads;  // entry (f a, g b) of the 32 x 32 element matrix
-      const int row = idx / 32, col = idx % 32;
-      const int f = row / 8, a = row % 8, g = col / 8, b = col % 8;
-      double v = 0.0;
-      if (f < 3 && g < 3) {
-        for (int al = 0; al < 3; ++al) v += dN[al][a] * T[3 * f + al][g][b];
-      } else if (f < 3) {
-        for (int al = 0; al < 3; ++al) v += dN[al][a] * W[kWP + 3 * f + al];
-        v *= Nv[b];
-      } else if (g < 3) {
-        for (int be = 0; be < 3; ++be) v += W[kWC + 3 * g + be] * dN[be][b];
-        v *= Nv[a];
-      } else {
-        v = W[kWD] * Nv[a] * Nv[b];
-        for (int al = 0; al < 3; ++al) v += W[kWK + al] * dN[al][a] * dN[al][b];
-      }
-      acc[s] += v;
-    }
-    __syncthreads();
-  }
-  const int ex = e % mc.nx, ey = (e / mc.nx) % mc.ny, ez = e / (mc.nx * mc.ny);
-  for (int s = 0; s < 8; ++s) {
-    const int idx = t + s * kAsmThreads;
-    const int row = idx / 32, col = idx % 32;
-    const int f = row / 8, a = row % 8, g = col / 8, b = col % 8;
-    const int ax = ex + (a & 1), ay = ey + ((a >> 1) & 1), az = ez + (a >> 2);
-    const int bx = ex + (b & 1), by = ey + ((b >> 1) & 1), bz = ez + (b >> 2);
-    const long long na = ax + (long long)mc.nnx * (ay + (long long)mc.nny * az);
-    const long long nb = bx + (long long)mc.nnx * (by + (long long)mc.nny * bz);
-    if (maskc && (maskc[f * mc.nn + na] || maskc[g * mc.nn + nb])) continue;
-    const int slot = (bx - ax + 1) + 3 * (by - ay + 1) + 9 * (bz - az + 1);
-    atomicAdd(A + (long long)(slot * 16 + f * 4 + g) * mc.nn + na, acc[s]);
-  }
-}
-
-// Dirichlet rows of the coarse operator: identity (slot 13 = centre, f == g).
-__global__ void k_q1_mask_identity(MeshDev mc, const uint8_t* __restrict__ maskc, double* __restrict__ A) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= mc.nn) return;
-  for (int f = 0; f < 4; ++f)
-    if (maskc[f * mc.nn + n]) A[(long long)(13 * 16 + f * 4 + f) * mc.nn + n] = 1.0;
-}
-
-cudaError_t launch_q1_assemble(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
-                               const uint8_t* maskc, double* A, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(A, 0, sizeof(double) * 27 * 16 * mc.nn, st);
-  if (e != cudaSuccess) return e;
-  k_q1_assemble<<<mc.nel, kAsmThreads, 0, st>>>(mc, Q, lin, B1, D1, maskc, A);
-  if (maskc) k_q1_mask_identity<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, maskc, A);
-  return cudaGetLastError();
-}
-
-// y = A x with the stencil storage (FP64), one thread per node; also the
-// diagonal when diag != nullptr.
+// y = A x with the stencil storage (FP64), one thread per node.
 __global__ void k_q1_spmv(MeshDev mc, const double* __restrict__ A, const double* __restrict__ x,
                           double* __restrict__ y) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -321,6 +239,202 @@ cudaError_t launch_q1_spmv(const MeshDev& mc, const double* A, const double* x, 
 }
 cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st) {
   k_q1_diag<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, d);
+  return cudaGetLastError();
+}
+
+// ---- sum-factorised element matrices of the order-1 level (FP64) ----------
+// One block per element.  The 67 stored words of the element's 125 (Q^3)
+// points give 67 "combinations" (word, test derivative, trial derivative):
+// 45 from the symmetric 9x9 block (the transposed block of an off-diagonal pair
+// is placed from the same result), 9 dP/dphi, 9 d(s_phi L)/dF, the phi value
+// term and the 3 phase-gradient terms.  Each combination's 8x8 block is
+//   sum_{ijk} D(i,j,k) X0[i][a0 b0] X1[j][a1 b1] X2[k][a2 b2],
+// Xd[q][a b] = F_r,d[q][a] F_c,d[q][b], F = B1 or its derivative D1,
+// contracted one direction at a time.  Output: Ke[e][32][32].
+constexpr int kQ1Combos = 67;
+constexpr int kQ1Threads = 256;
+
+__device__ __forceinline__ void q1_combo(int c, int& word, int& rk, int& ck) {
+  // rk/ck: 0 value, 1 + alpha derivative
+  if (c < 45) {
+    int m = 0, rem = c;
+    while (rem >= 9 - m) { rem -= 9 - m; ++m; }
+    const int n = m + rem;
+    word = sym9(m, n);
+    rk = 1 + m % 3;
+    ck = 1 + n % 3;
+  } else if (c < 54) {
+    const int m = c - 45;
+    word = kWP + m; rk = 1 + m % 3; ck = 0;
+  } else if (c < 63) {
+    const int n = c - 54;
+    word = kWC + n; rk = 0; ck = 1 + n % 3;
+  } else if (c == 63) {
+    word = kWD; rk = 0; ck = 0;
+  } else {
+    const int al = c - 64;
+    word = kWK + al; rk = 1 + al; ck = 1 + al;
+  }
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kQ1Threads)
+k_q1_elem(int nel, const double* __restrict__ lin, const double* __restrict__ B1, const double* __restrict__ D1,
+          double* __restrict__ Ke) {
+  constexpr int Q2 = Q * Q, Q3 = Q2 * Q;
+  constexpr int EB = elems_per_block(Q);
+  extern __shared__ double sm[];
+  double* Dw = sm;                          // [67][Q3]
+  double* T1 = Dw + kQ1Combos * Q3;         // [67][4][Q2]   (reused for results [67][64])
+  double* T2 = T1 + kQ1Combos * 4 * Q2;     // [67][16][Q]
+  __shared__ double F[2][Q][2];             // F[0] = B1, F[1] = D1
+  const int e = blockIdx.x;
+  const int t = threadIdx.x;
+  if (t < 2 * Q * 2) {
+    const int which = t / (2 * Q), r = t % (2 * Q);
+    F[which][r / 2][r % 2] = which ? D1[r] : B1[r];
+  }
+  const long long stride = (long long)Q3 * EB;
+  const long long base = (long long)(e / EB) * kLinWords * stride + (e % EB) * Q2;
+  for (int idx = t; idx < kQ1Combos * Q3; idx += kQ1Threads) {
+    const int c = idx / Q3, q = idx % Q3;
+    int word, rk, ck;
+    q1_combo(c, word, rk, ck);
+    const int k = q / Q2, jq = q % Q2;
+    Dw[idx] = lin[base + (long long)word * stride + (long long)k * Q2 * EB + jq];
+  }
+  __syncthreads();
+  // direction 0 (i): T1[c][a0 b0][j k]
+  for (int idx = t; idx < kQ1Combos * 4 * Q2; idx += kQ1Threads) {
+    const int c = idx / (4 * Q2), r = idx % (4 * Q2);
+    const int ab = r / Q2, jk = r % Q2;
+    int word, rk, ck;
+    q1_combo(c, word, rk, ck);
+    const int fa = (rk == 1), fb = (ck == 1);
+    const int a0 = ab >> 1, b0 = ab & 1;
+    const double* Dc = Dw + c * Q3 + jk * Q;
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) s += F[fa][i][a0] * F[fb][i][b0] * Dc[i];
+    T1[idx] = s;
+  }
+  __syncthreads();
+  // direction 1 (j): T2[c][a0b0 a1b1][k]
+  for (int idx = t; idx < kQ1Combos * 16 * Q; idx += kQ1Threads) {
+    const int c = idx / (16 * Q), r = idx % (16 * Q);
+    const int abab = r / Q, k = r % Q;
+    const int ab0 = abab >> 2, ab1 = abab & 3;
+    int word, rk, ck;
+    q1_combo(c, word, rk, ck);
+    const int fa = (rk == 2), fb = (ck == 2);
+    const int a1 = ab1 >> 1, b1 = ab1 & 1;
+    const double* Tc = T1 + c * 4 * Q2 + ab0 * Q2 + k * Q;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) s += F[fa][j][a1] * F[fb][j][b1] * Tc[j];
+    T2[idx] = s;
+  }
+  __syncthreads();
+  // direction 2 (k): result R[c][a][b], a = a0 + 2 a1 + 4 a2 (written over T1)
+  double* R = T1;
+  for (int idx = t; idx < kQ1Combos * 64; idx += kQ1Threads) {
+    const int c = idx / 64, r = idx % 64;
+    const int a = r / 8, b = r % 8;
+    const int a0 = a & 1, a1 = (a >> 1) & 1, a2 = a >> 2;
+    const int b0 = b & 1, b1 = (b >> 1) & 1, b2 = b >> 2;
+    int word, rk, ck;
+    q1_combo(c, word, rk, ck);
+    const int fa = (rk == 3), fb = (ck == 3);
+    const double* Tc = T2 + c * 16 * Q + ((a0 * 2 + b0) * 4 + (a1 * 2 + b1)) * Q;
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < Q; ++k) s += F[fa][k][a2] * F[fb][k][b2] * Tc[k];
+    R[idx] = s;
+  }
+  __syncthreads();
+  // element matrix: sum of the combinations of each (f, g) block
+  double* out = Ke + (long long)e * 1024;
+  for (int idx = t; idx < 1024; idx += kQ1Threads) {
+    const int row = idx / 32, col = idx % 32;
+    const int f = row / 8, a = row % 8, g = col / 8, b = col % 8;
+    double v = 0.0;
+    if (f < 3 && g < 3) {
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be) {
+          const int m = 3 * f + al, n = 3 * g + be;
+          const int mm = m <= n ? m : n, nn2 = m <= n ? n : m;
+          const int c = sym9(mm, nn2);  // combos are enumerated in the sym9 order
+          v += (m <= n) ? R[c * 64 + a * 8 + b] : R[c * 64 + b * 8 + a];
+        }
+    } else if (f < 3) {
+      for (int al = 0; al < 3; ++al) v += R[(45 + 3 * f + al) * 64 + a * 8 + b];
+    } else if (g < 3) {
+      for (int be = 0; be < 3; ++be) v += R[(54 + 3 * g + be) * 64 + a * 8 + b];
+    } else {
+      for (int c = 63; c < 67; ++c) v += R[c * 64 + a * 8 + b];
+    }
+    out[idx] = v;
+  }
+}
+
+// Stencil entry (slot, f, g) of node n: the sum, over the elements holding both
+// n and its neighbour m, of Ke[(f, a(n)), (g, b(m))]; Dirichlet rows/columns of
+// the identity.  One thread per (node, f, g); deterministic order.
+__global__ void k_q1_gather(MeshDev mc, const double* __restrict__ Ke, const uint8_t* __restrict__ maskc,
+                            double* __restrict__ A) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= mc.nn * 16) return;
+  const long long n = tid % mc.nn;
+  const int fg = (int)(tid / mc.nn);
+  const int f = fg / 4, g = fg % 4;
+  const int nnz_ = (int)(mc.nn / ((long long)mc.nnx * mc.nny));
+  const int I = (int)(n % mc.nnx), J = (int)((n / mc.nnx) % mc.nny), K = (int)(n / ((long long)mc.nnx * mc.nny));
+  const bool rowmask = maskc && maskc[f * mc.nn + n];
+  for (int slot = 0; slot < 27; ++slot) {
+    const int dx = slot % 3 - 1, dy = (slot / 3) % 3 - 1, dz = slot / 9 - 1;
+    const int I2 = I + dx, J2 = J + dy, K2 = K + dz;
+    double v = 0.0;
+    if (I2 >= 0 && J2 >= 0 && K2 >= 0 && I2 < mc.nnx && J2 < mc.nny && K2 < nnz_) {
+      const long long m = I2 + (long long)mc.nnx * (J2 + (long long)mc.nny * K2);
+      if (rowmask) {
+        v = (slot == 13 && f == g) ? 1.0 : 0.0;
+      } else if (!(maskc && maskc[g * mc.nn + m])) {
+        // elements whose closure holds both nodes
+        const int ex0 = max(max(I, I2) - 1, 0), ex1 = min(min(I, I2), mc.nx - 1);
+        const int ey0 = max(max(J, J2) - 1, 0), ey1 = min(min(J, J2), mc.ny - 1);
+        const int ez0 = max(max(K, K2) - 1, 0), ez1 = min(min(K, K2), mc.nz - 1);
+        for (int ez = ez0; ez <= ez1; ++ez)
+          for (int ey = ey0; ey <= ey1; ++ey)
+            for (int ex = ex0; ex <= ex1; ++ex) {
+              const long long e = ex + (long long)mc.nx * (ey + (long long)mc.ny * ez);
+              const int a = (I - ex) + 2 * ((J - ey) + 2 * (K - ez));
+              const int b = (I2 - ex) + 2 * ((J2 - ey) + 2 * (K2 - ez));
+              v += Ke[e * 1024 + (f * 8 + a) * 32 + g * 8 + b];
+            }
+      }
+    }
+    A[(long long)(slot * 16 + f * 4 + g) * mc.nn + n] = v;
+  }
+}
+
+cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
+                                  const uint8_t* maskc, double* Ke, double* A, cudaStream_t st) {
+  size_t smem = sizeof(double) * (size_t)(kQ1Combos * Q * Q * Q + kQ1Combos * 4 * Q * Q + kQ1Combos * 16 * Q);
+  switch (Q) {
+    case 2: cudaFuncSetAttribute(k_q1_elem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_q1_elem<2><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+    case 3: cudaFuncSetAttribute(k_q1_elem<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_q1_elem<3><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+    case 4: cudaFuncSetAttribute(k_q1_elem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_q1_elem<4><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+    case 5: cudaFuncSetAttribute(k_q1_elem<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_q1_elem<5><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long nt = mc.nn * 16;
+  k_q1_gather<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(mc, Ke, maskc, A);
   return cudaGetLastError();
 }
 

@@ -61,6 +61,7 @@ struct pff_solver {
   bool assembled = false;
   double *A = nullptr, *cdiag = nullptr, *cb = nullptr, *cx = nullptr, *cwork = nullptr;
   double *cV = nullptr, *cZ = nullptr;  // coarse GMRES basis
+  double* Ke = nullptr;                 // coarse element matrices [nel][32][32]
   long long coarse_iters = 0;
   double clmax = 1.0;
   long long n = 0;
@@ -461,7 +462,7 @@ int setup(pff_solver* s, cudaStream_t st) {
   if (s->assembled) {
     LevelWork& c = s->lv.back();
     pff_op* op = s->op;
-    S_CK(launch_q1_assemble(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->A, st));
+    S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->Ke, s->A, st));
     S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
     if (s->prm.coarse_solver == 0) S_RC(power_coarse(s, st));
   }
@@ -477,7 +478,7 @@ void free_solver(pff_solver* s) {
     cudaFree(w.diag); cudaFree(w.b); cudaFree(w.x); cudaFree(w.tmp); cudaFree(w.work);
   }
   cudaFree(s->A); cudaFree(s->cdiag); cudaFree(s->cb); cudaFree(s->cx); cudaFree(s->cwork);
-  cudaFree(s->cV); cudaFree(s->cZ);
+  cudaFree(s->cV); cudaFree(s->cZ); cudaFree(s->Ke);
   cudaFree(s->V); cudaFree(s->Z); cudaFree(s->r); cudaFree(s->dz); cudaFree(s->zold);
   cudaFree(s->partial); cudaFree(s->dots); cudaFree(s->hdev);
   cudaFree(s->pw64); cudaFree(s->pw32);
@@ -550,6 +551,7 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     if (e == cudaSuccess) e = cudaMalloc(&s->cb, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->cx, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->cwork, sizeof(double) * 3 * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&s->Ke, sizeof(double) * 1024 * (size_t)op->nel);
     if (e == cudaSuccess && prm->coarse_solver == 1) e = cudaMalloc(&s->cV, sizeof(double) * (prm->krylov_restart + 1) * nc);
     if (e == cudaSuccess && prm->coarse_solver == 1) e = cudaMalloc(&s->cZ, sizeof(double) * prm->krylov_restart * nc);
   }
