@@ -63,7 +63,12 @@ extern "C" {
 #define PFF_STATUS_NONFINITE 4   /* non-finite residual integrand */
 #define PFF_STATUS_PHASE 8       /* phase id >= nphase (phase 0 used) */
 
-typedef enum { PFF_F64 = 0, PFF_F32 = 1 } pff_prec;
+/* PFF_DF64: FP64 vectors, the Jacobian action's contractions carried in
+ * double-float arithmetic (pairs of FP32 words on the FP32 pipes, error about
+ * 2^-47 of the magnitudes per operation instead of 2^-53) and the stored
+ * linearisation read from its hi/lo FP32 planes (pff_op_enable_df).  Accepted
+ * by pff_jacobian_apply and pff_jacobian_transpose_apply only. */
+typedef enum { PFF_F64 = 0, PFF_F32 = 1, PFF_DF64 = 2 } pff_prec;
 
 typedef struct pff_ctx pff_ctx;
 typedef struct pff_basis pff_basis;
@@ -122,8 +127,14 @@ int pff_destroy_restriction(pff_restr* restr);
 int pff_create_operator(pff_ctx* ctx, pff_basis* fine, pff_restr* restr, pff_op** op);
 int pff_destroy_operator(pff_op* op);
 /* Also keep an FP32 copy of the stored linearisation (written by pff_residual),
- * needed by PFF_F32 applies. */
+ * needed by PFF_F32 applies.  Disabling frees it (and the PFF_DF64 planes). */
 int pff_op_enable_f32(pff_op* op, int enable);
+/* Keep the stored linearisation also as two FP32 planes hi = fl32(w),
+ * lo = fl32(w - hi) (written by pff_residual; 8 more bytes per word than FP64
+ * alone), needed by PFF_DF64 applies.  The hi plane doubles as the FP32 copy,
+ * so enabling also enables FP32.  Disabling stops the lo updates and keeps the
+ * memory until pff_op_enable_f32(op, 0). */
+int pff_op_enable_df(pff_op* op, int enable);
 int64_t pff_op_num_qpoints(const pff_op* op);
 int64_t pff_op_num_nodes(const pff_op* op);
 
@@ -227,6 +238,7 @@ typedef struct {
   double coarse_rtol;   /* Jacobi-GMRES relative tolerance on the coarsest level */
   int coarse_maxit;     /* Jacobi-GMRES iterations per coarse solve */
   int verbose;          /* 1: one line per Newton iteration on stderr */
+  int outer_prec;       /* fine-level action inside FGMRES: PFF_F64, or PFF_DF64 (pff_op_enable_df) */
 } pff_solver_params;
 
 typedef struct {

@@ -157,6 +157,32 @@ int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st) {
   return PFF_OK;
 }
 
+// Double-float action: FP64 vectors, contractions on the FP32 pipes with
+// pairs of floats, stored linearisation read from its hi/lo planes.
+int apply_df(pff_level* L, const double* x, double* y, int transpose, cudaStream_t st) {
+  pff_op* op = L->op;
+  PFF_REQUIRE(op->df && op->lin32, "PFF_DF64 apply needs pff_op_enable_df before pff_residual");
+  PFF_CK(launch_init_masked(0, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
+  ElemArgs<df64> a;
+  std::memset(&a, 0, sizeof(a));
+  a.mesh = L->mesh;
+  a.mask = level_mask(L);
+  a.B = L->tab.B64;
+  a.Dc = L->tab.Dc64;
+  a.Dt = L->tab.Dt64;
+  a.nq = op->nq;
+  a.x = x;
+  a.y = y;
+  const long long stride = stride_of(op->Q);
+  a.lin = op->lin32;
+  a.linP = op->lin32 + (transpose ? kWC : kWP) * stride;
+  a.linC = op->lin32 + (transpose ? kWP : kWC) * stride;
+  a.lo = op->lin_len;
+  a.transpose = transpose;
+  PFF_CK(elem_dispatch<df64>(op->Q, L->p + 1, kApply, a, st));
+  return PFF_OK;
+}
+
 template <typename T>
 int diag_t(pff_level* L, T* diag, cudaStream_t st) {
   pff_op* op = L->op;
@@ -395,12 +421,30 @@ int pff_op_enable_f32(pff_op* op, int enable) {
   if (enable && !op->lin32) {
     PFF_CK(cudaMalloc((void**)&op->lin32, sizeof(float) * op->lin_len));
     PFF_CK(cudaMemset(op->lin32, 0, sizeof(float) * op->lin_len));
+    op->lin32_planes = 1;
   }
   if (!enable && op->lin32) {
     cudaFree(op->lin32);
     op->lin32 = nullptr;
+    op->lin32_planes = 0;
+    op->df = 0;
   }
   op->f32 = enable ? 1 : 0;
+  return PFF_OK;
+}
+
+int pff_op_enable_df(pff_op* op, int enable) {
+  PFF_REQUIRE(op, "pff_op_enable_df: null operator");
+  if (enable && op->lin32_planes < 2) {
+    float* planes = nullptr;
+    PFF_CK(cudaMalloc((void**)&planes, sizeof(float) * 2 * op->lin_len));
+    PFF_CK(cudaMemset(planes, 0, sizeof(float) * 2 * op->lin_len));
+    cudaFree(op->lin32);
+    op->lin32 = planes;
+    op->lin32_planes = 2;
+  }
+  if (enable) op->f32 = 1;
+  op->df = enable ? 1 : 0;  // disabling keeps both planes allocated until pff_op_enable_f32(op, 0)
   return PFF_OK;
 }
 
@@ -471,7 +515,8 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   a.y = r;
   a.mask = op->mask;
   PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
-  if (op->f32 && op->lin32) PFF_CK(launch_to_f32(op->lin64, op->lin32, op->lin_len, st));
+  if (op->f32 && op->lin32)
+    PFF_CK(launch_split_df(op->lin64, op->lin32, op->df ? op->lin32 + op->lin_len : nullptr, op->lin_len, st));
   return PFF_OK;
 }
 
@@ -546,6 +591,7 @@ int pff_jacobian_apply(pff_level* L, pff_prec prec, const void* x, void* y, void
   PFF_REQUIRE(L && x && y, "pff_jacobian_apply: null argument");
   if (prec == PFF_F64) return apply_t<double>(L, (const double*)x, (double*)y, 0, S(stream));
   if (prec == PFF_F32) return apply_t<float>(L, (const float*)x, (float*)y, 0, S(stream));
+  if (prec == PFF_DF64) return apply_df(L, (const double*)x, (double*)y, 0, S(stream));
   return fail(PFF_ERR_INVALID, "pff_jacobian_apply: unknown precision");
 }
 
@@ -553,6 +599,7 @@ int pff_jacobian_transpose_apply(pff_level* L, pff_prec prec, const void* x, voi
   PFF_REQUIRE(L && x && y, "pff_jacobian_transpose_apply: null argument");
   if (prec == PFF_F64) return apply_t<double>(L, (const double*)x, (double*)y, 1, S(stream));
   if (prec == PFF_F32) return apply_t<float>(L, (const float*)x, (float*)y, 1, S(stream));
+  if (prec == PFF_DF64) return apply_df(L, (const double*)x, (double*)y, 1, S(stream));
   return fail(PFF_ERR_INVALID, "pff_jacobian_transpose_apply: unknown precision");
 }
 

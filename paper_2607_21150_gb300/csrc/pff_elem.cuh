@@ -9,12 +9,46 @@
 // linearisation is read from a tiled layout so that every load of a block is
 // one contiguous run: word w of slice k of block b sits at
 //   b * 67 * Q^3 * EB + w * Q^3 * EB + k * Q^2 * EB + threadIdx.x.
+//
+// The arithmetic type T is double, float or df64 (double-float pairs on the
+// FP32 pipes, FP64 vectors in and out); every multiply-add goes through
+// madd/mul/add so that one source serves all three.
 #pragma once
+#include "pff_df.cuh"
 #include "pff_internal.h"
 
 namespace pff {
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ double madd(double c, double a, double b) { return fma(a, b, c); }
+__device__ __forceinline__ float madd(float c, float a, float b) { return fmaf(a, b, c); }
+__device__ __forceinline__ df64 madd(df64 c, df64 a, df64 b) { return df_madd(c, a, b); }
+__device__ __forceinline__ double mul(double a, double b) { return a * b; }
+__device__ __forceinline__ float mul(float a, float b) { return a * b; }
+__device__ __forceinline__ df64 mul(df64 a, df64 b) { return df_mul(a, b); }
+__device__ __forceinline__ double add(double a, double b) { return a + b; }
+__device__ __forceinline__ float add(float a, float b) { return a + b; }
+__device__ __forceinline__ df64 add(df64 a, df64 b) { return df_add(a, b); }
+
+template <typename T> __device__ __forceinline__ T zero() { return T(0); }
+template <> __device__ __forceinline__ df64 zero<df64>() { return df_make(0.0f, 0.0f); }
+// storage value (vector entry or basis matrix) -> arithmetic type
+template <typename T, typename S> __device__ __forceinline__ T from_store(S x) { return (T)x; }
+template <> __device__ __forceinline__ df64 from_store<df64, double>(double x) { return df_from(x); }
+// arithmetic type -> vector entry
+__device__ __forceinline__ double to_vec(double v) { return v; }
+__device__ __forceinline__ float to_vec(float v) { return v; }
+__device__ __forceinline__ double to_vec(df64 v) { return df_to(v); }
+// stored linearisation word (df64: hi plane at p, lo plane at p + lo)
+template <typename T>
+__device__ __forceinline__ T ld_lin(const typename ElemTypes<T>::L* p, long long lo) {
+  if constexpr (sizeof(T) == sizeof(typename ElemTypes<T>::L)) {
+    return ldg(p);
+  } else {
+    return df_make(ldg(p), ldg(p + lo));
+  }
+}
 
 template <int P, int Q>
 __device__ __forceinline__ long long node_of(const MeshDev& m, int e, int a, int b, int c) {
@@ -28,8 +62,14 @@ __device__ __forceinline__ long long node_of(const MeshDev& m, int e, int a, int
 
 // Shared-memory layout per element: two ping-pong buffers of 4 fields x Q^3
 // values and a slice buffer of 8 x Q^2 values (x- and y-derivative outputs of
-// the four fields at one k).
+// the four fields at one k).  The FP32 action ("split" form) instead keeps the
+// x- and y-derivative outputs of all Q slices, 8 x Q^3 values starting at the
+// second buffer, so that its pointwise stage runs without barriers.
 template <int Q> __host__ __device__ constexpr int elem_smem_words() { return 8 * Q * Q * Q + 8 * Q * Q; }
+template <typename T> __host__ __device__ constexpr bool elem_split() { return sizeof(T) == 4; }
+template <int Q, typename T> __host__ __device__ constexpr int elem_smem_words_t() {
+  return elem_split<T>() ? 12 * Q * Q * Q : elem_smem_words<Q>();
+}
 template <int P, int Q> __host__ __device__ constexpr int mat_smem_words() { return 3 * Q * P + Q * Q; }
 
 template <int P, int Q, typename T>
@@ -52,11 +92,10 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
     long long n = valid ? node_of<P, Q>(a.mesh, e, aa, bb, cc) : 0;
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      T v = T(0);
+      T v = zero<T>();
       if (valid) {
         long long g = f * nn + n;
-        v = ldg(a.x + g);
-        if (a.mask && a.mask[g]) v = T(0);
+        if (!(a.mask && a.mask[g])) v = from_store<T>(ldg(a.x + g));
       }
       s.bufA[f * Q3 + idx] = v;
     }
@@ -68,9 +107,9 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const T* in = s.bufA + f * Q3 + r * P;
-      T acc = T(0);
+      T acc = zero<T>();
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc += s.B[i * P + k] * in[k];
+      for (int k = 0; k < P; ++k) acc = madd(acc, s.B[i * P + k], in[k]);
       s.bufB[f * Q3 + idx] = acc;
     }
   }
@@ -81,9 +120,9 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const T* in = s.bufB + f * Q3 + c * (P * Q) + i;
-      T acc = T(0);
+      T acc = zero<T>();
 #pragma unroll
-      for (int k = 0; k < P; ++k) acc += s.B[j * P + k] * in[k * Q];
+      for (int k = 0; k < P; ++k) acc = madd(acc, s.B[j * P + k], in[k * Q]);
       s.bufA[f * Q3 + idx] = acc;
     }
   }
@@ -98,9 +137,9 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
       for (int c = 0; c < P; ++c) col[c] = s.bufA[f * Q3 + c * Q2 + j * Q + i];
 #pragma unroll
       for (int k = 0; k < Q; ++k) {
-        T acc = T(0);
+        T acc = zero<T>();
 #pragma unroll
-        for (int c = 0; c < P; ++c) acc += s.B[k * P + c] * col[c];
+        for (int c = 0; c < P; ++c) acc = madd(acc, s.B[k * P + c], col[c]);
         s.bufB[f * Q3 + k * Q2 + j * Q + i] = acc;
       }
     }
@@ -115,12 +154,12 @@ __device__ __forceinline__ void grad_at(const ElemSmem<P, Q, T>& s, int i, int j
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const T* V = s.bufB + f * Q3;
-    T gx = T(0), gy = T(0), gz = T(0);
+    T gx = zero<T>(), gy = zero<T>(), gz = zero<T>();
 #pragma unroll
     for (int m = 0; m < Q; ++m) {
-      gx += s.Dc[i * Q + m] * V[k * Q2 + j * Q + m];
-      gy += s.Dc[j * Q + m] * V[k * Q2 + m * Q + i];
-      gz += s.Dc[k * Q + m] * V[m * Q2 + j * Q + i];
+      gx = madd(gx, s.Dc[i * Q + m], V[k * Q2 + j * Q + m]);
+      gy = madd(gy, s.Dc[j * Q + m], V[k * Q2 + m * Q + i]);
+      gz = madd(gz, s.Dc[k * Q + m], V[m * Q2 + j * Q + i]);
     }
     g[f][0] = gx; g[f][1] = gy; g[f][2] = gz;
   }
@@ -139,9 +178,9 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
   for (int f = 0; f < 4; ++f)
 #pragma unroll
     for (int c = 0; c < P; ++c) {
-      T acc = T(0);
+      T acc = zero<T>();
 #pragma unroll
-      for (int k = 0; k < Q; ++k) acc += s.B[k * P + c] * Y[f][k];
+      for (int k = 0; k < Q; ++k) acc = madd(acc, s.B[k * P + c], Y[f][k]);
       s.bufA[f * Q3 + c * Q2 + j * Q + i] = acc;
     }
   __syncthreads();
@@ -151,9 +190,9 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const T* in = s.bufA + f * Q3 + c * Q2 + ii;
-      T acc = T(0);
+      T acc = zero<T>();
 #pragma unroll
-      for (int jj = 0; jj < Q; ++jj) acc += s.B[jj * P + bb] * in[jj * Q];
+      for (int jj = 0; jj < Q; ++jj) acc = madd(acc, s.B[jj * P + bb], in[jj * Q]);
       s.bufB[f * Q3 + idx] = acc;
     }
   }
@@ -164,9 +203,9 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       const T* in = s.bufB + f * Q3 + r * Q;
-      T acc = T(0);
+      T acc = zero<T>();
 #pragma unroll
-      for (int ii = 0; ii < Q; ++ii) acc += s.B[ii * P + aa] * in[ii];
+      for (int ii = 0; ii < Q; ++ii) acc = madd(acc, s.B[ii * P + aa], in[ii]);
       s.bufA[f * Q3 + idx] = acc;
     }
   }
@@ -180,7 +219,7 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
     for (int f = 0; f < 4; ++f) {
       long long g = f * nn + n;
       if (a.mask && a.mask[g]) continue;
-      atomicAdd(a.y + g, s.bufA[f * Q3 + idx]);
+      atomicAdd(a.y + g, to_vec(s.bufA[f * Q3 + idx]));
     }
   }
 }
@@ -188,7 +227,8 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
 // Pointwise linear map of the Jacobian with the stored words (already scaled
 // by the quadrature weight and the parent-to-reference factors).
 template <typename T>
-__device__ __forceinline__ void jac_point(const T* lin, const T* linP, const T* linC, long long stride,
+__device__ __forceinline__ void jac_point(const typename ElemTypes<T>::L* lin, const typename ElemTypes<T>::L* linP,
+                                          const typename ElemTypes<T>::L* linC, long long stride, long long lo,
                                           const T g[4][3], T phi, T o[4][3], T& o0) {
   T gu[9];
 #pragma unroll
@@ -197,31 +237,37 @@ __device__ __forceinline__ void jac_point(const T* lin, const T* linP, const T* 
     for (int al = 0; al < 3; ++al) gu[3 * f + al] = g[f][al];
   T ou[9];
 #pragma unroll
-  for (int m = 0; m < 9; ++m) ou[m] = ldg(linP + m * stride) * phi;
+  for (int m = 0; m < 9; ++m) ou[m] = mul(ld_lin<T>(linP + m * stride, lo), phi);
   // symmetric 9x9 block
 #pragma unroll
   for (int m = 0; m < 9; ++m) {
 #pragma unroll
     for (int n = m; n < 9; ++n) {
-      T A = ldg(lin + (long long)sym9(m, n) * stride);
-      ou[m] += A * gu[n];
-      if (n != m) ou[n] += A * gu[m];
+      T A = ld_lin<T>(lin + (long long)sym9(m, n) * stride, lo);
+      ou[m] = madd(ou[m], A, gu[n]);
+      if (n != m) ou[n] = madd(ou[n], A, gu[m]);
     }
   }
-  T s0 = ldg(lin + kWD * stride) * phi;
+  T s0 = mul(ld_lin<T>(lin + kWD * stride, lo), phi);
 #pragma unroll
-  for (int m = 0; m < 9; ++m) s0 += ldg(linC + m * stride) * gu[m];
+  for (int m = 0; m < 9; ++m) s0 = madd(s0, ld_lin<T>(linC + m * stride, lo), gu[m]);
   o0 = s0;
 #pragma unroll
   for (int f = 0; f < 3; ++f)
 #pragma unroll
     for (int al = 0; al < 3; ++al) o[f][al] = ou[3 * f + al];
 #pragma unroll
-  for (int al = 0; al < 3; ++al) o[3][al] = ldg(lin + (kWK + al) * stride) * g[3][al];
+  for (int al = 0; al < 3; ++al) o[3][al] = mul(ld_lin<T>(lin + (kWK + al) * stride, lo), g[3][al]);
 }
 
+// Resident blocks per SM the register allocation is held to (Q = 5: 250
+// threads per block, 97 KB of shared memory at 8-byte words): two for FP64 and
+// double-float (<= 128 registers), three for FP32 (<= 85 registers).  With a
+// single resident block the barriers of the slice loop leave the SM idle.
+template <typename T> constexpr int elem_min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+
 template <int P, int Q, typename T, int MODE>
-__global__ void __launch_bounds__(Q * Q * elems_per_block(Q))
+__global__ void __launch_bounds__(Q * Q * elems_per_block(Q), elem_min_blocks<T>())
 k_elem(const ElemArgs<T> a) {
   constexpr int EB = elems_per_block(Q);
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
@@ -236,10 +282,14 @@ k_elem(const ElemArgs<T> a) {
   T* mats = sm;
   T* Bs = mats;
   T* Dcs = Bs + Q * P;
-  for (int idx = t; idx < Q * P; idx += blockDim.x) Bs[idx] = a.B[idx];
-  for (int idx = t; idx < Q * Q; idx += blockDim.x) Dcs[idx] = a.Dc[idx];
-  T* base = sm + mat_smem_words<P, Q>() + el * elem_smem_words<Q>();
-  ElemSmem<P, Q, T> s{base, base + 4 * Q3, base + 8 * Q3, Bs, Dcs, nullptr};
+  for (int idx = t; idx < Q * P; idx += blockDim.x) Bs[idx] = from_store<T>(a.B[idx]);
+  for (int idx = t; idx < Q * Q; idx += blockDim.x) Dcs[idx] = from_store<T>(a.Dc[idx]);
+  constexpr bool kSplit = elem_split<T>() && MODE == kApply;
+  T* base = sm + mat_smem_words<P, Q>() + el * elem_smem_words_t<Q, T>();
+  // split form: bufB first (read by every slice's gradients), then bufA which
+  // extends to the 8 x Q^3 derivative outputs of the pointwise stage
+  ElemSmem<P, Q, T> s = kSplit ? ElemSmem<P, Q, T>{base + 4 * Q3, base, nullptr, Bs, Dcs, nullptr}
+                               : ElemSmem<P, Q, T>{base, base + 4 * Q3, base + 8 * Q3, Bs, Dcs, nullptr};
   __syncthreads();
 
   if constexpr (MODE == kApply || MODE == kEval) forward<P, Q, T>(a, s, e, valid, ij);
@@ -267,22 +317,66 @@ k_elem(const ElemArgs<T> a) {
 #pragma unroll
   for (int f = 0; f < 4; ++f)
 #pragma unroll
-    for (int k = 0; k < Q; ++k) Y[f][k] = T(0);
+    for (int k = 0; k < Q; ++k) Y[f][k] = zero<T>();
 
   const long long blk_words = (long long)kLinWords * Q3 * EB;
   const long long stride = (long long)Q3 * EB;
+  if constexpr (kSplit) {
+    // pointwise stage of all slices without barriers: z-derivative and value
+    // terms into the registers of the own column, x- and y-derivative outputs
+    // to shared memory
+    T* oxy = s.bufA;  // [8][Q^3]
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T g[4][3], phi, o[4][3], o0 = zero<T>();
+      grad_at<P, Q, T>(s, i, j, k, g, phi);
+      if (valid) {
+        long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
+        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, g, phi, o, o0);
+      } else {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();
+      }
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+#pragma unroll
+        for (int kk = 0; kk < Q; ++kk) Y[f][kk] = madd(Y[f][kk], s.Dc[k * Q + kk], o[f][2]);
+        oxy[(2 * f) * Q3 + k * Q2 + ij] = o[f][0];
+        oxy[(2 * f + 1) * Q3 + k * Q2 + ij] = o[f][1];
+      }
+      Y[3][k] = add(Y[3][k], o0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < Q; ++k)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const T* ox = oxy + (2 * f) * Q3 + k * Q2;
+        const T* oy = oxy + (2 * f + 1) * Q3 + k * Q2;
+        T acc = Y[f][k];
+#pragma unroll
+        for (int m = 0; m < Q; ++m) {
+          acc = madd(acc, s.Dc[m * Q + i], ox[j * Q + m]);
+          acc = madd(acc, s.Dc[m * Q + j], oy[m * Q + i]);
+        }
+        Y[f][k] = acc;
+      }
+    __syncthreads();  // the derivative outputs are read; backward reuses the buffers
+    backward<P, Q, T>(a, s, e, valid, ij, Y);
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < Q; ++k) {
-    T o[4][3], o0 = T(0);
+    T o[4][3], o0 = zero<T>();
     if constexpr (MODE == kApply) {
       T g[4][3], phi;
       grad_at<P, Q, T>(s, i, j, k, g, phi);
       if (valid) {
         long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
-        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, g, phi, o, o0);
+        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, g, phi, o, o0);
       } else {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = T(0);
+        for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();
       }
     } else {  // kBack: integrands from the pointwise kernel
       if (valid) {
@@ -296,15 +390,15 @@ k_elem(const ElemArgs<T> a) {
         for (int al = 0; al < 3; ++al) o[3][al] = (T)a.scratch[(10 + al) * a.nq + q];
       } else {
 #pragma unroll
-        for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = T(0);
+        for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();
       }
     }
     // transposed z-derivative (own column) and the value term
 #pragma unroll
     for (int f = 0; f < 4; ++f)
 #pragma unroll
-      for (int kk = 0; kk < Q; ++kk) Y[f][kk] += s.Dc[k * Q + kk] * o[f][2];
-    Y[3][k] += o0;
+      for (int kk = 0; kk < Q; ++kk) Y[f][kk] = madd(Y[f][kk], s.Dc[k * Q + kk], o[f][2]);
+    Y[3][k] = add(Y[3][k], o0);
     // x- and y-derivative outputs of this slice through shared memory
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
@@ -314,13 +408,13 @@ k_elem(const ElemArgs<T> a) {
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      T acc = T(0);
+      T acc = Y[f][k];
 #pragma unroll
       for (int m = 0; m < Q; ++m) {
-        acc += s.Dc[m * Q + i] * s.slice[(2 * f) * Q2 + j * Q + m];
-        acc += s.Dc[m * Q + j] * s.slice[(2 * f + 1) * Q2 + m * Q + i];
+        acc = madd(acc, s.Dc[m * Q + i], s.slice[(2 * f) * Q2 + j * Q + m]);
+        acc = madd(acc, s.Dc[m * Q + j], s.slice[(2 * f + 1) * Q2 + m * Q + i]);
       }
-      Y[f][k] += acc;
+      Y[f][k] = acc;
     }
     __syncthreads();
   }
@@ -441,7 +535,13 @@ cudaError_t launch_elem_pq(int mode, const ElemArgs<T>& a, cudaStream_t st) {
   if (nblk == 0) return cudaSuccess;
   size_t smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words<Q>());
   dim3 block(Q * Q * EB);
-  if (mode == kApply) {
+  if (mode == kApply) smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words_t<Q, T>());
+  if constexpr (sizeof(T) != sizeof(typename ElemTypes<T>::L)) {  // double-float: the action only
+    if (mode != kApply) return cudaErrorInvalidValue;
+    auto k = k_elem<P, Q, T, kApply>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<nblk, block, smem, st>>>(a);
+  } else if (mode == kApply) {
     auto k = k_elem<P, Q, T, kApply>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k<<<nblk, block, smem, st>>>(a);

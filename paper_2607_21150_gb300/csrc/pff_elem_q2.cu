@@ -1,4 +1,4 @@
-// Element kernels for Q = 2 Gauss points per direction, every P <= Q, FP64 and FP32.
+// Element kernels for Q = 2 Gauss points per direction, every P <= Q, FP64, FP32 and double-float (action only).
 #include "pff_elem.cuh"
 
 namespace pff {
@@ -19,6 +19,7 @@ cudaError_t launch_diag_q2(int P, const ElemArgs<T>& a, cudaStream_t st) {
 }
 template cudaError_t launch_elem_q2<double>(int, int, const ElemArgs<double>&, cudaStream_t);
 template cudaError_t launch_elem_q2<float>(int, int, const ElemArgs<float>&, cudaStream_t);
+template cudaError_t launch_elem_q2<df64>(int, int, const ElemArgs<df64>&, cudaStream_t);
 template cudaError_t launch_diag_q2<double>(int, const ElemArgs<double>&, cudaStream_t);
 template cudaError_t launch_diag_q2<float>(int, const ElemArgs<float>&, cudaStream_t);
 

@@ -47,13 +47,15 @@ struct pff_op {
   uint8_t* phase = nullptr;
   uint8_t* flags = nullptr;
   double* lin64 = nullptr;
-  float* lin32 = nullptr;
+  float* lin32 = nullptr;     // FP32 copy; with df = 1 the hi plane [0, lin_len) and lo plane [lin_len, 2 lin_len)
   long long lin_len = 0;
   double* io = nullptr;
   uint8_t* mask = nullptr;
   double* dvals = nullptr;
   int* status = nullptr;
   int f32 = 0;
+  int df = 0;                 // maintain the double-float planes of the stored linearisation
+  int lin32_planes = 0;       // FP32 planes allocated at lin32 (0, 1 or 2)
   double* fint = nullptr;     // internal force work vector of pff_reaction (allocated on first use)
   double* sums = nullptr;     // 4 doubles
 };

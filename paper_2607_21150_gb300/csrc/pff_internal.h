@@ -98,8 +98,9 @@ cudaError_t launch_adjoint_point(const AdjArgs& a, cudaStream_t st);
 enum ElemMode { kApply = 0, kEval = 1, kBack = 2 };
 
 // Double-float value hi + lo (two FP32 words, about 48 significant bits); the
-// arithmetic lives in pff_df.cuh.
-struct df64 {
+// arithmetic lives in pff_df.cuh.  8-byte aligned so that shared-memory
+// accesses are single 64-bit transactions.
+struct __align__(8) df64 {
   float hi, lo;
 };
 
@@ -147,7 +148,6 @@ cudaError_t launch_pointwise(const PointArgs& a, cudaStream_t st);
 // Vector / transfer kernels (pff_vec.cu)
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
-cudaError_t launch_to_f32(const double* a, float* b, long long n, cudaStream_t st);
 // hi[i] = fl32(a[i]) and, when lo is not null, lo[i] = fl32(a[i] - hi[i]).
 cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long n, cudaStream_t st);
 cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st);

@@ -405,9 +405,10 @@ int fgmres(pff_solver* s, const double* b, double* x, double rtol, int maxit, in
   kw.m = s->prm.krylov_restart;
   kw.V = s->V;
   kw.Z = s->Z;
+  const pff_prec outer = (pff_prec)s->prm.outer_prec;
   auto A = [&](const double* in, double* out) {
-    if (s->transpose) return pff_jacobian_transpose_apply(F, PFF_F64, in, out, st);
-    return pff_jacobian_apply(F, PFF_F64, in, out, st);
+    if (s->transpose) return pff_jacobian_transpose_apply(F, outer, in, out, st);
+    return pff_jacobian_apply(F, outer, in, out, st);
   };
   auto M = [&](const double* in, double* out) { return precondition(s, in, out, st); };
   return gmres_flex(s, kw, A, M, b, x, rtol, maxit, iters, relres, st);
@@ -509,6 +510,7 @@ int pff_solver_default_params(pff_solver_params* p) {
   p->coarse_rtol = 1e-2;
   p->coarse_maxit = 200;
   p->verbose = 0;
+  p->outer_prec = PFF_F64;
   return PFF_OK;
 }
 
@@ -524,6 +526,10 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     if (levels[l]->op != op || levels[l]->p >= levels[l - 1]->p)
       return sfail(PFF_ERR_INVALID, "pff_create_solver: levels must share op with decreasing order");
   if (prm->mixed && !op->lin32) return sfail(PFF_ERR_INVALID, "pff_create_solver: mixed precision needs pff_op_enable_f32");
+  if (prm->outer_prec != PFF_F64 && prm->outer_prec != PFF_DF64)
+    return sfail(PFF_ERR_INVALID, "pff_create_solver: outer_prec must be PFF_F64 or PFF_DF64");
+  if (prm->outer_prec == PFF_DF64 && !op->df)
+    return sfail(PFF_ERR_INVALID, "pff_create_solver: outer_prec PFF_DF64 needs pff_op_enable_df");
   pff_solver* s = new pff_solver();
   s->op = op;
   s->prm = *prm;

@@ -40,13 +40,18 @@ cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* u
   return cudaGetLastError();
 }
 
-__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    b[i] = (float)a[i];
+// Double-float split of the stored linearisation: hi = fl32(a), lo = fl32(a - hi).
+__global__ void k_split_df(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = a[i];
+    const float h = __double2float_rn(v);
+    hi[i] = h;
+    if (lo) lo[i] = __double2float_rn(v - (double)h);
+  }
 }
-cudaError_t launch_to_f32(const double* a, float* b, long long n, cudaStream_t st) {
+cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_to_f32<<<grid_for(n), kVecThreads, 0, st>>>(a, b, n);
+  k_split_df<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, n);
   return cudaGetLastError();
 }
 

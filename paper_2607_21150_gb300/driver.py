@@ -16,12 +16,16 @@ from .session import Session
 
 class LoadStepper:
     def __init__(self, w: Workload, levels=None, mixed: bool = True, session: Session | None = None,
-                 **solver_params):
+                 df: bool = False, **solver_params):
+        """df: the fine-level action inside FGMRES in double-float arithmetic
+        (PFF_DF64) instead of FP64."""
         m = w.mesh
         if levels is None:
             levels = {4: [4, 2, 1], 3: [3, 1], 2: [2, 1], 1: [1]}[m.p]
         self.levels = list(levels)
-        self.s = session or Session(w, levels=[p for p in self.levels if p != m.p], f32=mixed)
+        self.s = session or Session(w, levels=[p for p in self.levels if p != m.p], f32=mixed, df=df)
+        if df:
+            solver_params.setdefault("outer_prec", pff.PFF_DF64)
         self.solver = self.s.solver(self.levels, mixed=int(mixed), **solver_params)
         self.w = w
         self.z = torch.from_numpy(np.ascontiguousarray(w.z, dtype=np.float64).ravel()).to(self.s.dev)

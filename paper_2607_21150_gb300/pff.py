@@ -14,6 +14,7 @@ from . import build as _build
 
 PFF_F64 = 0
 PFF_F32 = 1
+PFF_DF64 = 2
 STATUS_EIGEN, STATUS_DETF, STATUS_NONFINITE = 1, 2, 4
 
 _lib = None
@@ -40,7 +41,7 @@ class pff_solver_params(ctypes.Structure):
                 ("power_iters", ctypes.c_int), ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int),
                 ("krylov_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("line_search_max", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_rtol", ctypes.c_double),
-                ("coarse_maxit", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("coarse_maxit", ctypes.c_int), ("verbose", ctypes.c_int), ("outer_prec", ctypes.c_int)]
 
 
 class pff_newton_stats(ctypes.Structure):
@@ -76,6 +77,7 @@ _SIGS = {
     "pff_create_operator": ([_VP, _VP, _VP, ctypes.POINTER(_VP)], _I),
     "pff_destroy_operator": ([_VP], _I),
     "pff_op_enable_f32": ([_VP, _I], _I),
+    "pff_op_enable_df": ([_VP, _I], _I),
     "pff_op_num_qpoints": ([_VP], _I64),
     "pff_op_num_nodes": ([_VP], _I64),
     "pff_set_qpoint_state": ([_VP, _VP, _VP, _VP], _I),
@@ -227,6 +229,10 @@ def pff_destroy_operator(op):
 
 def pff_op_enable_f32(op, enable=True):
     _call("pff_op_enable_f32", op, 1 if enable else 0)
+
+
+def pff_op_enable_df(op, enable=True):
+    _call("pff_op_enable_df", op, 1 if enable else 0)
 
 
 def pff_op_num_qpoints(op):

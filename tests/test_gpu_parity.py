@@ -4,7 +4,10 @@ Tolerance (FP64): relative L2 error <= 1e-12 for the residual, the Jacobian
 action and its transpose, the diagonal, the transfers and the Chebyshev
 smoother; flags bit-exact at every point whose decision margin exceeds 1e-10
 (relative); trial history <= 1e-12 relative.  FP32 level applies are compared
-with the FP64 ones at the FP32 rounding level (<= 2e-5 relative L2).
+with the FP64 ones at the FP32 rounding level (<= 2e-5 relative L2).  The
+double-float action (PFF_DF64) is held to the FP64 bar against the oracle:
+each of its operations errs by about 2^-47 of the magnitudes involved, some
+200 operations feed one output, so its error stays near 1e-13.
 """
 import numpy as np
 import pytest
@@ -68,7 +71,7 @@ CASES = {
 def case(request, orc):
     w = CASES[request.param]()
     ref = orc.assemble(w)
-    s = Session(w)
+    s = Session(w, df=True)
     r = s.residual(w.z)
     torch.cuda.synchronize()
     return request.param, w, ref, s, r
@@ -97,6 +100,31 @@ def test_jacobian_apply(case):
     assert rel(np_(y), ref["K"] @ v) <= TOL, name
     yt = s.apply(x, transpose=True)
     assert rel(np_(yt), ref["K"].T @ v) <= TOL, name
+
+
+def test_df64_apply(case):
+    name, w, ref, s, r = case
+    v = inputs.random_vector(w.mesh.ndof, 1)
+    x = torch.from_numpy(v).cuda()
+    y = s.apply(x, prec=pff.PFF_DF64)
+    assert rel(np_(y), ref["K"] @ v) <= TOL, name
+    yt = s.apply(x, prec=pff.PFF_DF64, transpose=True)
+    assert rel(np_(yt), ref["K"].T @ v) <= TOL, name
+    # Dirichlet rows are the identity, bit for bit
+    if w.mask is not None:
+        mk = w.mask.ravel().astype(bool)
+        assert np.array_equal(np_(y)[mk], v[mk])
+
+
+def test_df64_needs_planes(orc):
+    w = inputs.cube()
+    s = Session(w)
+    s.residual(w.z)
+    x = torch.from_numpy(inputs.random_vector(w.mesh.ndof, 2)).cuda()
+    with pytest.raises(pff.PffError, match="pff_op_enable_df"):
+        s.apply(x, prec=pff.PFF_DF64)
+    with pytest.raises(pff.PffError):
+        pff.pff_assemble_diagonal(s.levels[w.mesh.p], pff.PFF_DF64, x, s.stream)
 
 
 def test_diagonal(case):
@@ -246,15 +274,17 @@ def test_full_size_tension_q4_sampled_rows(orc):
     w.z[mk] = w.dvals[mk]
     w.hist = inputs.random_history(w.mesh.nq, 4, H_max=400.0)
     w.hist[13] = np.maximum(w.hist[13], inputs.zero_history(1)[13, 0])
-    s = Session(w)
+    s = Session(w, df=True)
     r = np_(s.residual(w.z))
     x = inputs.random_vector(w.mesh.ndof, 8)
     xt = torch.from_numpy(x).cuda()
     jx, jtx, dg = np_(s.apply(xt)), np_(s.apply(xt, transpose=True)), np_(s.diag())
+    jx_df = np_(s.apply(xt, prec=pff.PFF_DF64))
+    jtx_df = np_(s.apply(xt, prec=pff.PFF_DF64, transpose=True))
     dofs = np.sort(rng.choice(w.mesh.ndof, 48, replace=False))
     dofs = np.concatenate([dofs, [0, w.mesh.ndof - 1, 3 * w.mesh.nn + w.mesh.nn // 2]])
     ref = orc.sample_rows(w, dofs, x)
-    for key, g in (("r", r), ("jx", jx), ("jtx", jtx), ("diag", dg)):
+    for key, g in (("r", r), ("jx", jx), ("jtx", jtx), ("diag", dg), ("jx", jx_df), ("jtx", jtx_df)):
         err = np.abs(g[dofs] - ref[key]) / np.maximum(np.abs(ref[key]), 1e-300)
         scale = np.abs(ref[key]).max()
         assert np.all(np.abs(g[dofs] - ref[key]) <= 1e-11 * scale + 1e-12 * np.abs(ref[key])), (key, err.max())
