@@ -260,6 +260,38 @@ __device__ __forceinline__ void jac_point(const typename ElemTypes<T>::L* lin, c
   for (int al = 0; al < 3; ++al) o[3][al] = mul(ld_lin<T>(lin + (kWK + al) * stride, lo), g[3][al]);
 }
 
+// L2 prefetch of slice k of this block's stored linearisation (FP32 action):
+// thread w < 67 requests the contiguous run of word w (Q^2 EB words) with one
+// bulk prefetch, so the next slice streams from HBM while this one computes
+// (64^3 Q4: 3.76 -> 3.48 ms; two or three slices ahead measured slower, and
+// the double-float action, issue-bound, lost 1-4 %).  Runs start on 8-byte
+// boundaries; the request is widened to 16-byte boundaries and clipped to the
+// plane.
+constexpr int kPrefetchAhead = 1;  // slices requested ahead of the one computed
+__device__ __forceinline__ void prefetch_run(uintptr_t base, long long first, long long run, long long plane) {
+  const uintptr_t lo = (base + 4 * first) & ~uintptr_t(15);
+  uintptr_t hi = (base + 4 * (first + run) + 15) & ~uintptr_t(15);
+  const uintptr_t end = (base + 4 * plane) & ~uintptr_t(15);
+  if (hi > end) hi = end;
+  if (hi <= lo) return;
+  asm volatile(
+      "{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tcp.async.bulk.prefetch.L2.global [ga], %1;\n\t}"
+      :: "l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+template <int Q, typename T>
+__device__ __forceinline__ void prefetch_slice(const ElemArgs<T>& a, int k, int t) {
+  if constexpr (sizeof(T) == 4) {
+    constexpr int EB = elems_per_block(Q);
+    constexpr long long run = (long long)Q * Q * EB;   // words of one (word, slice) run
+    if (t >= kLinWords || k >= Q) return;
+    const long long nblk = (a.mesh.nel + EB - 1) / EB;
+    const long long plane = nblk * kLinWords * Q * Q * Q * EB;
+    const long long first = blockIdx.x * kLinWords * Q * run + (long long)t * Q * run + k * run;
+    const uintptr_t base = reinterpret_cast<uintptr_t>(a.lin);
+    prefetch_run(base, first, run, plane);
+  }
+}
+
 // Resident blocks per SM the register allocation is held to (Q = 5: 250
 // threads per block, 97 KB of shared memory at 8-byte words): two for FP64 and
 // double-float (<= 128 registers), three for FP32 (<= 85 registers).  With a
@@ -291,6 +323,8 @@ k_elem(const ElemArgs<T> a) {
   ElemSmem<P, Q, T> s = kSplit ? ElemSmem<P, Q, T>{base + 4 * Q3, base, nullptr, Bs, Dcs, nullptr}
                                : ElemSmem<P, Q, T>{base, base + 4 * Q3, base + 8 * Q3, Bs, Dcs, nullptr};
   __syncthreads();
+  if constexpr (kSplit)
+    for (int k = 0; k < kPrefetchAhead; ++k) prefetch_slice<Q, T>(a, k, t);
 
   if constexpr (MODE == kApply || MODE == kEval) forward<P, Q, T>(a, s, e, valid, ij);
 
@@ -329,6 +363,7 @@ k_elem(const ElemArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
       T g[4][3], phi, o[4][3], o0 = zero<T>();
+      prefetch_slice<Q, T>(a, k + kPrefetchAhead, t);
       grad_at<P, Q, T>(s, i, j, k, g, phi);
       if (valid) {
         long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
