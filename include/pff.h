@@ -234,9 +234,14 @@ typedef struct {
   int newton_maxit;     /* Newton iterations per call */
   double newton_rtol;   /* stop when ||r|| <= newton_rtol * ||r_0|| */
   int line_search_max;  /* step halvings of the backtracking line search (0 = full steps) */
-  int coarse_solver;    /* coarsest assembled level: 0 Chebyshev(coarse_degree), 1 Jacobi-GMRES */
-  double coarse_rtol;   /* Jacobi-GMRES relative tolerance on the coarsest level */
-  int coarse_maxit;     /* Jacobi-GMRES iterations per coarse solve */
+  int coarse_solver;    /* coarsest assembled level: 0 Chebyshev(coarse_degree), 1 Jacobi-GMRES,
+                           2 GMRES preconditioned by a geometric h-multigrid V-cycle (full
+                           coarsening of the Q1 grid while the element counts are even and
+                           >= 4; Galerkin element matrices, trilinear transfers,
+                           Chebyshev(cheb_degree) smoothing, Chebyshev(coarse_degree) on
+                           the coarsest grid) */
+  double coarse_rtol;   /* coarse GMRES relative tolerance */
+  int coarse_maxit;     /* coarse GMRES iterations per coarse solve */
   int verbose;          /* 1: one line per Newton iteration on stderr */
   int outer_prec;       /* fine-level action inside FGMRES: PFF_F64, or PFF_DF64 (pff_op_enable_df) */
 } pff_solver_params;
@@ -255,8 +260,9 @@ typedef struct {
 } pff_newton_stats;
 
 /* Fills the defaults: mixed 1, Chebyshev(3) on [0.1, 1.1] lambda_max, coarsest
- * assembled level solved by Jacobi-GMRES to 1e-2 (at most 200 iterations;
- * Chebyshev(16) on [0.02, 1.1] when coarse_solver = 0), 10 Arnoldi steps,
+ * assembled level solved by GMRES to 1e-2 (at most 200 iterations)
+ * preconditioned by one h-multigrid V-cycle (coarse_solver 2; Chebyshev(16)
+ * on [0.02, 1.1] on its coarsest grid), 10 Arnoldi steps,
  * FGMRES(30) to 1e-3 with at most 200 iterations, Newton to 1e-8 in at most 20
  * iterations with up to 8 line-search halvings, quiet. */
 int pff_solver_default_params(pff_solver_params* params);
@@ -278,6 +284,16 @@ int pff_solver_level_lambda(const pff_solver* solver, int level, double* lmax);
 int pff_solver_vcycle(pff_solver* solver, const double* r, double* z, void* stream);
 /* y = A_c x with the assembled coarse operator (FP64 coarse vectors). */
 int pff_solver_coarse_apply(pff_solver* solver, const double* x, double* y, void* stream);
+/* Geometric h-hierarchy of coarse_solver 2 (level 0 = the assembled Q1 level;
+ * valid after pff_solver_setup): number of levels (0 without the hierarchy). */
+int pff_solver_num_hlevels(const pff_solver* solver);
+/* Element grid (dims[3], host) and lambda_max(D^-1 A_l) estimate of h-level l. */
+int pff_solver_hlevel_info(const pff_solver* solver, int level, int* dims, double* lmax);
+/* y = A_l x on h-level l (FP64 [4][N_n(l)] device vectors): the Galerkin
+ * operator P^T A_(l-1) P with the Dirichlet DoFs of the level set to identity. */
+int pff_solver_hlevel_apply(pff_solver* solver, int level, const double* x, double* y, void* stream);
+/* One h-multigrid V-cycle x = M_h^-1 b on h-level 0 (FP64 Q1-level vectors). */
+int pff_solver_hcycle(pff_solver* solver, const double* b, double* x, void* stream);
 /* FGMRES solve J x = b (x starts at 0); returns iterations and ||b - J x|| / ||b||. */
 int pff_solver_krylov(pff_solver* solver, const double* b, double* x, double rtol, int maxit, int* iters,
                       double* relres, void* stream);

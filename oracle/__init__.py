@@ -245,6 +245,36 @@ def prolongation(mesh, pc: int, pf: int | None = None):
     return sp.block_diag([P1] * 4, format="csr")
 
 
+def h_prolongation(nx: int, ny: int, nz: int):
+    """Prolongation of vertex-centred full coarsening on a structured order-1
+    grid of (2 nx, 2 ny, 2 nz) fine elements from (nx, ny, nz) coarse ones
+    (4 n_f x 4 n_c, all four fields): the coarse hat functions evaluated at the
+    fine vertices, P1[i, I] = max(0, 1 - |i / 2 - I|) per direction, and their
+    tensor product (x fastest)."""
+    import scipy.sparse as sp
+
+    def one_d(nc):
+        rows, cols, vals = [], [], []
+        for i in range(2 * nc + 1):
+            for I in range(nc + 1):
+                v = max(0.0, 1.0 - abs(0.5 * i - I))
+                if v > 0.0:
+                    rows.append(i)
+                    cols.append(I)
+                    vals.append(v)
+        return sp.csr_matrix((vals, (rows, cols)), shape=(2 * nc + 1, nc + 1))
+
+    P1 = sp.kron(one_d(nz), sp.kron(one_d(ny), one_d(nx))).tocsr()
+    return sp.block_diag([P1] * 4, format="csr")
+
+
+def h_coarse_mask(mask_f, nx: int, ny: int, nz: int):
+    """Coarse Dirichlet mask [4][n_c] of the h-coarsening: the mask of the
+    coincident fine vertex (2 I, 2 J, 2 K)."""
+    mf = np.asarray(mask_f).reshape(4, 2 * nz + 1, 2 * ny + 1, 2 * nx + 1)
+    return np.ascontiguousarray(mf[:, ::2, ::2, ::2]).reshape(4, -1)
+
+
 def masked_prolongation(P, mask_f, mask_c):
     """P with the rows of fine Dirichlet DoFs and columns of coarse Dirichlet
     DoFs removed: diag(1 - m_f) P diag(1 - m_c)."""

@@ -191,6 +191,17 @@ cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaSt
 cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
                                   const uint8_t* maskc, double* Ke, double* A, cudaStream_t st);
 cudaError_t launch_q1_spmv_t(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
+// Geometric h-hierarchy on the order-1 grid (full coarsening, trilinear
+// transfers): Galerkin element matrices of the coarse grid, their gather into
+// the stencil storage, the coarse mask, and the transfers.
+cudaError_t launch_q1_coarsen(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, const double* Kef,
+                              double* Kec, cudaStream_t st);
+cudaError_t launch_q1_gather(const MeshDev& mc, const double* Ke, const uint8_t* maskc, double* A, cudaStream_t st);
+cudaError_t launch_hmask(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, uint8_t* maskc, cudaStream_t st);
+cudaError_t launch_hprolong_add(const MeshDev& mc, const MeshDev& mf, const double* xc, double* xf,
+                                const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st);
+cudaError_t launch_hrestrict(const MeshDev& mc, const MeshDev& mf, const double* rf, double* rc,
+                             const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st);
 cudaError_t launch_sel_scale(double* y, const uint8_t* sel, double s, long long n, cudaStream_t st);
 cudaError_t launch_zero_masked(double* y, const uint8_t* mask, long long n, cudaStream_t st);
 

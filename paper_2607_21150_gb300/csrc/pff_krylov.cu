@@ -417,6 +417,162 @@ __global__ void k_q1_gather(MeshDev mc, const double* __restrict__ Ke, const uin
   }
 }
 
+// ---- geometric h-hierarchy on the order-1 grid ---------------------------
+// Coarse element E (2x2x2 fine elements c) of a vertex-centred full coarsening
+// with trilinear interpolation: the prolongation restricted to E maps the 8
+// coarse vertices to the 27 fine vertices inside E, so the Galerkin operator
+// is a sum of element matrices
+//   Ke_c[E] = sum_c W_c^T ((I - M) Ke_f[c] (I - M)) W_c,
+// W_c[(f, a), (f, A)] = prod_d w((c_d + a_d) / 2, A_d), w(x, 0) = 1 - x,
+// w(x, 1) = x, M the fine Dirichlet mask (prescribed DoFs take no correction).
+// One block per coarse element, the two contractions through shared memory.
+__device__ __forceinline__ double q1_weight(int c, int a, int A) {
+  double w = 1.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int cd = (c >> d) & 1, ad = (a >> d) & 1, Ad = (A >> d) & 1;
+    const double x = 0.5 * (cd + ad);
+    w *= Ad ? x : 1.0 - x;
+  }
+  return w;
+}
+
+__global__ void __launch_bounds__(256) k_q1_coarsen(MeshDev mf, MeshDev mc, const uint8_t* __restrict__ maskf,
+                                                    const double* __restrict__ Kef, double* __restrict__ Kec) {
+  __shared__ double Kf[1024], Y[1024], Kc[1024];
+  __shared__ int fnode[8];
+  const int E = blockIdx.x, t = threadIdx.x;
+  const int Ex = E % mc.nx, Ey = (E / mc.nx) % mc.ny, Ez = E / (mc.nx * mc.ny);
+  for (int idx = t; idx < 1024; idx += blockDim.x) Kc[idx] = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    const int ex = 2 * Ex + (c & 1), ey = 2 * Ey + ((c >> 1) & 1), ez = 2 * Ez + (c >> 2);
+    const long long e = ex + (long long)mf.nx * (ey + (long long)mf.ny * ez);
+    __syncthreads();  // Kf, Y and fnode of the previous child are consumed
+    if (t < 8)
+      fnode[t] = (int)((ex + (t & 1)) + (long long)mf.nnx * ((ey + ((t >> 1) & 1)) + (long long)mf.nny * (ez + (t >> 2))));
+    __syncthreads();
+    for (int idx = t; idx < 1024; idx += blockDim.x) {
+      const int row = idx >> 5, col = idx & 31;
+      double v = Kef[e * 1024 + idx];
+      if (maskf && (maskf[(row >> 3) * mf.nn + fnode[row & 7]] || maskf[(col >> 3) * mf.nn + fnode[col & 7]])) v = 0.0;
+      Kf[idx] = v;
+    }
+    __syncthreads();
+    // Y[(f, a)][(g, B)] = sum_b Kf[(f, a)][(g, b)] W_c[b][B]
+    for (int idx = t; idx < 1024; idx += blockDim.x) {
+      const int row = idx >> 5, g = (idx >> 3) & 3, B = idx & 7;
+      double acc = 0.0;
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc += Kf[row * 32 + g * 8 + b] * q1_weight(c, b, B);
+      Y[idx] = acc;
+    }
+    __syncthreads();
+    // Kc[(f, A)][(g, B)] += sum_a W_c[a][A] Y[(f, a)][(g, B)]
+    for (int idx = t; idx < 1024; idx += blockDim.x) {
+      const int f = idx >> 8, A = (idx >> 5) & 7, col = idx & 31;
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) acc += q1_weight(c, a, A) * Y[(f * 8 + a) * 32 + col];
+      Kc[idx] += acc;
+    }
+  }
+  __syncthreads();
+  for (int idx = t; idx < 1024; idx += blockDim.x) Kec[(long long)E * 1024 + idx] = Kc[idx];
+}
+
+// Coarse Dirichlet mask: a coarse vertex is prescribed where the coincident
+// fine vertex is.
+__global__ void k_hmask(MeshDev mf, MeshDev mc, const uint8_t* __restrict__ maskf, uint8_t* __restrict__ maskc) {
+  const long long N = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (N >= mc.nn) return;
+  const int I = (int)(N % mc.nnx), J = (int)((N / mc.nnx) % mc.nny), K = (int)(N / ((long long)mc.nnx * mc.nny));
+  const long long n = 2 * I + (long long)mf.nnx * (2 * J + (long long)mf.nny * 2 * K);
+  for (int f = 0; f < 4; ++f) maskc[f * mc.nn + N] = maskf ? maskf[f * mf.nn + n] : 0;
+}
+
+// x_f += P x_c on unmasked fine DoFs (trilinear, one thread per fine vertex).
+__global__ void k_hprolong_add(MeshDev mc, MeshDev mf, const double* __restrict__ xc, double* __restrict__ xf,
+                               const uint8_t* __restrict__ maskc, const uint8_t* __restrict__ maskf) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= mf.nn) return;
+  const int i = (int)(n % mf.nnx), j = (int)((n / mf.nnx) % mf.nny), k = (int)(n / ((long long)mf.nnx * mf.nny));
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int dz = 0; dz < 2; ++dz) {
+    if (dz && !(k & 1)) break;
+    const int K = (k >> 1) + dz;
+    const double wz = (k & 1) ? 0.5 : 1.0;
+    for (int dy = 0; dy < 2; ++dy) {
+      if (dy && !(j & 1)) break;
+      const int J = (j >> 1) + dy;
+      const double wy = (j & 1) ? 0.5 : 1.0;
+      for (int dx = 0; dx < 2; ++dx) {
+        if (dx && !(i & 1)) break;
+        const int I = (i >> 1) + dx;
+        const double w = wz * wy * ((i & 1) ? 0.5 : 1.0);
+        const long long N = I + (long long)mc.nnx * (J + (long long)mc.nny * K);
+        for (int f = 0; f < 4; ++f)
+          if (!(maskc && maskc[f * mc.nn + N])) acc[f] += w * xc[f * mc.nn + N];
+      }
+    }
+  }
+  for (int f = 0; f < 4; ++f)
+    if (!(maskf && maskf[f * mf.nn + n])) xf[f * mf.nn + n] += acc[f];
+}
+
+// r_c = P^T r_f (zero on masked DoFs), one thread per coarse vertex gathering
+// the fine vertices within one fine spacing.
+__global__ void k_hrestrict(MeshDev mc, MeshDev mf, const double* __restrict__ rf, double* __restrict__ rc,
+                            const uint8_t* __restrict__ maskc, const uint8_t* __restrict__ maskf) {
+  const long long N = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (N >= mc.nn) return;
+  const int I = (int)(N % mc.nnx), J = (int)((N / mc.nnx) % mc.nny), K = (int)(N / ((long long)mc.nnx * mc.nny));
+  const int nnzf = (int)(mf.nn / ((long long)mf.nnx * mf.nny));
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int k = 2 * K + dz;
+    if (k < 0 || k >= nnzf) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int j = 2 * J + dy;
+      if (j < 0 || j >= mf.nny) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = 2 * I + dx;
+        if (i < 0 || i >= mf.nnx) continue;
+        const double w = (dx ? 0.5 : 1.0) * (dy ? 0.5 : 1.0) * (dz ? 0.5 : 1.0);
+        const long long n = i + (long long)mf.nnx * (j + (long long)mf.nny * k);
+        for (int f = 0; f < 4; ++f)
+          if (!(maskf && maskf[f * mf.nn + n])) acc[f] += w * rf[f * mf.nn + n];
+      }
+    }
+  }
+  for (int f = 0; f < 4; ++f) rc[f * mc.nn + N] = (maskc && maskc[f * mc.nn + N]) ? 0.0 : acc[f];
+}
+
+cudaError_t launch_q1_coarsen(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, const double* Kef,
+                              double* Kec, cudaStream_t st) {
+  if (mc.nel == 0) return cudaSuccess;
+  k_q1_coarsen<<<mc.nel, 256, 0, st>>>(mf, mc, maskf, Kef, Kec);
+  return cudaGetLastError();
+}
+cudaError_t launch_q1_gather(const MeshDev& mc, const double* Ke, const uint8_t* maskc, double* A, cudaStream_t st) {
+  const long long nt = mc.nn * 16;
+  k_q1_gather<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(mc, Ke, maskc, A);
+  return cudaGetLastError();
+}
+cudaError_t launch_hmask(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, uint8_t* maskc, cudaStream_t st) {
+  k_hmask<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mf, mc, maskf, maskc);
+  return cudaGetLastError();
+}
+cudaError_t launch_hprolong_add(const MeshDev& mc, const MeshDev& mf, const double* xc, double* xf,
+                                const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
+  k_hprolong_add<<<(unsigned)((mf.nn + 255) / 256), 256, 0, st>>>(mc, mf, xc, xf, maskc, maskf);
+  return cudaGetLastError();
+}
+cudaError_t launch_hrestrict(const MeshDev& mc, const MeshDev& mf, const double* rf, double* rc,
+                             const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
+  k_hrestrict<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, mf, rf, rc, maskc, maskf);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
                                   const uint8_t* maskc, double* Ke, double* A, cudaStream_t st) {
   size_t smem = sizeof(double) * (size_t)(kQ1Combos * Q * Q * Q + kQ1Combos * 4 * Q * Q + kQ1Combos * 16 * Q);

@@ -8,7 +8,10 @@
 // * V-cycle: Chebyshev(k) pre- and post-smoothing on D^-1 J of every
 //   matrix-free level (FP64, or FP32 in the mixed variant), p-restriction /
 //   prolongation between levels, and on an order-1 coarsest level an FP64
-//   Chebyshev-Jacobi solve with the assembled Q1 Galerkin operator.
+//   solve with the assembled Q1 Galerkin operator: Chebyshev-Jacobi,
+//   Jacobi-GMRES, or GMRES preconditioned by a geometric h-multigrid V-cycle
+//   on the structured Q1 grid (the paper's algebraic coarse solver replaced
+//   by geometric coarsening, which the structured box allows).
 // * Eigenvalue bounds: lambda_max of D^-1 J per level by power iteration from a
 //   fixed seeded vector; smoothing interval [lo, hi] * lambda_max.
 #include <algorithm>
@@ -48,6 +51,19 @@ struct LevelWork {
   double lmax = 1.0;
 };
 
+// One level of the geometric h-hierarchy below the assembled Q1 level (level 0
+// aliases the Q1 level's operator, diagonal, element matrices and mask).
+struct HLevel {
+  MeshDev mesh;
+  long long n = 0;
+  double *Ke = nullptr, *A = nullptr, *diag = nullptr;
+  const uint8_t* mask = nullptr;
+  uint8_t* own_mask = nullptr;
+  double *b = nullptr, *x = nullptr, *r = nullptr, *work = nullptr;
+  double lmax = 1.0;
+  bool owns = false;
+};
+
 double now() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -62,6 +78,7 @@ struct pff_solver {
   double *A = nullptr, *cdiag = nullptr, *cb = nullptr, *cx = nullptr, *cwork = nullptr;
   double *cV = nullptr, *cZ = nullptr;  // coarse GMRES basis
   double* Ke = nullptr;                 // coarse element matrices [nel][32][32]
+  std::vector<HLevel> hl;               // geometric h-hierarchy (coarse_solver 2)
   long long coarse_iters = 0;
   double clmax = 1.0;
   long long n = 0;
@@ -147,7 +164,7 @@ int coarse_spmv(pff_solver* s, const MeshDev& mc, const double* x, double* y, cu
 }
 
 int coarse_cheb(pff_solver* s, cudaStream_t st) {
-  if (s->prm.coarse_solver == 1) return coarse_gmres(s, st);
+  if (s->prm.coarse_solver >= 1) return coarse_gmres(s, st);
   // FP64 Chebyshev-Jacobi on the assembled coarse operator, from x = 0.
   LevelWork& c = s->lv.back();
   const MeshDev& mc = c.L->mesh;
@@ -201,6 +218,60 @@ int vcycle(pff_solver* s, int l, cudaStream_t st) {
   return PFF_OK;
 }
 
+// ---- geometric h-multigrid on the assembled order-1 grid ------------------
+int h_spmv(pff_solver* s, const HLevel& h, const double* x, double* y, cudaStream_t st) {
+  if (s->transpose) S_CK(launch_q1_spmv_t(h.mesh, h.A, x, y, st));
+  else S_CK(launch_q1_spmv(h.mesh, h.A, x, y, st));
+  return PFF_OK;
+}
+
+// Chebyshev-Jacobi (Saad, Alg. 12.1) on an assembled level, from x = 0 or from
+// the given x.
+int h_cheb(pff_solver* s, HLevel& h, int degree, double lmin, double lmax, bool zero_init, cudaStream_t st) {
+  const long long n = h.n;
+  double* r = h.work;
+  double* d = h.work + n;
+  double* Ad = h.work + 2 * n;
+  const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  if (zero_init) {
+    S_CK(cudaMemsetAsync(h.x, 0, sizeof(double) * n, st));
+    S_CK(cudaMemsetAsync(Ad, 0, sizeof(double) * n, st));
+  } else {
+    S_RC(h_spmv(s, h, h.x, Ad, st));
+  }
+  S_CK(launch_cheb_init<double>(n, h.b, Ad, h.diag, r, d, 1.0 / theta, st));
+  for (int k = 0; k < degree; ++k) {
+    if (k == degree - 1) {
+      S_CK(launch_cheb_step<double>(n, h.x, d, r, Ad, h.diag, 0.0, 0.0, 1, st));
+      break;
+    }
+    S_RC(h_spmv(s, h, d, Ad, st));
+    const double rho_new = 1.0 / (2.0 * sigma - rho);
+    S_CK(launch_cheb_step<double>(n, h.x, d, r, Ad, h.diag, rho_new * rho, 2.0 * rho_new / delta, 0, st));
+    rho = rho_new;
+  }
+  return PFF_OK;
+}
+
+// V-cycle on h-level l for A_l x = b_l (x from zero): Chebyshev pre- and
+// post-smoothing, residual restriction by P^T, coarse correction, trilinear
+// prolongation; the coarsest grid takes Chebyshev(coarse_degree).
+int hcycle(pff_solver* s, int l, cudaStream_t st) {
+  HLevel& h = s->hl[l];
+  const pff_solver_params& p = s->prm;
+  if (l + 1 == (int)s->hl.size())
+    return h_cheb(s, h, p.coarse_degree, p.coarse_lo * h.lmax, p.cheb_hi * h.lmax, true, st);
+  S_RC(h_cheb(s, h, p.cheb_degree, p.cheb_lo * h.lmax, p.cheb_hi * h.lmax, true, st));
+  S_RC(h_spmv(s, h, h.x, h.r, st));
+  S_CK(launch_bminus<double>(h.r, h.b, h.n, st));
+  HLevel& c = s->hl[l + 1];
+  S_CK(launch_hrestrict(c.mesh, h.mesh, h.r, c.b, c.mask, h.mask, st));
+  S_RC(hcycle(s, l + 1, st));
+  S_CK(launch_hprolong_add(c.mesh, h.mesh, c.x, h.x, c.mask, h.mask, st));
+  return h_cheb(s, h, p.cheb_degree, p.cheb_lo * h.lmax, p.cheb_hi * h.lmax, false, st);
+}
+
 // Spectral radius of a small dense matrix (row-major k x k) by power iteration
 // on the host, with the growth rate averaged over the last iterations so that a
 // dominant complex pair is measured too.
@@ -225,12 +296,13 @@ double small_spectral_radius(const std::vector<double>& H, int k) {
   return std::exp(logsum / counted);
 }
 
-// lambda_max of D^-1 J for a level: k Arnoldi steps (Gram-Schmidt twice, FP64
-// basis in the FGMRES storage) from a seeded random-sign vector; the estimate is
-// the spectral radius of the k x k Hessenberg block (the survey's reading of the
-// eigenvalue bound of a Chebyshev smoother: a few Arnoldi/Lanczos steps).
-int arnoldi_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
-  const long long n = w.n;
+// lambda_max of D^-1 A: k Arnoldi steps (Gram-Schmidt twice, FP64 basis in the
+// FGMRES storage) from a seeded random-sign vector; the estimate is the spectral
+// radius of the k x k Hessenberg block (the reading of the eigenvalue bound of
+// a Chebyshev smoother: a few Arnoldi/Lanczos steps).  op(v, w) sets
+// w = D^-1 A v on FP64 vectors of length n.
+template <typename Op>
+int arnoldi_lmax(pff_solver* s, long long n, Op&& op, double* out, cudaStream_t st) {
   const int k = std::min(s->prm.power_iters, s->prm.krylov_restart);
   double* V = s->V;  // (restart + 1) fine vectors >= (k + 1) level vectors
   S_CK(cudaMemcpyAsync(V, s->pw64, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
@@ -242,15 +314,7 @@ int arnoldi_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
   for (int j = 0; j < k; ++j) {
     double* vj = V + (long long)j * n;
     double* wv = V + (long long)(j + 1) * n;
-    if (w.prec == PFF_F64) {
-      S_RC(pff_jacobian_apply(w.L, PFF_F64, vj, wv, st));
-      S_CK(launch_dscale<double>(wv, wv, (const double*)w.diag, n, st));
-    } else {
-      S_CK(launch_d2f((float*)w.x, vj, n, st));
-      S_RC(pff_jacobian_apply(w.L, PFF_F32, w.x, w.tmp, st));
-      S_CK(launch_dscale<float>((float*)w.tmp, (const float*)w.tmp, (const float*)w.diag, n, st));
-      S_CK(launch_f2d(wv, (const float*)w.tmp, n, st));
-    }
+    S_RC(op(vj, wv));
     for (int pass = 0; pass < 2; ++pass) {
       S_RC(dev_dots(s, V, n, j + 1, wv, n, h.data(), st));
       S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
@@ -270,8 +334,34 @@ int arnoldi_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
     for (int j = 0; j < kk; ++j) Hk[i * kk + j] = H[i * k + j];
   const double lam = small_spectral_radius(Hk, kk);
   if (!(lam > 0.0) || !std::isfinite(lam)) return sfail(PFF_ERR_DEVICE, "Arnoldi eigenvalue estimate failed");
-  w.lmax = lam;
+  *out = lam;
   return PFF_OK;
+}
+
+int arnoldi_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
+  const long long n = w.n;
+  auto op = [&](const double* vj, double* wv) -> int {
+    if (w.prec == PFF_F64) {
+      S_RC(pff_jacobian_apply(w.L, PFF_F64, vj, wv, st));
+      S_CK(launch_dscale<double>(wv, wv, (const double*)w.diag, n, st));
+    } else {
+      S_CK(launch_d2f((float*)w.x, vj, n, st));
+      S_RC(pff_jacobian_apply(w.L, PFF_F32, w.x, w.tmp, st));
+      S_CK(launch_dscale<float>((float*)w.tmp, (const float*)w.tmp, (const float*)w.diag, n, st));
+      S_CK(launch_f2d(wv, (const float*)w.tmp, n, st));
+    }
+    return PFF_OK;
+  };
+  return arnoldi_lmax(s, n, op, &w.lmax, st);
+}
+
+int arnoldi_hlevel(pff_solver* s, HLevel& h, cudaStream_t st) {
+  auto op = [&](const double* vj, double* wv) -> int {
+    S_CK(launch_q1_spmv(h.mesh, h.A, vj, wv, st));
+    S_CK(launch_dscale<double>(wv, wv, h.diag, h.n, st));
+    return PFF_OK;
+  };
+  return arnoldi_lmax(s, h.n, op, &h.lmax, st);
 }
 
 int power_coarse(pff_solver* s, cudaStream_t st) {
@@ -426,8 +516,9 @@ int precondition(pff_solver* s, const double* v, double* z, cudaStream_t st) {
   return PFF_OK;
 }
 
-// Coarsest level: Jacobi-preconditioned GMRES on the assembled FP64 operator to
-// coarse_rtol (at most coarse_maxit iterations), from x = 0.
+// Coarsest level: GMRES on the assembled FP64 operator to coarse_rtol (at most
+// coarse_maxit iterations), from x = 0, preconditioned by Jacobi
+// (coarse_solver 1) or by one h-multigrid V-cycle (coarse_solver 2).
 int coarse_gmres(pff_solver* s, cudaStream_t st) {
   LevelWork& c = s->lv.back();
   const MeshDev& mc = c.L->mesh;
@@ -441,6 +532,13 @@ int coarse_gmres(pff_solver* s, cudaStream_t st) {
   kw.Z = s->cZ;
   auto A = [&](const double* in, double* out) -> int { return coarse_spmv(s, mc, in, out, st); };
   auto M = [&](const double* in, double* out) -> int {
+    if (s->prm.coarse_solver == 2) {  // one h-multigrid V-cycle
+      HLevel& h0 = s->hl[0];
+      S_CK(cudaMemcpyAsync(h0.b, in, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      S_RC(hcycle(s, 0, st));
+      S_CK(cudaMemcpyAsync(out, h0.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      return PFF_OK;
+    }
     S_CK(launch_dscale<double>(out, in, s->cdiag, n, st));
     return PFF_OK;
   };
@@ -466,6 +564,17 @@ int setup(pff_solver* s, cudaStream_t st) {
     S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->Ke, s->A, st));
     S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
     if (s->prm.coarse_solver == 0) S_RC(power_coarse(s, st));
+    if (s->prm.coarse_solver == 2) {
+      for (size_t l = 1; l < s->hl.size(); ++l) {
+        HLevel& f = s->hl[l - 1];
+        HLevel& h = s->hl[l];
+        S_CK(launch_hmask(f.mesh, h.mesh, f.mask, h.own_mask, st));
+        S_CK(launch_q1_coarsen(f.mesh, h.mesh, f.mask, f.Ke, h.Ke, st));
+        S_CK(launch_q1_gather(h.mesh, h.Ke, h.mask, h.A, st));
+        S_CK(launch_q1_diag(h.mesh, h.A, h.diag, st));
+      }
+      for (HLevel& h : s->hl) S_RC(arnoldi_hlevel(s, h, st));
+    }
   }
   for (int l = 0; l < L; ++l) {
     if (l + 1 == L && s->assembled) continue;
@@ -480,6 +589,10 @@ void free_solver(pff_solver* s) {
   }
   cudaFree(s->A); cudaFree(s->cdiag); cudaFree(s->cb); cudaFree(s->cx); cudaFree(s->cwork);
   cudaFree(s->cV); cudaFree(s->cZ); cudaFree(s->Ke);
+  for (HLevel& h : s->hl) {
+    if (h.owns) { cudaFree(h.Ke); cudaFree(h.A); cudaFree(h.diag); cudaFree(h.own_mask); }
+    cudaFree(h.b); cudaFree(h.x); cudaFree(h.r); cudaFree(h.work);
+  }
   cudaFree(s->V); cudaFree(s->Z); cudaFree(s->r); cudaFree(s->dz); cudaFree(s->zold);
   cudaFree(s->partial); cudaFree(s->dots); cudaFree(s->hdev);
   cudaFree(s->pw64); cudaFree(s->pw32);
@@ -506,7 +619,7 @@ int pff_solver_default_params(pff_solver_params* p) {
   p->newton_maxit = 20;
   p->newton_rtol = 1e-8;
   p->line_search_max = 8;
-  p->coarse_solver = 1;
+  p->coarse_solver = 2;
   p->coarse_rtol = 1e-2;
   p->coarse_maxit = 200;
   p->verbose = 0;
@@ -526,6 +639,8 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     if (levels[l]->op != op || levels[l]->p >= levels[l - 1]->p)
       return sfail(PFF_ERR_INVALID, "pff_create_solver: levels must share op with decreasing order");
   if (prm->mixed && !op->lin32) return sfail(PFF_ERR_INVALID, "pff_create_solver: mixed precision needs pff_op_enable_f32");
+  if (prm->coarse_solver < 0 || prm->coarse_solver > 2)
+    return sfail(PFF_ERR_INVALID, "pff_create_solver: coarse_solver must be 0, 1 or 2");
   if (prm->outer_prec != PFF_F64 && prm->outer_prec != PFF_DF64)
     return sfail(PFF_ERR_INVALID, "pff_create_solver: outer_prec must be PFF_F64 or PFF_DF64");
   if (prm->outer_prec == PFF_DF64 && !op->df)
@@ -558,8 +673,47 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     if (e == cudaSuccess) e = cudaMalloc(&s->cx, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->cwork, sizeof(double) * 3 * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->Ke, sizeof(double) * 1024 * (size_t)op->nel);
-    if (e == cudaSuccess && prm->coarse_solver == 1) e = cudaMalloc(&s->cV, sizeof(double) * (prm->krylov_restart + 1) * nc);
-    if (e == cudaSuccess && prm->coarse_solver == 1) e = cudaMalloc(&s->cZ, sizeof(double) * prm->krylov_restart * nc);
+    if (e == cudaSuccess && prm->coarse_solver >= 1) e = cudaMalloc(&s->cV, sizeof(double) * (prm->krylov_restart + 1) * nc);
+    if (e == cudaSuccess && prm->coarse_solver >= 1) e = cudaMalloc(&s->cZ, sizeof(double) * prm->krylov_restart * nc);
+    if (prm->coarse_solver == 2) {
+      // h-levels: the Q1 level, then full coarsening while every direction has
+      // an even number of elements and keeps at least two
+      pff_level* Lc = s->lv.back().L;
+      HLevel h0;
+      h0.mesh = Lc->mesh;
+      h0.n = nc;
+      h0.Ke = s->Ke;
+      h0.A = s->A;
+      h0.diag = s->cdiag;
+      h0.mask = Lc->is_fine ? op->mask : Lc->mask;
+      s->hl.push_back(h0);
+      while (true) {
+        const MeshDev& mf = s->hl.back().mesh;
+        if (mf.nx % 2 || mf.ny % 2 || mf.nz % 2 || mf.nx < 4 || mf.ny < 4 || mf.nz < 4) break;
+        HLevel h;
+        h.mesh = mf;
+        h.mesh.nx = mf.nx / 2; h.mesh.ny = mf.ny / 2; h.mesh.nz = mf.nz / 2;
+        h.mesh.nel = h.mesh.nx * h.mesh.ny * h.mesh.nz;
+        h.mesh.nnx = h.mesh.nx + 1; h.mesh.nny = h.mesh.ny + 1;
+        h.mesh.nn = (long long)h.mesh.nnx * h.mesh.nny * (h.mesh.nz + 1);
+        h.mesh.offsets = nullptr;
+        h.n = 4 * h.mesh.nn;
+        h.owns = true;
+        if (e == cudaSuccess) e = cudaMalloc(&h.Ke, sizeof(double) * 1024 * (size_t)h.mesh.nel);
+        if (e == cudaSuccess) e = cudaMalloc(&h.A, sizeof(double) * 27 * 16 * (size_t)h.mesh.nn);
+        if (e == cudaSuccess) e = cudaMalloc(&h.diag, sizeof(double) * h.n);
+        if (e == cudaSuccess) e = cudaMalloc(&h.own_mask, h.n);
+        h.mask = h.own_mask;
+        s->hl.push_back(h);
+        if (e != cudaSuccess) break;
+      }
+      for (HLevel& h : s->hl) {
+        if (e == cudaSuccess) e = cudaMalloc(&h.b, sizeof(double) * h.n);
+        if (e == cudaSuccess) e = cudaMalloc(&h.x, sizeof(double) * h.n);
+        if (e == cudaSuccess) e = cudaMalloc(&h.r, sizeof(double) * h.n);
+        if (e == cudaSuccess) e = cudaMalloc(&h.work, sizeof(double) * 3 * h.n);
+      }
+    }
   }
   const int m = prm->krylov_restart;
   if (e == cudaSuccess) e = cudaMalloc(&s->V, sizeof(double) * (m + 1) * s->n);
@@ -630,6 +784,34 @@ int pff_solver_vcycle(pff_solver* s, const double* r, double* z, void* stream) {
 int pff_solver_coarse_apply(pff_solver* s, const double* x, double* y, void* stream) {
   if (!s || !x || !y || !s->assembled) return sfail(PFF_ERR_INVALID, "pff_solver_coarse_apply: needs an assembled coarse level");
   S_CK(launch_q1_spmv(s->lv.back().L->mesh, s->A, x, y, reinterpret_cast<cudaStream_t>(stream)));
+  return PFF_OK;
+}
+
+int pff_solver_num_hlevels(const pff_solver* s) { return s ? (int)s->hl.size() : 0; }
+
+int pff_solver_hlevel_info(const pff_solver* s, int level, int* dims, double* lmax) {
+  if (!s || !dims || !lmax || level < 0 || level >= (int)s->hl.size())
+    return sfail(PFF_ERR_INVALID, "pff_solver_hlevel_info: bad argument");
+  const HLevel& h = s->hl[level];
+  dims[0] = h.mesh.nx; dims[1] = h.mesh.ny; dims[2] = h.mesh.nz;
+  *lmax = h.lmax;
+  return PFF_OK;
+}
+
+int pff_solver_hlevel_apply(pff_solver* s, int level, const double* x, double* y, void* stream) {
+  if (!s || !x || !y || level < 0 || level >= (int)s->hl.size())
+    return sfail(PFF_ERR_INVALID, "pff_solver_hlevel_apply: bad argument");
+  S_CK(launch_q1_spmv(s->hl[level].mesh, s->hl[level].A, x, y, reinterpret_cast<cudaStream_t>(stream)));
+  return PFF_OK;
+}
+
+int pff_solver_hcycle(pff_solver* s, const double* b, double* x, void* stream) {
+  if (!s || !b || !x || s->hl.empty()) return sfail(PFF_ERR_INVALID, "pff_solver_hcycle: needs coarse_solver 2");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  HLevel& h0 = s->hl[0];
+  S_CK(cudaMemcpyAsync(h0.b, b, sizeof(double) * h0.n, cudaMemcpyDeviceToDevice, st));
+  S_RC(hcycle(s, 0, st));
+  S_CK(cudaMemcpyAsync(x, h0.x, sizeof(double) * h0.n, cudaMemcpyDeviceToDevice, st));
   return PFF_OK;
 }
 

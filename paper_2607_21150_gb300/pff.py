@@ -103,6 +103,10 @@ _SIGS = {
     "pff_solver_level_lambda": ([_VP, _I, ctypes.POINTER(_D)], _I),
     "pff_solver_vcycle": ([_VP, _VP, _VP, _VP], _I),
     "pff_solver_coarse_apply": ([_VP, _VP, _VP, _VP], _I),
+    "pff_solver_num_hlevels": ([_VP], _I),
+    "pff_solver_hlevel_info": ([_VP, _I, ctypes.POINTER(_I), ctypes.POINTER(_D)], _I),
+    "pff_solver_hlevel_apply": ([_VP, _I, _VP, _VP, _VP], _I),
+    "pff_solver_hcycle": ([_VP, _VP, _VP, _VP], _I),
     "pff_solver_krylov": ([_VP, _VP, _VP, _D, _I, ctypes.POINTER(_I), ctypes.POINTER(_D), _VP], _I),
     "pff_newton_solve": ([_VP, _VP, ctypes.POINTER(pff_newton_stats), _VP], _I),
     "pff_vec_axpby": ([_I, _I64, _D, _VP, _D, _VP, _VP], _I),
@@ -349,6 +353,26 @@ def pff_solver_vcycle(solver, r, z, stream=None):
 
 def pff_solver_coarse_apply(solver, x, y, stream=None):
     _call("pff_solver_coarse_apply", solver, _ptr(x), _ptr(y), _stream(stream))
+
+
+def pff_solver_num_hlevels(solver):
+    return int(lib().pff_solver_num_hlevels(solver))
+
+
+def pff_solver_hlevel_info(solver, level):
+    """(element grid (nx, ny, nz), lambda_max estimate) of h-level ``level``."""
+    dims = (_I * 3)()
+    lam = _D()
+    _call("pff_solver_hlevel_info", solver, int(level), dims, ctypes.byref(lam))
+    return (dims[0], dims[1], dims[2]), lam.value
+
+
+def pff_solver_hlevel_apply(solver, level, x, y, stream=None):
+    _call("pff_solver_hlevel_apply", solver, int(level), _ptr(x), _ptr(y), _stream(stream))
+
+
+def pff_solver_hcycle(solver, b, x, stream=None):
+    _call("pff_solver_hcycle", solver, _ptr(b), _ptr(x), _stream(stream))
 
 
 def pff_solver_krylov(solver, b, x, rtol, maxit, stream=None):

@@ -157,3 +157,61 @@ def test_newton_solution_matches_oracle(orc, mixed, outer):
     rates = h[1:] / h[:-1]
     assert rates.min() < 1e-2
     pff.pff_destroy_solver(solver)
+
+
+@pytest.fixture(scope="module")
+def setup_h(orc):
+    """Q2 box of 8 x 8 x 4 elements: order-1 level 8 x 8 x 4, one h-coarsening to 4 x 4 x 2."""
+    w = _box(8, 8, 4, 2, 21)
+    s = Session(w, levels=(1,))
+    s.residual(torch.from_numpy(w.z.ravel()).cuda())
+    solver = s.solver([2, 1], mixed=0, coarse_solver=2)
+    pff.pff_solver_setup(solver)
+    ref = orc.assemble(w)
+    m = w.mesh
+    mc0 = inputs.coarsen_mask(m, w.mask, 1)
+    A0 = orc.coarse_operator(ref["K"], orc.masked_prolongation(orc.prolongation(m, 1), w.mask, mc0), mc0)
+    mc1 = orc.h_coarse_mask(mc0, 4, 4, 2)
+    Ph = orc.masked_prolongation(orc.h_prolongation(4, 4, 2), mc0, mc1)
+    A1 = orc.coarse_operator(A0, Ph, mc1)
+    return w, s, solver, [A0, A1], [Ph]
+
+
+def test_h_hierarchy_galerkin_operators(setup_h):
+    w, s, solver, As, Ps = setup_h
+    assert pff.pff_solver_num_hlevels(solver) == 2
+    assert pff.pff_solver_hlevel_info(solver, 0)[0] == (8, 8, 4)
+    assert pff.pff_solver_hlevel_info(solver, 1)[0] == (4, 4, 2)
+    for l, A in enumerate(As):
+        x = inputs.random_vector(A.shape[0], 30 + l)
+        y = torch.zeros(len(x), dtype=torch.float64, device="cuda")
+        pff.pff_solver_hlevel_apply(solver, l, torch.from_numpy(x).cuda(), y)
+        assert rel(np_(y), A @ x) <= 1e-12, l
+
+
+def test_h_vcycle_matches_oracle(orc, setup_h):
+    w, s, solver, As, Ps = setup_h
+    lams = [pff.pff_solver_hlevel_info(solver, l)[1] for l in range(2)]
+    b = inputs.random_vector(As[0].shape[0], 40)
+    x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+    pff.pff_solver_hcycle(solver, torch.from_numpy(b).cuda(), x)
+    xr = orc.vcycle(As, Ps, [A.diagonal() for A in As], lams, b)
+    assert rel(np_(x), xr) <= 1e-11
+
+
+def test_newton_with_h_multigrid_coarse_solver(orc):
+    """Same Newton solution with the Jacobi-GMRES and the h-multigrid coarse
+    solver; the h-multigrid preconditioned coarse GMRES needs fewer iterations."""
+    w = _box(8, 8, 4, 2, 23, state=False)
+    z_ref, _, _ = orc.newton(w, rtol=1e-13)
+    its = {}
+    for cs in (1, 2):
+        s = Session(w, levels=(1,))
+        solver = s.solver([2, 1], mixed=0, coarse_solver=cs, newton_rtol=1e-11, krylov_rtol=1e-6)
+        z = torch.from_numpy(w.z.ravel().copy()).cuda()
+        st = pff.pff_newton_solve(solver, z)
+        assert st["converged"] == 1, (cs, st)
+        assert rel(np_(z), z_ref) <= 1e-9, cs
+        its[cs] = st["coarse_iterations"]
+        pff.pff_destroy_solver(solver)
+    assert its[2] < its[1]
