@@ -277,79 +277,82 @@ __device__ __forceinline__ void q1_combo(int c, int& word, int& rk, int& ck) {
   }
 }
 
+// One block (8 warps) per element; warp w takes the combinations c = w, w + 8,
+// ... and contracts them one direction at a time in its own shared scratch
+// (D[Q^3] -> T1[4][Q^2] -> T2[16][Q] -> R[c][64]) with the 1D products
+// X[(fa, fb)][i][(a, b)] = F_fa(i, a) F_fb(i, b) tabulated once per block; the
+// block then sums the combinations of each (f, g) block of Ke.
 template <int Q>
 __global__ void __launch_bounds__(kQ1Threads)
 k_q1_elem(int nel, const double* __restrict__ lin, const double* __restrict__ B1, const double* __restrict__ D1,
           double* __restrict__ Ke) {
   constexpr int Q2 = Q * Q, Q3 = Q2 * Q;
   constexpr int EB = elems_per_block(Q);
+  constexpr int kWarps = kQ1Threads / 32;
+  constexpr int kScratch = Q3 + 4 * Q2 + 16 * Q;
   extern __shared__ double sm[];
-  double* Dw = sm;                          // [67][Q3]
-  double* T1 = Dw + kQ1Combos * Q3;         // [67][4][Q2]   (reused for results [67][64])
-  double* T2 = T1 + kQ1Combos * 4 * Q2;     // [67][16][Q]
-  __shared__ double F[2][Q][2];             // F[0] = B1, F[1] = D1
+  double* R = sm;                                   // [67][64]
+  double* X = R + kQ1Combos * 64;                   // [4][Q][4]
+  double* W = X + 16 * Q;                           // [warps][kScratch]
+  int* ctab = reinterpret_cast<int*>(W + kWarps * kScratch);  // [67][3]: word, rk, ck
   const int e = blockIdx.x;
-  const int t = threadIdx.x;
-  if (t < 2 * Q * 2) {
-    const int which = t / (2 * Q), r = t % (2 * Q);
-    F[which][r / 2][r % 2] = which ? D1[r] : B1[r];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int idx = t; idx < 16 * Q; idx += kQ1Threads) {
+    const int p = idx / (4 * Q), i = (idx / 4) % Q, ab = idx % 4;
+    const int fa = p >> 1, fb = p & 1, a = ab >> 1, b = ab & 1;
+    const double Fa = fa ? D1[i * 2 + a] : B1[i * 2 + a];
+    const double Fb = fb ? D1[i * 2 + b] : B1[i * 2 + b];
+    X[idx] = Fa * Fb;
   }
+  for (int c = t; c < kQ1Combos; c += kQ1Threads) q1_combo(c, ctab[3 * c], ctab[3 * c + 1], ctab[3 * c + 2]);
+  __syncthreads();
   const long long stride = (long long)Q3 * EB;
   const long long base = (long long)(e / EB) * kLinWords * stride + (e % EB) * Q2;
-  for (int idx = t; idx < kQ1Combos * Q3; idx += kQ1Threads) {
-    const int c = idx / Q3, q = idx % Q3;
-    int word, rk, ck;
-    q1_combo(c, word, rk, ck);
-    const int k = q / Q2, jq = q % Q2;
-    Dw[idx] = lin[base + (long long)word * stride + (long long)k * Q2 * EB + jq];
-  }
-  __syncthreads();
-  // direction 0 (i): T1[c][a0 b0][j k]
-  for (int idx = t; idx < kQ1Combos * 4 * Q2; idx += kQ1Threads) {
-    const int c = idx / (4 * Q2), r = idx % (4 * Q2);
-    const int ab = r / Q2, jk = r % Q2;
-    int word, rk, ck;
-    q1_combo(c, word, rk, ck);
-    const int fa = (rk == 1), fb = (ck == 1);
-    const int a0 = ab >> 1, b0 = ab & 1;
-    const double* Dc = Dw + c * Q3 + jk * Q;
-    double s = 0.0;
+  double* D = W + warp * kScratch;
+  double* T1 = D + Q3;
+  double* T2 = T1 + 4 * Q2;
+  for (int c = warp; c < kQ1Combos; c += kWarps) {
+    const int word = ctab[3 * c], rk = ctab[3 * c + 1], ck = ctab[3 * c + 2];
+    for (int q = lane; q < Q3; q += 32) {
+      const int k = q / Q2, jq = q % Q2;
+      D[q] = lin[base + (long long)word * stride + (long long)k * Q2 * EB + jq];
+    }
+    __syncwarp();
+    // direction 0 (i): T1[a0 b0][j + Q k]
+    const double* X0 = X + ((rk == 1) * 2 + (ck == 1)) * 4 * Q;
+    for (int idx = lane; idx < 4 * Q2; idx += 32) {
+      const int ab = idx / Q2, jk = idx % Q2;
+      double s = 0.0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) s += F[fa][i][a0] * F[fb][i][b0] * Dc[i];
-    T1[idx] = s;
-  }
-  __syncthreads();
-  // direction 1 (j): T2[c][a0b0 a1b1][k]
-  for (int idx = t; idx < kQ1Combos * 16 * Q; idx += kQ1Threads) {
-    const int c = idx / (16 * Q), r = idx % (16 * Q);
-    const int abab = r / Q, k = r % Q;
-    const int ab0 = abab >> 2, ab1 = abab & 3;
-    int word, rk, ck;
-    q1_combo(c, word, rk, ck);
-    const int fa = (rk == 2), fb = (ck == 2);
-    const int a1 = ab1 >> 1, b1 = ab1 & 1;
-    const double* Tc = T1 + c * 4 * Q2 + ab0 * Q2 + k * Q;
-    double s = 0.0;
+      for (int i = 0; i < Q; ++i) s += X0[i * 4 + ab] * D[jk * Q + i];
+      T1[idx] = s;
+    }
+    __syncwarp();
+    // direction 1 (j): T2[(a0 b0) 4 + (a1 b1)][k]
+    const double* X1 = X + ((rk == 2) * 2 + (ck == 2)) * 4 * Q;
+    for (int idx = lane; idx < 16 * Q; idx += 32) {
+      const int abab = idx / Q, k = idx % Q;
+      const int ab0 = abab >> 2, ab1 = abab & 3;
+      const double* Tc = T1 + ab0 * Q2 + k * Q;
+      double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < Q; ++j) s += F[fa][j][a1] * F[fb][j][b1] * Tc[j];
-    T2[idx] = s;
-  }
-  __syncthreads();
-  // direction 2 (k): result R[c][a][b], a = a0 + 2 a1 + 4 a2 (written over T1)
-  double* R = T1;
-  for (int idx = t; idx < kQ1Combos * 64; idx += kQ1Threads) {
-    const int c = idx / 64, r = idx % 64;
-    const int a = r / 8, b = r % 8;
-    const int a0 = a & 1, a1 = (a >> 1) & 1, a2 = a >> 2;
-    const int b0 = b & 1, b1 = (b >> 1) & 1, b2 = b >> 2;
-    int word, rk, ck;
-    q1_combo(c, word, rk, ck);
-    const int fa = (rk == 3), fb = (ck == 3);
-    const double* Tc = T2 + c * 16 * Q + ((a0 * 2 + b0) * 4 + (a1 * 2 + b1)) * Q;
-    double s = 0.0;
+      for (int j = 0; j < Q; ++j) s += X1[j * 4 + ab1] * Tc[j];
+      T2[idx] = s;
+    }
+    __syncwarp();
+    // direction 2 (k): R[c][a][b], a = a0 + 2 a1 + 4 a2
+    const double* X2 = X + ((rk == 3) * 2 + (ck == 3)) * 4 * Q;
+    for (int r = lane; r < 64; r += 32) {
+      const int a = r / 8, b = r % 8;
+      const int a0 = a & 1, a1 = (a >> 1) & 1, a2 = a >> 2;
+      const int b0 = b & 1, b1 = (b >> 1) & 1, b2 = b >> 2;
+      const double* Tc = T2 + ((a0 * 2 + b0) * 4 + (a1 * 2 + b1)) * Q;
+      double s = 0.0;
 #pragma unroll
-    for (int k = 0; k < Q; ++k) s += F[fa][k][a2] * F[fb][k][b2] * Tc[k];
-    R[idx] = s;
+      for (int k = 0; k < Q; ++k) s += X2[k * 4 + a2 * 2 + b2] * Tc[k];
+      R[c * 64 + r] = s;
+    }
+    __syncwarp();
   }
   __syncthreads();
   // element matrix: sum of the combinations of each (f, g) block
@@ -575,7 +578,8 @@ cudaError_t launch_hrestrict(const MeshDev& mc, const MeshDev& mf, const double*
 
 cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
                                   const uint8_t* maskc, double* Ke, double* A, cudaStream_t st) {
-  size_t smem = sizeof(double) * (size_t)(kQ1Combos * Q * Q * Q + kQ1Combos * 4 * Q * Q + kQ1Combos * 16 * Q);
+  const size_t smem = sizeof(double) * (size_t)(kQ1Combos * 64 + 16 * Q + (kQ1Threads / 32) * (Q * Q * Q + 4 * Q * Q + 16 * Q)) +
+                      sizeof(int) * 3 * kQ1Combos;
   switch (Q) {
     case 2: cudaFuncSetAttribute(k_q1_elem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             k_q1_elem<2><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;

@@ -71,15 +71,16 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
   const double theta = log1p(Jm1);
   const double J = 1.0 + Jm1;
   double Fi[3][3];
-  Fi[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) / J;
-  Fi[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) / J;
-  Fi[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) / J;
-  Fi[1][0] = (F[1][2] * F[2][0] - F[1][0] * F[2][2]) / J;
-  Fi[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) / J;
-  Fi[1][2] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) / J;
-  Fi[2][0] = (F[1][0] * F[2][1] - F[1][1] * F[2][0]) / J;
-  Fi[2][1] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) / J;
-  Fi[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) / J;
+  const double rJ = 1.0 / J;
+  Fi[0][0] = (F[1][1] * F[2][2] - F[1][2] * F[2][1]) * rJ;
+  Fi[0][1] = (F[0][2] * F[2][1] - F[0][1] * F[2][2]) * rJ;
+  Fi[0][2] = (F[0][1] * F[1][2] - F[0][2] * F[1][1]) * rJ;
+  Fi[1][0] = (F[1][2] * F[2][0] - F[1][0] * F[2][2]) * rJ;
+  Fi[1][1] = (F[0][0] * F[2][2] - F[0][2] * F[2][0]) * rJ;
+  Fi[1][2] = (F[0][2] * F[1][0] - F[0][0] * F[1][2]) * rJ;
+  Fi[2][0] = (F[1][0] * F[2][1] - F[1][1] * F[2][0]) * rJ;
+  Fi[2][1] = (F[0][1] * F[2][0] - F[0][0] * F[2][1]) * rJ;
+  Fi[2][2] = (F[0][0] * F[1][1] - F[0][1] * F[1][0]) * rJ;
   double GG[3][3];  // F F^T - I
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) {
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
     double eps[3], ed[3];
     for (int p = 0; p < 3; ++p) eps[p] = 0.5 * log1p(x[p]);
     const double tr = eps[0] + eps[1] + eps[2];
-    for (int p = 0; p < 3; ++p) ed[p] = eps[p] - tr / 3.0;
+    for (int p = 0; p < 3; ++p) ed[p] = eps[p] - tr * (1.0 / 3.0);
     const double s2 = ed[0] * ed[0] + ed[1] * ed[1] + ed[2] * ed[2];
     double af = 1.0, da_dphi = 0.0;
     bool plastic = false;
@@ -182,6 +183,21 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
       const double rho02 = log_ratio(x[0], x[2]);
       const double rho12 = log_ratio(x[1], x[2]);
       const double b[3] = {1.0 + x[0], 1.0 + x[1], 1.0 + x[2]};
+      // symmetric basis of the principal frame in Voigt order: N dh N^T =
+      // sum_p dh_pp n_p n_p^T + sum_{p<t} dh_pt (n_p n_t^T + n_t n_p^T)
+      double E[6][6];
+      for (int v = 0; v < 6; ++v) {
+        int r, c;
+        vo_idx(v, r, c);
+        E[0][v] = N[r][0] * N[c][0];
+        E[1][v] = N[r][1] * N[c][1];
+        E[2][v] = N[r][2] * N[c][2];
+        E[3][v] = N[r][1] * N[c][2] + N[r][2] * N[c][1];
+        E[4][v] = N[r][0] * N[c][2] + N[r][2] * N[c][0];
+        E[5][v] = N[r][0] * N[c][1] + N[r][1] * N[c][0];
+      }
+      const double k01 = mu * af * rho01, k02 = mu * af * rho02, k12 = mu * af * rho12;
+      const double af_s2 = plastic ? af / s2 : 0.0;
       for (int d = 0; d < 10; ++d) {
         double lh[3][3];
         double dphi = 0.0;
@@ -197,22 +213,19 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
         const double trl = lh[0][0] + lh[1][1] + lh[2][2];
         double ded[3], edde = 0.0;
         for (int p = 0; p < 3; ++p) {
-          ded[p] = lh[p][p] - trl / 3.0;
+          ded[p] = lh[p][p] - trl * (1.0 / 3.0);
           edde += ed[p] * lh[p][p];
         }
         double da = dphi * da_dphi;
-        if (plastic) da -= af * edde / s2;
-        double dh[3][3];
-        for (int p = 0; p < 3; ++p) dh[p][p] = 2.0 * mu * (af * ded[p] + da * ed[p]);
-        dh[0][1] = dh[1][0] = mu * af * rho01 * (lh[0][1] * b[1] + b[0] * lh[1][0]);
-        dh[0][2] = dh[2][0] = mu * af * rho02 * (lh[0][2] * b[2] + b[0] * lh[2][0]);
-        dh[1][2] = dh[2][1] = mu * af * rho12 * (lh[1][2] * b[2] + b[1] * lh[2][1]);
+        if (plastic) da -= af_s2 * edde;
+        double dh[6];  // principal-frame dtau: 00, 11, 22, 12, 02, 01
+        for (int p = 0; p < 3; ++p) dh[p] = 2.0 * mu * (af * ded[p] + da * ed[p]);
+        dh[3] = k12 * (lh[1][2] * b[2] + b[1] * lh[2][1]);
+        dh[4] = k02 * (lh[0][2] * b[2] + b[0] * lh[2][0]);
+        dh[5] = k01 * (lh[0][1] * b[1] + b[0] * lh[1][0]);
         for (int v = 0; v < 6; ++v) {
-          int r, c;
-          vo_idx(v, r, c);
           double s = 0.0;
-          for (int p = 0; p < 3; ++p)
-            for (int t = 0; t < 3; ++t) s += N[r][p] * dh[p][t] * N[c][t];
+          for (int u = 0; u < 6; ++u) s += dh[u] * E[u][v];
           dtau[d][v] += s;
         }
         dpsi[d] += 2.0 * mu * af * af * edde + 2.0 * mu * af * s2 * da;

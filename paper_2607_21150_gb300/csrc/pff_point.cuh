@@ -15,7 +15,12 @@ static __device__ __forceinline__ void vo_idx(int v, int& r, int& c) {
 
 // Cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (in place).
 // On exit w = eigenvalues, V columns = eigenvectors.  Returns 0 when the
-// off-diagonal part vanished within the sweep cap.
+// off-diagonal part vanished within the sweep cap.  Each rotation annihilates
+// A[p][q] with tan(phi) = t the smaller root of t^2 + 2 theta t - 1 = 0,
+// theta = (A_qq - A_pp) / (2 A_pq), written as
+//   t = sgn 2 |A_pq| / (|A_qq - A_pp| + sqrt((A_qq - A_pp)^2 + 4 A_pq^2)),
+// c = 1 / sqrt(1 + t^2), s = t c: one division, one square root and one
+// reciprocal square root per rotation (the FP64 pipe is the binding unit).
 static __device__ inline int jacobi3(double A[3][3], double V[3][3], double w[3]) {
   for (int r = 0; r < 3; ++r)
     for (int c = 0; c < 3; ++c) V[r][c] = (r == c) ? 1.0 : 0.0;
@@ -27,24 +32,24 @@ static __device__ inline int jacobi3(double A[3][3], double V[3][3], double w[3]
     for (int pr = 0; pr < 3; ++pr) {
       const int p = (pr == 2) ? 1 : 0;
       const int q = (pr == 0) ? 1 : 2;
-      double apq = A[p][q];
+      const double apq = A[p][q];
       if (apq == 0.0) continue;
-      double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
-      double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-      double c = 1.0 / sqrt(t * t + 1.0);
-      double s = t * c;
-      double tau = s / (1.0 + c);
+      const double diff = A[q][q] - A[p][p];
+      const double sgn = ((diff >= 0.0) == (apq > 0.0) || diff == 0.0) ? 1.0 : -1.0;
+      const double t = sgn * 2.0 * fabs(apq) / (fabs(diff) + sqrt(diff * diff + 4.0 * apq * apq));
+      const double c = rsqrt(fma(t, t, 1.0));
+      const double s = t * c;
       A[p][p] -= t * apq;
       A[q][q] += t * apq;
       A[p][q] = A[q][p] = 0.0;
       const int r = 3 - p - q;
-      double arp = A[r][p], arq = A[r][q];
-      A[r][p] = A[p][r] = arp - s * (arq + tau * arp);
-      A[r][q] = A[q][r] = arq + s * (arp - tau * arq);
+      const double arp = A[r][p], arq = A[r][q];
+      A[r][p] = A[p][r] = c * arp - s * arq;
+      A[r][q] = A[q][r] = s * arp + c * arq;
       for (int k = 0; k < 3; ++k) {
-        double vkp = V[k][p], vkq = V[k][q];
-        V[k][p] = vkp - s * (vkq + tau * vkp);
-        V[k][q] = vkq + s * (vkp - tau * vkq);
+        const double vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - s * vkq;
+        V[k][q] = s * vkp + c * vkq;
       }
     }
   }
@@ -52,14 +57,28 @@ static __device__ inline int jacobi3(double A[3][3], double V[3][3], double w[3]
   return ok;
 }
 
-// (ln b_p - ln b_q) / (b_p - b_q) from the eigenvalues x = b - 1.
+// (ln b_p - ln b_q) / (b_p - b_q) from the eigenvalues x = b - 1:
+// log1p(y) / (y b_q) with y = (b_p - b_q) / b_q.  For |y| < 1/64 the Taylor
+// series of log1p(y) / y to y^8 (remainder below y^9 / 10 < 2e-17) replaces the
+// logarithm and the division.
 static __device__ __forceinline__ double log_ratio(double xp, double xq) {
-  double bq = 1.0 + xq;
-  double y = (xp - xq) / bq;
+  const double rb = 1.0 / (1.0 + xq);
+  const double y = (xp - xq) * rb;
   double l1;
-  if (fabs(y) < 1e-4) l1 = 1.0 - y * (0.5 - y * (1.0 / 3.0 - 0.25 * y));
-  else l1 = log1p(y) / y;
-  return l1 / bq;
+  if (fabs(y) < 0.015625) {
+    l1 = 1.0 / 9.0;
+    l1 = fma(l1, -y, 1.0 / 8.0);
+    l1 = fma(l1, -y, 1.0 / 7.0);
+    l1 = fma(l1, -y, 1.0 / 6.0);
+    l1 = fma(l1, -y, 1.0 / 5.0);
+    l1 = fma(l1, -y, 1.0 / 4.0);
+    l1 = fma(l1, -y, 1.0 / 3.0);
+    l1 = fma(l1, -y, 1.0 / 2.0);
+    l1 = fma(l1, -y, 1.0);
+  } else {
+    l1 = log1p(y) / y;
+  }
+  return l1 * rb;
 }
 
 
