@@ -28,6 +28,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Q4 Jacobian-apply GDoF/s & %HBM roofline; Newton step time FP64 vs mixed p-MG"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x max SM clock
+# DRAM bytes (read + write) per element of one Jacobian action, Q4 (P = Q = 5),
+# from one ncu capture of the same kernels at 16^3 elements (4096 elements:
+# FP64 301.0 MB, FP32 156.9 MB), scaled to a launch by the element count.
+TRAFFIC_PER_ELEMENT = {"f64": 301.0e6 / 4096, "f32": 156.9e6 / 4096}
 
 
 def peaks():
@@ -148,7 +152,7 @@ def oracle_sample(seconds_budget: float = 20.0):
                 gdofs=m.ndof / t_spmv / 1e9, gdofs_incl_assembly=m.ndof / (t_spmv + t_asm) / 1e9)
 
 
-def newton_compare(name: str, steps: int = 1):
+def newton_compare(name: str, steps: int = 1, variants=("mixed", "fp64")):
     """Load steps from the unloaded state with FP64 p-MG and with mixed p-MG (FP32
     levels and smoothers), both to ||r||/||r0|| <= 1e-8 with inner rtol 1e-3.
     Returns per-variant timings (host clock around synchronised phases) and the
@@ -159,6 +163,8 @@ def newton_compare(name: str, steps: int = 1):
     out = {"workload": name, "load_steps": steps}
     fields = {}
     for label, mixed in (("mixed", True), ("fp64", False)):
+        if label not in variants:
+            continue
         w = getattr(inputs, name)()
         lsp = LoadStepper(w, mixed=mixed, verbose=1)
         torch.cuda.synchronize()
@@ -185,9 +191,10 @@ def newton_compare(name: str, steps: int = 1):
         lsp.close()
         del lsp
         torch.cuda.empty_cache()
-    a, b = fields["fp64"], fields["mixed"]
-    out["field_rel_diff"] = float(np.linalg.norm(a - b) / np.linalg.norm(a))
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
+    if len(fields) == 2:
+        a, b = fields["fp64"], fields["mixed"]
+        out["field_rel_diff"] = float(np.linalg.norm(a - b) / np.linalg.norm(a))
+        out["speedup_mixed_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
     return out
 
 
@@ -279,7 +286,7 @@ def run_native(args):
 
     w = make_workload(args.config, seed=rank)
     m = w.mesh
-    s = Session(w, f32=True)
+    s = Session(w, f32=True, df=True)
     stream = torch.cuda.current_stream()
     z = torch.from_numpy(w.z.ravel()).cuda()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -306,6 +313,11 @@ def run_native(args):
     def apply32():
         pff.pff_jacobian_apply(L, pff.PFF_F32, x32, y32, stream)
 
+    ydf = torch.empty_like(x64)
+
+    def applydf():
+        pff.pff_jacobian_apply(L, pff.PFF_DF64, x64, ydf, stream)
+
     def timed(fn, K, W):
         for _ in range(W):
             fn()
@@ -328,6 +340,8 @@ def run_native(args):
     with ClockSampler() as clk:
         tot64, per64, wall64 = timed(apply64, args.steps, args.warmup)
     tot32, per32, _ = timed(apply32, args.steps, args.warmup)
+    totdf, _, _ = timed(applydf, args.steps, args.warmup)
+    df_rel = float(torch.linalg.norm(ydf - y64) / torch.linalg.norm(y64))
     # dominant kernel alone (the fused element kernel, without the y-init kernel)
     y64.zero_()
     ker = []
@@ -371,10 +385,14 @@ def run_native(args):
     bytes64 = 8 * ndof * 2 + ndof + 67 * 8 * m.nq
     bytes32 = 4 * ndof * 2 + ndof + 67 * 4 * m.nq
     t32 = tot32 / args.steps / 1e3
+    q4 = (P, Q) == (5, 5)
+    traffic64 = TRAFFIC_PER_ELEMENT["f64"] * m.nel if q4 else None
+    traffic32 = TRAFFIC_PER_ELEMENT["f32"] * m.nel if q4 else None
     s.close()
     del s
     torch.cuda.empty_cache()
-    newton = newton_compare(args.newton, args.newton_steps) if args.newton != "none" else None
+    newton = (newton_compare(args.newton, args.newton_steps, args.newton_variants.split(","))
+              if args.newton != "none" else None)
     adjoint = adjoint_timing(args.adjoint_steps) if args.adjoint_steps > 0 else None
     cpu = oracle_sample()
     line = {
@@ -386,13 +404,19 @@ def run_native(args):
                    "l2": "inputs larger than L2 (stored linearisation %.1f GB)" % (67 * 8 * m.nq / 1e9),
                    "microstructure": w.meta},
         "roofline": {"bound": "alu", "achieved": achieved_flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved_flops / FP64_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved_flops / FP64_PEAK_TFLOPS, "traffic": traffic64,
+                     "traffic_source": "ncu dram bytes per element at 16^3 Q4 x elements" if traffic64 else None,
+                     "algorithmic_bytes": bytes64,
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (unit count measured by an FMA-chain probe)",
                      "hbm_frac": bytes64 / t_apply / 1e9 / hbm_peak, "hbm_peak_gbs": hbm_peak,
                      "hbm_peak_source": src},
-        "fp32_level_apply": {"gdofs": ndof / t32 / 1e9, "ms": t32 * 1e3,
+        "fp32_level_apply": {"gdofs": ndof / t32 / 1e9, "ms": t32 * 1e3, "traffic": traffic32,
+                             "algorithmic_bytes": bytes32,
                              "achieved_gbs": bytes32 / t32 / 1e9, "hbm_frac": bytes32 / t32 / 1e9 / hbm_peak,
                              "bound": "hbm", "peak_gbs": hbm_peak, "peak_source": src},
+        "df64_apply": {"gdofs": ndof / (totdf / args.steps / 1e3) / 1e9, "ms": totdf / args.steps,
+                       "rel_l2_vs_fp64": df_rel,
+                       "note": "double-float action (FP32-pair arithmetic, FP64 vectors); not the headline"},
         "residual_ms": t_res, "kernel_status": status,
         "newton_step": newton,
         "adjoint": adjoint,
@@ -419,9 +443,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default="compress_q4", choices=["compress_q4", "tension_q4"])
-    ap.add_argument("--newton", default="tension_q4", choices=["none", "tension_q4", "compress_q4", "notched_q3"],
+    ap.add_argument("--newton", default="compress_q4", choices=["none", "tension_q4", "compress_q4", "notched_q3"],
                     help="workload of the FP64-vs-mixed Newton comparison")
     ap.add_argument("--newton-steps", type=int, default=1)
+    ap.add_argument("--newton-variants", default="mixed,fp64", help="comma list of mixed, fp64")
     ap.add_argument("--adjoint-steps", type=int, default=10, help="load steps of the adjoint timing (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
