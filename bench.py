@@ -219,6 +219,7 @@ def adjoint_timing(steps: int = 10, fd_check: bool = True):
     t2 = time.perf_counter()
     out = {"workload": f"adjoint_q2: Q2 {w.mesh.nx}^3 elements, {w.mesh.ndof} DoF, {steps} load steps, 12 parameters",
            "forward_s": t1 - t0, "backward_s": t2 - t1, "adjoint_krylov_iterations": int(sum(runner.adjoint_iters)),
+           "sub_steps": int(sum(len(x) for x in runner.schedule)),
            "loss": float(np.sum((F - target) ** 2)), "grad": g.tolist()}
     if fd_check:
         i = 4  # matrix Gc
@@ -226,7 +227,8 @@ def adjoint_timing(steps: int = 10, fd_check: bool = True):
         tp, tm = theta0.copy(), theta0.copy()
         tp[i] += h
         tm[i] -= h
-        fd = (np.sum((runner.forward(tp) - target) ** 2) - np.sum((runner.forward(tm) - target) ** 2)) / (2 * h)
+        sch = runner.schedule  # the perturbed runs replay the sub-steps of the gradient's run
+        fd = (np.sum((runner.forward(tp, sch) - target) ** 2) - np.sum((runner.forward(tm, sch) - target) ** 2)) / (2 * h)
         out["fd_check"] = {"param": "Gc matrix", "adjoint": float(g[i]), "central_difference": float(fd),
                            "rel_err": float(abs(g[i] - fd) / abs(fd))}
     runner.close()

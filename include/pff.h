@@ -105,6 +105,10 @@ int pff_version(void);
 /* Context: parameters of the constitutive model (host data, copied). */
 int pff_create_context(pff_ctx** ctx, const pff_problem* problem);
 int pff_destroy_context(pff_ctx* ctx);
+/* Time step of the next residual (Sec. 5 load stepping; adaptive cut-back
+ * shortens it): sets dt and the Maxwell factor mu dt / eta_d of every phase.
+ * dt > 0; applies to every operator built on ctx from its next call on. */
+int pff_context_set_time_step(pff_ctx* ctx, double dt);
 
 /* Basis: GLL(p+1) nodes, Gauss(q) points and weights, 1D interpolation B[q][p+1]
  * and collocated derivative D[q][q] (Sec. 4, B_I and B_xi).  1 <= p, p+1 <= q <= 5.
@@ -244,6 +248,8 @@ typedef struct {
   int coarse_maxit;     /* coarse GMRES iterations per coarse solve */
   int verbose;          /* 1: one line per Newton iteration on stderr */
   int outer_prec;       /* fine-level action inside FGMRES: PFF_F64, or PFF_DF64 (pff_op_enable_df) */
+  int newton_stall;     /* give up (converged = 0) once ||r|| fell by less than 2x over this many
+                           Newton iterations, so that a load-step cut-back starts early; 0 = never */
 } pff_solver_params;
 
 typedef struct {

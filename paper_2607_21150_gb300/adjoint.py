@@ -2,12 +2,15 @@
 backward, behind a torch.autograd.Function.
 
 Forward: the load steps of a workload with per-phase parameters theta (12:
-E_inf, nu_inf, sigma0, eta_d, Gc, l0 of each phase); the converged state z_n and
-the committed history entering step n are checkpointed on the device at every
-load-step boundary.  Backward: pff_adjoint_step walks the steps in reverse,
-recomputing each step's linearisation from its checkpoint, solving the
-transposed system and propagating the history adjoint; the result is
-dLoss/dtheta for dLoss/dF given by autograd."""
+E_inf, nu_inf, sigma0, eta_d, Gc, l0 of each phase), each advanced with the
+adaptive cut-back of LoadStepper.advance; the converged state and the committed
+history entering every converged sub-step are checkpointed on the device with
+the sub-step's time step.  Backward: pff_adjoint_step walks the sub-steps in
+reverse, recomputing each one's linearisation from its checkpoint (with its
+time step), solving the transposed system and propagating the history adjoint;
+the reaction weights dLoss/dF enter at the sub-steps that end a load step.  The
+result is dLoss/dtheta for the dLoss/dF given by autograd.  `schedule` replays
+a recorded sub-step sequence (finite-difference checks must keep it fixed)."""
 from __future__ import annotations
 
 import copy
@@ -32,7 +35,7 @@ class ReactionCurveRunner:
         self.adjoint_rtol = adjoint_rtol
         self.lsp = None
 
-    def forward(self, theta) -> np.ndarray:
+    def forward(self, theta, schedule=None) -> np.ndarray:
         if self.lsp is not None:
             self.lsp.close()
         w = copy.copy(self.w)
@@ -41,14 +44,17 @@ class ReactionCurveRunner:
                                krylov_rtol=self.krylov_rtol)
         s = self.lsp.s
         self.sel = torch.from_numpy(top_face_mask(w.mesh).ravel()).to(s.dev)
-        self.z_ckpt, self.h_ckpt, F = [], [], []
+        self.subs = []  # converged sub-steps: state after, history before, time step, end factor
+
+        def record(f0, f1, dt, hist_before, stats):
+            self.subs.append({"z": self.lsp.z.clone(), "h": hist_before, "dt": dt, "f1": f1})
+
+        self.lsp.on_substep = record
+        F, self.schedule = [], []
         for n in range(1, self.nsteps + 1):
-            self.h_ckpt.append(s.history(0).clone())
-            st = self.lsp.step(n)
-            if not st["converged"]:
-                raise RuntimeError(f"load step {n} did not converge: {st}")
-            self.z_ckpt.append(self.lsp.z.clone())
-            F.append(st["reaction"])
+            out = self.lsp.advance(n, None if schedule is None else schedule[n - 1])
+            self.schedule.append([st["load"] for st in out])
+            F.append(out[-1]["reaction"])
         return np.array(F)
 
     def backward(self, dLdF) -> np.ndarray:
@@ -58,10 +64,12 @@ class ReactionCurveRunner:
         hbar = None
         hb_prev = torch.zeros(15 * nq, dtype=torch.float64, device=s.dev)
         self.adjoint_iters = []
-        for n in range(self.nsteps, 0, -1):
-            its = pff.pff_adjoint_step(self.lsp.solver, self.z_ckpt[n - 1], self.h_ckpt[n - 1], self.sel,
-                                       float(dLdF[n - 1]), hbar, hb_prev, grad, self.adjoint_rtol, 400,
-                                       s.stream)
+        for sub in reversed(self.subs):
+            n = int(sub["f1"])
+            wF = float(dLdF[n - 1]) if sub["f1"] == n else 0.0
+            pff.pff_context_set_time_step(s.ctx, sub["dt"])
+            its = pff.pff_adjoint_step(self.lsp.solver, sub["z"], sub["h"], self.sel, wF, hbar, hb_prev, grad,
+                                       self.adjoint_rtol, 400, s.stream)
             self.adjoint_iters.append(its)
             hbar = hb_prev.clone()
         return grad

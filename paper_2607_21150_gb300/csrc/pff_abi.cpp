@@ -305,6 +305,17 @@ int pff_destroy_context(pff_ctx* ctx) {
   return PFF_OK;
 }
 
+int pff_context_set_time_step(pff_ctx* ctx, double dt) {
+  PFF_REQUIRE(ctx, "pff_context_set_time_step: null context");
+  PFF_REQUIRE(dt > 0.0 && std::isfinite(dt), "pff_context_set_time_step: dt must be positive and finite");
+  ctx->glob.dt = dt;
+  for (int i = 0; i < ctx->nphase; ++i) {
+    PhaseDev& ph = ctx->phase[i];
+    ph.cmax = (ph.has[1] && ph.eta_d > 0.0) ? ph.mu[1] * dt / ph.eta_d : 0.0;
+  }
+  return PFF_OK;
+}
+
 int pff_create_basis(pff_ctx* ctx, int p, int q, pff_basis** out) {
   PFF_REQUIRE(ctx && out, "pff_create_basis: null argument");
   PFF_REQUIRE(p >= 1 && q >= p + 1 && q <= kMaxQ, "pff_create_basis: need 1 <= p and p + 1 <= q <= 5");

@@ -624,6 +624,7 @@ int pff_solver_default_params(pff_solver_params* p) {
   p->coarse_maxit = 200;
   p->verbose = 0;
   p->outer_prec = PFF_F64;
+  p->newton_stall = 0;
   return PFF_OK;
 }
 
@@ -849,6 +850,8 @@ int pff_newton_solve(pff_solver* s, double* z, pff_newton_stats* stats, void* st
     stats->res = rn;
     if (rn <= s->prm.newton_rtol * r0 || rn == 0.0) { stats->converged = 1; break; }
     if (it >= s->prm.newton_maxit) break;
+    const int k = s->prm.newton_stall;
+    if (k > 0 && it >= k && it - k < 64 && rn > 0.5 * stats->res_history[it - k]) break;  // stagnation
     t0 = now();
     S_RC(setup(s, st));
     S_CK(cudaStreamSynchronize(st));

@@ -1,7 +1,10 @@
 """Load stepping (Sec. 5): for every load step, impose the step's Dirichlet
 values, solve the coupled system with Newton-FGMRES/p-multigrid, commit the
 quadrature-point history (Box 1 step 4) and record the reaction on the loaded
-face.  Host logic only; every numerical step is a libpff call."""
+face.  A step whose Newton solve fails is retried from the last converged state
+with half the load increment and half the time step (adaptive cut-back), and
+the increment grows again after successes.  Host logic only; every numerical
+step is a libpff call."""
 from __future__ import annotations
 
 import time
@@ -14,11 +17,50 @@ from .inputs import Workload, node_coords, top_face_mask
 from .session import Session
 
 
+class StepFailed(RuntimeError):
+    pass
+
+
+class StepController:
+    """Adaptive sub-stepping of the load factor from `start` to `target`.
+
+    attempt(f_from, f_to) -> bool runs one sub-step (load factor and time both
+    advance by f_to - f_from in units of the nominal step) and reports whether
+    it converged; a failed attempt must leave the state at f_from.  After a
+    failure the increment is halved (at most `max_cuts` failures in a row),
+    after a success it grows by `grow`, never past `target`.  Increments are
+    dyadic fractions of the nominal step, so the sub-step ends are exact."""
+
+    def __init__(self, max_cuts: int = 6, grow: float = 2.0):
+        self.max_cuts = max_cuts
+        self.grow = grow
+
+    def run(self, start: float, target: float, attempt, first: float | None = None):
+        f = float(start)
+        inc = float(target - start) if first is None else float(first)
+        done, cuts = [], 0
+        while f < target:
+            inc = min(inc, target - f)
+            f_to = target if f + inc >= target else f + inc
+            if attempt(f, f_to):
+                done.append((f, f_to))
+                f = f_to
+                cuts = 0
+                inc *= self.grow
+            else:
+                cuts += 1
+                if cuts > self.max_cuts:
+                    raise StepFailed(f"no convergence from load factor {f} after {self.max_cuts} cuts")
+                inc *= 0.5
+        return done
+
+
 class LoadStepper:
     def __init__(self, w: Workload, levels=None, mixed: bool = True, session: Session | None = None,
-                 df: bool = False, **solver_params):
+                 df: bool = False, max_cuts: int = 6, **solver_params):
         """df: the fine-level action inside FGMRES in double-float arithmetic
-        (PFF_DF64) instead of FP64."""
+        (PFF_DF64) instead of FP64.  max_cuts: consecutive halvings of a failing
+        load increment before `advance` gives up."""
         m = w.mesh
         if levels is None:
             levels = {4: [4, 2, 1], 3: [3, 1], 2: [2, 1], 1: [1]}[m.p]
@@ -26,8 +68,11 @@ class LoadStepper:
         self.s = session or Session(w, levels=[p for p in self.levels if p != m.p], f32=mixed, df=df)
         if df:
             solver_params.setdefault("outer_prec", pff.PFF_DF64)
+        solver_params.setdefault("newton_stall", 6)  # a stagnating solve hands over to the cut-back early
         self.solver = self.s.solver(self.levels, mixed=int(mixed), **solver_params)
         self.w = w
+        self.dt = float(w.glob[3])
+        self.controller = StepController(max_cuts=max_cuts)
         self.z = torch.from_numpy(np.ascontiguousarray(w.z, dtype=np.float64).ravel()).to(self.s.dev)
         self.unit = np.ascontiguousarray(w.dvals if w.dvals is not None else np.zeros((4, m.nn)), dtype=np.float64)
         self.top = torch.from_numpy(top_face_mask(m).ravel()).to(self.s.dev)
@@ -41,6 +86,8 @@ class LoadStepper:
             ext[2] = float(np.mean(self.unit[2][top[2]])) * Z
         self.extension = torch.from_numpy(ext.ravel()).to(self.s.dev)
         self.loaded = 0.0
+        # callback(f_from, f_to, dt, hist_before, stats) after every converged sub-step of `advance`
+        self.on_substep = None
 
     def set_load(self, factor: float):
         vals = torch.from_numpy((self.unit * factor).ravel()).to(self.s.dev)
@@ -48,21 +95,74 @@ class LoadStepper:
         self._vals = vals  # keep alive until the copy ran
         pff.pff_apply_dirichlet(self.s.op, self.z, self.s.stream)
 
-    def step(self, k: int):
-        """Load step k (Dirichlet values = k times the workload's per-step values)."""
-        t0 = time.perf_counter()
-        pff.pff_vec_axpby(pff.PFF_F64, self.z.numel(), float(k) - self.loaded, self.extension, 1.0, self.z,
+    def _solve_to(self, factor: float, dt: float):
+        """Predictor, Dirichlet values and Newton at load factor `factor` with time step dt."""
+        pff.pff_context_set_time_step(self.s.ctx, dt)
+        pff.pff_vec_axpby(pff.PFF_F64, self.z.numel(), factor - self.loaded, self.extension, 1.0, self.z,
                           self.s.stream)
-        self.loaded = float(k)
-        self.set_load(float(k))
-        stats = pff.pff_newton_solve(self.solver, self.z, self.s.stream)
+        self.set_load(factor)
+        return pff.pff_newton_solve(self.solver, self.z, self.s.stream)
+
+    def _commit(self, factor: float, stats, t0: float):
         pff.pff_commit_history(self.s.op, self.s.stream)
-        reaction = pff.pff_reaction(self.s.op, self.top, self.s.stream)[2]
-        stats["reaction"] = reaction
+        stats["reaction"] = pff.pff_reaction(self.s.op, self.top, self.s.stream)[2]
         stats["wall_s"] = time.perf_counter() - t0
-        stats["step"] = k
+        stats["load"] = factor
+        self.loaded = factor
         self.history.append(stats)
         return stats
+
+    def step(self, k: float):
+        """One Newton solve to load factor k from the current one, the time step
+        being (k - loaded) nominal steps; commits and returns the stats whether
+        or not it converged (no cut-back)."""
+        t0 = time.perf_counter()
+        k = float(k)
+        stats = self._solve_to(k, self.dt * (k - self.loaded))
+        stats["step"] = k
+        return self._commit(k, stats, t0)
+
+    def advance(self, k: float, schedule=None):
+        """Advance to load factor k with adaptive cut-back, or along the given
+        sub-step ends `schedule` (a replay: every sub-step must converge).
+        Returns the stats of the converged sub-steps; the last one holds the
+        reaction at k."""
+        k = float(k)
+        out = []
+
+        def attempt(f0, f1):
+            t0 = time.perf_counter()
+            z_prev = self.z.clone()
+            hist_before = self.s.history(0).clone() if self.on_substep else None
+            dt = self.dt * (f1 - f0)
+            try:
+                stats = self._solve_to(f1, dt)
+            except pff.PffError as e:  # kernel status or no admissible line-search step
+                if e.code != pff.ERR_DEVICE:
+                    raise
+                stats = {"converged": 0, "status": -1}
+            if not (stats["converged"] == 1 and stats["status"] == 0):
+                # the committed history is untouched until a sub-step converges
+                self.z.copy_(z_prev)
+                self.loaded = f0
+                return False
+            stats["step"] = k
+            stats["dt"] = dt
+            self._commit(f1, stats, t0)
+            out.append(stats)
+            if self.on_substep:
+                self.on_substep(f0, f1, dt, hist_before, stats)
+            return True
+
+        if schedule is None:
+            self.controller.run(self.loaded, k, attempt)
+        else:
+            for f1 in schedule:
+                if not attempt(self.loaded, float(f1)):
+                    raise StepFailed(f"replayed sub-step to {f1} did not converge")
+            if self.loaded != k:
+                raise StepFailed(f"schedule ends at {self.loaded}, not {k}")
+        return out
 
     def close(self):
         if self.solver is not None:

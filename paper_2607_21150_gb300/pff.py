@@ -20,8 +20,17 @@ STATUS_EIGEN, STATUS_DETF, STATUS_NONFINITE = 1, 2, 4
 _lib = None
 
 
+ERR_INVALID, ERR_CUDA, ERR_DEVICE, ERR_UNSUPPORTED = -1, -2, -3, -4
+
+
 class PffError(RuntimeError):
-    pass
+    """A libpff call returned a PFF_ERR_* code (``code``); ERR_DEVICE means a
+    kernel status word was set (det F <= 0, non-finite values, ...) or a solve
+    found no admissible step, with the device context intact."""
+
+    def __init__(self, msg, code=None):
+        super().__init__(msg)
+        self.code = code
 
 
 class pff_problem(ctypes.Structure):
@@ -41,7 +50,8 @@ class pff_solver_params(ctypes.Structure):
                 ("power_iters", ctypes.c_int), ("krylov_restart", ctypes.c_int), ("krylov_maxit", ctypes.c_int),
                 ("krylov_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("line_search_max", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_rtol", ctypes.c_double),
-                ("coarse_maxit", ctypes.c_int), ("verbose", ctypes.c_int), ("outer_prec", ctypes.c_int)]
+                ("coarse_maxit", ctypes.c_int), ("verbose", ctypes.c_int), ("outer_prec", ctypes.c_int),
+                ("newton_stall", ctypes.c_int)]
 
 
 class pff_newton_stats(ctypes.Structure):
@@ -69,6 +79,7 @@ _SIGS = {
     "pff_version": ([], _I),
     "pff_create_context": ([ctypes.POINTER(_VP), ctypes.POINTER(pff_problem)], _I),
     "pff_destroy_context": ([_VP], _I),
+    "pff_context_set_time_step": ([_VP, _D], _I),
     "pff_create_basis": ([_VP, _I, _I, ctypes.POINTER(_VP)], _I),
     "pff_basis_get": ([_VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pff_destroy_basis": ([_VP], _I),
@@ -167,7 +178,7 @@ def _stream(s):
 def _check(rc, name):
     if rc != 0:
         msg = lib().pff_last_error_message()
-        raise PffError(f"{name} failed ({rc}): {msg.decode() if msg else ''}")
+        raise PffError(f"{name} failed ({rc}): {msg.decode() if msg else ''}", rc)
 
 
 def _call(name, *args):
@@ -188,6 +199,10 @@ def pff_create_context(phase_params, at, eta, zeta, dt, s_phi):
 
 def pff_destroy_context(ctx):
     _call("pff_destroy_context", ctx)
+
+
+def pff_context_set_time_step(ctx, dt):
+    _call("pff_context_set_time_step", ctx, float(dt))
 
 
 def pff_create_basis(ctx, p, q):

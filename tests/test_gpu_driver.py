@@ -77,3 +77,34 @@ def test_load_steps_match_oracle(orc, at):
         assert np.linalg.norm(hg - hist) <= 1e-9 * np.linalg.norm(hist)
     assert lsp.history[-1]["reaction"] > lsp.history[0]["reaction"] > 0
     lsp.close()
+
+
+def test_substeps_match_oracle(orc):
+    """Sub-steps (load factor and time step halved) against the oracle's Newton
+    with the same time steps: 0 -> 0.5 -> 1 (dt/2 each), then 1 -> 2 (dt)."""
+    w = _tension_box(2)
+    lsp = LoadStepper(w, levels=[2, 1], mixed=False, newton_rtol=1e-11, krylov_rtol=1e-8)
+    out = lsp.advance(1, schedule=[0.5, 1.0]) + lsp.advance(2, schedule=[2.0])
+    assert [st["load"] for st in out] == [0.5, 1.0, 2.0]
+    dt0 = float(w.glob[3])
+    assert [st["dt"] for st in out] == [0.5 * dt0, 0.5 * dt0, dt0]
+    z = w.z.copy()
+    hist = w.hist.copy()
+    mk = w.mask.astype(bool)
+    top = inputs.top_face_mask(w.mesh).astype(bool)
+    for st, (f, dt) in zip(out, ((0.5, 0.5 * dt0), (1.0, 0.5 * dt0), (2.0, dt0))):
+        glob = w.glob.copy()
+        glob[3] = dt
+        z = z.copy()
+        z[mk] = (w.dvals * f)[mk]
+        wk = inputs.Workload("t", w.mesh, w.phases, glob, w.phase, z, hist, w.mask, w.dvals * f)
+        z, _, res = orc.newton(wk, rtol=1e-13)
+        fint = orc.assemble(inputs.Workload("t", w.mesh, w.phases, glob, w.phase, z, hist, None, None),
+                            matrix=False, mask=None, dvals=None)["r"]
+        hist = res["hist_new"]
+        react = float(fint[2][top[2]].sum())
+        assert abs(st["reaction"] - react) <= 1e-8 * abs(react)
+    zg = lsp.z.cpu().numpy().reshape(4, -1)
+    assert np.linalg.norm(zg - z) <= 1e-9 * np.linalg.norm(z)
+    assert np.linalg.norm(lsp.s.history(0).cpu().numpy() - hist) <= 1e-9 * np.linalg.norm(hist)
+    lsp.close()
