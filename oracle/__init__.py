@@ -90,6 +90,21 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+def phase_rows(phases):
+    """Phase parameter rows for the C oracle, 15 doubles each: the 12 of
+    ``inputs.phase_vector`` and the hardening law (H_lin, sigma_inf, beta),
+    padded with (0, sigma0, 0) = perfect plasticity when absent."""
+    ph = np.atleast_2d(np.asarray(phases, dtype=np.float64))
+    if ph.shape[1] == 15:
+        return np.ascontiguousarray(ph)
+    if ph.shape[1] != 12:
+        raise ValueError("phase rows must have 12 or 15 entries")
+    out = np.zeros((ph.shape[0], 15))
+    out[:, :12] = ph
+    out[:, 13] = ph[:, 11]
+    return out
+
+
 def _u8(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.uint8)
 
@@ -160,7 +175,7 @@ def pointwise(inputs, hist, phase, phases, glob, tangent: bool = True, commit: b
     hn = np.zeros((n, 15)) if commit else None
     flags = np.zeros(n, dtype=np.uint8)
     aux = np.zeros((n, 4))
-    lib().orc_pointwise(n, _p(inputs), _p(hist), _p(phase, ctypes.c_uint8), _p(phases), len(phases),
+    lib().orc_pointwise(n, _p(inputs), _p(hist), _p(phase, ctypes.c_uint8), _p(phase_rows(phases)), len(phases),
                         _p(glob), _p(f0), _p(f1), _p(D), _p(hn), _p(flags, ctypes.c_uint8), _p(aux))
     return dict(f0=f0, f1=f1.reshape(n, 4, 3), D=D, hist_new=hn, flags=flags,
                 psi_plus=aux[:, 0], margin_yield=aux[:, 1], margin_hist=aux[:, 2], theta=aux[:, 3])
@@ -190,7 +205,7 @@ def assemble(w, z=None, hist=None, matrix: bool = True, mask="workload", dvals="
     flags = np.zeros(m.nq, dtype=np.uint8)
     margins = np.zeros((m.nq, 3))
     L = lib()
-    handle = L.orc_assemble(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(w.phases)),
+    handle = L.orc_assemble(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(phase_rows(w.phases)),
                             len(w.phases), _p(_f64(w.glob)), _p(z), _p(hist),
                             _p(_u8(w.phase), ctypes.c_uint8), _p(mask, ctypes.c_uint8), _p(dvals),
                             1 if matrix else 0, _p(r), _p(hn), _p(flags, ctypes.c_uint8), _p(margins))
@@ -217,7 +232,7 @@ def sample_rows(w, dofs, x, z=None, hist=None):
     x = _f64(x)
     dims, h = _mesh_args(m)
     r, jx, jtx, dg = np.zeros(ns), np.zeros(ns), np.zeros(ns), np.zeros(ns)
-    lib().orc_sample_rows(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(w.phases)),
+    lib().orc_sample_rows(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(phase_rows(w.phases)),
                           len(w.phases), _p(_f64(w.glob)), _p(z), _p(hist),
                           _p(_u8(w.phase), ctypes.c_uint8), _p(_u8(w.mask), ctypes.c_uint8),
                           _p(None if w.dvals is None else _f64(w.dvals)), _p(x), ns,
@@ -385,7 +400,7 @@ def point_partials(inputs, hist, phase, phases, glob):
     n = inputs.shape[0]
     vals = np.zeros((n, 28))
     J = np.zeros((n, 28, 34))
-    lib().orc_point_partials(n, _p(inputs), _p(_f64(hist)), _p(_u8(phase), ctypes.c_uint8), _p(_f64(phases)),
+    lib().orc_point_partials(n, _p(inputs), _p(_f64(hist)), _p(_u8(phase), ctypes.c_uint8), _p(phase_rows(phases)),
                              len(phases), _p(_f64(glob)), _p(vals), _p(J))
     return vals, J
 

@@ -105,6 +105,9 @@ template <int N> inline Dual<N> operator/(double a, const Dual<N>& b) { return D
 template <int N> inline Dual<N> sqrt(const Dual<N>& a) {
   Dual<N> r; r.v = std::sqrt(a.v); for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / (2.0 * r.v); return r;
 }
+template <int N> inline Dual<N> exp(const Dual<N>& a) {
+  Dual<N> r; r.v = std::exp(a.v); for (int i = 0; i < N; ++i) r.d[i] = a.d[i] * r.v; return r;
+}
 template <int N> inline Dual<N> log1p(const Dual<N>& a) {
   Dual<N> r; r.v = std::log1p(a.v); for (int i = 0; i < N; ++i) r.d[i] = a.d[i] / (1.0 + a.v); return r;
 }
@@ -112,6 +115,7 @@ inline double val(double x) { return x; }
 template <int N> inline double val(const Dual<N>& x) { return x.v; }
 using std::sqrt;
 using std::log1p;
+using std::exp;
 
 // ----------------------------------------------------------------------------
 // 3x3 matrices
@@ -245,13 +249,18 @@ M3<double> expm(const M3<double>& A) {
 // ----------------------------------------------------------------------------
 // Material description
 // ----------------------------------------------------------------------------
-// Phase parameters, 12 doubles: Gc, l0, E_inf, nu_inf, hasM, E1, nu1, eta_d,
-// hasP, E2, nu2, sigma0  (units mm, MPa, s; eta_d = +inf allowed).
+// Phase parameters, kPhaseWords = 15 doubles: Gc, l0, E_inf, nu_inf, hasM, E1,
+// nu1, eta_d, hasP, E2, nu2, sigma0, H_lin, sigma_inf, beta (units mm, MPa, s;
+// eta_d = +inf allowed).  The last three are the linear + Voce hardening law of
+// the Prandtl branch (Eq. plasticity-strain-hardening-law); H_lin = 0,
+// sigma_inf = sigma0 is perfect plasticity.
+static const int kPhaseWords = 15;
 template <typename T>
 struct PhaseT {
   T Gc, l0, E0, nu0;
   int hasM; T E1, nu1, eta; bool eta_inf;
   int hasP; T E2, nu2, sig0;
+  T Hlin, sinf, beta;
 };
 typedef PhaseT<double> Phase;
 // Global parameters, 5 doubles: AT (1 or 2), eta (residual stiffness),
@@ -263,6 +272,7 @@ static Phase read_phase(const double* p) {
   ph.Gc = p[0]; ph.l0 = p[1]; ph.E0 = p[2]; ph.nu0 = p[3];
   ph.hasM = p[4] != 0.0; ph.E1 = p[5]; ph.nu1 = p[6]; ph.eta = p[7]; ph.eta_inf = !std::isfinite(p[7]);
   ph.hasP = p[8] != 0.0; ph.E2 = p[9]; ph.nu2 = p[10]; ph.sig0 = p[11];
+  ph.Hlin = p[12]; ph.sinf = p[13]; ph.beta = p[14];
   return ph;
 }
 template <typename T> PhaseT<T> lift(const Phase& p) {
@@ -270,7 +280,19 @@ template <typename T> PhaseT<T> lift(const Phase& p) {
   q.Gc = T(p.Gc); q.l0 = T(p.l0); q.E0 = T(p.E0); q.nu0 = T(p.nu0);
   q.hasM = p.hasM; q.E1 = T(p.E1); q.nu1 = T(p.nu1); q.eta = T(p.eta_inf ? 1.0 : p.eta); q.eta_inf = p.eta_inf;
   q.hasP = p.hasP; q.E2 = T(p.E2); q.nu2 = T(p.nu2); q.sig0 = T(p.sig0);
+  q.Hlin = T(p.Hlin); q.sinf = T(p.sinf); q.beta = T(p.beta);
   return q;
+}
+
+// Yield stress of the hardening law (Eq. plasticity-strain-hardening-law) and
+// its slope H = d sigma_y / d eps_p.
+template <typename T>
+T yield_stress(const PhaseT<T>& ph, const T& ep) {
+  return ph.sig0 + ph.Hlin * ep + (ph.sinf - ph.sig0) * (1.0 - exp(-ph.beta * ep));
+}
+template <typename T>
+T yield_slope(const PhaseT<T>& ph, const T& ep) {
+  return ph.Hlin + (ph.sinf - ph.sig0) * ph.beta * exp(-ph.beta * ep);
 }
 static Glob read_glob(const double* g) {
   Glob gl; gl.at = (int)g[0]; gl.eta_res = g[1]; gl.zeta = g[2]; gl.dt = g[3]; gl.s_phi = g[4];
@@ -369,13 +391,28 @@ void pointwise(const T G[3][3], const T& phi, const T gphi[3], const T* hist,
     if (br == 1) {
       if (!ph.eta_inf) a = 1.0 / (1.0 + g * (mu * gl.dt / ph.eta));
     } else if (br == 2) {
+      // Box 2 with the degraded trial stress (reading: g multiplies q_tr and the
+      // 3 mu dgam term, not sigma_y): admissible iff g q_tr - sigma_y(eps_p,n) <= 0
+      const T& epn = hist[12];
       double qv = 2.0 * val(mu) * std::sqrt(1.5 * val(s));
-      double fv = val(g) * qv - val(ph.sig0);  // degraded admissibility check
-      out.margin_yield = fv / val(ph.sig0);
+      double sy0 = val(yield_stress(ph, epn));
+      double fv = val(g) * qv - sy0;
+      out.margin_yield = fv / sy0;
       if (fv > 0.0) {
         T q = 2.0 * mu * sqrt(1.5 * s);
-        a = ph.sig0 / (g * q);
-        dgam = (g * q - ph.sig0) / (3.0 * g * mu);
+        // plastic step: Newton on f(dgam) = g q_tr - 3 g mu dgam - sigma_y(eps_p,n + dgam),
+        // from dgam = 0, to |f| <= 1e-14 sigma_y, then two more iterations so that
+        // the dual parts (implicit derivatives) converge with the value
+        T dg = T(0.0);
+        int extra = 0;
+        for (int it = 0; it < 60; ++it) {
+          T f = g * q - 3.0 * g * mu * dg - yield_stress(ph, epn + dg);
+          T den = -3.0 * g * mu - yield_slope(ph, epn + dg);
+          dg = dg - f / den;
+          if (std::fabs(val(f)) <= 1e-14 * sy0 && ++extra > 2) break;
+        }
+        dgam = dg;
+        a = 1.0 - 3.0 * mu * dg / q;
         out.flags |= 1;
       }
     }
@@ -688,7 +725,7 @@ static Problem make_problem(const int* dims, const double* h, const double* phas
   Problem pr;
   pr.m = make_mesh(dims, h);
   pr.eb = elem_basis(pr.m);
-  for (int i = 0; i < nphase; ++i) pr.phases.push_back(read_phase(phase_params + 12 * i));
+  for (int i = 0; i < nphase; ++i) pr.phases.push_back(read_phase(phase_params + kPhaseWords * i));
   pr.gl = read_glob(glob);
   pr.z = z; pr.hist = hist; pr.phase = phase;
   pr.nq = (long long)pr.m.nx * pr.m.ny * pr.m.nz * pr.eb.Q3;
@@ -744,7 +781,7 @@ int orc_pointwise(int n, const double* inputs, const double* hist, const uint8_t
                   const double* phase_params, int nphase, const double* glob,
                   double* f0, double* f1, double* Dh, double* hist_new, uint8_t* flags, double* aux) {
   std::vector<Phase> phases;
-  for (int i = 0; i < nphase; ++i) phases.push_back(read_phase(phase_params + 12 * i));
+  for (int i = 0; i < nphase; ++i) phases.push_back(read_phase(phase_params + kPhaseWords * i));
   Glob gl = read_glob(glob);
 #pragma omp parallel for schedule(dynamic, 64)
   for (int k = 0; k < n; ++k) {
@@ -1029,7 +1066,7 @@ int orc_point_partials(int n, const double* inputs, const double* hist, const ui
                        const double* phase_params, int nphase, const double* glob, double* out_vals,
                        double* out_J) {
   std::vector<Phase> phases;
-  for (int i = 0; i < nphase; ++i) phases.push_back(read_phase(phase_params + 12 * i));
+  for (int i = 0; i < nphase; ++i) phases.push_back(read_phase(phase_params + kPhaseWords * i));
   Glob gl = read_glob(glob);
 #pragma omp parallel for schedule(dynamic, 16)
   for (int k = 0; k < n; ++k) {

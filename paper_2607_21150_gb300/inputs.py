@@ -67,6 +67,22 @@ def phase_vector(d: dict) -> np.ndarray:
     return v
 
 
+def harden(phases, H_lin: float, sigma_inf: float, beta: float) -> np.ndarray:
+    """Phase rows widened to 15 doubles with the linear + Voce hardening law of
+    the Prandtl branch (Eq. plasticity-strain-hardening-law): H_lin, sigma_inf,
+    beta for every phase that has a Prandtl branch, (0, sigma0, 0) = perfect
+    plasticity for the others.  The paper's examples are perfectly plastic; the
+    values used with this are test inputs, not Table 2 data."""
+    ph = np.atleast_2d(np.asarray(phases, dtype=np.float64))
+    out = np.zeros((ph.shape[0], 15))
+    out[:, :12] = ph[:, :12]
+    out[:, 13] = ph[:, 11]
+    for k in range(ph.shape[0]):
+        if ph[k, 8]:
+            out[k, 12:15] = (H_lin, sigma_inf, beta)
+    return out
+
+
 def c0_of(at: int) -> float:
     """Normalisation constant of the AT1 (8/3) / AT2 (2) crack density."""
     return 8.0 / 3.0 if at == 1 else 2.0

@@ -10,6 +10,7 @@ maxwell-energy-dphi, prandtl-energy-dphi) for the coupled terms.  Valid at
 points with distinct eigenvalues of every branch's trial b.
 """
 import numpy as np
+from scipy.optimize import brentq
 
 VI = [0, 1, 2, 1, 0, 0]
 VJ = [0, 1, 2, 2, 2, 1]
@@ -28,8 +29,15 @@ def branches(phase_vec):
     if phase_vec[4]:
         out.append(("maxwell", phase_vec[5], phase_vec[6], phase_vec[7], 0))
     if phase_vec[8]:
-        out.append(("prandtl", phase_vec[9], phase_vec[10], phase_vec[11], 6))
+        law = tuple(phase_vec[11:15]) if len(phase_vec) == 15 else (phase_vec[11], 0.0, phase_vec[11], 0.0)
+        out.append(("prandtl", phase_vec[9], phase_vec[10], law, 6))
     return out
+
+
+def yield_stress(law, ep):
+    """Linear + Voce hardening law (Eq. plasticity-strain-hardening-law) and its slope."""
+    s0, Hl, sinf, beta = law
+    return s0 + Hl * ep + (sinf - s0) * (1 - np.exp(-beta * ep)), Hl + (sinf - s0) * beta * np.exp(-beta * ep)
 
 
 def point(inp, hist, phase_vec, glob):
@@ -54,17 +62,24 @@ def point(inp, hist, phase_vec, glob):
         eps = 0.5 * np.log(bi)
         epsd = eps - eps.sum() / 3
         q = 2 * mu * np.sqrt(1.5 * np.sum(epsd ** 2))
-        a, da_dphi, yield_ = 1.0, 0.0, False
+        a, da_dphi, yield_, dgam, Hs = 1.0, 0.0, False, 0.0, 0.0
         if kind == "maxwell" and np.isfinite(extra):
             c = mu * dt / extra
             a = 1 / (1 + c * g)
             da_dphi = -a * a * c * gp
-        elif kind == "prandtl" and g * q - extra > 0:
-            a = extra / (g * q)
-            da_dphi = -a * gp / g
+        elif kind == "prandtl" and g * q - yield_stress(extra, hist[12])[0] > 0:
+            # Box 2, degraded: g q - 3 g mu dgam - sigma_y(eps_p,n + dgam) = 0, bracketed
+            # root (f(0) > 0 >= f(dgam_max) for a non-decreasing sigma_y)
+            f = lambda x: g * q - 3 * g * mu * x - yield_stress(extra, hist[12] + x)[0]
+            hi = (g * q - yield_stress(extra, hist[12])[0]) / (3 * g * mu)
+            dgam = brentq(f, 0.0, hi, xtol=1e-300, rtol=1e-15, maxiter=500) if f(hi) < 0 else hi
+            Hs = yield_stress(extra, hist[12] + dgam)[1]
+            a = 1 - 3 * mu * dgam / q
+            # implicit derivative of dgam in phi (through g), Box A1 / App. C
+            da_dphi = -3 * mu / q * (q - 3 * mu * dgam) * gp / (3 * g * mu + Hs)
             yield_ = True
         br.append(dict(kind=kind, mu=mu, kap=kap, bi=bi, N=N, epsd=epsd, a=a, da_dphi=da_dphi,
-                       q=q, yield_=yield_, taui=2 * mu * a * epsd))
+                       q=q, yield_=yield_, taui=2 * mu * a * epsd, dgam=dgam, H=Hs, g=g))
     taud = sum(b["N"] @ np.diag(b["taui"]) @ b["N"].T for b in br)
     psid = sum(b["mu"] * b["a"] ** 2 * np.sum(b["epsd"] ** 2) for b in br)
     tauv = kap_tot * theta * np.eye(3)
@@ -100,7 +115,10 @@ def directional(inp, hist, phase_vec, glob, dF, dphi, dgphi):
         if b["kind"] == "prandtl" and b["yield_"]:
             taud_tr = 2 * mu * epsd
             dq = 1.5 * np.dot(taud_tr, 2 * mu * depsd_tr) / b["q"]   # Eq. plasticity-dq-trial-vonMises
-            da = da - a * dq / b["q"]
+            # Eq. plasticity-dtau-vonMises with the degraded consistency condition:
+            # d dgam = g dq / (3 g mu + H) at fixed phi, a = 1 - 3 mu dgam / q
+            ddgam = b["g"] * dq / (3 * b["g"] * mu + b["H"])
+            da = da - 3 * mu * ddgam / b["q"] + 3 * mu * b["dgam"] * dq / b["q"] ** 2
         depsd = a * depsd_tr + da * epsd                        # Box A1 (degraded form)
         dtaui = 2 * mu * depsd
         tau_i = b["taui"]
