@@ -62,6 +62,7 @@ extern "C" {
 #define PFF_STATUS_DETF 2        /* det F <= 0 at some quadrature point */
 #define PFF_STATUS_NONFINITE 4   /* non-finite residual integrand */
 #define PFF_STATUS_PHASE 8       /* phase id >= nphase (phase 0 used) */
+#define PFF_STATUS_RETURN 16     /* hardening return map: local Newton hit its cap (50) */
 
 /* PFF_DF64: FP64 vectors, the Jacobian action's contractions carried in
  * double-float arithmetic (pairs of FP32 words on the FP32 pipes, error about
@@ -109,6 +110,14 @@ int pff_destroy_context(pff_ctx* ctx);
  * shortens it): sets dt and the Maxwell factor mu dt / eta_d of every phase.
  * dt > 0; applies to every operator built on ctx from its next call on. */
 int pff_context_set_time_step(pff_ctx* ctx, double dt);
+/* Strain hardening of phase `phase`'s Prandtl branch (Eq.
+ * plasticity-strain-hardening-law): sigma_y(ep) = sigma0 + H_lin ep +
+ * (sigma_inf - sigma0)(1 - exp(-beta ep)), ep the accumulated plastic strain
+ * (history word 12), returned by the local Newton of Box 2 on the degraded
+ * consistency condition g q_tr - 3 g mu dgam - sigma_y(ep_n + dgam) = 0.
+ * Contexts start perfectly plastic (H_lin = 0, sigma_inf = sigma0).  Requires
+ * H_lin >= 0, beta >= 0, sigma_inf >= sigma0 (non-decreasing sigma_y). */
+int pff_context_set_hardening(pff_ctx* ctx, int phase, double H_lin, double sigma_inf, double beta);
 
 /* Basis: GLL(p+1) nodes, Gauss(q) points and weights, 1D interpolation B[q][p+1]
  * and collocated derivative D[q][q] (Sec. 4, B_I and B_xi).  1 <= p, p+1 <= q <= 5.

@@ -288,6 +288,10 @@ int pff_create_context(pff_ctx** out, const pff_problem* pr) {
     ph.l0 = v[1];
     ph.c0 = c0;
     ph.sig0 = v[11];
+    ph.Hlin = 0.0;
+    ph.sinf = v[11];
+    ph.beta = 0.0;
+    ph.hard = 0;
     ph.gc_c0l0 = v[0] / (c0 * v[1]);
     ph.kphi = pr->s_phi * 2.0 * v[0] * v[1] / c0;
   }
@@ -302,6 +306,21 @@ int pff_create_context(pff_ctx** out, const pff_problem* pr) {
 
 int pff_destroy_context(pff_ctx* ctx) {
   delete ctx;
+  return PFF_OK;
+}
+
+int pff_context_set_hardening(pff_ctx* ctx, int phase, double H_lin, double sigma_inf, double beta) {
+  PFF_REQUIRE(ctx, "pff_context_set_hardening: null context");
+  PFF_REQUIRE(phase >= 0 && phase < ctx->nphase, "pff_context_set_hardening: phase out of range");
+  PhaseDev& ph = ctx->phase[phase];
+  PFF_REQUIRE(ph.has[2], "pff_context_set_hardening: the phase has no Prandtl branch");
+  PFF_REQUIRE(H_lin >= 0.0 && beta >= 0.0 && sigma_inf >= ph.sig0 && std::isfinite(H_lin) && std::isfinite(beta) &&
+                  std::isfinite(sigma_inf),
+              "pff_context_set_hardening: need H_lin >= 0, beta >= 0, sigma_inf >= sigma0 (non-decreasing sigma_y)");
+  ph.Hlin = H_lin;
+  ph.sinf = sigma_inf;
+  ph.beta = beta;
+  ph.hard = (H_lin != 0.0 || (sigma_inf != ph.sig0 && beta != 0.0)) ? 1 : 0;
   return PFF_OK;
 }
 

@@ -24,6 +24,7 @@ namespace {
 struct Branch {
   bool has, plastic;
   double mu, af, s2, q, c;  // c: Maxwell mu dt / eta_d
+  double dgam, H, esig0;    // Prandtl: plastic increment, slope of sigma_y, d sigma_y / d sigma0 at ep_n + dgam
   double N[3][3], x[3], b[3], ed[3], ghat[3];
   double rho[3], gam[3];    // pairs (0,1), (0,2), (1,2)
   double Be[3][3];          // N diag(ghat) N^T
@@ -153,8 +154,13 @@ __global__ void __launch_bounds__(128) k_adjoint_point(const AdjArgs a) {
         B.af = 1.0 / (1.0 + B.c * g);
       } else if (br == 2) {
         B.q = 2.0 * B.mu * sqrt(1.5 * B.s2);
-        if (g * B.q - ph.sig0 > 0.0) {
-          B.af = ph.sig0 / (g * B.q);
+        if (g * B.q - yield_stress(ph, hist[12]) > 0.0) {
+          int ok;
+          B.dgam = return_map(ph, g, B.mu, B.q, hist[12], &ok);
+          if (!ok) status |= 16;
+          B.H = yield_slope(ph, hist[12] + B.dgam);
+          B.esig0 = ph.hard ? exp(-ph.beta * (hist[12] + B.dgam)) : 1.0;
+          B.af = 1.0 - 3.0 * B.mu * B.dgam / B.q;
           B.plastic = true;
         }
       }
@@ -267,15 +273,19 @@ __global__ void __launch_bounds__(128) k_adjoint_point(const AdjArgs a) {
         for (int p = 0; p < 3; ++p) ded[p] = deps[p] - dtr / 3.0;
         const double ds2 = 2.0 * edde;
         const double dmu = (br == 0) ? dmu0 : 0.0;
-        double da = 0.0, dq = 0.0;
+        double da = 0.0, dq = 0.0, ddgam = 0.0;
         if (br == 1) {
           if (B.c != 0.0) {
             const double dc = -B.c * dpar[3] / ph.eta_d;
             da = -B.af * B.af * (dc * g + B.c * dg);
           }
         } else if (br == 2 && B.plastic) {
+          // implicit derivative of the degraded consistency condition
+          // g q - 3 g mu dgam - sigma_y(ep_n + dgam; sigma0) = 0
           dq = B.q * edde / B.s2;
-          da = B.af * (dpar[2] / ph.sig0 - dg / g - dq / B.q);
+          ddgam = (g * dq + (B.q - 3.0 * B.mu * B.dgam) * dg - B.esig0 * dpar[2] - B.H * dh[12]) /
+                  (3.0 * g * B.mu + B.H);
+          da = -3.0 * B.mu * ddgam / B.q + 3.0 * B.mu * B.dgam * dq / (B.q * B.q);
         }
         double dth_[3][3];
         for (int p = 0; p < 3; ++p) dth_[p][p] = 2.0 * (dmu * B.af * B.ed[p] + B.mu * da * B.ed[p] + B.mu * B.af * ded[p]);
@@ -318,8 +328,7 @@ __global__ void __launch_bounds__(128) k_adjoint_point(const AdjArgs a) {
             dPhi[off + v] = s;
           }
         }
-        if (br == 2 && B.plastic)
-          dgam = dq / (3.0 * B.mu) - dpar[2] / (3.0 * g * B.mu) + ph.sig0 * dg / (3.0 * g * g * B.mu);
+        if (br == 2 && B.plastic) dgam = ddgam;
       }
       const double dtv = dkap0 * theta + ph.kap_tot * dth;
       const double dpsiv = 0.5 * dkap0 * theta * theta + ph.kap_tot * theta * dth;

@@ -25,7 +25,9 @@ struct PhaseDev {
   double mu[3], kap[3];   // branch 0 Hooke, 1 Maxwell, 2 Prandtl
   int has[3];
   double cmax;            // Maxwell: mu dt / eta_d (0 when eta_d = +inf)
-  double sig0;            // Prandtl perfect-plastic yield stress
+  double sig0;            // Prandtl initial yield stress
+  double Hlin, sinf, beta;// Prandtl hardening law sigma_y = sig0 + Hlin ep + (sinf - sig0)(1 - exp(-beta ep))
+  int hard;               // 0: perfect plasticity (Hlin = 0, sinf = sig0)
   double kap_tot;
   double gc_c0l0;         // Gc / (c0 l0)
   double kphi;            // s_phi * 2 Gc l0 / c0

@@ -139,20 +139,28 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
     const double tr = eps[0] + eps[1] + eps[2];
     for (int p = 0; p < 3; ++p) ed[p] = eps[p] - tr * (1.0 / 3.0);
     const double s2 = ed[0] * ed[0] + ed[1] * ed[1] + ed[2] * ed[2];
-    double af = 1.0, da_dphi = 0.0;
+    double af = 1.0, da_dphi = 0.0, cq = 0.0;
     bool plastic = false;
     if (br == 1) {
       af = 1.0 / (1.0 + ph.cmax * g);
       da_dphi = -af * af * ph.cmax * gp;
     } else if (br == 2) {
+      // Box 2, degraded: admissible iff g q_tr <= sigma_y(ep_n); else the local Newton
       const double qtr = 2.0 * mu * sqrt(1.5 * s2);
-      const double f = g * qtr - ph.sig0;
-      if (f > 0.0) {
-        af = ph.sig0 / (g * qtr);
-        da_dphi = -af * gp / g;
+      const double epn = a.hist[12 * nq + q];
+      if (g * qtr - yield_stress(ph, epn) > 0.0) {
+        int ok;
+        dgam = return_map(ph, g, mu, qtr, epn, &ok);
+        if (!ok) status |= 16;
+        const double Hs = yield_slope(ph, epn + dgam);
+        af = 1.0 - 3.0 * mu * dgam / qtr;
+        // implicit derivatives of dgam: d a = cq dq / q + da_dphi dphi
+        // (Eq. plasticity-dtau-vonMises with the degraded consistency condition)
+        const double den = 1.0 / (3.0 * g * mu + Hs);
+        cq = (1.0 - af) - 3.0 * g * mu * den;
+        da_dphi = -3.0 * mu * af * gp * den;
         plastic = true;
         flag |= 1;
-        dgam = f / (3.0 * g * mu);
       }
     }
     double ti[3];
@@ -197,7 +205,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
         E[5][v] = N[r][0] * N[c][1] + N[r][1] * N[c][0];
       }
       const double k01 = mu * af * rho01, k02 = mu * af * rho02, k12 = mu * af * rho12;
-      const double af_s2 = plastic ? af / s2 : 0.0;
+      const double cq_s2 = plastic ? cq / s2 : 0.0;  // d a / d(eps_d . d eps_d) = cq / s2 (dq / q = edde / s2)
       for (int d = 0; d < 10; ++d) {
         double lh[3][3];
         double dphi = 0.0;
@@ -217,7 +225,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
           edde += ed[p] * lh[p][p];
         }
         double da = dphi * da_dphi;
-        if (plastic) da -= af_s2 * edde;
+        if (plastic) da += cq_s2 * edde;
         double dh[6];  // principal-frame dtau: 00, 11, 22, 12, 02, 01
         for (int p = 0; p < 3; ++p) dh[p] = 2.0 * mu * (af * ded[p] + da * ed[p]);
         dh[3] = k12 * (lh[1][2] * b[2] + b[1] * lh[2][1]);

@@ -57,6 +57,36 @@ static __device__ inline int jacobi3(double A[3][3], double V[3][3], double w[3]
   return ok;
 }
 
+// Yield stress of the Prandtl branch and its slope H = d sigma_y / d ep (Eq.
+// plasticity-strain-hardening-law: linear + Voce).
+static __device__ __forceinline__ double yield_stress(const PhaseDev& ph, double ep) {
+  if (!ph.hard) return ph.sig0;
+  return ph.sig0 + ph.Hlin * ep + (ph.sinf - ph.sig0) * (1.0 - exp(-ph.beta * ep));
+}
+static __device__ __forceinline__ double yield_slope(const PhaseDev& ph, double ep) {
+  if (!ph.hard) return 0.0;
+  return ph.Hlin + (ph.sinf - ph.sig0) * ph.beta * exp(-ph.beta * ep);
+}
+
+// Plastic step of Box 2 with the degraded trial stress: the root dgam of
+//   g q_tr - 3 g mu dgam - sigma_y(ep_n + dgam) = 0
+// by Newton from the linearised step; perfect plasticity is the first step.
+// Sets *ok = 0 when 50 iterations leave |f| > 1e-14 max(sigma_y, g q_tr).
+static __device__ inline double return_map(const PhaseDev& ph, double g, double mu, double qtr, double epn, int* ok) {
+  const double f0 = g * qtr - yield_stress(ph, epn);
+  double dg = f0 / (3.0 * g * mu + yield_slope(ph, epn));
+  *ok = 1;
+  if (!ph.hard) return dg;
+  for (int it = 0; it < 50; ++it) {
+    const double sy = yield_stress(ph, epn + dg);
+    const double f = g * qtr - 3.0 * g * mu * dg - sy;
+    if (fabs(f) <= 1e-14 * fmax(sy, g * qtr)) return dg;
+    dg += f / (3.0 * g * mu + yield_slope(ph, epn + dg));
+  }
+  *ok = 0;
+  return dg;
+}
+
 // (ln b_p - ln b_q) / (b_p - b_q) from the eigenvalues x = b - 1:
 // log1p(y) / (y b_q) with y = (b_p - b_q) / b_q.  For |y| < 1/64 the Taylor
 // series of log1p(y) / y to y^8 (remainder below y^9 / 10 < 2e-17) replaces the

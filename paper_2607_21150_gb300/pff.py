@@ -80,6 +80,7 @@ _SIGS = {
     "pff_create_context": ([ctypes.POINTER(_VP), ctypes.POINTER(pff_problem)], _I),
     "pff_destroy_context": ([_VP], _I),
     "pff_context_set_time_step": ([_VP, _D], _I),
+    "pff_context_set_hardening": ([_VP, _I, _D, _D, _D], _I),
     "pff_create_basis": ([_VP, _I, _I, ctypes.POINTER(_VP)], _I),
     "pff_basis_get": ([_VP, _VP, _VP, _VP, _VP, _VP], _I),
     "pff_destroy_basis": ([_VP], _I),
@@ -189,11 +190,16 @@ def _call(name, *args):
 # ---------------------------------------------------------------- handles
 def pff_create_context(phase_params, at, eta, zeta, dt, s_phi):
     import numpy as np
-    pp = np.ascontiguousarray(phase_params, dtype=np.float64).reshape(-1, 12)
+    rows = np.atleast_2d(np.asarray(phase_params, dtype=np.float64))
+    pp = np.ascontiguousarray(rows[:, :12])
     pr = pff_problem(len(pp), pp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(at), float(eta),
                      float(zeta), float(dt), float(s_phi))
     h = _VP()
     _call("pff_create_context", ctypes.byref(h), ctypes.byref(pr))
+    if rows.shape[1] == 15:  # hardening law of the Prandtl branches
+        for k, r in enumerate(rows):
+            if r[8] and (r[12] != 0.0 or r[13] != r[11]):
+                pff_context_set_hardening(h, k, r[12], r[13], r[14])
     return h
 
 
@@ -203,6 +209,10 @@ def pff_destroy_context(ctx):
 
 def pff_context_set_time_step(ctx, dt):
     _call("pff_context_set_time_step", ctx, float(dt))
+
+
+def pff_context_set_hardening(ctx, phase, H_lin, sigma_inf, beta):
+    _call("pff_context_set_hardening", ctx, int(phase), float(H_lin), float(sigma_inf), float(beta))
 
 
 def pff_create_basis(ctx, p, q):

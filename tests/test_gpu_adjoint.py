@@ -5,7 +5,10 @@ Three load steps of a two-phase Q2 tension box (history carried between
 steps): the GPU reactions equal the oracle's (1e-9), the adjoint gradient of the
 reaction-curve misfit equals the oracle's (1e-7 relative per component) and
 central differences of the GPU loss (1e-6), and torch autograd through
-ReactionCurve returns the same gradient.
+ReactionCurve returns the same gradient.  Second variant: hardening Prandtl
+branches (linear + Voce, test values) with a live accumulated plastic strain,
+so that the return map's implicit derivatives and the history word eps_p
+enter the adjoint.
 """
 import numpy as np
 import pytest
@@ -27,9 +30,21 @@ def _adjoint_box():
     return w
 
 
-@pytest.fixture(scope="module")
-def problem(orc):
+def _hardened_box():
     w = _adjoint_box()
+    rows = inputs.harden(w.phases, 0.0, 0.0, 0.0)
+    rows[0, 11] = 300.0                       # matrix yields within the three steps
+    rows[:, 12] = 2000.0                      # H_lin
+    rows[:, 13] = 1.6 * rows[:, 11]           # sigma_inf
+    rows[:, 14] = 40.0                        # beta
+    w.phases = rows
+    w.hist[12] = np.random.default_rng(8).uniform(0.0, 0.02, w.mesh.nq)
+    return w
+
+
+@pytest.fixture(scope="module", params=["perfect", "hardening"])
+def problem(orc, request):
+    w = _adjoint_box() if request.param == "perfect" else _hardened_box()
     top = inputs.top_face_mask(w.mesh)
     theta0 = inputs.params_of(w.phases)
     nsteps = 3
@@ -59,7 +74,8 @@ def test_adjoint_gradient_matches_central_differences(problem):
     F = runner.forward(theta0)
     g = runner.backward(2.0 * (F - target))
     loss = lambda th: float(np.sum((runner.forward(th) - target) ** 2))
-    for i in (0, 1, 4, 5, 6, 7, 9, 10, 11):
+    idx = (0, 1, 4, 5, 6, 7, 9, 10, 11) if w.phases.shape[1] == 12 else (0, 1, 2, 4, 5, 6, 7, 9, 10, 11)
+    for i in idx:
         h = 1e-5 * abs(theta0[i])
         tp, tm = theta0.copy(), theta0.copy()
         tp[i] += h

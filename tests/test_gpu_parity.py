@@ -58,12 +58,22 @@ def _two_phase(nx, ny, nz, p, seed, mask=True, at=2):
     return inputs.Workload("box", m, phases, glob, phase, z, hist, mk, dv)
 
 
+def _hardened(nx, ny, nz, p, seed):
+    """Two-phase box whose Prandtl branches harden (linear + Voce, test values)
+    with a random accumulated plastic strain."""
+    w = _two_phase(nx, ny, nz, p, seed)
+    w.phases = inputs.harden(w.phases, 2000.0, 800.0, 40.0)
+    w.hist[12] = np.random.default_rng(seed + 3).uniform(0.0, 0.05, w.mesh.nq)
+    return w
+
+
 CASES = {
     "cube_q2": lambda: inputs.cube(),
     "cube_b_q2": lambda: inputs.cube(hist_seed=2, H_max=80.0),
     "box_q4_ragged": lambda: _two_phase(3, 2, 2, 4, 5),      # 12 elements: 2 blocks of 10, ragged
     "box_q3_ragged": lambda: _two_phase(3, 3, 2, 3, 7, at=1),  # 18 elements: blocks of 16
     "box_q1": lambda: _two_phase(5, 4, 4, 1, 9),              # 80 elements: blocks of 64
+    "box_q3_hardening": lambda: _hardened(3, 2, 2, 3, 31),
 }
 
 
