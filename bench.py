@@ -198,6 +198,47 @@ def newton_compare(name: str, steps: int = 1, variants=("mixed", "fp64")):
     return out
 
 
+# load steps per Newton-comparison workload beyond the first: the 16^3 Q4
+# tension test runs its 10 load steps; the 48^3 Q3 notched bar (36 M DoF) one
+# step (its 40-step crack-propagation run is a separate, longer measurement).
+NEWTON_STEPS = {"tension_q4": 10, "notched_q3": 1, "compress_q4": 1}
+
+
+def apply_config(name: str, steps: int, warmup: int):
+    """FP64 and FP32 fine-level action on another workload (CUDA events)."""
+    import torch
+    from paper_2607_21150_gb300 import inputs, pff
+    from paper_2607_21150_gb300.session import Session
+    w = make_workload(name, seed=0)
+    m = w.mesh
+    s = Session(w, f32=True)
+    stream = torch.cuda.current_stream()
+    s.residual(torch.from_numpy(w.z.ravel()).cuda())
+    L = s.levels[m.p]
+    x = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, m.ndof)).cuda()
+    y = torch.empty_like(x)
+    x32, y32 = x.float(), torch.empty(m.ndof, dtype=torch.float32, device="cuda")
+    out = {"workload": f"{name}: Q{m.p} {m.nx}x{m.ny}x{m.nz} elements, {m.ndof} DoF"}
+    for label, fn in (("fp64", lambda: pff.pff_jacobian_apply(L, pff.PFF_F64, x, y, stream)),
+                      ("fp32", lambda: pff.pff_jacobian_apply(L, pff.PFF_F32, x32, y32, stream))):
+        for _ in range(warmup):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        out[f"{label}_ms"] = ms
+        out[f"{label}_gdofs"] = m.ndof / (ms / 1e3) / 1e9
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return out
+
+
 def adjoint_timing(steps: int = 10, fd_check: bool = True):
     """Gradient of the reaction-curve misfit (twin-experiment target) for the
     adjoint workload: forward load steps with checkpoints, then the discrete
@@ -288,7 +329,7 @@ def run_native(args):
 
     w = make_workload(args.config, seed=rank)
     m = w.mesh
-    s = Session(w, f32=True, df=True)
+    s = Session(w, levels=(2, 1) if m.p == 4 else (), f32=True, df=True)
     stream = torch.cuda.current_stream()
     z = torch.from_numpy(w.z.ravel()).cuda()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -368,6 +409,21 @@ def run_native(args):
 
     tot_e2e, _, _ = timed(e2e_step, args.steps, 1)
 
+    # p-multigrid level actions on the same quadrature points (Galerkin levels)
+    levels = {}
+    for pl in sorted((p for p in s.levels if p != m.p), reverse=True):
+        nl = 4 * s.nn(pl)
+        Ll = s.levels[pl]
+        xl = torch.from_numpy(np.random.default_rng(2).uniform(-1, 1, nl)).cuda()
+        yl = torch.empty_like(xl)
+        xl32, yl32 = xl.float(), torch.empty(nl, dtype=torch.float32, device="cuda")
+        t64l, _, _ = timed(lambda: pff.pff_jacobian_apply(Ll, pff.PFF_F64, xl, yl, stream), args.steps, args.warmup)
+        t32l, _, _ = timed(lambda: pff.pff_jacobian_apply(Ll, pff.PFF_F32, xl32, yl32, stream), args.steps,
+                           args.warmup)
+        levels[f"Q{pl}"] = {"ndof": nl, "fp64_ms": t64l / args.steps, "fp32_ms": t32l / args.steps,
+                            "fp64_gdofs": nl / (t64l / args.steps / 1e3) / 1e9,
+                            "fp32_gdofs": nl / (t32l / args.steps / 1e3) / 1e9}
+
     # max over ranks
     tmax = torch.tensor([tot64], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -393,8 +449,15 @@ def run_native(args):
     s.close()
     del s
     torch.cuda.empty_cache()
-    newton = (newton_compare(args.newton, args.newton_steps, args.newton_variants.split(","))
-              if args.newton != "none" else None)
+    newton, newton_configs = None, {}
+    for k, name in enumerate([] if args.newton == "none" else args.newton.split(",")):
+        steps = args.newton_steps if k == 0 else NEWTON_STEPS.get(name, 1)
+        res = newton_compare(name, steps, args.newton_variants.split(","))
+        if k == 0:
+            newton = res
+        else:
+            newton_configs[name] = res
+    apply_small = apply_config("tension_q4", args.steps, args.warmup) if args.newton != "none" else None
     adjoint = adjoint_timing(args.adjoint_steps) if args.adjoint_steps > 0 else None
     cpu = oracle_sample()
     line = {
@@ -421,6 +484,9 @@ def run_native(args):
                        "note": "double-float action (FP32-pair arithmetic, FP64 vectors); not the headline"},
         "residual_ms": t_res, "kernel_status": status,
         "newton_step": newton,
+        "newton_configs": newton_configs,
+        "level_applies": levels,
+        "apply_tension_q4": apply_small,
         "adjoint": adjoint,
         "e2e": {"value": world * ndof * args.steps / (tot_e2e / 1e3) / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
@@ -445,9 +511,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default="compress_q4", choices=["compress_q4", "tension_q4"])
-    ap.add_argument("--newton", default="compress_q4", choices=["none", "tension_q4", "compress_q4", "notched_q3"],
-                    help="workload of the FP64-vs-mixed Newton comparison")
-    ap.add_argument("--newton-steps", type=int, default=1)
+    ap.add_argument("--newton", default="compress_q4,tension_q4,notched_q3",
+                    help="comma list of workloads (compress_q4, tension_q4, notched_q3) of the FP64-vs-mixed "
+                         "Newton comparison, the first one reported as newton_step; or none")
+    ap.add_argument("--newton-steps", type=int, default=1, help="load steps of the first --newton workload")
     ap.add_argument("--newton-variants", default="mixed,fp64", help="comma list of mixed, fp64")
     ap.add_argument("--adjoint-steps", type=int, default=10, help="load steps of the adjoint timing (0 = skip)")
     args = ap.parse_args()
