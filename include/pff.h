@@ -259,6 +259,8 @@ typedef struct {
   int outer_prec;       /* fine-level action inside FGMRES: PFF_F64, or PFF_DF64 (pff_op_enable_df) */
   int newton_stall;     /* give up (converged = 0) once ||r|| fell by less than 2x over this many
                            Newton iterations, so that a load-step cut-back starts early; 0 = never */
+  int eig_every;        /* re-estimate the lambda_max bounds every eig_every-th Newton iteration of a
+                           solve (1 = every one); 0 = only on the first (later ones reuse them) */
 } pff_solver_params;
 
 typedef struct {

@@ -206,38 +206,42 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
       }
       const double k01 = mu * af * rho01, k02 = mu * af * rho02, k12 = mu * af * rho12;
       const double cq_s2 = plastic ? cq / s2 : 0.0;  // d a / d(eps_d . d eps_d) = cq / s2 (dq / q = edde / s2)
-      for (int d = 0; d < 10; ++d) {
-        double lh[3][3];
-        double dphi = 0.0;
-        if (d < 9) {
-          const int aa = d / 3, BB = d % 3;
-          for (int p = 0; p < 3; ++p)
-            for (int r = 0; r < 3; ++r) lh[p][r] = N[aa][p] * V[BB][r];
-        } else {
-          for (int p = 0; p < 3; ++p)
-            for (int r = 0; r < 3; ++r) lh[p][r] = 0.0;
-          dphi = 1.0;
-        }
-        const double trl = lh[0][0] + lh[1][1] + lh[2][2];
-        double ded[3], edde = 0.0;
-        for (int p = 0; p < 3; ++p) {
-          ded[p] = lh[p][p] - trl * (1.0 / 3.0);
-          edde += ed[p] * lh[p][p];
-        }
-        double da = dphi * da_dphi;
-        if (plastic) da += cq_s2 * edde;
-        double dh[6];  // principal-frame dtau: 00, 11, 22, 12, 02, 01
-        for (int p = 0; p < 3; ++p) dh[p] = 2.0 * mu * (af * ded[p] + da * ed[p]);
-        dh[3] = k12 * (lh[1][2] * b[2] + b[1] * lh[2][1]);
-        dh[4] = k02 * (lh[0][2] * b[2] + b[0] * lh[2][0]);
-        dh[5] = k01 * (lh[0][1] * b[1] + b[0] * lh[1][0]);
-        for (int v = 0; v < 6; ++v) {
-          double s = 0.0;
-          for (int u = 0; u < 6; ++u) s += dh[u] * E[u][v];
-          dtau[d][v] += s;
-        }
-        dpsi[d] += 2.0 * mu * af * af * edde + 2.0 * mu * af * s2 * da;
+      // The nine F-directions ell = e_a (x) F^-T e_B have ell_hat = n_a v_B^T
+      // (rows of N and V), and every term of the branch tangent is bilinear in
+      // (n_a, v_B): dtau_v(a, B) = (N M_v V^T)[a][B] with the 3x3 coefficient
+      // matrices M_v of the principal-frame map ell_hat -> dh (Box A1, the
+      // divided differences off the diagonal), and dpsi(a, B) = c (N diag(ed) V^T)[a][B].
+      //   dh_q (diagonal) = sum_p ell_pp [2 mu a (delta_qp - 1/3) + 2 mu cq_s2 ed_q ed_p]
+      //   dh_12 = k12 (b_2 ell_12 + b_1 ell_21), dh_02, dh_01 alike.
+      double cdiag[3][3];  // cdiag[q][p]: coefficient of ell_pp in dh_q
+      for (int qq = 0; qq < 3; ++qq)
+        for (int p = 0; p < 3; ++p)
+          cdiag[qq][p] = 2.0 * mu * (af * ((qq == p ? 1.0 : 0.0) - 1.0 / 3.0) + cq_s2 * ed[qq] * ed[p]);
+#pragma unroll 1
+      for (int v = 0; v < 6; ++v) {
+        double M[3][3];
+        for (int p = 0; p < 3; ++p) M[p][p] = cdiag[0][p] * E[0][v] + cdiag[1][p] * E[1][v] + cdiag[2][p] * E[2][v];
+        M[1][2] = k12 * b[2] * E[3][v];
+        M[2][1] = k12 * b[1] * E[3][v];
+        M[0][2] = k02 * b[2] * E[4][v];
+        M[2][0] = k02 * b[0] * E[4][v];
+        M[0][1] = k01 * b[1] * E[5][v];
+        M[1][0] = k01 * b[0] * E[5][v];
+        double T[3][3];  // N M
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) T[r][c] = N[r][0] * M[0][c] + N[r][1] * M[1][c] + N[r][2] * M[2][c];
+        for (int aa = 0; aa < 3; ++aa)
+          for (int BB = 0; BB < 3; ++BB)
+            dtau[3 * aa + BB][v] += T[aa][0] * V[BB][0] + T[aa][1] * V[BB][1] + T[aa][2] * V[BB][2];
+        // phi direction: dh_q = 2 mu da_dphi ed_q
+        dtau[9][v] += 2.0 * mu * da_dphi * (ed[0] * E[0][v] + ed[1] * E[1][v] + ed[2] * E[2][v]);
       }
+      // energy: dpsi = 2 mu a^2 edde + 2 mu a s2 da = 2 mu a (a + cq) edde in the F-directions
+      const double cpsi = 2.0 * mu * af * (af + (plastic ? cq : 0.0));
+      for (int aa = 0; aa < 3; ++aa)
+        for (int BB = 0; BB < 3; ++BB)
+          dpsi[3 * aa + BB] += cpsi * (N[aa][0] * ed[0] * V[BB][0] + N[aa][1] * ed[1] * V[BB][1] + N[aa][2] * ed[2] * V[BB][2]);
+      dpsi[9] += 2.0 * mu * af * s2 * da_dphi;
     }
   }
 

@@ -551,7 +551,10 @@ int coarse_gmres(pff_solver* s, cudaStream_t st) {
   return PFF_OK;
 }
 
-int setup(pff_solver* s, cudaStream_t st) {
+// Diagonals, coarse operators and eigenvalue bounds for the current stored
+// linearisation.  `eig` = false keeps the previous lambda_max estimates (the
+// eig_every option of a Newton solve).
+int setup(pff_solver* s, cudaStream_t st, bool eig = true) {
   const int L = (int)s->lv.size();
   for (int l = 0; l < L; ++l) {
     LevelWork& w = s->lv[l];
@@ -563,7 +566,7 @@ int setup(pff_solver* s, cudaStream_t st) {
     pff_op* op = s->op;
     S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->Ke, s->A, st));
     S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
-    if (s->prm.coarse_solver == 0) S_RC(power_coarse(s, st));
+    if (s->prm.coarse_solver == 0 && eig) S_RC(power_coarse(s, st));
     if (s->prm.coarse_solver == 2) {
       for (size_t l = 1; l < s->hl.size(); ++l) {
         HLevel& f = s->hl[l - 1];
@@ -573,10 +576,11 @@ int setup(pff_solver* s, cudaStream_t st) {
         S_CK(launch_q1_gather(h.mesh, h.Ke, h.mask, h.A, st));
         S_CK(launch_q1_diag(h.mesh, h.A, h.diag, st));
       }
-      for (HLevel& h : s->hl) S_RC(arnoldi_hlevel(s, h, st));
+      if (eig)
+        for (HLevel& h : s->hl) S_RC(arnoldi_hlevel(s, h, st));
     }
   }
-  for (int l = 0; l < L; ++l) {
+  for (int l = 0; l < L && eig; ++l) {
     if (l + 1 == L && s->assembled) continue;
     S_RC(arnoldi_level(s, s->lv[l], st));
   }
@@ -625,6 +629,7 @@ int pff_solver_default_params(pff_solver_params* p) {
   p->verbose = 0;
   p->outer_prec = PFF_F64;
   p->newton_stall = 0;
+  p->eig_every = 1;
   return PFF_OK;
 }
 
@@ -853,7 +858,8 @@ int pff_newton_solve(pff_solver* s, double* z, pff_newton_stats* stats, void* st
     const int k = s->prm.newton_stall;
     if (k > 0 && it >= k && it - k < 64 && rn > 0.5 * stats->res_history[it - k]) break;  // stagnation
     t0 = now();
-    S_RC(setup(s, st));
+    const int ev = s->prm.eig_every;
+    S_RC(setup(s, st, ev > 0 ? (it % ev == 0) : (it == 0)));
     S_CK(cudaStreamSynchronize(st));
     stats->t_setup += now() - t0;
     t0 = now();

@@ -51,7 +51,7 @@ class pff_solver_params(ctypes.Structure):
                 ("krylov_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("line_search_max", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_rtol", ctypes.c_double),
                 ("coarse_maxit", ctypes.c_int), ("verbose", ctypes.c_int), ("outer_prec", ctypes.c_int),
-                ("newton_stall", ctypes.c_int)]
+                ("newton_stall", ctypes.c_int), ("eig_every", ctypes.c_int)]
 
 
 class pff_newton_stats(ctypes.Structure):

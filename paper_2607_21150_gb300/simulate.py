@@ -1,0 +1,55 @@
+"""Load-stepping simulation of a workload: python -m paper_2607_21150_gb300.simulate
+--workload notched_q3 --steps 40 [--fp64] [--max-cuts 6].
+
+Runs LoadStepper.advance for load steps 1..steps (adaptive cut-back) and prints
+one JSON line per load step (reaction on the loaded face, sub-steps, Newton and
+Krylov iterations, wall time), then a summary line."""
+from __future__ import annotations
+
+import argparse
+import json
+import sys
+import time
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="notched_q3",
+                    choices=["notched_q3", "tension_q4", "compress_q4", "adjoint_q2"])
+    ap.add_argument("--n", type=int, default=None, help="elements per direction (workload default if omitted)")
+    ap.add_argument("--steps", type=int, default=None, help="load steps (workload default if omitted)")
+    ap.add_argument("--fp64", action="store_true", help="FP64 multigrid levels instead of FP32")
+    ap.add_argument("--max-cuts", type=int, default=6)
+    args = ap.parse_args(argv)
+    import torch
+    from . import inputs
+    from .driver import LoadStepper, StepFailed
+    make = getattr(inputs, args.workload)
+    w = make() if args.n is None else make(n=args.n)
+    steps = args.steps or int(w.meta.get("steps", 10))
+    t0 = time.perf_counter()
+    lsp = LoadStepper(w, mixed=not args.fp64, max_cuts=args.max_cuts)
+    print(json.dumps({"workload": args.workload, "ndof": w.mesh.ndof, "nq": w.mesh.nq, "steps": steps,
+                      "mixed": not args.fp64, "setup_s": time.perf_counter() - t0}), flush=True)
+    t_all = time.perf_counter()
+    status = "completed"
+    for k in range(1, steps + 1):
+        t1 = time.perf_counter()
+        try:
+            out = lsp.advance(k)
+        except StepFailed as e:
+            status = f"stopped at step {k}: {e}"
+            break
+        torch.cuda.synchronize()
+        print(json.dumps({"step": k, "reaction": out[-1]["reaction"], "sub_steps": len(out),
+                          "newton_iterations": sum(st["newton_iterations"] for st in out),
+                          "krylov_iterations": sum(st["krylov_iterations"] for st in out),
+                          "wall_s": time.perf_counter() - t1}), flush=True)
+    print(json.dumps({"status": status, "wall_s": time.perf_counter() - t_all,
+                      "attempts": len(lsp.history)}), flush=True)
+    lsp.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

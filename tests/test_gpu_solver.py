@@ -140,13 +140,15 @@ def test_fgmres_linear_solve(orc):
     pff.pff_destroy_solver(solver)
 
 
-@pytest.mark.parametrize("mixed,outer", [(0, 0), (1, 0), (1, 2)])
-def test_newton_solution_matches_oracle(orc, mixed, outer):
-    """outer = 2: the FGMRES operator is the double-float action (PFF_DF64)."""
+@pytest.mark.parametrize("mixed,outer,eig_every", [(0, 0, 1), (1, 0, 1), (1, 2, 1), (1, 0, 0)])
+def test_newton_solution_matches_oracle(orc, mixed, outer, eig_every):
+    """outer = 2: the FGMRES operator is the double-float action (PFF_DF64);
+    eig_every = 0: eigenvalue bounds estimated on the first Newton iteration only."""
     w = _box(2, 2, 3, 2, 11, state=False)
     z_ref, hist_ref, _ = orc.newton(w, rtol=1e-13)
     s = Session(w, levels=(1,), f32=bool(mixed), df=(outer == pff.PFF_DF64))
-    solver = s.solver([2, 1], mixed=mixed, newton_rtol=1e-11, krylov_rtol=1e-6, outer_prec=outer)
+    solver = s.solver([2, 1], mixed=mixed, newton_rtol=1e-11, krylov_rtol=1e-6, outer_prec=outer,
+                      eig_every=eig_every)
     z = torch.from_numpy(w.z.ravel().copy()).cuda()
     st = pff.pff_newton_solve(solver, z)
     assert st["converged"] == 1, st
