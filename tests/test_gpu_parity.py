@@ -298,3 +298,35 @@ def test_full_size_tension_q4_sampled_rows(orc):
         err = np.abs(g[dofs] - ref[key]) / np.maximum(np.abs(ref[key]), 1e-300)
         scale = np.abs(ref[key]).max()
         assert np.all(np.abs(g[dofs] - ref[key]) <= 1e-11 * scale + 1e-12 * np.abs(ref[key])), (key, err.max())
+
+
+@pytest.mark.parametrize("name", ["compress_q4", "notched_q3", "adjoint_q2"])
+def test_full_size_workloads_sampled_rows(orc, name):
+    """The bench's workloads at full size and in its launch configuration (fine
+    level of a session with the p-levels, FP32 and double-float copies):
+    64^3 Q4 compression (67.9 M DoF), 48^3 Q3 notched bar (36.4 M DoF), 24^3 Q2
+    adjoint box (0.47 M DoF).  Residual, J x, J^T x, diag(J) and the
+    double-float action at sampled rows against the oracle's element rows at
+    the FP64 bar; the FP32 action at the FP32 rounding level."""
+    import bench
+    w = bench.make_workload(name, seed=0)
+    m = w.mesh
+    s = Session(w, levels=(2, 1) if m.p == 4 else (1,), f32=True, df=True)
+    r = np_(s.residual(w.z))
+    assert s.status() == 0
+    x = inputs.random_vector(m.ndof, 8)
+    xt = torch.from_numpy(x).cuda()
+    out = {"r": r, "jx": np_(s.apply(xt)), "jtx": np_(s.apply(xt, transpose=True)), "diag": np_(s.diag())}
+    jx_df = np_(s.apply(xt, prec=pff.PFF_DF64))
+    jx_32 = np_(s.apply(xt.float(), prec=pff.PFF_F32)).astype(np.float64)
+    s.close()
+    rng = np.random.default_rng(5)
+    dofs = np.sort(rng.choice(m.ndof, 40, replace=False))
+    dofs = np.concatenate([dofs, [0, m.ndof - 1, 3 * m.nn + m.nn // 2, 2 * m.nn + m.nn - 1]])
+    ref = orc.sample_rows(w, dofs, x)
+    for key, g in list(out.items()) + [("jx", jx_df)]:
+        scale = np.abs(ref[key]).max()
+        err = np.abs(g[dofs] - ref[key])
+        assert np.all(err <= 1e-11 * scale + 1e-12 * np.abs(ref[key])), (name, key, (err / scale).max())
+    scale = np.abs(ref["jx"]).max()
+    assert np.all(np.abs(jx_32[dofs] - ref["jx"]) <= 2e-5 * scale), (name, "fp32")
