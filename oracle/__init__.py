@@ -61,21 +61,21 @@ def lib():
         L.orc_logm1p.argtypes = [dp, dp]
         L.orc_expm.argtypes = [dp, dp]
         L.orc_assemble.argtypes = [ip, dp, dp, ctypes.c_int, dp, dp, dp, u8p, u8p, dp,
-                                   ctypes.c_int, dp, dp, u8p, dp]
+                                   ctypes.c_int, dp, dp, u8p, dp, dp]
         L.orc_assemble.restype = ctypes.c_void_p
         L.orc_csr_nnz.argtypes = [ctypes.c_void_p]
         L.orc_csr_nnz.restype = ctypes.c_longlong
         L.orc_csr_get.argtypes = [ctypes.c_void_p, llp, llp, dp]
         L.orc_csr_free.argtypes = [ctypes.c_void_p]
         L.orc_sample_rows.argtypes = [ip, dp, dp, ctypes.c_int, dp, dp, dp, u8p, u8p, dp, dp,
-                                      ctypes.c_int, llp, dp, dp, dp, dp]
+                                      ctypes.c_int, llp, dp, dp, dp, dp, dp]
         L.orc_prolong_coo.argtypes = [ip, ctypes.c_int, ctypes.c_int, llp, llp, dp]
         L.orc_prolong_coo.restype = ctypes.c_longlong
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_csr_spmv.argtypes = [ctypes.c_longlong, llp, llp, dp, dp, dp]
         L.orc_point_partials.argtypes = [ctypes.c_int, dp, dp, u8p, dp, ctypes.c_int, dp, dp, dp]
-        L.orc_qpoint_inputs.argtypes = [ip, dp, dp, dp]
-        L.orc_apply_bt.argtypes = [ip, dp, dp, ctypes.c_int, dp]
+        L.orc_qpoint_inputs.argtypes = [ip, dp, dp, dp, dp]
+        L.orc_apply_bt.argtypes = [ip, dp, dp, ctypes.c_int, dp, dp]
         _lib = L
     return _lib
 
@@ -103,6 +103,13 @@ def phase_rows(phases):
     out[:, :12] = ph
     out[:, 13] = ph[:, 11]
     return out
+
+
+def geometry(w):
+    """Nodal coordinates [3][nn] of a mapped mesh (the workload's ``X``), or None
+    for the affine box of ``w.mesh``."""
+    X = getattr(w, "X", None)
+    return None if X is None else np.ascontiguousarray(X, dtype=np.float64)
 
 
 def _u8(a):
@@ -208,7 +215,8 @@ def assemble(w, z=None, hist=None, matrix: bool = True, mask="workload", dvals="
     handle = L.orc_assemble(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(phase_rows(w.phases)),
                             len(w.phases), _p(_f64(w.glob)), _p(z), _p(hist),
                             _p(_u8(w.phase), ctypes.c_uint8), _p(mask, ctypes.c_uint8), _p(dvals),
-                            1 if matrix else 0, _p(r), _p(hn), _p(flags, ctypes.c_uint8), _p(margins))
+                            1 if matrix else 0, _p(r), _p(hn), _p(flags, ctypes.c_uint8), _p(margins),
+                            _p(geometry(w)))
     out = dict(r=r.reshape(4, m.nn), hist_new=hn, flags=flags, margins=margins)
     if matrix:
         nnz = L.orc_csr_nnz(handle)
@@ -236,7 +244,7 @@ def sample_rows(w, dofs, x, z=None, hist=None):
                           len(w.phases), _p(_f64(w.glob)), _p(z), _p(hist),
                           _p(_u8(w.phase), ctypes.c_uint8), _p(_u8(w.mask), ctypes.c_uint8),
                           _p(None if w.dvals is None else _f64(w.dvals)), _p(x), ns,
-                          _p(dofs, ctypes.c_longlong), _p(r), _p(jx), _p(jtx), _p(dg))
+                          _p(dofs, ctypes.c_longlong), _p(r), _p(jx), _p(jtx), _p(dg), _p(geometry(w)))
     return dict(r=r, jx=jx, jtx=jtx, diag=dg)
 
 
@@ -405,18 +413,19 @@ def point_partials(inputs, hist, phase, phases, glob):
     return vals, J
 
 
-def qpoint_inputs(mesh, y):
+def qpoint_inputs(mesh, y, X=None):
     dims, h = _mesh_args(mesh)
     out = np.zeros((mesh.nq, 14))
-    lib().orc_qpoint_inputs(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(y)), _p(out))
+    lib().orc_qpoint_inputs(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(y)), _p(out),
+                            _p(None if X is None else _f64(X)))
     return out[:, :13], out[:, 13]
 
 
-def apply_bt(mesh, pseudo, weighted):
+def apply_bt(mesh, pseudo, weighted, X=None):
     dims, h = _mesh_args(mesh)
     out = np.zeros(4 * mesh.nn)
     lib().orc_apply_bt(dims.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _p(h), _p(_f64(pseudo)),
-                       1 if weighted else 0, _p(out))
+                       1 if weighted else 0, _p(out), _p(None if X is None else _f64(X)))
     return out
 
 
@@ -465,15 +474,15 @@ def adjoint_gradient(w, theta, nsteps, top, target):
         ww.hist = hprev
         ww.dvals = w.dvals * n
         wF = 2.0 * (F[n - 1] - target[n - 1])
-        a, wq = qpoint_inputs(m, z)
+        a, wq = qpoint_inputs(m, z, geometry(w))
         _, Jp = point_partials(a, hprev.T.copy(), w.phase, ww.phases, w.glob)
         K = assemble(ww, z=z, matrix=True)["K"]
         Kint = assemble(ww, z=z, matrix=True, mask=None, dvals=None)["K"]
         qa = np.einsum("qr,qrc->qc", hbar, Jp[:, 13:28, 0:13])
-        g = wF * (Kint.T @ sel) + apply_bt(m, qa, weighted=False)
+        g = wF * (Kint.T @ sel) + apply_bt(m, qa, weighted=False, X=geometry(w))
         g[mk] = 0.0
         lam = spla.spsolve(K.T.tocsc(), g)
-        pv, _ = qpoint_inputs(m, (wF * sel - lam).reshape(4, -1))
+        pv, _ = qpoint_inputs(m, (wF * sel - lam).reshape(4, -1), geometry(w))
         p = pv * wq[:, None]
         hb_new = np.einsum("qr,qrc->qc", p, Jp[:, 0:13, 13:28]) + np.einsum("qr,qrc->qc", hbar, Jp[:, 13:28, 13:28])
         gq = np.einsum("qr,qrc->qc", p, Jp[:, 0:13, 28:34]) + np.einsum("qr,qrc->qc", hbar, Jp[:, 13:28, 28:34])

@@ -608,6 +608,52 @@ static ElemBasis elem_basis(const Mesh& m) {
   return eb;
 }
 
+// The same for element e of a mapped mesh with nodal coordinates X [3][nn]
+// (isoparametric: X(xi) = sum_a X_a N_a(xi)): J = dX/dxi = sum_a X_a (x) grad_xi N_a,
+// reference gradients grad_X N_a = J^-T grad_xi N_a, weight w_q det J.
+static ElemBasis elem_basis_geo(const Mesh& m, const double* X, long long e) {
+  ElemBasis eb;
+  int P = m.p + 1, Q = m.Q;
+  eb.P3 = P * P * P; eb.Q3 = Q * Q * Q;
+  eb.N.resize(eb.Q3 * eb.P3); eb.dN.resize(eb.Q3 * eb.P3 * 3); eb.wdet.resize(eb.Q3);
+  std::vector<long long> nodes(eb.P3);
+  elem_nodes(m, e, nodes.data());
+  std::vector<double> dxi(eb.P3 * 3);
+  for (int k = 0; k < Q; ++k) for (int j = 0; j < Q; ++j) for (int i = 0; i < Q; ++i) {
+    int q = i + Q * (j + Q * k);
+    double xi[3] = {m.xq[i], m.xq[j], m.xq[k]};
+    double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int c = 0; c < P; ++c) for (int b = 0; b < P; ++b) for (int a = 0; a < P; ++a) {
+      int A = a + P * (b + P * c);
+      double l0 = lagr(m.xg.data(), P, a, xi[0]), l1 = lagr(m.xg.data(), P, b, xi[1]), l2 = lagr(m.xg.data(), P, c, xi[2]);
+      double d0 = dlagr(m.xg.data(), P, a, xi[0]), d1 = dlagr(m.xg.data(), P, b, xi[1]), d2 = dlagr(m.xg.data(), P, c, xi[2]);
+      eb.N[q * eb.P3 + A] = l0 * l1 * l2;
+      dxi[A * 3 + 0] = d0 * l1 * l2;
+      dxi[A * 3 + 1] = l0 * d1 * l2;
+      dxi[A * 3 + 2] = l0 * l1 * d2;
+      for (int d = 0; d < 3; ++d)
+        for (int al = 0; al < 3; ++al) J[d][al] += X[d * m.nn + nodes[A]] * dxi[A * 3 + al];
+    }
+    double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                 J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    double G[3][3];  // G = J^-1 (d xi / dX), by cofactors
+    G[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+    G[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+    G[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+    G[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+    G[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+    G[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+    G[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+    G[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+    G[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+    eb.wdet[q] = m.wq[i] * m.wq[j] * m.wq[k] * det;
+    for (int A = 0; A < eb.P3; ++A)
+      for (int d = 0; d < 3; ++d)
+        eb.dN[(q * eb.P3 + A) * 3 + d] = dxi[A * 3 + 0] * G[0][d] + dxi[A * 3 + 1] * G[1][d] + dxi[A * 3 + 2] * G[2][d];
+  }
+  return eb;
+}
+
 typedef Dual<13> D13;
 
 struct Problem {
@@ -619,15 +665,18 @@ struct Problem {
   const double* hist;     // [15][nq]
   const uint8_t* phase;   // [nq]
   long long nq;
+  const double* X;        // nodal coordinates [3][nn] of a mapped mesh, or null (box)
 };
+static ElemBasis basis_of(const Problem& pr, long long e) {
+  return pr.X ? elem_basis_geo(pr.m, pr.X, e) : pr.eb;
+}
 
 // One element: residual r_e[f*P3+a], optionally the pointwise tangents
 // Dh[q][16][16] (rows: f0 (4), f1 (12); cols: values (4), gradients (12)),
 // trial history and flags.
-static void element_eval(const Problem& pr, long long e, double* re, double* Dh,
+static void element_eval(const Problem& pr, const ElemBasis& eb, long long e, double* re, double* Dh,
                          double* hist_new, uint8_t* flags, double* margins) {
   const Mesh& m = pr.m;
-  const ElemBasis& eb = pr.eb;
   int P3 = eb.P3, Q3 = eb.Q3;
   std::vector<long long> nodes(P3);
   elem_nodes(m, e, nodes.data());
@@ -690,8 +739,7 @@ static void element_eval(const Problem& pr, long long e, double* re, double* Dh,
 
 // Element matrix K_e[(f,a),(g,b)] = sum_q w_q det J  B_q^T Dh_q B_q, where
 // row r of B_q is a value (N_a) or a reference gradient component (dN_a/dX_A).
-static void element_matrix(const Problem& pr, const double* Dh, double* Ke) {
-  const ElemBasis& eb = pr.eb;
+static void element_matrix(const ElemBasis& eb, const double* Dh, double* Ke) {
   int P3 = eb.P3, Q3 = eb.Q3, n = 4 * P3;
   for (int i = 0; i < n * n; ++i) Ke[i] = 0.0;
   std::vector<double> Bv(16 * P3);  // Bv[r*P3+a] for rows r of one field pattern
@@ -721,8 +769,10 @@ static void element_matrix(const Problem& pr, const double* Dh, double* Ke) {
 }
 
 static Problem make_problem(const int* dims, const double* h, const double* phase_params, int nphase,
-                            const double* glob, const double* z, const double* hist, const uint8_t* phase) {
+                            const double* glob, const double* z, const double* hist, const uint8_t* phase,
+                            const double* X) {
   Problem pr;
+  pr.X = X;
   pr.m = make_mesh(dims, h);
   pr.eb = elem_basis(pr.m);
   for (int i = 0; i < nphase; ++i) pr.phases.push_back(read_phase(phase_params + kPhaseWords * i));
@@ -845,8 +895,8 @@ int orc_expm(const double* A, double* E) {
 void* orc_assemble(const int* dims, const double* h, const double* phase_params, int nphase,
                    const double* glob, const double* z, const double* hist, const uint8_t* phase,
                    const uint8_t* mask, const double* dvals, int want_matrix,
-                   double* r, double* hist_new, uint8_t* flags, double* margins) {
-  Problem pr = make_problem(dims, h, phase_params, nphase, glob, z, hist, phase);
+                   double* r, double* hist_new, uint8_t* flags, double* margins, const double* X) {
+  Problem pr = make_problem(dims, h, phase_params, nphase, glob, z, hist, phase, X);
   const Mesh& m = pr.m;
   int P3 = pr.eb.P3, Q3 = pr.eb.Q3, ne = 4 * P3;
   long long nel = (long long)m.nx * m.ny * m.nz;
@@ -898,9 +948,10 @@ void* orc_assemble(const int* dims, const double* h, const double* phase_params,
     if (want_matrix) { Dhb.assign(nc * Q3 * 256, 0.0); Keb.assign(nc * (size_t)ne * ne, 0.0); }
 #pragma omp parallel for schedule(dynamic, 1)
     for (long long c = 0; c < nc; ++c) {
-      element_eval(pr, e0 + c, &reb[c * ne], want_matrix ? &Dhb[c * Q3 * 256] : nullptr,
+      const ElemBasis eb = basis_of(pr, e0 + c);
+      element_eval(pr, eb, e0 + c, &reb[c * ne], want_matrix ? &Dhb[c * Q3 * 256] : nullptr,
                    &hnb[c * 15 * Q3], &flb[c * Q3], &mgb[c * Q3 * 3]);
-      if (want_matrix) element_matrix(pr, &Dhb[c * Q3 * 256], &Keb[c * (size_t)ne * ne]);
+      if (want_matrix) element_matrix(eb, &Dhb[c * Q3 * 256], &Keb[c * (size_t)ne * ne]);
     }
     std::vector<long long> nodes(P3);
     for (long long c = 0; c < nc; ++c) {
@@ -955,8 +1006,9 @@ void orc_csr_free(void* h) { delete (CSR*)h; }
 int orc_sample_rows(const int* dims, const double* h, const double* phase_params, int nphase,
                     const double* glob, const double* z, const double* hist, const uint8_t* phase,
                     const uint8_t* mask, const double* dvals, const double* x,
-                    int ns, const long long* dofs, double* r_out, double* jx_out, double* jtx_out, double* diag_out) {
-  Problem pr = make_problem(dims, h, phase_params, nphase, glob, z, hist, phase);
+                    int ns, const long long* dofs, double* r_out, double* jx_out, double* jtx_out, double* diag_out,
+                    const double* X) {
+  Problem pr = make_problem(dims, h, phase_params, nphase, glob, z, hist, phase, X);
   const Mesh& m = pr.m;
   int P3 = pr.eb.P3, Q3 = pr.eb.Q3, ne = 4 * P3;
   // collect the elements needed
@@ -982,8 +1034,9 @@ int orc_sample_rows(const int* dims, const double* h, const double* phase_params
   for (long long t = 0; t < (long long)need.size(); ++t) {
     std::vector<double> Dh(Q3 * 256), hn(15 * Q3), mg(3 * Q3);
     std::vector<uint8_t> fl(Q3);
-    element_eval(pr, need[t], &re_all[t * ne], Dh.data(), hn.data(), fl.data(), mg.data());
-    element_matrix(pr, Dh.data(), &Ke_all[t * (size_t)ne * ne]);
+    const ElemBasis eb = basis_of(pr, need[t]);
+    element_eval(pr, eb, need[t], &re_all[t * ne], Dh.data(), hn.data(), fl.data(), mg.data());
+    element_matrix(eb, Dh.data(), &Ke_all[t * (size_t)ne * ne]);
   }
   std::vector<long long> nodes(P3);
   for (int s = 0; s < ns; ++s) {
@@ -1099,13 +1152,14 @@ int orc_point_partials(int n, const double* inputs, const double* hist, const ui
 
 // Interpolation of a nodal field y [4][nn] to every quadrature point:
 // out[nq][14] = (grad_X y_u (9), y_phi, grad_X y_phi (3), w_q det J).
-int orc_qpoint_inputs(const int* dims, const double* h, const double* y, double* out) {
+int orc_qpoint_inputs(const int* dims, const double* h, const double* y, double* out, const double* X) {
   Mesh m = make_mesh(dims, h);
-  ElemBasis eb = elem_basis(m);
+  const ElemBasis ebox = elem_basis(m);
   long long nel = (long long)m.nx * m.ny * m.nz;
-  int P3 = eb.P3, Q3 = eb.Q3;
+  int P3 = ebox.P3, Q3 = ebox.Q3;
 #pragma omp parallel for schedule(static)
   for (long long e = 0; e < nel; ++e) {
+    const ElemBasis eb = X ? elem_basis_geo(m, X, e) : ebox;
     std::vector<long long> nodes(P3);
     elem_nodes(m, e, nodes.data());
     for (int q = 0; q < Q3; ++q) {
@@ -1125,14 +1179,16 @@ int orc_qpoint_inputs(const int* dims, const double* h, const double* y, double*
 
 // out [4][nn] = sum_q B_q^T pseudo_q (optionally times w_q det J): the
 // transpose of orc_qpoint_inputs, with pseudo[nq][13] in the same layout.
-int orc_apply_bt(const int* dims, const double* h, const double* pseudo, int weighted, double* out) {
+int orc_apply_bt(const int* dims, const double* h, const double* pseudo, int weighted, double* out,
+                 const double* X) {
   Mesh m = make_mesh(dims, h);
-  ElemBasis eb = elem_basis(m);
+  const ElemBasis ebox = elem_basis(m);
   long long nel = (long long)m.nx * m.ny * m.nz;
-  int P3 = eb.P3, Q3 = eb.Q3;
+  int P3 = ebox.P3, Q3 = ebox.Q3;
   for (long long i = 0; i < 4 * m.nn; ++i) out[i] = 0.0;
   std::vector<long long> nodes(P3);
   for (long long e = 0; e < nel; ++e) {
+    const ElemBasis eb = X ? elem_basis_geo(m, X, e) : ebox;
     elem_nodes(m, e, nodes.data());
     for (int q = 0; q < Q3; ++q) {
       const double* p = pseudo + 13 * (size_t)(e * Q3 + q);

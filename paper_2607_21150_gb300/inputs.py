@@ -174,6 +174,51 @@ def node_coords(m: Mesh) -> np.ndarray:
                      Z.transpose(2, 1, 0).ravel()], axis=1)
 
 
+def mapped_coords(m: Mesh, kind: str = "smooth", amp: float = 0.1, seed: int = 0, M=None) -> np.ndarray:
+    """Nodal coordinates [3][nn] of a mapped mesh on the box of ``m``:
+
+    * ``affine``: X' = M X (M given, det M > 0);
+    * ``vertices``: every element vertex moved by U[-amp, amp] h per direction
+      (seeded), the element's GLL nodes placed by trilinear interpolation of
+      its eight vertices (straight-edged hexahedra, conforming faces);
+    * ``smooth``: X'_d = X_d + amp h_d sin(2 pi X_{d+1} / L_{d+1}) sin(pi X_{d+2} / L_{d+2}),
+      evaluated at every node (curved elements)."""
+    X = node_coords(m)
+    if kind == "affine":
+        return np.ascontiguousarray((X @ np.asarray(M, dtype=float).T).T)
+    h = np.array(m.h)
+    L = np.array(m.L)
+    if kind == "smooth":
+        Y = X.copy()
+        for d in range(3):
+            d1, d2 = (d + 1) % 3, (d + 2) % 3
+            Y[:, d] += amp * h[d] * np.sin(2 * np.pi * X[:, d1] / L[d1]) * np.sin(np.pi * X[:, d2] / L[d2])
+        return np.ascontiguousarray(Y.T)
+    if kind != "vertices":
+        raise ValueError(kind)
+    rng = np.random.default_rng(seed)
+    V = np.stack(np.meshgrid(np.arange(m.nx + 1) * h[0], np.arange(m.ny + 1) * h[1], np.arange(m.nz + 1) * h[2],
+                             indexing="ij"), -1)
+    V = V + rng.uniform(-amp, amp, V.shape) * h
+    g = (gll_points(m.p) + 1.0) * 0.5
+    out = np.zeros((3, m.nn))
+    for ez in range(m.nz):
+        for ey in range(m.ny):
+            for ex in range(m.nx):
+                for c in range(m.p + 1):
+                    for b in range(m.p + 1):
+                        for a in range(m.p + 1):
+                            t = (g[a], g[b], g[c])
+                            x = np.zeros(3)
+                            for k in range(8):
+                                i, j, l = k & 1, (k >> 1) & 1, k >> 2
+                                wgt = (t[0] if i else 1 - t[0]) * (t[1] if j else 1 - t[1]) * (t[2] if l else 1 - t[2])
+                                x += wgt * V[ex + i, ey + j, ez + l]
+                            n = (m.p * ex + a) + m.nnx * ((m.p * ey + b) + m.nny * (m.p * ez + c))
+                            out[:, n] = x
+    return out
+
+
 def qpoint_coords(m: Mesh) -> np.ndarray:
     """Reference coordinates of every Gauss point, shape [nq, 3] (q = e Q^3 + i + Q (j + Q k))."""
     g = gauss_points(m.Q)
@@ -416,6 +461,7 @@ class Workload:
     mask: np.ndarray | None = None
     dvals: np.ndarray | None = None
     meta: dict = field(default_factory=dict)
+    X: np.ndarray | None = None   # nodal coordinates [3][nn] of a mapped mesh (None: the box of `mesh`)
 
 
 def cube(nx: int = 4, p: int = 2, seed_state: int = 0, hist_seed: int | None = None,
