@@ -158,6 +158,17 @@ int pff_set_qpoint_state(pff_op* op, const uint8_t* phase, const double* hist_co
  * [4][N_n] (device, copied; values may be NULL = zero; mask NULL = none). */
 int pff_set_dirichlet(pff_op* op, const uint8_t* mask, const double* values, void* stream);
 
+/* Mapped mesh (curved or distorted hexahedra on the same logical grid and
+ * restriction): X = nodal coordinates [3][N_n] (device, FP64, read once) of
+ * the isoparametric element maps X(xi) = sum_a X_a N_a(xi).  Stores d xi / dX
+ * and w_q det J at every Gauss point (10 FP64 words per point); from then on
+ * the residual, the stored linearisation (all words in the parent frame, plus
+ * three off-diagonal phase-gradient words) and every level operator use them.
+ * X = NULL returns to the affine box of the restriction.  Fails with
+ * PFF_ERR_INVALID (and keeps the box) if det J <= 0 at some Gauss point.
+ * Synchronises the stream. */
+int pff_op_set_geometry(pff_op* op, const double* X, void* stream);
+
 /* Residual R(z) (Eq. matrix-free-residual-compact), FP64: r = internal
  * residual on free DoFs, r = z - ubar on Dirichlet DoFs.  Also writes the
  * trial history (Box 1 step 4), the flags, and the stored linearisation used

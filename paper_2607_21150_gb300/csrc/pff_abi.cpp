@@ -136,6 +136,7 @@ ElemArgs<T> level_args(const pff_level* L) {
   a.Dt = tabDt<T>(L->tab);
   a.lin = linOf<T>(L->op);
   a.nq = L->op->nq;
+  a.kx = L->op->geo != nullptr;
   for (int d = 0; d < 3; ++d) a.s[d] = L->op->geom.s[d];
   return a;
 }
@@ -171,6 +172,7 @@ int apply_df(pff_level* L, const double* x, double* y, int transpose, cudaStream
   a.Dc = L->tab.Dc64;
   a.Dt = L->tab.Dt64;
   a.nq = op->nq;
+  a.kx = op->geo != nullptr;
   a.x = x;
   a.y = y;
   const long long stride = stride_of(op->Q);
@@ -440,7 +442,7 @@ int pff_destroy_operator(pff_op* op) {
   cudaFree(op->hist_c); cudaFree(op->hist_t); cudaFree(op->phase); cudaFree(op->flags);
   cudaFree(op->lin64); cudaFree(op->lin32); cudaFree(op->io); cudaFree(op->mask);
   cudaFree(op->dvals); cudaFree(op->status);
-  cudaFree(op->fint); cudaFree(op->sums);
+  cudaFree(op->fint); cudaFree(op->sums); cudaFree(op->geo);
   free_tables(op->tab);
   delete op;
   return PFF_OK;
@@ -507,6 +509,49 @@ int pff_set_dirichlet(pff_op* op, const uint8_t* mask, const double* values, voi
   return PFF_OK;
 }
 
+int pff_op_set_geometry(pff_op* op, const double* X, void* stream) {
+  PFF_REQUIRE(op, "pff_op_set_geometry: null operator");
+  cudaStream_t st = S(stream);
+  if (!X) {
+    PFF_CK(cudaStreamSynchronize(st));
+    cudaFree(op->geo);
+    op->geo = nullptr;
+    return PFF_OK;
+  }
+  const long long nn = op->mesh.nn, nq = op->nq;
+  if (!op->geo) PFF_CK(cudaMalloc((void**)&op->geo, sizeof(double) * 10 * nq));
+  // parent Jacobians dX_f / dxi_al at every Gauss point: an eval of the
+  // coordinates (fourth field zero) with unit parent-to-reference factors
+  double* xc = nullptr;
+  PFF_CK(cudaMalloc((void**)&xc, sizeof(double) * 4 * nn));
+  cudaError_t e = cudaMemcpyAsync(xc, X, sizeof(double) * 3 * nn, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(xc + 3 * nn, 0, sizeof(double) * nn, st);
+  ElemArgs<double> a;
+  std::memset(&a, 0, sizeof(a));
+  a.mesh = op->mesh;
+  a.x = xc;
+  a.B = op->tab.B64;
+  a.Dc = op->tab.Dc64;
+  a.Dt = op->tab.Dt64;
+  a.scratch = op->io;
+  a.nq = nq;
+  for (int d = 0; d < 3; ++d) a.s[d] = 1.0;
+  if (e == cudaSuccess) e = elem_dispatch<double>(op->Q, op->p + 1, kEval, a, st);
+  if (e == cudaSuccess) e = launch_geometry(op->io, op->geo, op->geom, op->Q, nq, op->status, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(xc);
+  if (e != cudaSuccess) return fail(PFF_ERR_CUDA, std::string("pff_op_set_geometry: ") + cudaGetErrorString(e));
+  int h = 0;
+  PFF_CK(cudaMemcpy(&h, op->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h & 2) {
+    PFF_CK(cudaMemset(op->status, 0, sizeof(int)));
+    cudaFree(op->geo);
+    op->geo = nullptr;
+    return fail(PFF_ERR_INVALID, "pff_op_set_geometry: det J <= 0 at some Gauss point (inverted element)");
+  }
+  return PFF_OK;
+}
+
 int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   PFF_REQUIRE(op && z && r, "pff_residual: null argument");
   cudaStream_t st = S(stream);
@@ -522,6 +567,7 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   a.Dt = op->tab.Dt64;
   a.scratch = op->io;
   a.nq = op->nq;
+  a.geo = op->geo;
   for (int d = 0; d < 3; ++d) a.s[d] = op->geom.s[d];
   PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kEval, a, st));
   PointArgs pa;
@@ -540,6 +586,7 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   pa.flags = op->flags;
   pa.lin = op->lin64;
   pa.status = op->status;
+  pa.geo = op->geo;
   pa.want_tangent = 1;
   PFF_CK(launch_pointwise(pa, st));
   a.y = r;

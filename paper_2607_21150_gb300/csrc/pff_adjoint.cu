@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(128) k_adjoint_point(const AdjArgs a) {
     const int Q = a.Q, Q2 = Q * Q, Q3 = Q2 * Q;
     const int lq = (int)(q % Q3);
     const int qi = lq % Q, qj = (lq / Q) % Q, qk = lq / Q2;
-    const double wdet = a.geom.wq[qi] * a.geom.wq[qj] * a.geom.wq[qk] * a.geom.detJ;
+    const double wdet = a.geo ? a.geo[9 * nq + q] : a.geom.wq[qi] * a.geom.wq[qj] * a.geom.wq[qk] * a.geom.detJ;
+    double hvs[9];  // mapped mesh, mode 0: reference-frame components, transformed after the loop
     int pid = a.phase_id[q];
     int status = 0;
     if (pid >= a.nphase) { status |= 8; pid = 0; }
@@ -362,8 +363,12 @@ __global__ void __launch_bounds__(128) k_adjoint_point(const AdjArgs a) {
       for (int v = 0; v < 15; ++v) hv += hb[v] * dPhi[v];
       if (a.mode == 0) {
         // parent-frame pseudo-integrand for the transposed basis (no weight)
-        const double val = (d < 9) ? hv * a.geom.s[d % 3] : hv;
-        a.qa_out[d * nq + q] = val;
+        if (a.geo && d < 9) {
+          hvs[d] = hv;
+        } else {
+          const double val = (d < 9) ? hv * a.geom.s[d % 3] : hv;
+          a.qa_out[d * nq + q] = val;
+        }
       } else {
         double pv = 0.0;
         for (int m = 0; m < 13; ++m) pv += pw[m] * df[m];
@@ -371,6 +376,12 @@ __global__ void __launch_bounds__(128) k_adjoint_point(const AdjArgs a) {
         else atomicAdd(&red[pid * 6 + (d - 15)], pv + hv);
       }
     }
+    if (a.mode == 0 && a.geo)  // parent component al of field f: sum_A (d xi_al / dX_A) hv_(f, A)
+      for (int f = 0; f < 3; ++f)
+        for (int al = 0; al < 3; ++al)
+          a.qa_out[(3 * f + al) * nq + q] = a.geo[(3 * al) * nq + q] * hvs[3 * f] +
+                                            a.geo[(3 * al + 1) * nq + q] * hvs[3 * f + 1] +
+                                            a.geo[(3 * al + 2) * nq + q] * hvs[3 * f + 2];
     if (a.mode == 0)
       for (int m = 10; m < 13; ++m) a.qa_out[m * nq + q] = 0.0;
     if (status) atomicOr(a.status, status);

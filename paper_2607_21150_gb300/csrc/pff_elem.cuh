@@ -229,7 +229,7 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
 template <typename T>
 __device__ __forceinline__ void jac_point(const typename ElemTypes<T>::L* lin, const typename ElemTypes<T>::L* linP,
                                           const typename ElemTypes<T>::L* linC, long long stride, long long lo,
-                                          const T g[4][3], T phi, T o[4][3], T& o0) {
+                                          int kx, const T g[4][3], T phi, T o[4][3], T& o0) {
   T gu[9];
 #pragma unroll
   for (int f = 0; f < 3; ++f)
@@ -258,6 +258,14 @@ __device__ __forceinline__ void jac_point(const typename ElemTypes<T>::L* lin, c
     for (int al = 0; al < 3; ++al) o[f][al] = ou[3 * f + al];
 #pragma unroll
   for (int al = 0; al < 3; ++al) o[3][al] = mul(ld_lin<T>(lin + (kWK + al) * stride, lo), g[3][al]);
+  if (kx) {  // mapped mesh: symmetric off-diagonal coefficients 01, 02, 12
+    const T k01 = ld_lin<T>(lin + (kWKX + 0) * stride, lo);
+    const T k02 = ld_lin<T>(lin + (kWKX + 1) * stride, lo);
+    const T k12 = ld_lin<T>(lin + (kWKX + 2) * stride, lo);
+    o[3][0] = madd(madd(o[3][0], k01, g[3][1]), k02, g[3][2]);
+    o[3][1] = madd(madd(o[3][1], k01, g[3][0]), k12, g[3][2]);
+    o[3][2] = madd(madd(o[3][2], k02, g[3][0]), k12, g[3][1]);
+  }
 }
 
 // L2 prefetch of slice k of this block's stored linearisation (FP32 action):
@@ -335,13 +343,28 @@ k_elem(const ElemArgs<T> a) {
         T g[4][3], phi;
         grad_at<P, Q, T>(s, i, j, k, g, phi);
         long long q = (long long)e * Q3 + k * Q2 + j * Q + i;
+        if (a.geo) {  // mapped mesh: reference gradient = parent gradient x d xi / dX
+          double G[3][3];
 #pragma unroll
-        for (int f = 0; f < 3; ++f)
+          for (int al = 0; al < 3; ++al)
 #pragma unroll
-          for (int al = 0; al < 3; ++al) a.scratch[(3 * f + al) * a.nq + q] = (double)g[f][al] * a.s[al];
+            for (int A = 0; A < 3; ++A) G[al][A] = a.geo[(3 * al + A) * a.nq + q];
+#pragma unroll
+          for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int A = 0; A < 3; ++A) {
+              const double v = (double)g[f][0] * G[0][A] + (double)g[f][1] * G[1][A] + (double)g[f][2] * G[2][A];
+              a.scratch[((f < 3) ? 3 * f + A : 10 + A) * a.nq + q] = v;
+            }
+        } else {
+#pragma unroll
+          for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int al = 0; al < 3; ++al) a.scratch[(3 * f + al) * a.nq + q] = (double)g[f][al] * a.s[al];
+#pragma unroll
+          for (int al = 0; al < 3; ++al) a.scratch[(10 + al) * a.nq + q] = (double)g[3][al] * a.s[al];
+        }
         a.scratch[9 * a.nq + q] = (double)phi;
-#pragma unroll
-        for (int al = 0; al < 3; ++al) a.scratch[(10 + al) * a.nq + q] = (double)g[3][al] * a.s[al];
       }
     }
     return;
@@ -367,7 +390,7 @@ k_elem(const ElemArgs<T> a) {
       grad_at<P, Q, T>(s, i, j, k, g, phi);
       if (valid) {
         long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
-        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, g, phi, o, o0);
+        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, a.kx, g, phi, o, o0);
       } else {
 #pragma unroll
         for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();
@@ -408,7 +431,7 @@ k_elem(const ElemArgs<T> a) {
       grad_at<P, Q, T>(s, i, j, k, g, phi);
       if (valid) {
         long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
-        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, g, phi, o, o0);
+        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, a.kx, g, phi, o, o0);
       } else {
 #pragma unroll
         for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();
@@ -489,8 +512,9 @@ k_diag(const ElemArgs<T> a) {
   const long long stride = (long long)Q3 * EB;
   // term list: (field, word, dim-kinds mask, weight)
   // u fields: pairs alpha <= beta; phase field: value term and 3 gradient terms
+  const int nterms = a.kx ? 25 : 22;
 #pragma unroll 1
-  for (int term = 0; term < 22; ++term) {
+  for (int term = 0; term < nterms; ++term) {
     int f, word, kx, ky, kz;
     T wgt = T(1);
     if (term < 18) {
@@ -508,10 +532,16 @@ k_diag(const ElemArgs<T> a) {
     } else {
       f = 3;
       if (term == 18) { word = kWD; kx = ky = kz = 0; }
-      else {
+      else if (term < 22) {
         int al = term - 19;
         word = kWK + al;
         kx = (al == 0) ? 2 : 0; ky = (al == 1) ? 2 : 0; kz = (al == 2) ? 2 : 0;
+      } else {  // off-diagonal phase-gradient pair (al, be): 2 K_al,be d_al N d_be N
+        const int pr = term - 22;               // 01, 02, 12
+        const int al = (pr == 2) ? 1 : 0, be = (pr == 0) ? 1 : 2;
+        word = kWKX + pr;
+        wgt = T(2);
+        kx = (al == 0) + (be == 0); ky = (al == 1) + (be == 1); kz = (al == 2) + (be == 2);
       }
     }
     const T* Mx = M + kx * Q * P;

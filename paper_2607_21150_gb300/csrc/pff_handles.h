@@ -56,6 +56,7 @@ struct pff_op {
   int f32 = 0;
   int df = 0;                 // maintain the double-float planes of the stored linearisation
   int lin32_planes = 0;       // FP32 planes allocated at lin32 (0, 1 or 2)
+  double* geo = nullptr;      // mapped mesh: [10][nq] d xi / dX and w det J (null: the affine box)
   double* fint = nullptr;     // internal force work vector of pff_reaction (allocated on first use)
   double* sums = nullptr;     // 4 doubles
 };

@@ -7,11 +7,14 @@ namespace pff {
 
 constexpr int kMaxPhase = 8;
 constexpr int kMaxQ = 5;          // quadrature points per direction (Q <= p_fine + 1 <= 5)
-constexpr int kLinWords = 67;     // stored pointwise linearisation words per quadrature point
+constexpr int kLinWords = 70;     // stored pointwise linearisation words per quadrature point
 // word layout: [0,45) upper triangle of the 9x9 block dP/dF (row-major, m <= n,
 // m = 3 i + A), [45,54) dP/dphi, [54,63) d(s_phi L)/dF, [63] d(s_phi L)/dphi,
-// [64,67) diagonal coefficients of the phase-gradient term.
-constexpr int kWA = 0, kWP = 45, kWC = 54, kWD = 63, kWK = 64;
+// [64,67) diagonal coefficients of the phase-gradient term, [67,70) its
+// off-diagonal coefficients (01, 02, 12), non-zero on mapped meshes only.
+// All words are in the parent frame (w_q det J and d xi / dX folded in).
+constexpr int kWA = 0, kWP = 45, kWC = 54, kWD = 63, kWK = 64, kWKX = 67;
+constexpr int kLinWordsExport = 67;  // words returned by pff_get_linearization
 
 // Elements handled by one thread block of the element kernels: Q*Q threads per element.
 __host__ __device__ constexpr int elems_per_block(int Q) { return 256 / (Q * Q); }
@@ -70,6 +73,7 @@ struct PointArgs {
   const uint8_t* phase_id;// [nq]
   uint8_t* flags;         // [nq]
   double* lin;            // tiled stored linearisation (FP64)
+  const double* geo;      // mapped mesh: [10][nq] d xi_alpha / dX_A (word 3 alpha + A), w det J; null = box
   int* status;            // device status word (bit0 eigen sweeps, bit1 J <= 0, bit2 non-finite, bit3 phase id)
   int want_tangent;
 };
@@ -92,6 +96,7 @@ struct AdjArgs {
   double* qa_out;         // mode 0
   double* hbar_out;       // mode 1
   double* gtheta;         // mode 1, [nphase][6]
+  const double* geo;      // mapped mesh: [10][nq] d xi / dX and w det J; null = box
   int* status;
 };
 cudaError_t launch_adjoint_point(const AdjArgs& a, cudaStream_t st);
@@ -129,9 +134,11 @@ struct ElemArgs {
   const L* linP;          // words multiplying dphi in the u rows (dP/dphi or, transposed, dL/dF)
   const L* linC;          // words multiplying grad u in the phi row
   double* scratch;        // [13][nq] (eval / back)
-  double s[3];            // d xi / d X (eval)
+  double s[3];            // d xi / d X (eval, box)
+  const double* geo;      // mapped mesh (eval): [10][nq] d xi / dX per point; null = box
   long long nq;
   int transpose;
+  int kx;                 // 1: add the off-diagonal phase-gradient words (mapped meshes)
   long long lo;           // df64: offset (in words) from the hi plane to the lo plane
 };
 
@@ -146,6 +153,11 @@ PFF_DECLARE_ELEM_Q(4)
 PFF_DECLARE_ELEM_Q(5)
 
 cudaError_t launch_pointwise(const PointArgs& a, cudaStream_t st);
+// geo[10][nq] from the parent Jacobians J[3f + al][nq] (= d X_f / d xi_al, the
+// first nine rows of an eval): d xi / dX = J^-1 and w_q det J; status bit 2
+// where det J <= 0.
+cudaError_t launch_geometry(const double* J, double* geo, const Geom& g, int Q, long long nq, int* status,
+                            cudaStream_t st);
 
 // Vector / transfer kernels (pff_vec.cu)
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
@@ -191,7 +203,7 @@ cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaSt
 // Sum-factorised element matrices (Ke: [nel][32][32] work space) and a
 // deterministic gather into the stencil storage.
 cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
-                                  const uint8_t* maskc, double* Ke, double* A, cudaStream_t st);
+                                  const uint8_t* maskc, double* Ke, double* A, int kx, cudaStream_t st);
 cudaError_t launch_q1_spmv_t(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
 // Geometric h-hierarchy on the order-1 grid (full coarsening, trilinear
 // transfers): Galerkin element matrices of the coarse grid, their gather into

@@ -251,7 +251,7 @@ cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaSt
 //   sum_{ijk} D(i,j,k) X0[i][a0 b0] X1[j][a1 b1] X2[k][a2 b2],
 // Xd[q][a b] = F_r,d[q][a] F_c,d[q][b], F = B1 or its derivative D1,
 // contracted one direction at a time.  Output: Ke[e][32][32].
-constexpr int kQ1Combos = 67;
+constexpr int kQ1Combos = 70;  // 67 on the affine box (no off-diagonal phase-gradient words)
 constexpr int kQ1Threads = 256;
 
 __device__ __forceinline__ void q1_combo(int c, int& word, int& rk, int& ck) {
@@ -271,9 +271,12 @@ __device__ __forceinline__ void q1_combo(int c, int& word, int& rk, int& ck) {
     word = kWC + n; rk = 0; ck = 1 + n % 3;
   } else if (c == 63) {
     word = kWD; rk = 0; ck = 0;
-  } else {
+  } else if (c < 67) {
     const int al = c - 64;
     word = kWK + al; rk = 1 + al; ck = 1 + al;
+  } else {  // off-diagonal phase-gradient pairs 01, 02, 12 (mapped meshes)
+    const int pr = c - 67;
+    word = kWKX + pr; rk = 1 + ((pr == 2) ? 1 : 0); ck = 1 + ((pr == 0) ? 1 : 2);
   }
 }
 
@@ -284,8 +287,8 @@ __device__ __forceinline__ void q1_combo(int c, int& word, int& rk, int& ck) {
 // block then sums the combinations of each (f, g) block of Ke.
 template <int Q>
 __global__ void __launch_bounds__(kQ1Threads)
-k_q1_elem(int nel, const double* __restrict__ lin, const double* __restrict__ B1, const double* __restrict__ D1,
-          double* __restrict__ Ke) {
+k_q1_elem(int nel, int ncombo, const double* __restrict__ lin, const double* __restrict__ B1,
+          const double* __restrict__ D1, double* __restrict__ Ke) {
   constexpr int Q2 = Q * Q, Q3 = Q2 * Q;
   constexpr int EB = elems_per_block(Q);
   constexpr int kWarps = kQ1Threads / 32;
@@ -304,14 +307,14 @@ k_q1_elem(int nel, const double* __restrict__ lin, const double* __restrict__ B1
     const double Fb = fb ? D1[i * 2 + b] : B1[i * 2 + b];
     X[idx] = Fa * Fb;
   }
-  for (int c = t; c < kQ1Combos; c += kQ1Threads) q1_combo(c, ctab[3 * c], ctab[3 * c + 1], ctab[3 * c + 2]);
+  for (int c = t; c < ncombo; c += kQ1Threads) q1_combo(c, ctab[3 * c], ctab[3 * c + 1], ctab[3 * c + 2]);
   __syncthreads();
   const long long stride = (long long)Q3 * EB;
   const long long base = (long long)(e / EB) * kLinWords * stride + (e % EB) * Q2;
   double* D = W + warp * kScratch;
   double* T1 = D + Q3;
   double* T2 = T1 + 4 * Q2;
-  for (int c = warp; c < kQ1Combos; c += kWarps) {
+  for (int c = warp; c < ncombo; c += kWarps) {
     const int word = ctab[3 * c], rk = ctab[3 * c + 1], ck = ctab[3 * c + 2];
     for (int q = lane; q < Q3; q += 32) {
       const int k = q / Q2, jq = q % Q2;
@@ -375,6 +378,7 @@ k_q1_elem(int nel, const double* __restrict__ lin, const double* __restrict__ B1
       for (int be = 0; be < 3; ++be) v += R[(54 + 3 * g + be) * 64 + a * 8 + b];
     } else {
       for (int c = 63; c < 67; ++c) v += R[c * 64 + a * 8 + b];
+      for (int c = 67; c < ncombo; ++c) v += R[c * 64 + a * 8 + b] + R[c * 64 + b * 8 + a];
     }
     out[idx] = v;
   }
@@ -577,18 +581,18 @@ cudaError_t launch_hrestrict(const MeshDev& mc, const MeshDev& mf, const double*
 }
 
 cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
-                                  const uint8_t* maskc, double* Ke, double* A, cudaStream_t st) {
+                                  const uint8_t* maskc, double* Ke, double* A, int kx, cudaStream_t st) {
   const size_t smem = sizeof(double) * (size_t)(kQ1Combos * 64 + 16 * Q + (kQ1Threads / 32) * (Q * Q * Q + 4 * Q * Q + 16 * Q)) +
                       sizeof(int) * 3 * kQ1Combos;
   switch (Q) {
     case 2: cudaFuncSetAttribute(k_q1_elem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<2><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+            k_q1_elem<2><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
     case 3: cudaFuncSetAttribute(k_q1_elem<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<3><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+            k_q1_elem<3><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
     case 4: cudaFuncSetAttribute(k_q1_elem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<4><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+            k_q1_elem<4><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
     case 5: cudaFuncSetAttribute(k_q1_elem<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<5><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, lin, B1, D1, Ke); break;
+            k_q1_elem<5><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();

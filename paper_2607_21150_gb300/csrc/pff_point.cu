@@ -38,8 +38,13 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
   const int lq = (int)(q % Q3);
   const int qi = lq % Q, qj = (lq / Q) % Q, qk = lq / Q2;
   const long long e = q / Q3;
-  const double wdet = a.geom.wq[qi] * a.geom.wq[qj] * a.geom.wq[qk] * a.geom.detJ;
+  const bool mapped = a.geo != nullptr;
+  const double wdet = mapped ? a.geo[9 * nq + q] : a.geom.wq[qi] * a.geom.wq[qj] * a.geom.wq[qk] * a.geom.detJ;
   const double* sg = a.geom.s;
+  double Gx[3][3];  // mapped mesh: d xi_al / dX_A
+  if (mapped)
+    for (int al = 0; al < 3; ++al)
+      for (int A = 0; A < 3; ++A) Gx[al][A] = a.geo[(3 * al + A) * nq + q];
 
   double Hm[3][3];
   for (int r = 0; r < 3; ++r)
@@ -274,10 +279,18 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
   for (int r = 0; r < 3; ++r)
     for (int A = 0; A < 3; ++A) Pm[r][A] = tdeg[r][0] * Fi[A][0] + tdeg[r][1] * Fi[A][1] + tdeg[r][2] * Fi[A][2];
   double outv[13];
-  for (int r = 0; r < 3; ++r)
-    for (int A = 0; A < 3; ++A) outv[3 * r + A] = wdet * sg[A] * Pm[r][A];
+  if (mapped) {
+    for (int r = 0; r < 3; ++r)
+      for (int al = 0; al < 3; ++al)
+        outv[3 * r + al] = wdet * (Gx[al][0] * Pm[r][0] + Gx[al][1] * Pm[r][1] + Gx[al][2] * Pm[r][2]);
+    for (int al = 0; al < 3; ++al)
+      outv[10 + al] = wdet * ph.kphi * (Gx[al][0] * gphi[0] + Gx[al][1] * gphi[1] + Gx[al][2] * gphi[2]);
+  } else {
+    for (int r = 0; r < 3; ++r)
+      for (int A = 0; A < 3; ++A) outv[3 * r + A] = wdet * sg[A] * Pm[r][A];
+    for (int A = 0; A < 3; ++A) outv[10 + A] = wdet * sg[A] * ph.kphi * gphi[A];
+  }
   outv[9] = wdet * gl.s_phi * L;
-  for (int A = 0; A < 3; ++A) outv[10 + A] = wdet * sg[A] * ph.kphi * gphi[A];
   for (int v = 0; v < 13; ++v) {
     if (!isfinite(outv[v])) status |= 4;
     a.io[v * nq + q] = outv[v];
@@ -298,6 +311,8 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
     double* lin = a.lin + blk * (long long)kLinWords * stride + (long long)qk * Q2 * EB + el * Q2 + qj * Q + qi;
     const double app = (gl.at == 1) ? 0.0 : 2.0;
     const double cL = 2.0 * Hh + ph.gc_c0l0 * app + gl.zeta / gl.dt;
+    // mapped mesh: reference-frame columns kept, transformed to the parent frame below
+    double Dm[9][9], Pv[9], Lv[9], Lphi = 0.0;
     for (int d = 0; d < 10; ++d) {
       const double dphi = (d == 9) ? 1.0 : 0.0;
       const int aa = (d < 9) ? d / 3 : 0, BB = (d < 9) ? d % 3 : 0;
@@ -321,7 +336,15 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
       for (int r = 0; r < 3; ++r)
         for (int A = 0; A < 3; ++A) dP[r][A] = M[r][0] * Fi[A][0] + M[r][1] * Fi[A][1] + M[r][2] * Fi[A][2];
       const double dL = cL * dphi + gp * (active ? dpsip : 0.0);
-      if (d < 9) {
+      if (mapped) {
+        if (d < 9) {
+          for (int m = 0; m < 9; ++m) Dm[m][d] = dP[m / 3][m % 3];
+          Lv[d] = dL;
+        } else {
+          for (int m = 0; m < 9; ++m) Pv[m] = dP[m / 3][m % 3];
+          Lphi = dL;
+        }
+      } else if (d < 9) {
         const int n = 3 * aa + BB;
         for (int m = 0; m <= n; ++m) {
           const int r = m / 3, A = m % 3;
@@ -333,7 +356,39 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
         lin[(long long)kWD * stride] = wdet * gl.s_phi * dL;
       }
     }
-    for (int A = 0; A < 3; ++A) lin[(long long)(kWK + A) * stride] = wdet * sg[A] * sg[A] * ph.kphi;
+    if (!mapped) {
+      for (int A = 0; A < 3; ++A) lin[(long long)(kWK + A) * stride] = wdet * sg[A] * sg[A] * ph.kphi;
+      for (int pr = 0; pr < 3; ++pr) lin[(long long)(kWKX + pr) * stride] = 0.0;
+    } else {
+      // parent frame: A_hat[(r, al), (c, be)] = w det J sum_{A,B} G[al][A] D[(r, A), (c, B)] G[be][B]
+      double T[9][9];
+      for (int m = 0; m < 9; ++m)
+        for (int c = 0; c < 3; ++c)
+          for (int be = 0; be < 3; ++be)
+            T[m][3 * c + be] = Dm[m][3 * c] * Gx[be][0] + Dm[m][3 * c + 1] * Gx[be][1] + Dm[m][3 * c + 2] * Gx[be][2];
+      for (int n = 0; n < 9; ++n)
+        for (int m = 0; m <= n; ++m) {
+          const int r = m / 3, al = m % 3;
+          const double v = Gx[al][0] * T[3 * r][n] + Gx[al][1] * T[3 * r + 1][n] + Gx[al][2] * T[3 * r + 2][n];
+          lin[(long long)(kWA + sym9(m, n)) * stride] = wdet * v;
+        }
+      for (int r = 0; r < 3; ++r)
+        for (int al = 0; al < 3; ++al) {
+          lin[(long long)(kWP + 3 * r + al) * stride] =
+              wdet * (Gx[al][0] * Pv[3 * r] + Gx[al][1] * Pv[3 * r + 1] + Gx[al][2] * Pv[3 * r + 2]);
+          lin[(long long)(kWC + 3 * r + al) * stride] =
+              wdet * gl.s_phi * (Gx[al][0] * Lv[3 * r] + Gx[al][1] * Lv[3 * r + 1] + Gx[al][2] * Lv[3 * r + 2]);
+        }
+      lin[(long long)kWD * stride] = wdet * gl.s_phi * Lphi;
+      double K[3][3];
+      for (int al = 0; al < 3; ++al)
+        for (int be = 0; be < 3; ++be)
+          K[al][be] = wdet * ph.kphi * (Gx[al][0] * Gx[be][0] + Gx[al][1] * Gx[be][1] + Gx[al][2] * Gx[be][2]);
+      for (int al = 0; al < 3; ++al) lin[(long long)(kWK + al) * stride] = K[al][al];
+      lin[(long long)(kWKX + 0) * stride] = K[0][1];
+      lin[(long long)(kWKX + 1) * stride] = K[0][2];
+      lin[(long long)(kWKX + 2) * stride] = K[1][2];
+    }
   }
   if (status) atomicOr(a.status, status);
 }

@@ -564,7 +564,8 @@ int setup(pff_solver* s, cudaStream_t st, bool eig = true) {
   if (s->assembled) {
     LevelWork& c = s->lv.back();
     pff_op* op = s->op;
-    S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->Ke, s->A, st));
+    S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->Ke, s->A,
+                               op->geo != nullptr, st));
     S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
     if (s->prm.coarse_solver == 0 && eig) S_RC(power_coarse(s, st));
     if (s->prm.coarse_solver == 2) {
@@ -930,6 +931,8 @@ ElemArgs<double> fine_args(pff_op* op) {
   a.Dt = op->tab.Dt64;
   a.lin = op->lin64;
   a.nq = op->nq;
+  a.geo = op->geo;
+  a.kx = op->geo != nullptr;
   for (int d = 0; d < 3; ++d) a.s[d] = op->geom.s[d];
   return a;
 }
@@ -946,6 +949,7 @@ AdjArgs adj_args(pff_op* op) {
   a.hist = op->hist_c;
   a.phase_id = op->phase;
   a.status = op->status;
+  a.geo = op->geo;
   return a;
 }
 

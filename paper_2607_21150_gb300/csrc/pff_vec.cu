@@ -206,7 +206,8 @@ cudaError_t launch_cheb_step(long long n, T* x, T* d, T* r, const T* Ad, const T
 }
 
 
-// Stored linearisation from the tiled layout to the canonical order [67][N_q].
+// Stored linearisation from the tiled layout to the canonical order [67][N_q]
+// (the off-diagonal phase-gradient words of mapped meshes are not exported).
 __global__ void k_untile(const double* __restrict__ lin, double* __restrict__ out, long long nq, int Q) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= nq) return;
@@ -216,7 +217,7 @@ __global__ void k_untile(const double* __restrict__ lin, double* __restrict__ ou
   const int i = lq % Q, j = (lq / Q) % Q, k = lq / Q2;
   const long long stride = (long long)Q3 * EB;
   const long long base = (e / EB) * kLinWords * stride + (long long)k * Q2 * EB + (e % EB) * Q2 + j * Q + i;
-  for (int w = 0; w < kLinWords; ++w) out[w * nq + q] = lin[base + w * stride];
+  for (int w = 0; w < kLinWordsExport; ++w) out[w * nq + q] = lin[base + w * stride];
 }
 cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
@@ -281,5 +282,42 @@ template cudaError_t launch_cheb_step<double>(long long, double*, double*, doubl
                                               double, double, int, cudaStream_t);
 template cudaError_t launch_cheb_step<float>(long long, float*, float*, float*, const float*, const float*, double,
                                              double, int, cudaStream_t);
+
+// Geometry of a mapped mesh at every quadrature point from the parent Jacobian
+// J = dX / dxi (rows 3 f + al of an eval of the nodal coordinates):
+// geo[3 al + A] = (J^-1)[al][A] = d xi_al / dX_A, geo[9] = w_q det J.
+__global__ void k_geometry(const double* __restrict__ J, double* __restrict__ geo, Geom g, int Q, long long nq,
+                           int* __restrict__ status) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  double A[3][3];
+  for (int f = 0; f < 3; ++f)
+    for (int al = 0; al < 3; ++al) A[f][al] = J[(3 * f + al) * nq + q];
+  const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+                     A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  if (!(det > 0.0)) atomicOr(status, 2);
+  const double r = 1.0 / det;
+  double G[3][3];
+  G[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) * r;
+  G[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * r;
+  G[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * r;
+  G[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) * r;
+  G[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * r;
+  G[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * r;
+  G[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) * r;
+  G[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * r;
+  G[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * r;
+  for (int al = 0; al < 3; ++al)
+    for (int B = 0; B < 3; ++B) geo[(3 * al + B) * nq + q] = G[al][B];
+  const int Q2 = Q * Q;
+  const int lq = (int)(q % ((long long)Q2 * Q));
+  geo[9 * nq + q] = g.wq[lq % Q] * g.wq[(lq / Q) % Q] * g.wq[lq / Q2] * det;
+}
+cudaError_t launch_geometry(const double* J, double* geo, const Geom& g, int Q, long long nq, int* status,
+                            cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  k_geometry<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(J, geo, g, Q, nq, status);
+  return cudaGetLastError();
+}
 
 }  // namespace pff

@@ -90,6 +90,7 @@ _SIGS = {
     "pff_destroy_operator": ([_VP], _I),
     "pff_op_enable_f32": ([_VP, _I], _I),
     "pff_op_enable_df": ([_VP, _I], _I),
+    "pff_op_set_geometry": ([_VP, _VP, _VP], _I),
     "pff_op_num_qpoints": ([_VP], _I64),
     "pff_op_num_nodes": ([_VP], _I64),
     "pff_set_qpoint_state": ([_VP, _VP, _VP, _VP], _I),
@@ -262,6 +263,10 @@ def pff_op_enable_f32(op, enable=True):
 
 def pff_op_enable_df(op, enable=True):
     _call("pff_op_enable_df", op, 1 if enable else 0)
+
+
+def pff_op_set_geometry(op, X, stream=None):
+    _call("pff_op_set_geometry", op, _ptr(X), _stream(stream))
 
 
 def pff_op_num_qpoints(op):

@@ -23,6 +23,10 @@ class Session:
             self.offsets = torch.from_numpy(element_offsets(m)).to(self.dev)
         self.restr = pff.pff_create_restriction(self.ctx, (m.nx, m.ny, m.nz, *m.h), m.p, self.offsets, m.nn)
         self.op = pff.pff_create_operator(self.ctx, self.basis, self.restr)
+        self.X = None
+        if getattr(w, "X", None) is not None:  # mapped mesh
+            self.X = torch.from_numpy(np.ascontiguousarray(w.X, dtype=np.float64)).to(self.dev)
+            pff.pff_op_set_geometry(self.op, self.X, self.stream)
         if f32:
             pff.pff_op_enable_f32(self.op, True)
         if df:

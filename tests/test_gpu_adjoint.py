@@ -8,7 +8,7 @@ central differences of the GPU loss (1e-6), and torch autograd through
 ReactionCurve returns the same gradient.  Second variant: hardening Prandtl
 branches (linear + Voce, test values) with a live accumulated plastic strain,
 so that the return map's implicit derivatives and the history word eps_p
-enter the adjoint.
+enter the adjoint.  Third variant: a curved mesh (mapped geometry).
 """
 import numpy as np
 import pytest
@@ -42,9 +42,15 @@ def _hardened_box():
     return w
 
 
-@pytest.fixture(scope="module", params=["perfect", "hardening"])
+def _mapped_box():
+    w = _adjoint_box()
+    w.X = inputs.mapped_coords(w.mesh, "smooth", amp=0.15)
+    return w
+
+
+@pytest.fixture(scope="module", params=["perfect", "hardening", "mapped"])
 def problem(orc, request):
-    w = _adjoint_box() if request.param == "perfect" else _hardened_box()
+    w = {"perfect": _adjoint_box, "hardening": _hardened_box, "mapped": _mapped_box}[request.param]()
     top = inputs.top_face_mask(w.mesh)
     theta0 = inputs.params_of(w.phases)
     nsteps = 3

@@ -67,6 +67,14 @@ def _hardened(nx, ny, nz, p, seed):
     return w
 
 
+def _mapped(nx, ny, nz, p, seed, kind):
+    """Two-phase box on a mapped mesh: smoothly curved elements or straight-edged
+    distorted hexahedra (isoparametric geometry from nodal coordinates)."""
+    w = _two_phase(nx, ny, nz, p, seed)
+    w.X = inputs.mapped_coords(w.mesh, kind, amp=0.15, seed=seed)
+    return w
+
+
 CASES = {
     "cube_q2": lambda: inputs.cube(),
     "cube_b_q2": lambda: inputs.cube(hist_seed=2, H_max=80.0),
@@ -74,6 +82,8 @@ CASES = {
     "box_q3_ragged": lambda: _two_phase(3, 3, 2, 3, 7, at=1),  # 18 elements: blocks of 16
     "box_q1": lambda: _two_phase(5, 4, 4, 1, 9),              # 80 elements: blocks of 64
     "box_q3_hardening": lambda: _hardened(3, 2, 2, 3, 31),
+    "box_q4_curved": lambda: _mapped(3, 2, 2, 4, 41, "smooth"),
+    "box_q2_distorted": lambda: _mapped(3, 3, 2, 2, 43, "vertices"),
 }
 
 

@@ -217,3 +217,27 @@ def test_newton_with_h_multigrid_coarse_solver(orc):
         its[cs] = st["coarse_iterations"]
         pff.pff_destroy_solver(solver)
     assert its[2] < its[1]
+
+
+def test_mapped_mesh_coarse_operator_and_vcycle(orc):
+    """Curved Q4 mesh: the assembled order-1 operator (with the off-diagonal
+    phase-gradient combinations) equals P^T K P of the oracle, and one FP64
+    V-cycle equals the oracle's."""
+    w = _box(3, 2, 2, 4, 3)
+    w.X = inputs.mapped_coords(w.mesh, "smooth", amp=0.15)
+    s = Session(w, levels=(2, 1))
+    s.residual(torch.from_numpy(w.z.ravel()).cuda())
+    solver = s.solver([4, 2, 1], mixed=0, coarse_solver=0)
+    pff.pff_solver_setup(solver)
+    ref, Ks, Ps = _hierarchy(orc, w, [4, 2, 1])
+    xc = inputs.random_vector(Ks[-1].shape[0], 5)
+    y = torch.zeros(len(xc), dtype=torch.float64, device="cuda")
+    pff.pff_solver_coarse_apply(solver, torch.from_numpy(xc).cuda(), y)
+    assert rel(np_(y), Ks[-1] @ xc) <= 1e-12
+    lams = [pff.pff_solver_level_lambda(solver, l) for l in range(3)]
+    r = inputs.random_vector(w.mesh.ndof, 6)
+    z = torch.zeros(w.mesh.ndof, dtype=torch.float64, device="cuda")
+    pff.pff_solver_vcycle(solver, torch.from_numpy(r).cuda(), z)
+    zr = orc.vcycle(Ks, Ps, [K.diagonal() for K in Ks], lams, r)
+    assert rel(np_(z), zr) <= 1e-11
+    pff.pff_destroy_solver(solver)
