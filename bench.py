@@ -217,21 +217,35 @@ def newton_compare(name: str, steps: int = 1, variants=("mixed", "fp64")):
 NEWTON_STEPS = {"tension_q4": 10, "notched_q3": 1, "compress_q4": 1}
 
 
-def apply_config(name: str, steps: int, warmup: int):
-    """FP64 and FP32 fine-level action on another workload (CUDA events)."""
+def apply_config(name: str, steps: int, warmup: int, mapped: str | None = None):
+    """FP64 and FP32 fine-level action, and the residual, on another workload
+    (CUDA events); `mapped` = a mapped-mesh kind of inputs.mapped_coords."""
     import torch
     from paper_2607_21150_gb300 import inputs, pff
     from paper_2607_21150_gb300.session import Session
     w = make_workload(name, seed=0)
     m = w.mesh
+    if mapped:
+        w.X = inputs.mapped_coords(m, mapped, amp=0.15)
     s = Session(w, f32=True)
     stream = torch.cuda.current_stream()
-    s.residual(torch.from_numpy(w.z.ravel()).cuda())
+    zt = torch.from_numpy(w.z.ravel()).cuda()
+    s.residual(zt)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    s.residual(zt)
+    b.record(stream)
+    torch.cuda.synchronize()
+    t_res = a.elapsed_time(b)
+    status = s.status()
     L = s.levels[m.p]
     x = torch.from_numpy(np.random.default_rng(1).uniform(-1, 1, m.ndof)).cuda()
     y = torch.empty_like(x)
     x32, y32 = x.float(), torch.empty(m.ndof, dtype=torch.float32, device="cuda")
-    out = {"workload": f"{name}: Q{m.p} {m.nx}x{m.ny}x{m.nz} elements, {m.ndof} DoF"}
+    out = {"workload": f"{name}: Q{m.p} {m.nx}x{m.ny}x{m.nz} elements, {m.ndof} DoF"
+                       + (f", mapped mesh ({mapped}, amplitude 0.15 h)" if mapped else ""),
+           "residual_ms": t_res, "kernel_status": status}
     for label, fn in (("fp64", lambda: pff.pff_jacobian_apply(L, pff.PFF_F64, x, y, stream)),
                       ("fp32", lambda: pff.pff_jacobian_apply(L, pff.PFF_F32, x32, y32, stream))):
         for _ in range(warmup):
@@ -471,6 +485,8 @@ def run_native(args):
         else:
             newton_configs[name] = res
     apply_small = apply_config("tension_q4", args.steps, args.warmup) if args.newton != "none" else None
+    apply_mapped = (apply_config(args.config, args.steps, args.warmup, mapped="smooth")
+                    if args.newton != "none" else None)
     adjoint = adjoint_timing(args.adjoint_steps) if args.adjoint_steps > 0 else None
     cpu = oracle_sample()
     line = {
@@ -500,6 +516,7 @@ def run_native(args):
         "newton_configs": newton_configs,
         "level_applies": levels,
         "apply_tension_q4": apply_small,
+        "apply_mapped_mesh": apply_mapped,
         "adjoint": adjoint,
         "e2e": {"value": world * ndof * args.steps / (tot_e2e / 1e3) / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
