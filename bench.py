@@ -30,8 +30,9 @@ METRIC = "Q4 Jacobian-apply GDoF/s & %HBM roofline; Newton step time FP64 vs mix
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) per element of one Jacobian action, Q4 (P = Q = 5),
 # from one ncu capture of the same kernels at 16^3 elements (4096 elements:
-# FP64 301.0 MB, FP32 156.9 MB), scaled to a launch by the element count.
-TRAFFIC_PER_ELEMENT = {"f64": 301.0e6 / 4096, "f32": 156.9e6 / 4096}
+# FP64 297.09 + 7.55 MB, FP32 151.00 + 4.23 MB), scaled to a launch by the
+# element count.
+TRAFFIC_PER_ELEMENT = {"f64": (297.09e6 + 7.55e6) / 4096, "f32": (151.00e6 + 4.23e6) / 4096}
 
 
 def peaks():
@@ -165,21 +166,22 @@ def oracle_sample(seconds_budget: float = 20.0):
                 gdofs=m.ndof / t_spmv / 1e9, gdofs_incl_assembly=m.ndof / (t_spmv + t_asm) / 1e9)
 
 
-def newton_compare(name: str, steps: int = 1, variants=("mixed", "fp64")):
-    """Load steps from the unloaded state with FP64 p-MG and with mixed p-MG (FP32
-    levels and smoothers), both to ||r||/||r0|| <= 1e-8 with inner rtol 1e-3.
+def newton_compare(name: str, steps: int = 1, variants=("mixed", "mixed_df", "fp64")):
+    """Load steps from the unloaded state with FP64 p-MG, with mixed p-MG (FP32
+    levels and smoothers) and with mixed p-MG whose outer FGMRES operator is the
+    double-float action, all to ||r||/||r0|| <= 1e-8 with inner rtol 1e-3.
     Returns per-variant timings (host clock around synchronised phases) and the
-    relative difference of the two converged fields."""
+    relative difference of each converged field from the FP64 one."""
     import torch
     from paper_2607_21150_gb300 import inputs
     from paper_2607_21150_gb300.driver import LoadStepper
     out = {"workload": name, "load_steps": steps}
     fields = {}
-    for label, mixed in (("mixed", True), ("fp64", False)):
+    for label, mixed, df in (("mixed", True, False), ("mixed_df", True, True), ("fp64", False, False)):
         if label not in variants:
             continue
         w = getattr(inputs, name)()
-        lsp = LoadStepper(w, mixed=mixed, verbose=1)
+        lsp = LoadStepper(w, mixed=mixed, df=df, verbose=1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         its = kr = 0
@@ -204,10 +206,13 @@ def newton_compare(name: str, steps: int = 1, variants=("mixed", "fp64")):
         lsp.close()
         del lsp
         torch.cuda.empty_cache()
-    if len(fields) == 2:
-        a, b = fields["fp64"], fields["mixed"]
-        out["field_rel_diff"] = float(np.linalg.norm(a - b) / np.linalg.norm(a))
-        out["speedup_mixed_vs_fp64"] = out["fp64"]["wall_s"] / out["mixed"]["wall_s"]
+    if "fp64" in fields:
+        a = fields["fp64"]
+        for label in ("mixed", "mixed_df"):
+            if label in fields:
+                sfx = "" if label == "mixed" else "_df"
+                out["field_rel_diff" + sfx] = float(np.linalg.norm(a - fields[label]) / np.linalg.norm(a))
+                out[f"speedup_{label}_vs_fp64"] = out["fp64"]["wall_s"] / out[label]["wall_s"]
     return out
 
 
@@ -547,7 +552,8 @@ def main():
                     help="comma list of workloads (compress_q4, tension_q4, notched_q3) of the FP64-vs-mixed "
                          "Newton comparison, the first one reported as newton_step; or none")
     ap.add_argument("--newton-steps", type=int, default=1, help="load steps of the first --newton workload")
-    ap.add_argument("--newton-variants", default="mixed,fp64", help="comma list of mixed, fp64")
+    ap.add_argument("--newton-variants", default="mixed,mixed_df,fp64",
+                    help="comma list of mixed, mixed_df (double-float outer action), fp64")
     ap.add_argument("--adjoint-steps", type=int, default=10, help="load steps of the adjoint timing (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":

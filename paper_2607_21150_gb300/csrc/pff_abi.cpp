@@ -593,7 +593,8 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   a.mask = op->mask;
   PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
   if (op->f32 && op->lin32)
-    PFF_CK(launch_split_df(op->lin64, op->lin32, op->df ? op->lin32 + op->lin_len : nullptr, op->lin_len, st));
+    PFF_CK(launch_split_df(op->lin64, op->lin32, op->df ? op->lin32 + op->lin_len : nullptr,
+                           op->lin_len / (kLinWords * stride_of(op->Q)), op->Q, st));
   return PFF_OK;
 }
 

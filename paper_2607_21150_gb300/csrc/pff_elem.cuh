@@ -20,6 +20,14 @@
 namespace pff {
 
 template <typename T> __device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+// Loads of the stored linearisation: the read-only path for the FP64 and FP32
+// actions, streaming loads (evict-first) for the two planes of the
+// double-float action (64^3 Q4: 16.0 -> 10.3 ms; the FP32 action measured
+// 2.9 ms with the read-only path, 3.0 ms with streaming loads).
+template <bool STREAM> __device__ __forceinline__ float ld_lin1(const float* p) { return STREAM ? __ldcs(p) : __ldg(p); }
+template <bool STREAM> __device__ __forceinline__ float4 ld_lin4(const float* p) {
+  return STREAM ? __ldcs(reinterpret_cast<const float4*>(p)) : __ldg(reinterpret_cast<const float4*>(p));
+}
 
 __device__ __forceinline__ double madd(double c, double a, double b) { return fma(a, b, c); }
 __device__ __forceinline__ float madd(float c, float a, float b) { return fmaf(a, b, c); }
@@ -46,7 +54,21 @@ __device__ __forceinline__ T ld_lin(const typename ElemTypes<T>::L* p, long long
   if constexpr (sizeof(T) == sizeof(typename ElemTypes<T>::L)) {
     return ldg(p);
   } else {
-    return df_make(ldg(p), ldg(p + lo));
+    return df_make(ld_lin1<true>(p), ld_lin1<true>(p + lo));
+  }
+}
+
+// four consecutive words of the FP32 quad layout (df64: hi plane at p, lo
+// plane at p + lo); p is 16-byte aligned
+template <typename T>
+__device__ __forceinline__ void ld_quad(const float* p, long long lo, T w[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 h = ld_lin4<false>(p);
+    w[0] = h.x; w[1] = h.y; w[2] = h.z; w[3] = h.w;
+  } else {
+    const float4 h = ld_lin4<true>(p);
+    const float4 l = ld_lin4<true>(p + lo);
+    w[0] = df_make(h.x, l.x); w[1] = df_make(h.y, l.y); w[2] = df_make(h.z, l.z); w[3] = df_make(h.w, l.w);
   }
 }
 
@@ -87,7 +109,13 @@ template <int P, int Q, typename T>
 __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, Q, T>& s, int e, bool valid, int ij) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   const long long nn = a.mesh.nn;
-  for (int idx = ij; idx < P3; idx += Q2) {
+  // every thread's gather loads (values and mask bytes) are independent and
+  // issued together: one memory round trip instead of one per node and a
+  // second one behind each mask byte
+#pragma unroll
+  for (int r = 0; r < (P3 + Q2 - 1) / Q2; ++r) {
+    const int idx = ij + r * Q2;
+    if (idx >= P3) break;
     int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);
     long long n = valid ? node_of<P, Q>(a.mesh, e, aa, bb, cc) : 0;
 #pragma unroll
@@ -95,7 +123,9 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
       T v = zero<T>();
       if (valid) {
         long long g = f * nn + n;
-        if (!(a.mask && a.mask[g])) v = from_store<T>(ldg(a.x + g));
+        const auto xv = ldg(a.x + g);
+        const bool fixed = a.mask && ldg(a.mask + g);
+        if (!fixed) v = from_store<T>(xv);
       }
       s.bufA[f * Q3 + idx] = v;
     }
@@ -212,13 +242,16 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
   __syncthreads();
   if (!valid) return;
   const long long nn = a.mesh.nn;
-  for (int idx = ij; idx < P3; idx += Q2) {
+#pragma unroll
+  for (int r = 0; r < (P3 + Q2 - 1) / Q2; ++r) {
+    const int idx = ij + r * Q2;
+    if (idx >= P3) break;
     int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);
     long long n = node_of<P, Q>(a.mesh, e, aa, bb, cc);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       long long g = f * nn + n;
-      if (a.mask && a.mask[g]) continue;
+      if (a.mask && ldg(a.mask + g)) continue;
       atomicAdd(a.y + g, to_vec(s.bufA[f * Q3 + idx]));
     }
   }
@@ -268,13 +301,90 @@ __device__ __forceinline__ void jac_point(const typename ElemTypes<T>::L* lin, c
   }
 }
 
+// The same map reading the FP32 planes in the quad layout: q = the point's
+// first quad (quads at stride qs), tl = its word 64 (tail words at stride ts).
+// Every quad is used as it arrives, in word order: the 9x9 block, dP/dphi and
+// d(s_phi L)/dF (their roles swapped for the transpose, TR), d(s_phi L)/dphi.
+template <typename T, bool TR>
+__device__ __forceinline__ void jac_point_q(const float* q, long long qs, const float* tl, long long ts, long long lo,
+                                            int kx, const T g[4][3], T phi, T o[4][3], T& o0) {
+  T gu[9];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) gu[3 * f + al] = g[f][al];
+  T ou[9], s0 = zero<T>();
+#pragma unroll
+  for (int m = 0; m < 9; ++m) ou[m] = zero<T>();
+  T cur[4];
+#pragma unroll
+  for (int m = 0; m < 9; ++m) {  // upper triangle of the symmetric 9x9 block, row-major
+#pragma unroll
+    for (int n = m; n < 9; ++n) {
+      const int wd = sym9(m, n);
+      if ((wd & 3) == 0) ld_quad<T>(q + (wd >> 2) * qs, lo, cur);
+      const T w = cur[wd & 3];
+      ou[m] = madd(ou[m], w, gu[n]);
+      if (n != m) ou[n] = madd(ou[n], w, gu[m]);
+    }
+  }
+#pragma unroll
+  for (int wd = kWP; wd < kLinQuadWords; ++wd) {  // the quad of word 44 is loaded
+    if ((wd & 3) == 0) ld_quad<T>(q + (wd >> 2) * qs, lo, cur);
+    const T w = cur[wd & 3];
+    if (wd < kWC) {
+      if (TR) s0 = madd(s0, w, gu[wd - kWP]);
+      else ou[wd - kWP] = madd(ou[wd - kWP], w, phi);
+    } else if (wd < kWD) {
+      if (TR) ou[wd - kWC] = madd(ou[wd - kWC], w, phi);
+      else s0 = madd(s0, w, gu[wd - kWC]);
+    } else {
+      s0 = madd(s0, w, phi);
+    }
+  }
+  o0 = s0;
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int al = 0; al < 3; ++al) o[f][al] = ou[3 * f + al];
+#pragma unroll
+  for (int al = 0; al < 3; ++al) o[3][al] = mul(ld_lin<T>(tl + al * ts, lo), g[3][al]);
+  if (kx) {  // mapped mesh: symmetric off-diagonal coefficients 01, 02, 12
+    const T k01 = ld_lin<T>(tl + 3 * ts, lo);
+    const T k02 = ld_lin<T>(tl + 4 * ts, lo);
+    const T k12 = ld_lin<T>(tl + 5 * ts, lo);
+    o[3][0] = madd(madd(o[3][0], k01, g[3][1]), k02, g[3][2]);
+    o[3][1] = madd(madd(o[3][1], k01, g[3][0]), k12, g[3][2]);
+    o[3][2] = madd(madd(o[3][2], k02, g[3][0]), k12, g[3][1]);
+  }
+}
+
+// Jacobian map at point (slice k, thread t) of this block: FP64 planar words
+// or the FP32 quad layout.
+template <int Q, typename T>
+__device__ __forceinline__ void jac_at(const ElemArgs<T>& a, int k, int t, const T g[4][3], T phi, T o[4][3], T& o0) {
+  constexpr long long EB = elems_per_block(Q);
+  constexpr long long run = (long long)Q * Q * EB, stride = run * Q;
+  const long long blk = blockIdx.x * (long long)kLinWords * stride;
+  if constexpr (sizeof(typename ElemTypes<T>::L) == 4) {
+    const float* q = a.lin + blk + lin32_word(0, k, t, stride, run);
+    const float* tl = a.lin + blk + lin32_word(kLinQuadWords, k, t, stride, run);
+    if (a.transpose) jac_point_q<T, true>(q, 4 * stride, tl, stride, a.lo, a.kx, g, phi, o, o0);
+    else jac_point_q<T, false>(q, 4 * stride, tl, stride, a.lo, a.kx, g, phi, o, o0);
+  } else {
+    const long long off = blk + (long long)k * run + t;
+    jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, a.kx, g, phi, o, o0);
+  }
+}
+
 // L2 prefetch of slice k of this block's stored linearisation (FP32 action):
-// thread w < 67 requests the contiguous run of word w (Q^2 EB words) with one
-// bulk prefetch, so the next slice streams from HBM while this one computes
-// (64^3 Q4: 3.76 -> 3.48 ms; two or three slices ahead measured slower, and
-// the double-float action, issue-bound, lost 1-4 %).  Runs start on 8-byte
-// boundaries; the request is widened to 16-byte boundaries and clipped to the
-// plane.
+// threads 0..15 request the contiguous run of one quad plane (4 Q^2 EB words),
+// the next three (six on mapped meshes) the run of one tail word (Q^2 EB words),
+// each with one bulk prefetch, so the next slice streams from HBM while this
+// one computes (64^3 Q4: 3.76 -> 3.48 ms; two or three slices ahead measured
+// slower, and the double-float action, issue-bound, lost 1-4 %).  Tail runs
+// start on 8-byte boundaries; the request is widened to 16-byte boundaries and
+// clipped to the plane.
 constexpr int kPrefetchAhead = 1;  // slices requested ahead of the one computed
 __device__ __forceinline__ void prefetch_run(uintptr_t base, long long first, long long run, long long plane) {
   const uintptr_t lo = (base + 4 * first) & ~uintptr_t(15);
@@ -291,12 +401,14 @@ __device__ __forceinline__ void prefetch_slice(const ElemArgs<T>& a, int k, int 
   if constexpr (sizeof(T) == 4) {
     constexpr int EB = elems_per_block(Q);
     constexpr long long run = (long long)Q * Q * EB;   // words of one (word, slice) run
-    if (t >= kLinWords || k >= Q) return;
+    constexpr int NQ = kLinQuadWords / 4;
+    if (t >= NQ + (a.kx ? kLinWords - kLinQuadWords : kWKX - kLinQuadWords) || k >= Q) return;
     const long long nblk = (a.mesh.nel + EB - 1) / EB;
     const long long plane = nblk * kLinWords * Q * Q * Q * EB;
-    const long long first = blockIdx.x * kLinWords * Q * run + (long long)t * Q * run + k * run;
+    const long long blk = blockIdx.x * kLinWords * Q * run;
     const uintptr_t base = reinterpret_cast<uintptr_t>(a.lin);
-    prefetch_run(base, first, run, plane);
+    if (t < NQ) prefetch_run(base, blk + lin32_word(4 * t, k, 0, Q * run, run), 4 * run, plane);
+    else prefetch_run(base, blk + lin32_word(kLinQuadWords + t - NQ, k, 0, Q * run, run), run, plane);
   }
 }
 
@@ -376,8 +488,6 @@ k_elem(const ElemArgs<T> a) {
 #pragma unroll
     for (int k = 0; k < Q; ++k) Y[f][k] = zero<T>();
 
-  const long long blk_words = (long long)kLinWords * Q3 * EB;
-  const long long stride = (long long)Q3 * EB;
   if constexpr (kSplit) {
     // pointwise stage of all slices without barriers: z-derivative and value
     // terms into the registers of the own column, x- and y-derivative outputs
@@ -389,8 +499,7 @@ k_elem(const ElemArgs<T> a) {
       prefetch_slice<Q, T>(a, k + kPrefetchAhead, t);
       grad_at<P, Q, T>(s, i, j, k, g, phi);
       if (valid) {
-        long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
-        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, a.kx, g, phi, o, o0);
+        jac_at<Q, T>(a, k, t, g, phi, o, o0);
       } else {
 #pragma unroll
         for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();
@@ -430,8 +539,7 @@ k_elem(const ElemArgs<T> a) {
       T g[4][3], phi;
       grad_at<P, Q, T>(s, i, j, k, g, phi);
       if (valid) {
-        long long off = blockIdx.x * blk_words + (long long)k * Q2 * EB + t;
-        jac_point<T>(a.lin + off, a.linP + off, a.linC + off, stride, a.lo, a.kx, g, phi, o, o0);
+        jac_at<Q, T>(a, k, t, g, phi, o, o0);
       } else {
 #pragma unroll
         for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();
@@ -551,7 +659,8 @@ k_diag(const ElemArgs<T> a) {
     T col[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      long long off = blockIdx.x * blk_words + (long long)word * stride + (long long)k * Q2 * EB + t;
+      const long long off = blockIdx.x * blk_words + (sizeof(T) == 4 ? lin32_word(word, k, t, stride, Q2 * EB)
+                                                                    : (long long)word * stride + (long long)k * Q2 * EB + t);
       col[k] = valid ? ldg(a.lin + off) * wgt : T(0);
     }
 #pragma unroll

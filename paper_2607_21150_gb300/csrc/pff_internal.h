@@ -15,9 +15,22 @@ constexpr int kLinWords = 70;     // stored pointwise linearisation words per qu
 // All words are in the parent frame (w_q det J and d xi / dX folded in).
 constexpr int kWA = 0, kWP = 45, kWC = 54, kWD = 63, kWK = 64, kWKX = 67;
 constexpr int kLinWordsExport = 67;  // words returned by pff_get_linearization
+// FP32 planes (level actions, double-float hi/lo): words [0, 64) interleaved by
+// four, so that one 128-bit load fetches four words of one point; words
+// [64, 70) as in the FP64 layout.  Offset of word w of slice k, thread t within
+// a block's region (q3eb = Q^3 EB words per word plane, q2eb = Q^2 EB per slice):
+constexpr int kLinQuadWords = 64;
+__host__ __device__ constexpr long long lin32_word(int w, int k, int t, long long q3eb, long long q2eb) {
+  return w < kLinQuadWords ? (long long)(w >> 2) * 4 * q3eb + (long long)k * 4 * q2eb + 4LL * t + (w & 3)
+                           : (long long)w * q3eb + (long long)k * q2eb + t;
+}
 
 // Elements handled by one thread block of the element kernels: Q*Q threads per element.
 __host__ __device__ constexpr int elems_per_block(int Q) { return 256 / (Q * Q); }
+// 128-bit alignment of the FP32 quad planes needs an even Q^3 EB for every Q
+static_assert((2 * 2 * 2 * elems_per_block(2)) % 2 == 0 && (3 * 3 * 3 * elems_per_block(3)) % 2 == 0 &&
+              (4 * 4 * 4 * elems_per_block(4)) % 2 == 0 && (5 * 5 * 5 * elems_per_block(5)) % 2 == 0,
+              "FP32 quad layout needs Q^3 EB even");
 
 __host__ __device__ constexpr int sym9(int m, int n) {  // m <= n
   return m * 9 - (m * (m - 1)) / 2 + (n - m);
@@ -163,7 +176,7 @@ cudaError_t launch_geometry(const double* J, double* geo, const Geom& g, int Q, 
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
 // hi[i] = fl32(a[i]) and, when lo is not null, lo[i] = fl32(a[i] - hi[i]).
-cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long n, cudaStream_t st);
+cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nblk, int Q, cudaStream_t st);
 cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st);
 cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st);
 cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st);

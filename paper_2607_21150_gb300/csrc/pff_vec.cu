@@ -40,18 +40,47 @@ cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* u
   return cudaGetLastError();
 }
 
-// Double-float split of the stored linearisation: hi = fl32(a), lo = fl32(a - hi).
-__global__ void k_split_df(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double v = a[i];
-    const float h = __double2float_rn(v);
-    hi[i] = h;
-    if (lo) lo[i] = __double2float_rn(v - (double)h);
+// FP32 planes of the stored linearisation: hi = fl32(a), lo = fl32(a - hi)
+// (lo optional), words [0, 64) of every point regrouped by four (the quad
+// layout of lin32_word), words [64, 70) in place.  One thread per output float4
+// of the quad region (four coalesced FP64 reads, one 128-bit write), then one
+// per tail word.
+__global__ void k_split_df(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo,
+                           long long nblk, long long q3eb) {
+  const long long bw = (long long)kLinWords * q3eb;
+  const long long qpb = (kLinQuadWords / 4) * q3eb;                // float4 per block
+  const long long tpb = (long long)(kLinWords - kLinQuadWords) * q3eb;
+  const long long nq4 = nblk * qpb, n = nq4 + nblk * tpb;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+    if (u < nq4) {
+      const long long b = u / qpb, rem = u % qpb;
+      const long long quad = rem / q3eb, r2 = rem % q3eb;
+      const double* src = a + b * bw + 4 * quad * q3eb + r2;
+      float h[4], l[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double v = src[c * q3eb];
+        h[c] = __double2float_rn(v);
+        l[c] = __double2float_rn(v - (double)h[c]);
+      }
+      const long long o = b * bw + quad * 4 * q3eb + 4 * r2;
+      *reinterpret_cast<float4*>(hi + o) = make_float4(h[0], h[1], h[2], h[3]);
+      if (lo) *reinterpret_cast<float4*>(lo + o) = make_float4(l[0], l[1], l[2], l[3]);
+    } else {
+      const long long v = u - nq4, b = v / tpb;
+      const long long i = b * bw + (long long)kLinQuadWords * q3eb + v % tpb;
+      const double x = a[i];
+      const float h = __double2float_rn(x);
+      hi[i] = h;
+      if (lo) lo[i] = __double2float_rn(x - (double)h);
+    }
   }
 }
-cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long n, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
-  k_split_df<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, n);
+cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nblk, int Q, cudaStream_t st) {
+  if (nblk == 0) return cudaSuccess;
+  const long long q3eb = (long long)Q * Q * Q * elems_per_block(Q);
+  const long long n = nblk * ((kLinQuadWords / 4) + (kLinWords - kLinQuadWords)) * q3eb;
+  k_split_df<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, nblk, q3eb);
   return cudaGetLastError();
 }
 
