@@ -2,8 +2,9 @@
 
 * pff_reaction = the oracle's internal force summed over the top-face u_z DoFs;
 * three load steps of the tension box (Newton to 1e-11, history committed after
-  every step) reproduce the oracle's trajectory (Newton with direct solves,
-  commit of its own trial history) to 1e-9 in the fields and the reactions.
+  every step; FP64 levels, or FP32 levels with the double-float outer action)
+  reproduce the oracle's trajectory (Newton with direct solves, commit of its
+  own trial history) to 1e-9 in the fields and the reactions.
 """
 import numpy as np
 import pytest
@@ -49,10 +50,11 @@ def test_reaction_matches_oracle_internal_force(orc):
     assert got[0] == 0.0 and got[3] == 0.0
 
 
-@pytest.mark.parametrize("at", [1, 2])
-def test_load_steps_match_oracle(orc, at):
+@pytest.mark.parametrize("at,mixed", [(1, False), (2, False), (2, True)])
+def test_load_steps_match_oracle(orc, at, mixed):
+    """mixed: FP32 levels and the default double-float outer action."""
     w = _tension_box(at)
-    lsp = LoadStepper(w, levels=[2, 1], mixed=False, newton_rtol=1e-11, krylov_rtol=1e-8)
+    lsp = LoadStepper(w, levels=[2, 1], mixed=mixed, newton_rtol=1e-11, krylov_rtol=1e-8)
     # oracle trajectory
     z = w.z.copy()
     hist = w.hist.copy()
