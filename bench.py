@@ -343,6 +343,26 @@ def run_reference(args):
     return 0
 
 
+def max_over_ranks(values, world: int):
+    """Element-wise maximum of per-rank timings over all ranks: one all-reduce,
+    on a CUDA tensor under NCCL and a CPU tensor under gloo."""
+    vals = [float(v) for v in values]
+    if world <= 1:
+        return vals
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu().tolist()]
+
+
+def whole_job_rate(world: int, units_per_rank: float, steps: int, t_ms: float) -> float:
+    """Units of all ranks per second, in 1e9, for `steps` steps on every rank
+    whose slowest rank took t_ms (weak scaling: every rank holds its own units)."""
+    return world * units_per_rank * steps / (t_ms / 1e3) / 1e9
+
+
 # --------------------------------------------------------------------------- GPU
 def run_native(args):
     import torch
@@ -456,11 +476,8 @@ def run_native(args):
                             "fp64_gdofs": nl / (t64l / args.steps / 1e3) / 1e9,
                             "fp32_gdofs": nl / (t32l / args.steps / 1e3) / 1e9}
 
-    # max over ranks
-    tmax = torch.tensor([tot64], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    tot64 = float(tmax.item())
+    # every timed leg: the slowest rank's time
+    tot64, tot32, totdf, tot_e2e = max_over_ranks([tot64, tot32, totdf, tot_e2e], world)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -469,7 +486,7 @@ def run_native(args):
     P, Q = m.p + 1, m.Q
     flops_el = apply_counts(P, Q)
     t_apply = tot64 / args.steps / 1e3
-    value = world * ndof * args.steps / (tot64 / 1e3) / 1e9
+    value = whole_job_rate(world, ndof, args.steps, tot64)
     achieved_flops = flops_el * m.nel / t_apply / 1e12
     hbm_peak, src = peaks()
     bytes64 = 8 * ndof * 2 + ndof + 67 * 8 * m.nq
@@ -523,7 +540,7 @@ def run_native(args):
         "apply_tension_q4": apply_small,
         "apply_mapped_mesh": apply_mapped,
         "adjoint": adjoint,
-        "e2e": {"value": world * ndof * args.steps / (tot_e2e / 1e3) / 1e9, "unit": "GDoF/s",
+        "e2e": {"value": whole_job_rate(world, ndof, args.steps, tot_e2e), "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
         "gpu_launches": 2 * args.steps,
         "cpu_baseline": {"value": cpu["gdofs"], "unit": "GDoF/s", "cores": cpu["threads"], "kind": "oracle",
