@@ -149,6 +149,17 @@ def oracle_sample(seconds_budget: float = 20.0):
         if time.perf_counter() - t0 > min(5.0, seconds_budget):
             break
     t_spmv = (time.perf_counter() - t0) / reps
+    threads = oracle.num_threads()
+    oracle.set_num_threads(1)  # the same loop on one core
+    reps1 = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.spmv(K, x)
+        reps1 += 1
+        if time.perf_counter() - t0 > min(2.0, seconds_budget):
+            break
+    t_spmv1 = (time.perf_counter() - t0) / reps1
+    oracle.set_num_threads(threads)
     t0 = time.perf_counter()
     oracle.assemble(w, matrix=False)
     t_res = time.perf_counter() - t0
@@ -162,8 +173,9 @@ def oracle_sample(seconds_budget: float = 20.0):
     _, hres, _ = oracle.newton(wn, rtol=1e-8)
     t_newton = time.perf_counter() - t0
     return dict(ndof=m.ndof, nel=m.nel, t_assemble=t_asm, t_spmv=t_spmv, t_residual=t_res, t_newton=t_newton,
-                newton_iterations=len(hres) - 1, threads=oracle.num_threads(),
-                gdofs=m.ndof / t_spmv / 1e9, gdofs_incl_assembly=m.ndof / (t_spmv + t_asm) / 1e9)
+                newton_iterations=len(hres) - 1, threads=threads,
+                gdofs=m.ndof / t_spmv / 1e9, gdofs_1core=m.ndof / t_spmv1 / 1e9,
+                gdofs_incl_assembly=m.ndof / (t_spmv + t_asm) / 1e9)
 
 
 def newton_compare(name: str, steps: int = 1, variants=("mixed", "mixed_df", "fp64")):
@@ -547,6 +559,7 @@ def run_native(args):
                          "sample": f"{cpu['nel']}-element Q4 sub-box ({cpu['ndof']} DoF) of the same workload; "
                                    f"CSR SpMV of the oracle's assembled Jacobian "
                                    f"(assembly {cpu['t_assemble']:.2f} s not included)",
+                         "value_1core": cpu["gdofs_1core"],
                          "residual_s": cpu["t_residual"], "assembly_s": cpu["t_assemble"],
                          "newton_step_s_2x2x2": cpu["t_newton"], "newton_iterations": cpu["newton_iterations"]},
         "clocks": clk.summary(),

@@ -72,6 +72,7 @@ def lib():
         L.orc_prolong_coo.argtypes = [ip, ctypes.c_int, ctypes.c_int, llp, llp, dp]
         L.orc_prolong_coo.restype = ctypes.c_longlong
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
         L.orc_csr_spmv.argtypes = [ctypes.c_longlong, llp, llp, dp, dp, dp]
         L.orc_point_partials.argtypes = [ctypes.c_int, dp, dp, u8p, dp, ctypes.c_int, dp, dp, dp]
         L.orc_qpoint_inputs.argtypes = [ip, dp, dp, dp, dp]
@@ -118,6 +119,11 @@ def _u8(a):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the oracle's parallel loops from now on."""
+    lib().orc_set_num_threads(int(n))
 
 
 def spmv(K, x):

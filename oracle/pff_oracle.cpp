@@ -1225,4 +1225,13 @@ int orc_num_threads() {
 #endif
 }
 
+// Threads of the following parallel loops (timing with one core and with all).
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 }  // extern "C"
