@@ -7,8 +7,10 @@
 // shared memory one direction at a time; gradients at the Gauss points use
 // the collocated derivative D_c (exact because p <= Q - 1).  The pointwise
 // linearisation is read from a tiled layout so that every load of a block is
-// one contiguous run: word w of slice k of block b sits at
-//   b * 67 * Q^3 * EB + w * Q^3 * EB + k * Q^2 * EB + threadIdx.x.
+// one contiguous run: in FP64, word w of slice k of block b sits at
+//   b * kLinWords * Q^3 * EB + w * Q^3 * EB + k * Q^2 * EB + threadIdx.x;
+// the FP32 planes group words 0..63 of a point by four (lin32_word), so that
+// one 128-bit load fetches four words.
 //
 // The arithmetic type T is double, float or df64 (double-float pairs on the
 // FP32 pipes, FP64 vectors in and out); every multiply-add goes through
