@@ -136,7 +136,8 @@ int pff_destroy_restriction(pff_restr* restr);
 
 /* Fine-level operator: allocates the quadrature-point state (committed and
  * trial history, phase ids, flags), the FP64 stored linearisation
- * (67 words per point) and the residual work space. */
+ * (70 words per point, 67 of them used on an affine box) and the residual
+ * work space. */
 int pff_create_operator(pff_ctx* ctx, pff_basis* fine, pff_restr* restr, pff_op** op);
 int pff_destroy_operator(pff_op* op);
 /* Also keep an FP32 copy of the stored linearisation (written by pff_residual),

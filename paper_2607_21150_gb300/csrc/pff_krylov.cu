@@ -243,11 +243,12 @@ cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaSt
 }
 
 // ---- sum-factorised element matrices of the order-1 level (FP64) ----------
-// One block per element.  The 67 stored words of the element's 125 (Q^3)
-// points give 67 "combinations" (word, test derivative, trial derivative):
-// 45 from the symmetric 9x9 block (the transposed block of an off-diagonal pair
-// is placed from the same result), 9 dP/dphi, 9 d(s_phi L)/dF, the phi value
-// term and the 3 phase-gradient terms.  Each combination's 8x8 block is
+// One block per element.  The stored words of the element's 125 (Q^3) points
+// give 67 "combinations" (word, test derivative, trial derivative) on the box
+// and 70 on a mapped mesh: 45 from the symmetric 9x9 block (the transposed
+// block of an off-diagonal pair is placed from the same result), 9 dP/dphi,
+// 9 d(s_phi L)/dF, the phi value term, the 3 diagonal phase-gradient terms and
+// (mapped) the 3 off-diagonal ones.  Each combination's 8x8 block is
 //   sum_{ijk} D(i,j,k) X0[i][a0 b0] X1[j][a1 b1] X2[k][a2 b2],
 // Xd[q][a b] = F_r,d[q][a] F_c,d[q][b], F = B1 or its derivative D1,
 // contracted one direction at a time.  Output: Ke[e][32][32].

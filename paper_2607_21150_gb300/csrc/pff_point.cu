@@ -22,7 +22,8 @@
 // maxwell-energy-dphi, prandtl-energy-dphi).  The reference-frame tangent
 // dP = (d tau_degr - tau_degr ell^T) F^-T is evaluated column by column for the
 // nine unit directions of F and for phi, scaled by the quadrature weight and
-// the parent-to-reference factors and stored in the tiled 67-word layout.
+// the parent-to-reference factors (mapped meshes: transformed to the parent
+// frame with d xi / dX) and stored in the tiled layout of kLinWords words.
 #include <cmath>
 
 #include "pff_internal.h"
