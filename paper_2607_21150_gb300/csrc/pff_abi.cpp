@@ -470,7 +470,9 @@ int pff_op_enable_df(pff_op* op, int enable) {
   if (enable && op->lin32_planes < 2) {
     float* planes = nullptr;
     PFF_CK(cudaMalloc((void**)&planes, sizeof(float) * 2 * op->lin_len));
-    PFF_CK(cudaMemset(planes, 0, sizeof(float) * 2 * op->lin_len));
+    const cudaError_t e = cudaMemset(planes, 0, sizeof(float) * 2 * op->lin_len);
+    if (e != cudaSuccess) cudaFree(planes);  // keep the operator as it was
+    PFF_CK(e);
     cudaFree(op->lin32);
     op->lin32 = planes;
     op->lin32_planes = 2;
