@@ -48,6 +48,38 @@ def test_argument_errors_without_gpu(libpff):
     pff.pff_destroy_context(ctx)
 
 
+def test_degenerate_arguments_rejected_without_gpu(libpff):
+    """Empty and degenerate inputs are refused on the host with PFF_ERR_INVALID
+    before any device work: an empty element grid, non-positive element sizes,
+    orders outside 1..4, moduli outside E > 0, -1 < nu < 0.5, a non-positive
+    time step, and hardening laws that would lower the yield stress."""
+    from paper_2607_21150_gb300 import inputs, pff
+
+    def invalid(fn, *args, match):
+        with pytest.raises(pff.PffError, match=match) as e:
+            fn(*args)
+        assert e.value.code == pff.ERR_INVALID
+
+    row = inputs.phase_vector(inputs.EX3_MATRIX)
+    bad_nu = row.copy()
+    bad_nu[3] = 0.5
+    invalid(pff.pff_create_context, bad_nu[None], 2, 1e-3, 1e-2, 0.01, 1.0, match="moduli")
+    invalid(pff.pff_create_context, row[None], 2, 1e-3, 1e-2, 0.0, 1.0, match="dt")
+    ctx = pff.pff_create_context(row[None], 2, 1e-3, 1e-2, 0.01, 1.0)
+    for nx, ny, nz in ((0, 2, 2), (2, 0, 2), (2, 2, 0)):
+        invalid(pff.pff_create_restriction, ctx, (nx, ny, nz, 0.1, 0.1, 0.1), 2, None, 1, match="empty element grid")
+    invalid(pff.pff_create_restriction, ctx, (2, 2, 2, 0.1, -0.1, 0.1), 2, None, 125, match="element sizes")
+    invalid(pff.pff_create_restriction, ctx, (2, 2, 2, 0.1, 0.1, 0.1), 5, None, 1331, match="p <= 4")
+    invalid(pff.pff_create_basis, ctx, 0, 2, match="p \\+ 1 <= q")
+    invalid(pff.pff_create_basis, ctx, 4, 6, match="p \\+ 1 <= q")
+    invalid(pff.pff_context_set_time_step, ctx, -1.0, match="dt")
+    invalid(pff.pff_context_set_hardening, ctx, 0, 100.0, 0.5 * row[11], 10.0, match="sigma_inf >= sigma0")
+    invalid(pff.pff_context_set_hardening, ctx, 1, 100.0, 2.0 * row[11], 10.0, match="phase out of range")
+    r = pff.pff_create_restriction(ctx, (1, 1, 1, 0.1, 0.1, 0.1), 1, None, 8)   # one element is valid
+    pff.pff_destroy_restriction(r)
+    pff.pff_destroy_context(ctx)
+
+
 @pytest.mark.parametrize("p,q", [(1, 2), (2, 3), (3, 4), (4, 5), (2, 5), (1, 5)])
 def test_library_basis_tables_match_oracle(libpff, orc, p, q):
     from paper_2607_21150_gb300 import inputs, pff
