@@ -84,6 +84,7 @@ CASES = {
     "box_q3_hardening": lambda: _hardened(3, 2, 2, 3, 31),
     "box_q4_curved": lambda: _mapped(3, 2, 2, 4, 41, "smooth"),
     "box_q2_distorted": lambda: _mapped(3, 3, 2, 2, 43, "vertices"),
+    "box_q4_single": lambda: _two_phase(1, 1, 1, 4, 51),      # one element: 9 of the block's 10 idle
 }
 
 
@@ -145,6 +146,31 @@ def test_df64_needs_planes(orc):
         s.apply(x, prec=pff.PFF_DF64)
     with pytest.raises(pff.PffError):
         pff.pff_assemble_diagonal(s.levels[w.mesh.p], pff.PFF_DF64, x, s.stream)
+
+
+def test_degenerate_actions(orc):
+    """x = 0 gives y = 0 exactly in every precision; with every DoF prescribed
+    the action is the identity, bit for bit."""
+    w = _two_phase(3, 2, 2, 4, 53)
+    s = Session(w, f32=True, df=True)
+    s.residual(w.z)
+    L = s.levels[w.mesh.p]
+    n = w.mesh.ndof
+    for prec, dt in ((pff.PFF_F64, torch.float64), (pff.PFF_DF64, torch.float64), (pff.PFF_F32, torch.float32)):
+        x = torch.zeros(n, dtype=dt, device="cuda")
+        y = torch.full((n,), 7.0, dtype=dt, device="cuda")
+        pff.pff_jacobian_apply(L, prec, x, y, s.stream)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(y).item() == 0
+    full = torch.ones(n, dtype=torch.uint8, device="cuda")
+    pff.pff_set_dirichlet(s.op, full, torch.zeros(n, dtype=torch.float64, device="cuda"), s.stream)
+    v = torch.from_numpy(inputs.random_vector(n, 5)).cuda()
+    for prec, xv in ((pff.PFF_F64, v), (pff.PFF_DF64, v), (pff.PFF_F32, v.float())):
+        for fn in (pff.pff_jacobian_apply, pff.pff_jacobian_transpose_apply):
+            y = torch.empty_like(xv)
+            fn(L, prec, xv, y, s.stream)
+            torch.cuda.synchronize()
+            assert torch.equal(y, xv)
 
 
 def test_diagonal(case):
