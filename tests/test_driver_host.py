@@ -1,6 +1,9 @@
 """Host logic of the adaptive load stepping (no GPU): the step controller of
 LoadStepper.advance halves a failing increment, regrows it after successes,
-never passes the target and gives up after the allowed number of cuts."""
+never passes the target and gives up after the allowed number of cuts; and,
+with a fake session and fake library calls, what LoadStepper.advance does
+around the device work."""
+import numpy as np
 import pytest
 
 from paper_2607_21150_gb300.driver import StepController, StepFailed
@@ -53,3 +56,122 @@ def test_state_stays_at_the_last_converged_factor():
 
     StepController().run(0.0, 2.0, attempt)
     assert state["f"] == 2.0
+
+
+# ---------------------------------------------------------------------------
+# LoadStepper.advance with a fake session and fake library calls: what the
+# stepper does around the device work (time step per sub-step, predictor,
+# undo of a failed sub-step, commit only after convergence, callbacks, replay).
+# ---------------------------------------------------------------------------
+class _FakeSession:
+    def __init__(self, w):
+        import torch
+        self.w = w
+        self.dev = torch.device("cpu")
+        self.ctx = "ctx"
+        self.op = "op"
+        self.mask = None
+        self.stream = None
+        self.hist = torch.zeros(3)
+
+    def solver(self, levels, **params):
+        return "solver"
+
+    def history(self, which=0):
+        return self.hist
+
+    def close(self):
+        pass
+
+
+def _fake_library(monkeypatch, limit, device_error_above=None):
+    import torch
+    from paper_2607_21150_gb300 import driver
+    log = {"dt": [], "commits": 0, "solves": []}
+
+    def set_dt(ctx, dt):
+        log["dt"].append(dt)
+
+    def axpby(prec, n, a, x, b, y, stream=None):
+        y.mul_(b).add_(a * x)
+
+    def newton(solver, z, stream=None):
+        f0, f1 = log["from"], log["to"]
+        log["solves"].append((f0, f1))
+        if device_error_above is not None and f1 - f0 > device_error_above:
+            z.add_(1e6)
+            raise driver.pff.PffError("no admissible step", driver.pff.ERR_DEVICE)
+        ok = f1 - f0 <= limit
+        z.add_(1e6 if not ok else 0.0)          # a failed solve leaves garbage behind
+        return {"converged": int(ok), "status": 0, "newton_iterations": 3, "krylov_iterations": 9}
+
+    def commit(op, stream=None):
+        log["commits"] += 1
+
+    monkeypatch.setattr(driver.pff, "pff_context_set_time_step", set_dt)
+    monkeypatch.setattr(driver.pff, "pff_vec_axpby", axpby)
+    monkeypatch.setattr(driver.pff, "pff_set_dirichlet", lambda *a, **k: None)
+    monkeypatch.setattr(driver.pff, "pff_apply_dirichlet", lambda *a, **k: None)
+    monkeypatch.setattr(driver.pff, "pff_newton_solve", newton)
+    monkeypatch.setattr(driver.pff, "pff_commit_history", commit)
+    monkeypatch.setattr(driver.pff, "pff_reaction", lambda op, top, stream=None: [0.0, 0.0, 5.0 * log["to"], 0.0])
+    return log
+
+
+def _stepper(monkeypatch, limit, **kw):
+    from paper_2607_21150_gb300 import inputs
+    from paper_2607_21150_gb300.driver import LoadStepper
+    w = inputs.cube(nx=2, p=2)
+    w.mask, w.dvals = inputs.dirichlet_tension(w.mesh, 1e-3)
+    log = _fake_library(monkeypatch, limit, **kw)
+    lsp = LoadStepper(w, session=_FakeSession(w))
+    orig = lsp._solve_to
+
+    def solve_to(factor, dt):        # remember the sub-step the fake Newton works on
+        log["from"], log["to"] = lsp.loaded, factor
+        return orig(factor, dt)
+
+    lsp._solve_to = solve_to
+    return lsp, log, w
+
+
+def test_advance_cuts_back_and_undoes_failed_substeps(monkeypatch):
+    import torch
+    lsp, log, w = _stepper(monkeypatch, limit=0.3)
+    seen = []
+    lsp.on_substep = lambda f0, f1, dt, h, st: seen.append((f0, f1, dt))
+    z0 = lsp.z.clone()
+    out = lsp.advance(1)
+    ends = [st["load"] for st in out]
+    assert ends == [0.25, 0.5, 0.75, 1.0]
+    assert log["commits"] == 4                                   # failed attempts never commit
+    dt0 = float(w.glob[3])
+    assert [s[2] for s in seen] == [0.25 * dt0] * 4
+    assert [(s[0], s[1]) for s in seen] == [(0.0, 0.25), (0.25, 0.5), (0.5, 0.75), (0.75, 1.0)]
+    # every attempt's time step is its increment times the nominal one
+    assert np.allclose(log["dt"], [dt0 * (b - a) for a, b in log["solves"]])
+    # z = start + the predictor of the converged increments only (failed solves undone)
+    assert torch.allclose(lsp.z, z0 + 1.0 * lsp.extension)
+    assert out[-1]["reaction"] == 5.0 and lsp.loaded == 1.0
+
+
+def test_device_error_counts_as_a_failed_substep(monkeypatch):
+    import torch
+    lsp, log, w = _stepper(monkeypatch, limit=1.0, device_error_above=0.5)
+    z0 = lsp.z.clone()
+    out = lsp.advance(1)
+    assert [st["load"] for st in out] == [0.5, 1.0]
+    assert torch.allclose(lsp.z, z0 + lsp.extension)
+
+
+def test_replayed_schedule_must_converge_and_end_at_the_target(monkeypatch):
+    from paper_2607_21150_gb300.driver import StepFailed
+    lsp, log, w = _stepper(monkeypatch, limit=0.3)
+    out = lsp.advance(1, schedule=[0.25, 0.5, 0.75, 1.0])
+    assert [st["load"] for st in out] == [0.25, 0.5, 0.75, 1.0]
+    assert log["solves"] == [(0.0, 0.25), (0.25, 0.5), (0.5, 0.75), (0.75, 1.0)]   # no cut-back in a replay
+    with pytest.raises(StepFailed, match="did not converge"):
+        lsp.advance(2, schedule=[2.0])
+    lsp2, _, _ = _stepper(monkeypatch, limit=1.0)
+    with pytest.raises(StepFailed, match="schedule ends"):
+        lsp2.advance(1, schedule=[0.5])
