@@ -2,9 +2,11 @@
 // GMRES with adaptive classical Gram-Schmidt refinement, p-multigrid with
 // Chebyshev smoothing), host-driven, every vector operation a device kernel.
 //
-// * Outer: Newton on the FP64 residual; each linear solve is FGMRES(m), FP64,
-//   right-preconditioned by one V-cycle (flexible because the coarse solve and
-//   the mixed-precision cycle are not exactly linear in FP64).
+// * Outer: Newton on the FP64 residual with a backtracking line search; each
+//   linear solve is FGMRES(m) with FP64 vectors and inner products, its
+//   operator the FP64 or the double-float fine action (outer_prec), right-
+//   preconditioned by one V-cycle (flexible because the coarse solve and the
+//   mixed-precision cycle are not exactly linear in FP64).
 // * V-cycle: Chebyshev(k) pre- and post-smoothing on D^-1 J of every
 //   matrix-free level (FP64, or FP32 in the mixed variant), p-restriction /
 //   prolongation between levels, and on an order-1 coarsest level an FP64
@@ -12,8 +14,10 @@
 //   Jacobi-GMRES, or GMRES preconditioned by a geometric h-multigrid V-cycle
 //   on the structured Q1 grid (the paper's algebraic coarse solver replaced
 //   by geometric coarsening, which the structured box allows).
-// * Eigenvalue bounds: lambda_max of D^-1 J per level by power iteration from a
-//   fixed seeded vector; smoothing interval [lo, hi] * lambda_max.
+// * Eigenvalue bounds: lambda_max of D^-1 J per level (and per h-level) as the
+//   spectral radius of the Hessenberg matrix of a few Arnoldi steps from a
+//   seeded random-sign vector, re-estimated every eig_every Newton iterations
+//   (0: only on the first); smoothing interval [lo, hi] * lambda_max.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
