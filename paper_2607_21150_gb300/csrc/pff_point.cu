@@ -20,10 +20,14 @@
 // prandtl-dtau-dphi, linearized-local-damage-residual,
 // history-field-linearization, energy-displacement-linearization,
 // maxwell-energy-dphi, prandtl-energy-dphi).  The reference-frame tangent
-// dP = (d tau_degr - tau_degr ell^T) F^-T is evaluated column by column for the
-// nine unit directions of F and for phi, scaled by the quadrature weight and
-// the parent-to-reference factors (mapped meshes: transformed to the parent
-// frame with d xi / dX) and stored in the tiled layout of kLinWords words.
+// dP = (d tau_degr - tau_degr ell^T) F^-T is evaluated for the nine unit
+// directions of F together: with ell = e_a (x) F^-T e_B the principal-frame
+// increment is n_a v_B^T (rows of N and of V = F^-1 N), so every Voigt
+// component v of d tau is the 3x3 product (N M_v V^T)[a][B] with a small
+// coefficient matrix M_v per branch; then the direction phi.  The words are
+// scaled by the quadrature weight and the parent-to-reference factors (mapped
+// meshes: transformed to the parent frame with d xi / dX) and stored in the
+// tiled layout of kLinWords words.
 #include <cmath>
 
 #include "pff_internal.h"
