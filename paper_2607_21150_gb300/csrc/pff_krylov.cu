@@ -1,5 +1,7 @@
-// Krylov vector kernels (FP64 inner products), precision conversions and the
-// assembled coarse (Q1) operator of the p-multigrid hierarchy.
+// Krylov vector kernels (FP64 inner products), precision conversions, the
+// assembled coarse (Q1) operator of the p-multigrid hierarchy (element
+// matrices, stencil gather, SpMV and diagonal) and the geometric h-multigrid
+// below it (Galerkin coarsening, masks, prolongation and restriction).
 #include "pff_internal.h"
 
 namespace pff {

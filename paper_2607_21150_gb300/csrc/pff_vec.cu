@@ -1,5 +1,7 @@
-// Vector kernels: Dirichlet initialisation, precision conversion, the
-// p-multigrid transfer operators and the Chebyshev smoother updates.
+// Vector kernels: Dirichlet initialisation, the FP32 (and double-float)
+// planes of the stored linearisation, the p-multigrid transfer operators, the
+// Chebyshev smoother updates, the export of the linearisation, reaction sums
+// and the geometric factors of mapped meshes.
 #include "pff_internal.h"
 
 namespace pff {
