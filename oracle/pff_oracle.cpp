@@ -173,7 +173,9 @@ template <typename T> double frob_val(const M3<T>& A) {
   double s = 0.0; for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) s += val(A.a[i][j]) * val(A.a[i][j]); return std::sqrt(s);
 }
 
-// log(I + X) for |X|_F <= 1/4 by the power series sum_k (-1)^(k+1) X^k / k.
+// log(I + X) for |X|_F <= 1/4 by the power series sum_k (-1)^(k+1) X^k / k
+// (the Hencky strain eps = log(b)/2 of Sec. 2.2 with b = I + X, taken as a
+// matrix function; X is formed without b, the log1p form of Sec. 2.2).
 // The number of terms makes |X|^(k-1) < 1e-19 so that both the value and its
 // first derivative are converged to below FP64 rounding.
 template <typename T> M3<T> log1p_series(const M3<T>& X) {
@@ -216,7 +218,7 @@ template <typename T> M3<T> sqrtm_db(const M3<T>& A) {
   }
   return Y;
 }
-// log(I + X): the series when small, else inverse scaling and squaring
+// log(I + X) (Sec. 2.2): the series when small, else inverse scaling and squaring
 // (square roots until the argument is within 1/4 of I, then 2^s times the series).
 template <typename T> M3<T> logm_1p(const M3<T>& X) {
   if (frob_val(X) <= 0.25) return log1p_series(X);
@@ -230,7 +232,8 @@ template <typename T> M3<T> logm_1p(const M3<T>& X) {
   }
   return scale(log1p_series(Xs), std::ldexp(1.0, s));
 }
-// exp(A) by scaling and squaring of the Taylor series (primal only).
+// exp(A) by scaling and squaring of the Taylor series (primal only): the
+// exponential map of the history commit, Box 1 step 4.
 M3<double> expm(const M3<double>& A) {
   double r = frob_val(A);
   int s = 0;
@@ -303,7 +306,8 @@ static const int VOIGT_I[6] = {0, 1, 2, 1, 0, 0};
 static const int VOIGT_J[6] = {0, 1, 2, 2, 2, 1};
 
 // exp(A) by scaling and squaring of the Taylor series (term count and scaling
-// decided on primal values, so that dual parts follow the same expression).
+// decided on primal values, so that dual parts follow the same expression);
+// the exponential map of Box 1 step 4 inside the differentiated path.
 template <typename T> M3<T> expm_t(const M3<T>& A) {
   double r = frob_val(A);
   int s = 0;
@@ -496,7 +500,8 @@ static void legendre(int n, double x, double& P, double& dP) {
   P = p1;
   dP = (std::fabs(x) < 1.0) ? n * (x * p1 - p0) / (x * x - 1.0) : 0.5 * x * n * (n + 1) * std::pow(x, n + 1);
 }
-// Gauss points: roots of P_Q by Newton from Chebyshev guesses; w = 2/((1-x^2) P'^2).
+// Gauss points (the quadrature of Sec. 4): roots of P_Q by Newton from
+// Chebyshev guesses; w = 2/((1-x^2) P'^2).
 static void gauss(int Q, double* x, double* w) {
   for (int i = 0; i < Q; ++i) {
     double xi = -std::cos(M_PI * (i + 0.75) / (Q + 0.5));
@@ -511,7 +516,8 @@ static void gauss(int Q, double* x, double* w) {
   std::sort(x, x + Q);
   for (int i = 0; i < Q; ++i) { double P, dP; legendre(Q, x[i], P, dP); w[i] = 2.0 / ((1.0 - x[i] * x[i]) * dP * dP); }
 }
-// GLL points: -1, +1 and the roots of P_p' (Newton with P'' from Legendre's equation).
+// GLL points (the nodes of the Sec. 4 elements): -1, +1 and the roots of P_p'
+// (Newton with P'' from Legendre's equation).
 static void gll(int p, double* x) {
   x[0] = -1.0; x[p] = 1.0;
   for (int i = 1; i < p; ++i) {
@@ -528,7 +534,8 @@ static void gll(int p, double* x) {
   if (p % 2 == 0) x[p / 2] = 0.0;
 }
 // Lagrange basis l_a(t) on nodes xn[0..P-1] (product formula) and l_a'(t)
-// (sum over the dropped factor of the remaining products).
+// (sum over the dropped factor of the remaining products): the 1D factors of
+// the tensor-product basis B_I, B_xi of Sec. 4.
 static double lagr(const double* xn, int P, int a, double t) {
   double r = 1.0;
   for (int b = 0; b < P; ++b) if (b != a) r *= (t - xn[b]) / (xn[a] - xn[b]);
@@ -671,9 +678,11 @@ static ElemBasis basis_of(const Problem& pr, long long e) {
   return pr.X ? elem_basis_geo(pr.m, pr.X, e) : pr.eb;
 }
 
-// One element: residual r_e[f*P3+a], optionally the pointwise tangents
-// Dh[q][16][16] (rows: f0 (4), f1 (12); cols: values (4), gradients (12)),
-// trial history and flags.
+// One element: residual r_e[f*P3+a] (Eq. matrix-free-residual-compact, full
+// quadrature: every 3D basis function at every Gauss point), optionally the
+// pointwise tangents Dh[q][16][16] (rows: f0 (4), f1 (12); cols: values (4),
+// gradients (12); Eq. matrix-free-jacobian, by dual numbers), trial history
+// (Box 1 step 4) and flags.
 static void element_eval(const Problem& pr, const ElemBasis& eb, long long e, double* re, double* Dh,
                          double* hist_new, uint8_t* flags, double* margins) {
   const Mesh& m = pr.m;
@@ -886,7 +895,8 @@ int orc_expm(const double* A, double* E) {
   return 0;
 }
 
-// Global assembly.  dims = {nx,ny,nz,p,Q}; h = {hx,hy,hz}; z [4][nn];
+// Global assembly (Sec. 4: the element operators summed with E^T P^T; here
+// explicitly into CSR).  dims = {nx,ny,nz,p,Q}; h = {hx,hy,hz}; z [4][nn];
 // hist [15][nq] (SoA); phase [nq]; mask [4][nn] (uint8, may be NULL);
 // dvals [4][nn] Dirichlet values (may be NULL).  Produces the residual
 // r [4][nn] (masked rows r = z - ubar), trial history [15][nq], flags [nq],
@@ -1070,7 +1080,8 @@ int orc_sample_rows(const int* dims, const double* h, const double* phase_params
   return 0;
 }
 
-// p-prolongation from order pc to order pf on the same element grid: entry
+// p-prolongation of the multigrid of Sec. 5 from order pc to order pf on the
+// same element grid: entry
 // P[fine node, coarse node] = coarse Lagrange basis at the fine GLL node.
 // Returns the number of entries written as COO (rows, cols, vals), per field
 // block 0 (the 4 fields repeat the same block).  Call with rows == NULL to size.
