@@ -20,6 +20,18 @@ Functions and the passages they follow:
 * ``coarse_operator``  -- Galerkin product P^T A P (equal to rediscretisation at the fine
                           Gauss points).
 * ``chebyshev``        -- textbook Chebyshev iteration on D^-1 A (Saad, Alg. 12.1).
+* ``masked_prolongation``, ``vcycle`` -- Dirichlet-masked transfers and the textbook
+                          multigrid V-cycle of Sec. 5 (Chebyshev smoothing, R = P^T).
+* ``h_prolongation``, ``h_coarse_mask`` -- trilinear full coarsening of the structured
+                          order-1 grid (the geometric coarse solver standing in for the
+                          paper's algebraic one, Sec. 5).
+* ``newton``           -- Newton's method with direct solves (Sec. 5, exact linear solves).
+* ``load_steps``, ``adjoint_gradient``, ``point_partials`` -- load-step sequences with
+                          history commit (Box 1 step 4) and the discrete adjoint of a
+                          reaction-curve misfit (assembled transposes, dual-number partials).
+* ``geometry``         -- nodal coordinates of a mapped mesh: isoparametric element maps
+                          of the Sec. 4 basis (the box is the special case).
+* ``spmv``, ``lagrange``, ``logm1p``, ``expm`` -- the compiled loops exposed for pins.
 """
 from __future__ import annotations
 

@@ -8,7 +8,9 @@
 // What it computes (paper: "Matrix-free phase-field modeling of fracture in
 // micromechanical testing simulations of inelastic materials"):
 //   * the pointwise Peric-Dettmer update of Box 1 with the Hooke, Maxwell and
-//     perfectly plastic Prandtl branches (Sec. 2.3, Eqs. hencky-tau-current,
+//     Prandtl branches, the last perfectly plastic or hardening (linear +
+//     Voce, Eq. plasticity-strain-hardening-law, Box 2 local Newton carried
+//     in dual numbers) (Sec. 2.3, Eqs. hencky-tau-current,
 //     viscoelasticity-deviatoric-strain-update-hencky,
 //     plasticity-deviatoric-strain-update-perfect), degraded in series by the
 //     fracture element of Sec. 3 (Eqs. linear-Psi-plus,
