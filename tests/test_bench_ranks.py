@@ -85,3 +85,15 @@ def test_reference_arm_two_ranks():
     assert d["impl"] == "reference" and d["n_gpus"] == 2
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_reference_config_matches_the_native_label():
+    """The reference arm reports the native arm's workload label (computed from
+    the mesh alone) and samples a 4^3 box of the same generator."""
+    import bench
+    from paper_2607_21150_gb300 import inputs
+    assert bench.workload_label("compress_q4") == \
+        "compress_q4: Q4 64x64x64 elements, 67898372 DoF, 32768000 quadrature points"
+    m = inputs.tension_q4().mesh
+    assert bench.workload_label("tension_q4") == \
+        f"tension_q4: Q{m.p} {m.nx}x{m.ny}x{m.nz} elements, {m.ndof} DoF, {m.nq} quadrature points"
