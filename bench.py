@@ -116,16 +116,16 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- CPU oracle
-def oracle_sample(seconds_budget: float = 20.0):
+def oracle_sample(name: str = "compress_q4", seconds_budget: float = 20.0):
     """The FP64 oracle as it stands on the host cores, on a bounded sample of the
-    Q4 workload: a 4x4x4-element sub-box of the same material/state recipe.
+    Q4 workload `name`: a 4x4x4-element box of the same generator and state recipe.
     Times the CSR assembly (element matrices by full quadrature) once and the
     CSR SpMV (the oracle's Jacobian action) repeatedly."""
     import oracle
     from paper_2607_21150_gb300 import inputs
     oracle.build()
     n = 4
-    w = inputs.compress_q4(n=n)
+    w = getattr(inputs, name)(n=n)
     rng = np.random.default_rng(7)
     m = w.mesh
     h = min(m.h) / m.p
@@ -165,7 +165,7 @@ def oracle_sample(seconds_budget: float = 20.0):
     t_res = time.perf_counter() - t0
     # one load step from the unloaded state by Newton with direct solves, on a
     # 2x2x2-element sub-box (the 4^3 one takes minutes in the sparse direct solver)
-    wn = inputs.compress_q4(n=2)
+    wn = getattr(inputs, name)(n=2)
     mkn = wn.mask.astype(bool)
     wn.z = np.zeros((4, wn.mesh.nn))
     wn.z[mkn] = wn.dvals[mkn]
@@ -533,7 +533,7 @@ def run_native(args):
     apply_mapped = (apply_config(args.config, args.steps, args.warmup, mapped="smooth")
                     if args.newton != "none" else None)
     adjoint = adjoint_timing(args.adjoint_steps) if args.adjoint_steps > 0 else None
-    cpu = oracle_sample()
+    cpu = oracle_sample(args.config)
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot64 / args.steps, "higher_is_better": True, "scaling": "weak",
