@@ -88,3 +88,32 @@ def test_element_offsets_structured_map():
     for e in (0, 5, m.nel - 1):
         pts = X[off[e]]
         assert np.allclose(pts.max(0) - pts.min(0), m.h)       # one element's box
+
+
+def test_adjoint_parameter_vector_layout():
+    """theta = (E_inf, nu_inf, sigma0, eta_d, Gc, l0) per phase: the slots name
+    the Table 2 entries they claim, with_params inverts params_of, and the
+    oracle's own copy of the layout agrees."""
+    import oracle
+    ph = np.stack([I.phase_vector(I.EX3_MATRIX), I.phase_vector(I.EX3_PARTICLE_ADJ)])
+    th = I.params_of(ph)
+    d = I.EX3_MATRIX
+    assert list(th[:6]) == [d["E0"], d["nu0"], d["prandtl"][2], d["maxwell"][2], d["Gc"], d["l0"]]
+    assert np.array_equal(I.with_params(ph, th), ph)
+    th2 = th * np.arange(1, 13)
+    assert np.array_equal(I.params_of(I.with_params(ph, th2)), th2)
+    assert np.array_equal(oracle.get_params(ph), th)
+    assert np.array_equal(oracle.set_params(ph, th2), I.with_params(ph, th2))
+
+
+def test_twin_target_and_hardening_rows():
+    th = np.arange(1.0, 13.0)
+    a, b = I.twin_target(th), I.twin_target(th)
+    assert np.array_equal(a, b) and not np.array_equal(a, th)
+    f = a / th
+    assert np.all(f > np.exp(-0.5)) and np.all(f < np.exp(0.5))      # lognormal, sigma 0.1
+    ph = np.stack([I.phase_vector(I.EX3_MATRIX), I.phase_vector(I.EX3_PARTICLE)])
+    hr = I.harden(ph, 2000.0, 800.0, 40.0)
+    assert hr.shape == (2, 15) and np.array_equal(hr[:, :12], ph)
+    assert list(hr[0, 12:]) == [2000.0, 800.0, 40.0]                  # the phase with a Prandtl branch
+    assert list(hr[1, 12:]) == [0.0, ph[1, 11], 0.0]                  # perfect plasticity row otherwise
