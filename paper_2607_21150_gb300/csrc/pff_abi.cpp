@@ -521,6 +521,12 @@ int pff_op_set_geometry(pff_op* op, const double* X, void* stream) {
     return PFF_OK;
   }
   const long long nn = op->mesh.nn, nq = op->nq;
+  // the status word reports inverted elements here; bits still pending from
+  // earlier calls are set aside and put back afterwards
+  int h0 = 0;
+  PFF_CK(cudaStreamSynchronize(st));
+  PFF_CK(cudaMemcpy(&h0, op->status, sizeof(int), cudaMemcpyDeviceToHost));
+  PFF_CK(cudaMemset(op->status, 0, sizeof(int)));
   if (!op->geo) PFF_CK(cudaMalloc((void**)&op->geo, sizeof(double) * 10 * nq));
   // parent Jacobians dX_f / dxi_al at every Gauss point: an eval of the
   // coordinates (fourth field zero) with unit parent-to-reference factors
@@ -545,8 +551,8 @@ int pff_op_set_geometry(pff_op* op, const double* X, void* stream) {
   if (e != cudaSuccess) return fail(PFF_ERR_CUDA, std::string("pff_op_set_geometry: ") + cudaGetErrorString(e));
   int h = 0;
   PFF_CK(cudaMemcpy(&h, op->status, sizeof(int), cudaMemcpyDeviceToHost));
+  PFF_CK(cudaMemcpy(op->status, &h0, sizeof(int), cudaMemcpyHostToDevice));
   if (h & 2) {
-    PFF_CK(cudaMemset(op->status, 0, sizeof(int)));
     cudaFree(op->geo);
     op->geo = nullptr;
     return fail(PFF_ERR_INVALID, "pff_op_set_geometry: det J <= 0 at some Gauss point (inverted element)");
