@@ -100,7 +100,10 @@ typedef struct {
   double hx, hy, hz;
 } pff_box;
 
+/* Text of the last failing call on this thread (thread-local; empty if none;
+ * valid until the next failing call on the thread). */
 const char* pff_last_error_message(void);
+/* ABI version of this library (1). */
 int pff_version(void);
 
 /* Context: parameters of the constitutive model (host data, copied). */
@@ -360,6 +363,10 @@ int pff_vec_axpby(pff_prec prec, int64_t n, double a, const void* x, double b, v
 int pff_commit_history(pff_op* op, void* stream);
 /* Copies of the per-point data (device destinations). which = 0 committed, 1 trial. */
 int pff_get_history(pff_op* op, int which, double* hist, void* stream);
+/* Per-point decision flags of the last pff_residual (uint8 [N_q], device
+ * destination): bit 0 the Prandtl branch yielded (Box 1 step 2), bit 1 the
+ * crack-driving history was raised (psi+ > H_n), bit 2 the tensile branch of
+ * the energy split (theta >= 0). */
 int pff_get_flags(pff_op* op, uint8_t* flags, void* stream);
 /* Copy of the stored linearisation in the canonical point order: out[67][N_q]
  * (device FP64); for tests and diagnostics. */
