@@ -1,5 +1,7 @@
 """Load-stepping simulation of a workload: python -m paper_2607_21150_gb300.simulate
---workload notched_q3 --steps 40 [--fp64] [--max-cuts 6].
+--workload notched_q3 --steps 40 [--fp64] [--max-cuts 6] [--verbose]
+[--param NAME=VALUE ...] (NAME a field of pff_solver_params, e.g. cheb_degree,
+krylov_rtol, eig_every, coarse_maxit).
 
 Runs LoadStepper.advance for load steps 1..steps (adaptive cut-back) and prints
 one JSON line per load step (reaction on the loaded face, sub-steps, Newton and
@@ -20,17 +22,32 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None, help="load steps (workload default if omitted)")
     ap.add_argument("--fp64", action="store_true", help="FP64 multigrid levels instead of FP32")
     ap.add_argument("--max-cuts", type=int, default=6)
+    ap.add_argument("--verbose", action="store_true", help="the solver's per-iteration log on stderr")
+    ap.add_argument("--param", action="append", default=[], metavar="NAME=VALUE",
+                    help="solver parameter, a field of pff_solver_params (repeatable)")
     args = ap.parse_args(argv)
+    import ctypes
+
     import torch
-    from . import inputs
+    from . import inputs, pff
     from .driver import LoadStepper, StepFailed
+    fields = dict(pff.pff_solver_params._fields_)
+    params = {}
+    for kv in args.param:
+        name, _, val = kv.partition("=")
+        if name not in fields or not val:
+            ap.error(f"--param {kv}: expected NAME=VALUE with NAME one of {', '.join(fields)}")
+        params[name] = int(val) if fields[name] is ctypes.c_int else float(val)
+    if args.verbose:
+        params["verbose"] = 1
     make = getattr(inputs, args.workload)
     w = make() if args.n is None else make(n=args.n)
     steps = args.steps or int(w.meta.get("steps", 10))
     t0 = time.perf_counter()
-    lsp = LoadStepper(w, mixed=not args.fp64, max_cuts=args.max_cuts)
+    lsp = LoadStepper(w, mixed=not args.fp64, max_cuts=args.max_cuts, **params)
     print(json.dumps({"workload": args.workload, "ndof": w.mesh.ndof, "nq": w.mesh.nq, "steps": steps,
-                      "mixed": not args.fp64, "setup_s": time.perf_counter() - t0}), flush=True)
+                      "mixed": not args.fp64, "solver_params": params,
+                      "setup_s": time.perf_counter() - t0}), flush=True)
     t_all = time.perf_counter()
     status = "completed"
     for k in range(1, steps + 1):

@@ -15,7 +15,7 @@ class _Fake:
     made = []
 
     def __init__(self, w, mixed=True, max_cuts=6, **kw):
-        self.mixed, self.max_cuts = mixed, max_cuts
+        self.mixed, self.max_cuts, self.kw = mixed, max_cuts, kw
         self.history = []
         _Fake.made.append(self)
 
@@ -44,3 +44,18 @@ def test_cli_lines_and_clean_stop(monkeypatch, capsys):
     assert steps[1]["newton_iterations"] == 7 and steps[1]["krylov_iterations"] == 35
     assert tail["status"].startswith("stopped at step 3") and tail["attempts"] == 4
     assert _Fake.made[-1].mixed is False and _Fake.made[-1].max_cuts == 3
+
+
+def test_cli_solver_parameters(monkeypatch, capsys):
+    monkeypatch.setattr(driver, "LoadStepper", _Fake)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    rc = simulate.main(["--workload", "tension_q4", "--n", "2", "--steps", "1", "--verbose",
+                        "--param", "cheb_degree=6", "--param", "krylov_rtol=1e-4", "--param", "eig_every=0"])
+    assert rc == 0
+    kw = _Fake.made[-1].kw
+    assert kw == {"cheb_degree": 6, "krylov_rtol": 1e-4, "eig_every": 0, "verbose": 1}
+    assert isinstance(kw["cheb_degree"], int) and isinstance(kw["krylov_rtol"], float)
+    head = json.loads(capsys.readouterr().out.splitlines()[0])
+    assert head["solver_params"]["cheb_degree"] == 6
+    with pytest.raises(SystemExit):
+        simulate.main(["--workload", "tension_q4", "--n", "2", "--param", "no_such=1"])
