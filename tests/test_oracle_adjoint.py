@@ -28,3 +28,23 @@ def test_oracle_adjoint_matches_central_differences(orc):
         tm[i] -= h
         fd = (loss(tp) - loss(tm)) / (2 * h)
         assert abs(g[i] - fd) <= 1e-6 * abs(fd) + 1e-9 * np.abs(g * theta0).max() / abs(theta0[i]), (i, g[i], fd)
+
+
+def test_oracle_adjoint_on_a_curved_mesh(orc):
+    """The same check on a smoothly curved mesh (the geometric factors enter the
+    residual, the pull-back and the reaction), for four parameters."""
+    w = _adjoint_box()
+    w.X = inputs.mapped_coords(w.mesh, "smooth", amp=0.15)
+    top = inputs.top_face_mask(w.mesh)
+    theta0 = orc.get_params(w.phases)
+    nsteps = 3
+    target, _, _ = orc.load_steps(w, inputs.twin_target(theta0), nsteps, top)
+    g, F = orc.adjoint_gradient(w, theta0, nsteps, top, target)
+    loss = lambda th: float(np.sum((orc.load_steps(w, th, nsteps, top)[0] - target) ** 2))
+    for i in (0, 2, 4, 11):   # E_inf, sigma0, Gc of the matrix; l0 of the particle
+        h = 1e-5 * abs(theta0[i])
+        tp, tm = theta0.copy(), theta0.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (loss(tp) - loss(tm)) / (2 * h)
+        assert abs(g[i] - fd) <= 1e-6 * abs(fd) + 1e-9 * np.abs(g * theta0).max() / abs(theta0[i]), (i, g[i], fd)
