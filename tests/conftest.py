@@ -1,3 +1,5 @@
+"""Test configuration: the repository root on sys.path, the `gpu` marker
+(tests that need a CUDA GPU), and the shared fixtures below."""
 import os
 import sys
 

@@ -1,6 +1,7 @@
-"""Pin of the oracle's discrete adjoint: the gradient of a reaction-curve misfit
-through three load steps (history carried between steps) equals central finite
-differences of the loss for all twelve per-phase parameters."""
+"""Pins of the oracle's discrete adjoint: the gradient of a reaction-curve
+misfit through three load steps (history carried between steps) equals central
+finite differences of the loss, for all twelve per-phase parameters on the box,
+and for four of them on a curved mesh and with a hardening Prandtl branch."""
 import numpy as np
 
 from paper_2607_21150_gb300 import inputs
