@@ -35,7 +35,7 @@
 //     activity, sign of the volumetric strain) are taken on primal values and
 //     frozen, exactly as the linearisation of Appendix C does.
 //
-// Readings of points the paper leaves open (listed in the design doc as well):
+// Readings of points the paper leaves open:
 //   R1  theta = ln J is the volumetric strain of every branch and decides the
 //       Amor split; each branch's deviator uses its own trace.
 //   R4  the history is active iff psi+ > H_n (strict).
