@@ -93,3 +93,21 @@ def test_library_basis_tables_match_oracle(libpff, orc, p, q):
     assert np.abs(Dc @ B - oD).max() < 1e-12
     pff.pff_destroy_basis(b)
     pff.pff_destroy_context(ctx)
+
+
+def test_hardening_rows_through_the_binding(libpff):
+    """15-column phase rows carry the hardening law to pff_context_set_hardening
+    (host only): valid rows are accepted, a law that would lower the yield
+    stress is refused, and perfect-plasticity rows make no call."""
+    from paper_2607_21150_gb300 import inputs, pff
+    ph = np.stack([inputs.phase_vector(inputs.EX3_MATRIX), inputs.phase_vector(inputs.EX3_PARTICLE)])
+    ctx = pff.pff_create_context(inputs.harden(ph, 2000.0, 800.0, 40.0), 1, 1e-3, 1e-2, 0.01, 1.0)
+    pff.pff_destroy_context(ctx)
+    perfect = inputs.harden(ph, 0.0, 0.0, 0.0)
+    perfect[:, 13] = perfect[:, 11]                                 # (0, sigma0, 0): perfect plasticity
+    ctx = pff.pff_create_context(perfect, 1, 1e-3, 1e-2, 0.01, 1.0)
+    pff.pff_destroy_context(ctx)
+    bad = inputs.harden(ph, 2000.0, 0.5 * ph[0, 11], 40.0)
+    with pytest.raises(pff.PffError, match="sigma_inf >= sigma0") as e:
+        pff.pff_create_context(bad, 1, 1e-3, 1e-2, 0.01, 1.0)
+    assert e.value.code == pff.ERR_INVALID
