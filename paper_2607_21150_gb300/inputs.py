@@ -182,10 +182,32 @@ def mapped_coords(m: Mesh, kind: str = "smooth", amp: float = 0.1, seed: int = 0
       (seeded), the element's GLL nodes placed by trilinear interpolation of
       its eight vertices (straight-edged hexahedra, conforming faces);
     * ``smooth``: X'_d = X_d + amp h_d sin(2 pi X_{d+1} / L_{d+1}) sin(pi X_{d+2} / L_{d+2}),
-      evaluated at every node (curved elements)."""
+      evaluated at every node (curved elements);
+    * ``cylinder``: every cross-section square mapped onto its inscribed disk
+      (radius min(Lx, Ly) / 2) by the elliptical grid map
+      x' = u sqrt(1 - v^2 / 2), y' = v sqrt(1 - u^2 / 2) of u, v in [-1, 1]
+      (a single patch: the corner angles open to 180 degrees, so the Jacobian
+      vanishes at the four corner lines and only Gauss points see it positive);
+    * ``dogbone``: the cross-section scaled about its centre by
+      s(z) = 1 - amp (1 + cos(2 pi (z / Lz - 1/2))) / 2, a smooth neck of
+      relative depth amp at mid-length (exact volume Lx Ly Lz (1 - amp + 3 amp^2 / 8))."""
     X = node_coords(m)
     if kind == "affine":
         return np.ascontiguousarray((X @ np.asarray(M, dtype=float).T).T)
+    if kind in ("cylinder", "dogbone"):
+        Lx, Ly, Lz = m.L
+        cx, cy = 0.5 * Lx, 0.5 * Ly
+        Y = X.copy()
+        if kind == "cylinder":
+            R = 0.5 * min(Lx, Ly)
+            u, v = 2.0 * X[:, 0] / Lx - 1.0, 2.0 * X[:, 1] / Ly - 1.0
+            Y[:, 0] = cx + R * u * np.sqrt(1.0 - 0.5 * v * v)
+            Y[:, 1] = cy + R * v * np.sqrt(1.0 - 0.5 * u * u)
+        else:
+            sz = 1.0 - amp * 0.5 * (1.0 + np.cos(2.0 * np.pi * (X[:, 2] / Lz - 0.5)))
+            Y[:, 0] = cx + sz * (X[:, 0] - cx)
+            Y[:, 1] = cy + sz * (X[:, 1] - cy)
+        return np.ascontiguousarray(Y.T)
     h = np.array(m.h)
     L = np.array(m.L)
     if kind == "smooth":
