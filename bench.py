@@ -43,6 +43,30 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def pipe_rates(stream, iters: int = 20000):
+    """FP64 FMA, FP64 tensor-core (mma.sync m8n8k4) and FP32 FMA throughput of
+    this GPU at its current clocks, by the library's pipe-rate probe: best of
+    three launches of 8 blocks of 256 threads per SM, CUDA events."""
+    import torch
+    from paper_2607_21150_gb300 import pff
+    out = {}
+    blocks, threads = 152 * 8, 256
+    sink = torch.zeros(blocks * threads, dtype=torch.float64, device="cuda")
+    for name, kind, it in (("dfma", pff.PFF_PROBE_DFMA, iters), ("dmma", pff.PFF_PROBE_DMMA, iters // 4),
+                           ("ffma", pff.PFF_PROBE_FFMA, 8 * iters)):
+        pff.pff_probe_pipe(kind, 64, blocks, threads, sink, stream)
+        best = 0.0
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fl = pff.pff_probe_pipe(kind, it, blocks, threads, sink, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, fl / (a.elapsed_time(b) / 1e3) / 1e12)
+        out[name + "_tflops"] = best
+    return out
+
+
 def make_workload(name: str, seed: int = 0):
     from paper_2607_21150_gb300 import inputs
     w = getattr(inputs, name)()
@@ -436,13 +460,19 @@ def run_native(args):
     def applydf():
         pff.pff_jacobian_apply(L, pff.PFF_DF64, x64, ydf, stream)
 
-    def timed(fn, K, W):
+    launches = {}
+
+    def timed(fn, K, W, label=None):
+        """W untimed calls, then K calls bracketed by CUDA events on the launching
+        stream (barrier and synchronize on both sides); also counts the
+        library's kernel launches inside the timed calls."""
         for _ in range(W):
             fn()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+        n0 = pff.pff_kernel_launches()
         wall0 = time.perf_counter()
         for a, b in evs:
             a.record(stream)
@@ -452,24 +482,18 @@ def run_native(args):
         if world > 1:
             dist.barrier()
         wall = time.perf_counter() - wall0
+        if label:
+            launches[label] = pff.pff_kernel_launches() - n0
         per = [a.elapsed_time(b) for a, b in evs]
         return sum(per), per, wall
 
     with ClockSampler() as clk:
-        tot64, per64, wall64 = timed(apply64, args.steps, args.warmup)
+        tot64, per64, wall64 = timed(apply64, args.steps, args.warmup, "fp64")
+    with ClockSampler() as clk_probe:
+        rates = pipe_rates(stream)
     tot32, per32, _ = timed(apply32, args.steps, args.warmup)
     totdf, _, _ = timed(applydf, args.steps, args.warmup)
     df_rel = float(torch.linalg.norm(ydf - y64) / torch.linalg.norm(y64))
-    # dominant kernel alone (the fused element kernel, without the y-init kernel)
-    y64.zero_()
-    ker = []
-    for _ in range(max(3, args.steps)):
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        apply64()
-        b.record(stream)
-        ker.append((a, b))
-    torch.cuda.synchronize()
 
     # end to end through the C ABI with host buffers: pinned x -> device, apply, y -> pinned host
     xh = x64.cpu().pin_memory()
@@ -482,7 +506,7 @@ def run_native(args):
         pff.pff_jacobian_apply(L, pff.PFF_F64, xd, yd, stream)
         yh.copy_(yd, non_blocking=True)
 
-    tot_e2e, _, _ = timed(e2e_step, args.steps, 1)
+    tot_e2e, _, _ = timed(e2e_step, args.steps, 3, "e2e")
 
     # p-multigrid level actions on the same quadrature points (Galerkin levels)
     levels = {}
@@ -546,7 +570,10 @@ def run_native(args):
                      "frac": achieved_flops / FP64_PEAK_TFLOPS, "traffic": traffic64,
                      "traffic_source": "ncu dram bytes per element at 16^3 Q4 x elements" if traffic64 else None,
                      "algorithmic_bytes": bytes64,
-                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2070 MHz (unit count measured by an FMA-chain probe)",
+                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived from unit "
+                                    "counts and the maximum clock; pipe_rates has the live probe)",
+                     "pipe_rates": {**rates, "clocks": clk_probe.summary(),
+                                    "frac_of_probe_dfma": achieved_flops / rates["dfma_tflops"]},
                      "hbm_frac": bytes64 / t_apply / 1e9 / hbm_peak, "hbm_peak_gbs": hbm_peak,
                      "hbm_peak_source": src},
         "fp32_level_apply": {"gdofs": ndof / t32 / 1e9, "ms": t32 * 1e3, "traffic": traffic32,
@@ -565,7 +592,9 @@ def run_native(args):
         "adjoint": adjoint,
         "e2e": {"value": whole_job_rate(world, ndof, args.steps, tot_e2e), "unit": "GDoF/s",
                 "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches["fp64"],
+        "gpu_launches_note": "libpff kernels launched inside the timed FP64-action region (pff_kernel_launches "
+                             "before and after it); per action: the y initialisation and the fused element kernel",
         "cpu_baseline": {"value": cpu["gdofs"], "unit": "GDoF/s", "cores": cpu["threads"], "kind": "oracle",
                          "sample": f"{cpu['nel']}-element Q4 sub-box ({cpu['ndof']} DoF) of the same workload; "
                                    f"CSR SpMV of the oracle's assembled Jacobian "

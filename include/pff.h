@@ -105,6 +105,10 @@ typedef struct {
 const char* pff_last_error_message(void);
 /* ABI version of this library (1). */
 int pff_version(void);
+/* Kernels this library has launched in this process so far (all devices and
+ * host threads; counted on the host at each launch).  The difference across a
+ * region of calls is the number of kernels those calls launched. */
+int64_t pff_kernel_launches(void);
 
 /* Context: parameters of the constitutive model (host data, copied). */
 int pff_create_context(pff_ctx** ctx, const pff_problem* problem);
@@ -240,8 +244,10 @@ int pff_chebyshev_smooth_noalloc(pff_level* level, pff_prec prec, int degree, do
 /* ----------------------------------------------------------------------------
  * Newton-Krylov solver with p-multigrid preconditioning (Sec. 5: Newton, GMRES
  * with adaptive classical Gram-Schmidt refinement, p-multigrid with Chebyshev
- * smoothing; the paper's AMG coarse solve is replaced by Chebyshev-Jacobi on the
- * assembled order-1 Galerkin operator).  Outer iterations, Krylov vectors and
+ * smoothing; the paper's AMG coarse solve is replaced by GMRES on the assembled
+ * order-1 Galerkin operator, preconditioned by a geometric h-multigrid V-cycle
+ * on its structured grid (coarse_solver 2, the default; Jacobi-preconditioned
+ * GMRES and Chebyshev-Jacobi remain as 1 and 0)).  Outer iterations, Krylov vectors and
  * inner products are FP64; with mixed = 1 the level operators and smoothers run
  * in FP32 (stored tangent copied by pff_op_enable_f32), the coarsest assembled
  * solve stays FP64.
@@ -375,6 +381,21 @@ int pff_get_linearization(pff_op* op, double* out, void* stream);
 /* Synchronises `stream`, returns the kernel status bits accumulated since the
  * last call in *status and clears them. */
 int pff_get_status(pff_op* op, void* stream, int* status);
+
+/* Pipe-rate probe (measurement aid; the paper has no counterpart): launches
+ * `blocks` x `threads` threads that each run 8 independent dependent chains of
+ * `iters` multiply-adds on one arithmetic pipe, and returns in *flops the
+ * floating-point operations that launch performs, so that flops / (launch
+ * time) is the pipe's throughput on this GPU at its current clocks:
+ *   PFF_PROBE_DFMA  FP64 FMA (2 flop each), PFF_PROBE_FFMA  FP32 FMA,
+ *   PFF_PROBE_DMMA  FP64 tensor-core mma.sync m8n8k4 (512 flop per warp op).
+ * sink: device FP64 [blocks * threads] receiving the chains' final sums
+ * (keeps them live).  Asynchronous on the stream; iters a multiple of 4,
+ * threads a multiple of 32 in [32, 1024]; PFF_ERR_INVALID otherwise. */
+#define PFF_PROBE_DFMA 0
+#define PFF_PROBE_FFMA 1
+#define PFF_PROBE_DMMA 2
+int pff_probe_pipe(int kind, int64_t iters, int blocks, int threads, double* sink, double* flops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -32,6 +32,9 @@ Functions and the passages they follow:
 * ``geometry``         -- nodal coordinates of a mapped mesh: isoparametric element maps
                           of the Sec. 4 basis (the box is the special case).
 * ``spmv``, ``lagrange``, ``logm1p``, ``expm`` -- the compiled loops exposed for pins.
+* ``crack_c0``, ``s_phi``, ``psi_c`` -- the crack-density normalisation, the phase-field
+                          residual scale (Eq. damage-residual-scaling) and the AT1
+                          threshold (Sec. 3.1), derived here from the phase rows.
 """
 from __future__ import annotations
 
@@ -116,6 +119,27 @@ def phase_rows(phases):
     out[:, :12] = ph
     out[:, 13] = ph[:, 11]
     return out
+
+
+def crack_c0(at: int) -> float:
+    """Normalisation c0 = 4 int_0^1 sqrt(alpha(s)) ds of the crack density
+    (Sec. 3.1): alpha = s (AT1) gives 4 * 2/3 = 8/3, alpha = s^2 (AT2) gives 4 * 1/2 = 2."""
+    return 4.0 * (2.0 / 3.0 if at == 1 else 0.5)
+
+
+def s_phi(matrix_row, at: int) -> float:
+    """Phase-field residual scale of Eq. damage-residual-scaling from the matrix
+    phase's row (``phase_rows`` layout: Gc, l0, E_inf first): E c0 / (2 l0 Gc)."""
+    Gc, l0, E = float(matrix_row[0]), float(matrix_row[1]), float(matrix_row[2])
+    return E * crack_c0(at) / (2.0 * l0 * Gc)
+
+
+def psi_c(phase_row) -> float:
+    """AT1 elastic threshold of Sec. 3.1: the crack-driving energy below which the
+    homogeneous AT1 local residual keeps phi = 0, psi_c = 3 Gc / (16 l0) (from
+    g'(0) psi_c + Gc alpha'(0) / (c0 l0) = 0 with g'(0) = -2, alpha' = 1, c0 = 8/3)."""
+    Gc, l0 = float(phase_row[0]), float(phase_row[1])
+    return Gc / (crack_c0(1) * l0) / 2.0
 
 
 def geometry(w):

@@ -23,6 +23,10 @@ from .driver import LoadStepper
 from .inputs import Workload, top_face_mask, with_params
 
 
+class StaleCheckpoints(RuntimeError):
+    """backward() was asked for a forward run whose checkpoints were replaced."""
+
+
 class ReactionCurveRunner:
     def __init__(self, w: Workload, nsteps: int, levels=None, mixed: bool = False, newton_rtol: float = 1e-11,
                  krylov_rtol: float = 1e-8, adjoint_rtol: float = 1e-10):
@@ -34,6 +38,7 @@ class ReactionCurveRunner:
         self.krylov_rtol = krylov_rtol
         self.adjoint_rtol = adjoint_rtol
         self.lsp = None
+        self.generation = 0   # forward runs so far; the checkpoints belong to the last one
 
     def forward(self, theta, schedule=None) -> np.ndarray:
         if self.lsp is not None:
@@ -50,6 +55,7 @@ class ReactionCurveRunner:
             self.subs.append({"z": self.lsp.z.clone(), "h": hist_before, "dt": dt, "f1": f1})
 
         self.lsp.on_substep = record
+        self.generation += 1
         F, self.schedule = [], []
         for n in range(1, self.nsteps + 1):
             out = self.lsp.advance(n, None if schedule is None else schedule[n - 1])
@@ -57,7 +63,15 @@ class ReactionCurveRunner:
             F.append(out[-1]["reaction"])
         return np.array(F)
 
-    def backward(self, dLdF) -> np.ndarray:
+    def backward(self, dLdF, generation: int | None = None) -> np.ndarray:
+        """dLoss/dtheta of the last forward run; `generation` (the value of
+        self.generation right after the forward run it belongs to) must be that
+        run, else StaleCheckpoints."""
+        if generation is not None and generation != self.generation:
+            raise StaleCheckpoints(f"backward for forward run {generation}, but the runner holds the checkpoints "
+                                   f"of run {self.generation}: repeat the forward run before differentiating it")
+        if self.lsp is None:
+            raise StaleCheckpoints("backward without a forward run (or after close())")
         s = self.lsp.s
         nq = self.w.mesh.nq
         grad = np.zeros(6 * len(self.w.phases))
@@ -78,19 +92,23 @@ class ReactionCurveRunner:
         if self.lsp is not None:
             self.lsp.close()
             self.lsp = None
+        self.generation += 1
 
 
 class ReactionCurve(torch.autograd.Function):
     """F = ReactionCurve.apply(theta, runner): reaction per load step (CPU tensor);
-    gradients flow to theta through the discrete adjoint."""
+    gradients flow to theta through the discrete adjoint.  The graph's backward
+    needs the runner's checkpoints of this very forward run: if the runner ran
+    forward again in between, backward raises StaleCheckpoints."""
 
     @staticmethod
     def forward(ctx, theta, runner):
         ctx.runner = runner
         F = runner.forward(theta.detach().cpu().double().numpy())
+        ctx.generation = runner.generation
         return torch.as_tensor(F, dtype=theta.dtype)
 
     @staticmethod
     def backward(ctx, gF):
-        g = ctx.runner.backward(gF.detach().cpu().double().numpy())
+        g = ctx.runner.backward(gF.detach().cpu().double().numpy(), ctx.generation)
         return torch.as_tensor(g, dtype=gF.dtype), None

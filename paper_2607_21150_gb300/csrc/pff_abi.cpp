@@ -1,6 +1,7 @@
 // C ABI of libpff: handles, parameter derivation, kernel launches.
 #include "../../include/pff.h"
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -15,6 +16,7 @@ using namespace pff;
 namespace {
 
 thread_local std::string g_err;
+std::atomic<long long> g_launches{0};
 
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -245,12 +247,14 @@ static int cheb_t(pff_level* L, int degree, double lmin, double lmax, const T* d
 
 namespace pff {
 int set_last_error(int code, const char* msg) { return fail(code, msg); }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace pff
 
 extern "C" {
 
 const char* pff_last_error_message(void) { return g_err.c_str(); }
 int pff_version(void) { return 1; }
+int64_t pff_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int pff_create_context(pff_ctx** out, const pff_problem* pr) {
   PFF_REQUIRE(out && pr, "pff_create_context: null argument");

@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(128) k_adjoint_point(const AdjArgs a) {
 
 cudaError_t launch_adjoint_point(const AdjArgs& a, cudaStream_t st) {
   if (a.nq == 0) return cudaSuccess;
-  k_adjoint_point<<<(unsigned)((a.nq + 127) / 128), 128, 0, st>>>(a);
+  k_adjoint_point<<<(unsigned)((a.nq + 127) / 128), 128, 0, st>>>(a); note_launch();
   return cudaGetLastError();
 }
 

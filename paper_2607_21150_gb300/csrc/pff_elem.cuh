@@ -717,19 +717,19 @@ cudaError_t launch_elem_pq(int mode, const ElemArgs<T>& a, cudaStream_t st) {
     if (mode != kApply) return cudaErrorInvalidValue;
     auto k = k_elem<P, Q, T, kApply>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<nblk, block, smem, st>>>(a);
+    k<<<nblk, block, smem, st>>>(a); note_launch();
   } else if (mode == kApply) {
     auto k = k_elem<P, Q, T, kApply>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<nblk, block, smem, st>>>(a);
+    k<<<nblk, block, smem, st>>>(a); note_launch();
   } else if (mode == kEval) {
     auto k = k_elem<P, Q, T, kEval>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<nblk, block, smem, st>>>(a);
+    k<<<nblk, block, smem, st>>>(a); note_launch();
   } else {
     auto k = k_elem<P, Q, T, kBack>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<nblk, block, smem, st>>>(a);
+    k<<<nblk, block, smem, st>>>(a); note_launch();
   }
   return cudaGetLastError();
 }
@@ -742,7 +742,7 @@ cudaError_t launch_diag_pq(const ElemArgs<T>& a, cudaStream_t st) {
   size_t smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words<Q>());
   auto k = k_diag<P, Q, T>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k<<<nblk, Q * Q * EB, smem, st>>>(a);
+  k<<<nblk, Q * Q * EB, smem, st>>>(a); note_launch();
   return cudaGetLastError();
 }
 

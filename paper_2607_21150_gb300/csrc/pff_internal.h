@@ -234,6 +234,9 @@ cudaError_t launch_zero_masked(double* y, const uint8_t* mask, long long n, cuda
 
 // Records the message returned by pff_last_error_message and returns code (pff_abi.cpp).
 int set_last_error(int code, const char* msg);
+// Counts one kernel launch of this library (read by pff_kernel_launches); every
+// <<<...>>> launch site calls it right after the launch.
+void note_launch();
 
 // Host basis data (pff_basis.cpp)
 void gll_nodes(int p, double* x);

@@ -68,7 +68,8 @@ cudaError_t launch_mdot(const TV* V, long long ldv, int k, const T* w, long long
     k_mdot_partial<TV, T, 8><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, k, w, n, partial);
   else
     k_mdot_partial<TV, T, 1><<<kRedBlocks, kRedThreads, 0, st>>>(V, ldv, k, w, n, partial);
-  k_mdot_final<<<k, 256, 0, st>>>(partial, k, out);
+  note_launch();
+  k_mdot_final<<<k, 256, 0, st>>>(partial, k, out); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_mdot<double, double>(const double*, long long, int, const double*, long long, double*,
@@ -92,7 +93,7 @@ __global__ void k_maxpy(double* __restrict__ w, const double* __restrict__ V, lo
 cudaError_t launch_maxpy(double* w, const double* V, long long ldv, int k, const double* h, double sign, long long n,
                          cudaStream_t st) {
   if (k <= 0 || n == 0) return cudaSuccess;
-  k_maxpy<<<kRedBlocks * 2, 256, 0, st>>>(w, V, ldv, k, h, sign, n);
+  k_maxpy<<<kRedBlocks * 2, 256, 0, st>>>(w, V, ldv, k, h, sign, n); note_launch();
   return cudaGetLastError();
 }
 
@@ -105,7 +106,7 @@ __global__ void k_axpby(T* __restrict__ y, const T* __restrict__ x, double a, do
 template <typename T>
 cudaError_t launch_axpby(T* y, const T* x, double a, double b, long long n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_axpby<T><<<kRedBlocks * 2, 256, 0, st>>>(y, x, a, b, n);
+  k_axpby<T><<<kRedBlocks * 2, 256, 0, st>>>(y, x, a, b, n); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_axpby<double>(double*, const double*, double, double, long long, cudaStream_t);
@@ -120,7 +121,7 @@ __global__ void k_bminus(T* __restrict__ y, const T* __restrict__ b, long long n
 template <typename T>
 cudaError_t launch_bminus(T* y, const T* b, long long n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_bminus<T><<<kRedBlocks * 2, 256, 0, st>>>(y, b, n);
+  k_bminus<T><<<kRedBlocks * 2, 256, 0, st>>>(y, b, n); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_bminus<double>(double*, const double*, long long, cudaStream_t);
@@ -135,7 +136,7 @@ __global__ void k_dscale(T* __restrict__ y, const T* __restrict__ x, const T* __
 template <typename T>
 cudaError_t launch_dscale(T* y, const T* x, const T* d, long long n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_dscale<T><<<kRedBlocks * 2, 256, 0, st>>>(y, x, d, n);
+  k_dscale<T><<<kRedBlocks * 2, 256, 0, st>>>(y, x, d, n); note_launch();
   return cudaGetLastError();
 }
 template cudaError_t launch_dscale<double>(double*, const double*, const double*, long long, cudaStream_t);
@@ -148,12 +149,12 @@ __global__ void k_convert(B* __restrict__ y, const A* __restrict__ x, long long 
 }
 cudaError_t launch_d2f(float* y, const double* x, long long n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_convert<double, float><<<kRedBlocks * 2, 256, 0, st>>>(y, x, n);
+  k_convert<double, float><<<kRedBlocks * 2, 256, 0, st>>>(y, x, n); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_f2d(double* y, const float* x, long long n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_convert<float, double><<<kRedBlocks * 2, 256, 0, st>>>(y, x, n);
+  k_convert<float, double><<<kRedBlocks * 2, 256, 0, st>>>(y, x, n); note_launch();
   return cudaGetLastError();
 }
 
@@ -207,7 +208,7 @@ __global__ void k_q1_spmv_t(MeshDev mc, const double* __restrict__ A, const doub
   for (int g = 0; g < 4; ++g) y[g * mc.nn + m] = acc[g];
 }
 cudaError_t launch_q1_spmv_t(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st) {
-  k_q1_spmv_t<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, x, y);
+  k_q1_spmv_t<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, x, y); note_launch();
   return cudaGetLastError();
 }
 
@@ -221,12 +222,12 @@ __global__ void k_zero_masked(double* __restrict__ y, const uint8_t* __restrict_
     if (mask[i]) y[i] = 0.0;
 }
 cudaError_t launch_sel_scale(double* y, const uint8_t* sel, double s, long long n, cudaStream_t st) {
-  k_sel_scale<<<kRedBlocks * 2, 256, 0, st>>>(y, sel, s, n);
+  k_sel_scale<<<kRedBlocks * 2, 256, 0, st>>>(y, sel, s, n); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_zero_masked(double* y, const uint8_t* mask, long long n, cudaStream_t st) {
   if (!mask) return cudaSuccess;
-  k_zero_masked<<<kRedBlocks * 2, 256, 0, st>>>(y, mask, n);
+  k_zero_masked<<<kRedBlocks * 2, 256, 0, st>>>(y, mask, n); note_launch();
   return cudaGetLastError();
 }
 
@@ -236,11 +237,11 @@ __global__ void k_q1_diag(MeshDev mc, const double* __restrict__ A, double* __re
   for (int f = 0; f < 4; ++f) d[f * mc.nn + n] = A[(long long)(13 * 16 + f * 4 + f) * mc.nn + n];
 }
 cudaError_t launch_q1_spmv(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st) {
-  k_q1_spmv<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, x, y);
+  k_q1_spmv<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, x, y); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st) {
-  k_q1_diag<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, d);
+  k_q1_diag<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, d); note_launch();
   return cudaGetLastError();
 }
 
@@ -560,26 +561,26 @@ __global__ void k_hrestrict(MeshDev mc, MeshDev mf, const double* __restrict__ r
 cudaError_t launch_q1_coarsen(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, const double* Kef,
                               double* Kec, cudaStream_t st) {
   if (mc.nel == 0) return cudaSuccess;
-  k_q1_coarsen<<<mc.nel, 256, 0, st>>>(mf, mc, maskf, Kef, Kec);
+  k_q1_coarsen<<<mc.nel, 256, 0, st>>>(mf, mc, maskf, Kef, Kec); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_q1_gather(const MeshDev& mc, const double* Ke, const uint8_t* maskc, double* A, cudaStream_t st) {
   const long long nt = mc.nn * 16;
-  k_q1_gather<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(mc, Ke, maskc, A);
+  k_q1_gather<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(mc, Ke, maskc, A); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_hmask(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, uint8_t* maskc, cudaStream_t st) {
-  k_hmask<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mf, mc, maskf, maskc);
+  k_hmask<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mf, mc, maskf, maskc); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_hprolong_add(const MeshDev& mc, const MeshDev& mf, const double* xc, double* xf,
                                 const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
-  k_hprolong_add<<<(unsigned)((mf.nn + 255) / 256), 256, 0, st>>>(mc, mf, xc, xf, maskc, maskf);
+  k_hprolong_add<<<(unsigned)((mf.nn + 255) / 256), 256, 0, st>>>(mc, mf, xc, xf, maskc, maskf); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_hrestrict(const MeshDev& mc, const MeshDev& mf, const double* rf, double* rc,
                              const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
-  k_hrestrict<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, mf, rf, rc, maskc, maskf);
+  k_hrestrict<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, mf, rf, rc, maskc, maskf); note_launch();
   return cudaGetLastError();
 }
 
@@ -589,19 +590,19 @@ cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, c
                       sizeof(int) * 3 * kQ1Combos;
   switch (Q) {
     case 2: cudaFuncSetAttribute(k_q1_elem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<2><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
+            k_q1_elem<2><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
     case 3: cudaFuncSetAttribute(k_q1_elem<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<3><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
+            k_q1_elem<3><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
     case 4: cudaFuncSetAttribute(k_q1_elem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<4><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
+            k_q1_elem<4><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
     case 5: cudaFuncSetAttribute(k_q1_elem<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<5><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); break;
+            k_q1_elem<5><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long nt = mc.nn * 16;
-  k_q1_gather<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(mc, Ke, maskc, A);
+  k_q1_gather<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(mc, Ke, maskc, A); note_launch();
   return cudaGetLastError();
 }
 

@@ -20,8 +20,10 @@ namespace {
 constexpr long long kNoAllocMaxEntries = 1LL << 21;  // per work vector: 4 * N_n <= 2 097 152
 constexpr int kMaxDevices = 64;
 
-// Three work vectors of up to kNoAllocMaxEntries doubles (FP32 calls use the
-// first half of each vector's bytes).  Shared by every call on a device.
+// Three work vectors of up to kNoAllocMaxEntries doubles each.  FP64 calls
+// place them at doubles 0, n and 2n; FP32 calls pack their three vectors of
+// n floats contiguously at floats 0, n and 2n, i.e. in the first half of the
+// array.  Shared by every call on a device.
 static __device__ __align__(256) double g_smooth_scratch[3 * kNoAllocMaxEntries];
 
 std::mutex g_mu;

@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
 cudaError_t launch_pointwise(const PointArgs& a, cudaStream_t st) {
   if (a.nq == 0) return cudaSuccess;
   long long nb = (a.nq + 127) / 128;
-  k_pointwise<<<(unsigned)nb, 128, 0, st>>>(a);
+  k_pointwise<<<(unsigned)nb, 128, 0, st>>>(a); note_launch();
   return cudaGetLastError();
 }
 

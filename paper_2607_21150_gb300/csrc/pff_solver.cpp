@@ -441,17 +441,23 @@ int gmres_flex(pff_solver* s, const Krylov& kw, ApplyA&& applyA, ApplyM&& applyM
       double hsq = 0.0;
       for (int i = 0; i <= j; ++i) hsq += h[i] * h[i];
       std::vector<double> hcol(h.begin(), h.begin() + j + 1);
-      S_RC(dev_dots(s, kw.V, n, j + 2, w, n, h.data(), st));
-      double ww2 = h[j + 1];
-      double h2sq = 0.0;
-      for (int i = 0; i <= j; ++i) h2sq += h[i] * h[i];
-      if (h2sq > 1e-24 * ww2 || ww - hsq < 0.5 * ww) {
+      // ||w||^2 after the projection is ww - hsq; a second pass only when the
+      // first one removed more than half of ||w||^2 (cancellation has cost
+      // accuracy: Daniel-Gragg-Kaufman-Stewart criterion), otherwise the
+      // estimate is accurate to a few rounding errors and no further
+      // reduction is needed
+      double ww2 = ww - hsq;
+      if (ww2 < 0.5 * ww) {
+        S_RC(dev_dots(s, kw.V, n, j + 2, w, n, h.data(), st));
+        ww2 = h[j + 1];
+        double h2sq = 0.0;
+        for (int i = 0; i <= j; ++i) h2sq += h[i] * h[i];
         S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
         S_CK(launch_maxpy(w, kw.V, n, j + 1, s->hdev, -1.0, n, st));
         for (int i = 0; i <= j; ++i) hcol[i] += h[i];
         ww2 = std::max(ww2 - h2sq, 0.0);
       }
-      double hn = std::sqrt(ww2);
+      double hn = std::sqrt(std::max(ww2, 0.0));
       for (int i = 0; i <= j; ++i) H[i * m + j] = hcol[i];
       H[(j + 1) * m + j] = hn;
       if (hn > 0.0) S_CK(launch_axpby<double>(w, w, 1.0 / hn, 0.0, n, st));

@@ -39,6 +39,7 @@ cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* u
     k_init_masked<double><<<grid_for(n), kVecThreads, 0, st>>>((double*)y, (const double*)x, ubar, mask, n, mode);
   else
     k_init_masked<float><<<grid_for(n), kVecThreads, 0, st>>>((float*)y, (const float*)x, ubar, mask, n, mode);
+  note_launch();
   return cudaGetLastError();
 }
 
@@ -82,7 +83,7 @@ cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nbl
   if (nblk == 0) return cudaSuccess;
   const long long q3eb = (long long)Q * Q * Q * elems_per_block(Q);
   const long long n = nblk * ((kLinQuadWords / 4) + (kLinWords - kLinQuadWords)) * q3eb;
-  k_split_df<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, nblk, q3eb);
+  k_split_df<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, nblk, q3eb); note_launch();
   return cudaGetLastError();
 }
 
@@ -134,7 +135,7 @@ cudaError_t launch_prolong(const MeshDev& mc, const MeshDev& mf, const T* I1, co
                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
   if (mf.nn == 0) return cudaSuccess;
   unsigned nb = (unsigned)((mf.nn + 255) / 256);
-  k_prolong<T><<<nb, 256, 0, st>>>(mc, mf, I1, xc, xf, maskc, maskf);
+  k_prolong<T><<<nb, 256, 0, st>>>(mc, mf, I1, xc, xf, maskc, maskf); note_launch();
   return cudaGetLastError();
 }
 
@@ -190,7 +191,7 @@ cudaError_t launch_restrict(const MeshDev& mc, const MeshDev& mf, const T* I1, c
   cudaError_t err = cudaMemsetAsync(rc, 0, sizeof(T) * 4 * mc.nn, st);
   if (err != cudaSuccess) return err;
   if (n == 0) return cudaSuccess;
-  k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mc, mf, I1, rf, rc, maskc, maskf);
+  k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mc, mf, I1, rf, rc, maskc, maskf); note_launch();
   return cudaGetLastError();
 }
 
@@ -225,14 +226,14 @@ template <typename T>
 cudaError_t launch_cheb_init(long long n, const T* b, const T* Ax, const T* diag, T* r, T* d, double inv_theta,
                              cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_cheb_init<T><<<grid_for(n), kVecThreads, 0, st>>>(n, b, Ax, diag, r, d, (T)inv_theta);
+  k_cheb_init<T><<<grid_for(n), kVecThreads, 0, st>>>(n, b, Ax, diag, r, d, (T)inv_theta); note_launch();
   return cudaGetLastError();
 }
 template <typename T>
 cudaError_t launch_cheb_step(long long n, T* x, T* d, T* r, const T* Ad, const T* diag, double c_d, double c_r,
                              int last, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_cheb_step<T><<<grid_for(n), kVecThreads, 0, st>>>(n, x, d, r, Ad, diag, (T)c_d, (T)c_r, last);
+  k_cheb_step<T><<<grid_for(n), kVecThreads, 0, st>>>(n, x, d, r, Ad, diag, (T)c_d, (T)c_r, last); note_launch();
   return cudaGetLastError();
 }
 
@@ -252,7 +253,7 @@ __global__ void k_untile(const double* __restrict__ lin, double* __restrict__ ou
 }
 cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
-  k_untile<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(lin, out, nq, Q);
+  k_untile<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(lin, out, nq, Q); note_launch();
   return cudaGetLastError();
 }
 
@@ -265,7 +266,7 @@ __global__ void k_apply_dirichlet(double* __restrict__ z, const double* __restri
 }
 cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st) {
   if (n == 0 || !mask) return cudaSuccess;
-  k_apply_dirichlet<<<grid_for(n), kVecThreads, 0, st>>>(z, ubar, mask, n);
+  k_apply_dirichlet<<<grid_for(n), kVecThreads, 0, st>>>(z, ubar, mask, n); note_launch();
   return cudaGetLastError();
 }
 
@@ -293,7 +294,7 @@ __global__ void k_masked_field_sums(const double* __restrict__ v, const uint8_t*
 cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, 4 * sizeof(double), st);
   if (e != cudaSuccess || nn == 0) return e;
-  k_masked_field_sums<<<grid_for(nn), kVecThreads, 0, st>>>(v, sel, nn, out);
+  k_masked_field_sums<<<grid_for(nn), kVecThreads, 0, st>>>(v, sel, nn, out); note_launch();
   return cudaGetLastError();
 }
 
@@ -347,7 +348,7 @@ __global__ void k_geometry(const double* __restrict__ J, double* __restrict__ ge
 cudaError_t launch_geometry(const double* J, double* geo, const Geom& g, int Q, long long nq, int* status,
                             cudaStream_t st) {
   if (nq == 0) return cudaSuccess;
-  k_geometry<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(J, geo, g, Q, nq, status);
+  k_geometry<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(J, geo, g, Q, nq, status); note_launch();
   return cudaGetLastError();
 }
 

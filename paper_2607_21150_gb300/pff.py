@@ -15,6 +15,7 @@ from . import build as _build
 PFF_F64 = 0
 PFF_F32 = 1
 PFF_DF64 = 2
+PFF_PROBE_DFMA, PFF_PROBE_FFMA, PFF_PROBE_DMMA = 0, 1, 2
 STATUS_EIGEN, STATUS_DETF, STATUS_NONFINITE = 1, 2, 4
 
 _lib = None
@@ -77,6 +78,7 @@ _I64 = ctypes.c_int64
 _SIGS = {
     "pff_last_error_message": ([], ctypes.c_char_p),
     "pff_version": ([], _I),
+    "pff_kernel_launches": ([], _I64),
     "pff_create_context": ([ctypes.POINTER(_VP), ctypes.POINTER(pff_problem)], _I),
     "pff_destroy_context": ([_VP], _I),
     "pff_context_set_time_step": ([_VP, _D], _I),
@@ -129,6 +131,7 @@ _SIGS = {
     "pff_get_flags": ([_VP, _VP, _VP], _I),
     "pff_get_linearization": ([_VP, _VP, _VP], _I),
     "pff_get_status": ([_VP, _VP, ctypes.POINTER(_I)], _I),
+    "pff_probe_pipe": ([_I, _I64, _I, _I, _VP, ctypes.POINTER(_D), _VP], _I),
 }
 
 
@@ -454,3 +457,16 @@ def pff_get_status(op, stream=None):
     st = _I()
     _call("pff_get_status", op, _stream(stream), ctypes.byref(st))
     return int(st.value)
+
+
+def pff_probe_pipe(kind, iters, blocks, threads, sink, stream=None):
+    """Launch the pipe-rate probe; returns the flops the launch performs."""
+    f = _D()
+    _call("pff_probe_pipe", int(kind), int(iters), int(blocks), int(threads), _ptr(sink), ctypes.byref(f),
+          _stream(stream))
+    return f.value
+
+
+def pff_kernel_launches():
+    """Kernels libpff has launched in this process so far."""
+    return int(lib().pff_kernel_launches())

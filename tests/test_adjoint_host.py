@@ -89,3 +89,29 @@ def test_forward_records_and_backward_replays(monkeypatch):
     runner.forward(theta, schedule=runner.schedule)
     assert _FakeStepper.instances[-1].schedules == [[1], [1.5, 2], [3]]
     runner.close()
+
+
+def test_backward_of_a_replaced_forward_run_raises(monkeypatch):
+    """Two ReactionCurve graphs on one runner: the second forward replaces the
+    checkpoints, so the first graph's backward must raise instead of returning
+    the gradient of the second run; the second graph's backward works."""
+    monkeypatch.setattr(adjoint, "LoadStepper", _FakeStepper)
+    monkeypatch.setattr(adjoint.pff, "pff_context_set_time_step", lambda ctx, dt: None)
+
+    def fake_step(solver, z, h, sel, wF, hbar, hb_prev, grad, rtol, maxit, stream):
+        grad += wF
+        return 1
+
+    monkeypatch.setattr(adjoint.pff, "pff_adjoint_step", fake_step)
+    w = inputs.cube(nx=2, p=2)
+    runner = adjoint.ReactionCurveRunner(w, nsteps=2)
+    th = torch.tensor(inputs.params_of(w.phases), dtype=torch.float64, requires_grad=True)
+    F1 = adjoint.ReactionCurve.apply(th, runner)
+    F2 = adjoint.ReactionCurve.apply(th * 1.0, runner)
+    with pytest.raises(adjoint.StaleCheckpoints):
+        F1.sum().backward()
+    F2.sum().backward()
+    assert torch.all(th.grad == 2.0)          # dL/dF = 1 at both load-step ends
+    runner.close()
+    with pytest.raises(adjoint.StaleCheckpoints):
+        runner.backward(np.ones(2))

@@ -3,12 +3,19 @@ central finite differences.
 
 Three load steps of a two-phase Q2 tension box (history carried between
 steps): the GPU reactions equal the oracle's (1e-9), the adjoint gradient of the
-reaction-curve misfit equals the oracle's (1e-7 relative per component) and
-central differences of the GPU loss (1e-6), and torch autograd through
-ReactionCurve returns the same gradient.  Second variant: hardening Prandtl
-branches (linear + Voce, test values) with a live accumulated plastic strain,
-so that the return map's implicit derivatives and the history word eps_p
-enter the adjoint.  Third variant: a curved mesh (mapped geometry).
+reaction-curve misfit equals the oracle's (1e-9 relative per component, plus
+1e-11 of the largest |dL/dtheta_j theta_j| / |theta_i| for components that
+vanish) and central differences of the GPU loss in all twelve parameters
+(1e-6, plus 1e-9 of the same scale), and torch autograd through
+ReactionCurve returns the same gradient.  The forward Newton solves run to
+1e-12, their linear solves to 1e-10 and the adjoint solves to 1e-12 (measured
+on a GB300: largest component deviation from the oracle 3e-11 at these
+tolerances, 2.5e-10 at the runner's defaults 1e-11 / 1e-8 / 1e-10).
+
+Second variant: hardening Prandtl branches (linear + Voce, test values) with
+a live accumulated plastic strain, so that the return map's implicit
+derivatives and the history word eps_p enter the adjoint.  Third variant: a
+curved mesh (mapped geometry).
 """
 import numpy as np
 import pytest
@@ -56,7 +63,7 @@ def problem(orc, request):
     nsteps = 3
     target, _, _ = orc.load_steps(w, inputs.twin_target(theta0), nsteps, top)
     g_ref, F_ref = orc.adjoint_gradient(w, theta0, nsteps, top, target)
-    runner = ReactionCurveRunner(w, nsteps, levels=[2, 1])
+    runner = ReactionCurveRunner(w, nsteps, levels=[2, 1], newton_rtol=1e-12, krylov_rtol=1e-10, adjoint_rtol=1e-12)
     return w, theta0, nsteps, target, g_ref, F_ref, runner
 
 
@@ -72,7 +79,7 @@ def test_adjoint_gradient_matches_oracle(problem):
     g = runner.backward(2.0 * (F - target))
     scale = np.abs(g_ref * theta0).max()
     for i in range(12):
-        assert abs(g[i] - g_ref[i]) <= 1e-7 * abs(g_ref[i]) + 1e-11 * scale / abs(theta0[i]), (i, g[i], g_ref[i])
+        assert abs(g[i] - g_ref[i]) <= 1e-9 * abs(g_ref[i]) + 1e-11 * scale / abs(theta0[i]), (i, g[i], g_ref[i])
 
 
 def test_adjoint_gradient_matches_central_differences(problem):
@@ -80,8 +87,7 @@ def test_adjoint_gradient_matches_central_differences(problem):
     F = runner.forward(theta0)
     g = runner.backward(2.0 * (F - target))
     loss = lambda th: float(np.sum((runner.forward(th) - target) ** 2))
-    idx = (0, 1, 4, 5, 6, 7, 9, 10, 11) if w.phases.shape[1] == 12 else (0, 1, 2, 4, 5, 6, 7, 9, 10, 11)
-    for i in idx:
+    for i in range(12):
         h = 1e-5 * abs(theta0[i])
         tp, tm = theta0.copy(), theta0.copy()
         tp[i] += h
@@ -99,5 +105,5 @@ def test_autograd_function(problem):
     scale = np.abs(g_ref * theta0).max()
     g = theta.grad.numpy()
     for i in range(12):
-        assert abs(g[i] - g_ref[i]) <= 1e-7 * abs(g_ref[i]) + 1e-11 * scale / abs(theta0[i])
+        assert abs(g[i] - g_ref[i]) <= 1e-9 * abs(g_ref[i]) + 1e-11 * scale / abs(theta0[i])
     runner.close()

@@ -26,7 +26,7 @@ def _tension_box(at=2):
     m = inputs.Mesh(2, 2, 3, 2, 3, (0.02, 0.02, 0.03))
     rng = np.random.default_rng(5)
     phases = np.stack([inputs.phase_vector(inputs.EX3_MATRIX), inputs.phase_vector(inputs.EX3_PARTICLE)])
-    glob = inputs.glob_vector(at, 1e-3, 1e-2, 0.002 / 0.4, inputs.s_phi_of(inputs.EX3_MATRIX, at))
+    glob = inputs.glob_vector(at, 1e-3, 1e-2, 0.002 / 0.4, inputs.EX3_MATRIX["s_phi"][at])
     phase = (rng.random(m.nq) < 0.3).astype(np.uint8)
     mask, dv = inputs.dirichlet_tension(m, 0.002 * m.L[2])
     hist = inputs.zero_history(m.nq)

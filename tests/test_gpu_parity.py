@@ -47,7 +47,7 @@ def _two_phase(nx, ny, nz, p, seed, mask=True, at=2):
     m = inputs.Mesh(nx, ny, nz, p, p + 1, (0.01 * nx, 0.01 * ny, 0.01 * nz))
     rng = np.random.default_rng(seed)
     phases = np.stack([inputs.phase_vector(inputs.EX3_MATRIX), inputs.phase_vector(inputs.EX3_PARTICLE)])
-    glob = inputs.glob_vector(at, 1e-3, 1e-2, 0.005, inputs.s_phi_of(inputs.EX3_MATRIX, at))
+    glob = inputs.glob_vector(at, 1e-3, 1e-2, 0.005, inputs.EX3_MATRIX["s_phi"][at])
     phase = (rng.random(m.nq) < 0.4).astype(np.uint8)
     z = inputs.random_state(m, seed, u_amp=2e-4, phi_max=0.6)
     hist = inputs.random_history(m.nq, seed + 1, H_max=3000.0)
@@ -189,14 +189,22 @@ def test_offsets_restriction_matches_structured(orc):
     assert rel(np_(b.apply(v)), np_(a.apply(v))) <= 1e-14
 
 
-def test_fp32_apply_close_to_fp64(orc):
+def test_fp32_apply_matches_oracle(orc):
+    """FP32 action and its transpose (FP32 vectors, FP32 stored words) against
+    the oracle's assembled K and K^T at the FP32 rounding level: each of the
+    ~200 operations that feed one output errs by at most 2^-24 of the
+    magnitudes involved, and the inputs themselves are rounded to FP32, so the
+    relative L2 error stays near 1e-6; the bound is 2e-5."""
     w = _two_phase(3, 2, 2, 4, 13)
+    ref = orc.assemble(w)
     s = Session(w, f32=True)
     s.residual(w.z)
     v = inputs.random_vector(w.mesh.ndof, 4)
-    y64 = np_(s.apply(torch.from_numpy(v).cuda()))
-    y32 = np_(s.apply(torch.from_numpy(v.astype(np.float32)).cuda(), prec=pff.PFF_F32))
-    assert rel(y32, y64) <= 2e-5
+    v32 = torch.from_numpy(v.astype(np.float32)).cuda()
+    y32 = np_(s.apply(v32, prec=pff.PFF_F32))
+    yt32 = np_(s.apply(v32, prec=pff.PFF_F32, transpose=True))
+    assert rel(y32, ref["K"] @ v) <= 2e-5, rel(y32, ref["K"] @ v)
+    assert rel(yt32, ref["K"].T @ v) <= 2e-5, rel(yt32, ref["K"].T @ v)
 
 
 @pytest.mark.parametrize("pf,levels", [(4, (2, 1)), (2, (1,)), (3, (1,))])
@@ -310,7 +318,8 @@ def test_linearization_vs_oracle_tangent(orc):
 
 def test_full_size_tension_q4_sampled_rows(orc):
     """16^3 Q4 two-phase tension workload (1.1 M DoF) at full size: residual,
-    J x, J^T x and diag(J) at sampled rows against the oracle's element rows."""
+    J x, J^T x and diag(J) at sampled rows against the oracle's element rows,
+    relative L2 over the sampled rows <= 1e-12."""
     w = inputs.tension_q4()
     rng = np.random.default_rng(3)
     w.z = w.z + 0.0
@@ -331,9 +340,7 @@ def test_full_size_tension_q4_sampled_rows(orc):
     dofs = np.concatenate([dofs, [0, w.mesh.ndof - 1, 3 * w.mesh.nn + w.mesh.nn // 2]])
     ref = orc.sample_rows(w, dofs, x)
     for key, g in (("r", r), ("jx", jx), ("jtx", jtx), ("diag", dg), ("jx", jx_df), ("jtx", jtx_df)):
-        err = np.abs(g[dofs] - ref[key]) / np.maximum(np.abs(ref[key]), 1e-300)
-        scale = np.abs(ref[key]).max()
-        assert np.all(np.abs(g[dofs] - ref[key]) <= 1e-11 * scale + 1e-12 * np.abs(ref[key])), (key, err.max())
+        assert rel(g[dofs], ref[key]) <= 1e-12, (key, rel(g[dofs], ref[key]))
 
 
 @pytest.mark.parametrize("name", ["compress_q4", "notched_q3", "adjoint_q2"])
@@ -343,7 +350,8 @@ def test_full_size_workloads_sampled_rows(orc, name):
     64^3 Q4 compression (67.9 M DoF), 48^3 Q3 notched bar (36.4 M DoF), 24^3 Q2
     adjoint box (0.47 M DoF).  Residual, J x, J^T x, diag(J) and the
     double-float action at sampled rows against the oracle's element rows at
-    the FP64 bar; the FP32 action at the FP32 rounding level."""
+    the FP64 bar (relative L2 over the sampled rows <= 1e-12); the FP32 action
+    at the FP32 rounding level (2e-5)."""
     import bench
     w = bench.make_workload(name, seed=0)
     m = w.mesh
@@ -361,8 +369,5 @@ def test_full_size_workloads_sampled_rows(orc, name):
     dofs = np.concatenate([dofs, [0, m.ndof - 1, 3 * m.nn + m.nn // 2, 2 * m.nn + m.nn - 1]])
     ref = orc.sample_rows(w, dofs, x)
     for key, g in list(out.items()) + [("jx", jx_df)]:
-        scale = np.abs(ref[key]).max()
-        err = np.abs(g[dofs] - ref[key])
-        assert np.all(err <= 1e-11 * scale + 1e-12 * np.abs(ref[key])), (name, key, (err / scale).max())
-    scale = np.abs(ref["jx"]).max()
-    assert np.all(np.abs(jx_32[dofs] - ref["jx"]) <= 2e-5 * scale), (name, "fp32")
+        assert rel(g[dofs], ref[key]) <= 1e-12, (name, key, rel(g[dofs], ref[key]))
+    assert rel(jx_32[dofs], ref["jx"]) <= 2e-5, (name, "fp32", rel(jx_32[dofs], ref["jx"]))

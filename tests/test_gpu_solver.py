@@ -37,7 +37,7 @@ def _box(nx, ny, nz, p, seed, state=True):
     m = inputs.Mesh(nx, ny, nz, p, p + 1, (0.01 * nx, 0.01 * ny, 0.01 * nz))
     rng = np.random.default_rng(seed)
     phases = np.stack([inputs.phase_vector(inputs.EX3_MATRIX), inputs.phase_vector(inputs.EX3_PARTICLE)])
-    glob = inputs.glob_vector(2, 1e-3, 1e-2, 0.005, inputs.s_phi_of(inputs.EX3_MATRIX, 2))
+    glob = inputs.glob_vector(2, 1e-3, 1e-2, 0.005, inputs.EX3_MATRIX["s_phi"][2])
     phase = (rng.random(m.nq) < 0.4).astype(np.uint8)
     mask, dv = inputs.dirichlet_tension(m, 2e-4 * m.L[2])
     if state:

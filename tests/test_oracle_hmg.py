@@ -46,7 +46,7 @@ def test_galerkin_equals_rediscretisation(orc):
     mf = inputs.Mesh(4, 4, 2, 1, 2, L)
     mc = inputs.Mesh(2, 2, 1, 1, 2, L)
     phases = inputs.phase_vector(inputs.EX3_MATRIX)[None]
-    glob = inputs.glob_vector(2, 1e-3, 1e-2, 0.005, inputs.s_phi_of(inputs.EX3_MATRIX, 2))
+    glob = inputs.glob_vector(2, 1e-3, 1e-2, 0.005, inputs.EX3_MATRIX["s_phi"][2])
 
     def K_of(m):
         w = inputs.Workload("h", m, phases, glob, np.zeros(m.nq, np.uint8), np.zeros((4, m.nn)),

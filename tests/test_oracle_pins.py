@@ -206,13 +206,20 @@ def test_rigid_rotation_objectivity(orc):
 
 def test_at1_threshold_stationary(orc):
     """AT1: with H = psi_c = 3 Gc / (16 l0), u = 0, phi = 0 the local residual L vanishes
-    (the energy threshold of Sec. 3)."""
+    (the energy threshold of Sec. 3); slightly above psi_c the residual drives phi
+    up (L < 0), slightly below it keeps phi at 0 (L > 0).  This pins the oracle's
+    own psi_c, which the input module's explicit constants are checked against."""
     ph = _phase()
-    Gc, l0 = ph[0], ph[1]
-    psi_c = 3 * Gc / (16 * l0)
-    out = orc.pointwise(_inp(np.zeros((3, 3)))[None], _hist(H=psi_c), np.zeros(1, np.uint8), ph[None],
-                        _glob(at=1, eta=0.0))
-    assert abs(out["f0"][0, 3]) < 1e-12 * psi_c
+    psi_c = orc.psi_c(ph)
+    assert abs(psi_c - 3 * ph[0] / (16 * ph[1])) <= 1e-15 * psi_c
+    for H, sign in ((psi_c, 0), (1.01 * psi_c, -1), (0.99 * psi_c, 1)):
+        out = orc.pointwise(_inp(np.zeros((3, 3)))[None], _hist(H=H), np.zeros(1, np.uint8), ph[None],
+                            _glob(at=1, eta=0.0))
+        L = out["f0"][0, 3]
+        if sign == 0:
+            assert abs(L) < 1e-12 * psi_c
+        else:
+            assert np.sign(L) == sign
 
 
 def test_tangent_matches_appendix_bc(orc):
@@ -443,3 +450,42 @@ def test_golden_table2_parameters():
                                             ex3["matrix"]["sigma0_MPa"])
     assert inputs.EX3_MATRIX["maxwell"][2] == ex3["matrix"]["eta_d_GPa_s"] * gpa
     assert inputs.EX2_MATRIX["maxwell"][2] == g["example2"]["matrix"]["eta_d_GPa_s"][0] * gpa
+
+
+def test_golden_derived_constants(orc):
+    """s_phi (Eq. damage-residual-scaling) and the AT1 threshold psi_c (Sec. 3.1),
+    worked out by hand from Table 2 (tests/golden/derived_constants.json): the
+    oracle's own derivation from the phase rows and the explicit constants the
+    input module hands to both sides must both equal them."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "derived_constants.json")))
+    phases = {"example3 matrix": inputs.EX3_MATRIX, "example3 particle": inputs.EX3_PARTICLE,
+              "example2 matrix": inputs.EX2_MATRIX, "example2 particle": inputs.EX2_PARTICLE}
+    for e in g["s_phi"]:
+        d = phases[e["phase"]]
+        row = inputs.phase_vector(d)
+        assert (row[0], row[1], row[2]) == (e["Gc"], e["l0_mm"], e["E_MPa"])
+        assert abs(orc.s_phi(row, e["at"]) - e["value"]) <= 1e-15 * e["value"]
+        assert d["s_phi"][e["at"]] == e["value"]
+    for e in g["psi_c"]:
+        d = phases[e["phase"]]
+        row = inputs.phase_vector(d)
+        assert (row[0], row[1]) == (e["Gc"], e["l0_mm"])
+        assert abs(orc.psi_c(row) - e["value"]) <= 1e-15 * e["value"]
+        assert d["psi_c"] == e["value"]
+    assert inputs.EX3_PARTICLE_ADJ["psi_c"] == orc.psi_c(inputs.phase_vector(inputs.EX3_PARTICLE_ADJ))
+    assert (orc.crack_c0(1), orc.crack_c0(2)) == (8.0 / 3.0, 2.0)
+
+
+def test_workloads_carry_the_derived_constants(orc):
+    """The workloads' global s_phi and AT1 starting history equal the oracle's
+    derivation from their own phase rows (the matrix phase is row 0)."""
+    for w in (inputs.cube(), inputs.tension_q4(n=2), inputs.compress_q4(n=2), inputs.adjoint_q2(n=2)):
+        at = int(w.glob[0])
+        assert abs(w.glob[4] - orc.s_phi(w.phases[0], at)) <= 1e-15 * w.glob[4]
+        for k in range(len(w.phases)):
+            sel = w.phase == k
+            want = orc.psi_c(w.phases[k]) if at == 1 else 0.0
+            if np.any(sel):
+                assert np.all(np.abs(w.hist[13][sel] - want) <= 1e-15 * max(want, 1.0))

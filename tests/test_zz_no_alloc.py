@@ -38,7 +38,7 @@ def _workload():
     m = inputs.Mesh(3, 2, 2, 4, 5, (0.03, 0.02, 0.02))
     rng = np.random.default_rng(41)
     phases = np.stack([inputs.phase_vector(inputs.EX3_MATRIX), inputs.phase_vector(inputs.EX3_PARTICLE)])
-    glob = inputs.glob_vector(2, 1e-3, 1e-2, 0.005, inputs.s_phi_of(inputs.EX3_MATRIX, 2))
+    glob = inputs.glob_vector(2, 1e-3, 1e-2, 0.005, inputs.EX3_MATRIX["s_phi"][2])
     phase = (rng.random(m.nq) < 0.4).astype(np.uint8)
     z = inputs.random_state(m, 41, u_amp=2e-4, phi_max=0.6)
     hist = inputs.random_history(m.nq, 42, H_max=3000.0)
