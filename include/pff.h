@@ -63,13 +63,19 @@ extern "C" {
 #define PFF_STATUS_NONFINITE 4   /* non-finite residual integrand */
 #define PFF_STATUS_PHASE 8       /* phase id >= nphase (phase 0 used) */
 #define PFF_STATUS_RETURN 16     /* hardening return map: local Newton hit its cap (50) */
+#define PFF_STATUS_PIPE 32       /* PFF_F32_BF16 action: a wait for staged words gave up (result invalid) */
 
 /* PFF_DF64: FP64 vectors, the Jacobian action's contractions carried in
  * double-float arithmetic (pairs of FP32 words on the FP32 pipes, error about
  * 2^-47 of the magnitudes per operation instead of 2^-53) and the stored
  * linearisation read from its hi/lo FP32 planes (pff_op_enable_df).  Accepted
- * by pff_jacobian_apply and pff_jacobian_transpose_apply only. */
-typedef enum { PFF_F64 = 0, PFF_F32 = 1, PFF_DF64 = 2 } pff_prec;
+ * by pff_jacobian_apply and pff_jacobian_transpose_apply only.
+ * PFF_F32_BF16: FP32 vectors and arithmetic, the stored linearisation read as
+ * BF16 words (8 significant bits, relative rounding error <= 2^-9 per word;
+ * pff_op_enable_bf16): the p-multigrid level precision that halves the word
+ * stream.  Accepted by the actions and pff_chebyshev_smooth(_noalloc);
+ * pff_assemble_diagonal, pff_prolong and pff_restrict treat it as PFF_F32. */
+typedef enum { PFF_F64 = 0, PFF_F32 = 1, PFF_DF64 = 2, PFF_F32_BF16 = 3 } pff_prec;
 
 typedef struct pff_ctx pff_ctx;
 typedef struct pff_basis pff_basis;
@@ -156,6 +162,10 @@ int pff_op_enable_f32(pff_op* op, int enable);
  * so enabling also enables FP32.  Disabling stops the lo updates and keeps the
  * memory until pff_op_enable_f32(op, 0). */
 int pff_op_enable_df(pff_op* op, int enable);
+/* Keep the stored linearisation also as BF16 words (72 per point, 144 bytes;
+ * written by pff_residual, round to nearest even from FP64), needed by
+ * PFF_F32_BF16 applies.  Disabling frees them. */
+int pff_op_enable_bf16(pff_op* op, int enable);
 int64_t pff_op_num_qpoints(const pff_op* op);
 int64_t pff_op_num_nodes(const pff_op* op);
 
@@ -282,6 +292,8 @@ typedef struct {
                            Newton iterations, so that a load-step cut-back starts early; 0 = never */
   int eig_every;        /* re-estimate the lambda_max bounds every eig_every-th Newton iteration of a
                            solve (1 = every one); 0 = only on the first (later ones reuse them) */
+  int level_words;      /* mixed = 1: stored words of the FP32 level actions and smoothers, 32 (the FP32
+                           copy) or 16 (BF16 words, PFF_F32_BF16; needs pff_op_enable_bf16) */
 } pff_solver_params;
 
 typedef struct {

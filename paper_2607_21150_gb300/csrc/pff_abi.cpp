@@ -143,12 +143,18 @@ ElemArgs<T> level_args(const pff_level* L) {
   return a;
 }
 
+// w16: FP32 action reading the BF16 words (PFF_F32_BF16) instead of the FP32 copy.
 template <typename T>
-int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st) {
+int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool w16 = false) {
   pff_op* op = L->op;
-  PFF_REQUIRE(linOf<T>(op) != nullptr, "FP32 apply needs pff_op_enable_f32 before pff_residual");
+  if (w16) PFF_REQUIRE(op->bf16 && op->lin16, "PFF_F32_BF16 apply needs pff_op_enable_bf16 before pff_residual");
+  else PFF_REQUIRE(linOf<T>(op) != nullptr, "FP32 apply needs pff_op_enable_f32 before pff_residual");
   PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
   ElemArgs<T> a = level_args<T>(L);
+  if (w16) {
+    a.lin16 = op->lin16;
+    a.status = op->status;
+  }
   a.x = x;
   a.y = y;
   long long stride = stride_of(op->Q);
@@ -220,7 +226,7 @@ int ensure_prolong_table(pff_level* c, pff_level* f) {
 
 template <typename T>
 static int cheb_t(pff_level* L, int degree, double lmin, double lmax, const T* diag, const T* b, T* x, T* work,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool w16 = false) {
   const long long n = 4 * L->mesh.nn;
   T* r = work;
   T* d = work + n;
@@ -228,7 +234,7 @@ static int cheb_t(pff_level* L, int degree, double lmin, double lmax, const T* d
   const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
-  int rc = apply_t<T>(L, x, Ad, 0, st);
+  int rc = apply_t<T>(L, x, Ad, 0, st, w16);
   if (rc) return rc;
   PFF_CK(launch_cheb_init<T>(n, b, Ad, diag, r, d, 1.0 / theta, st));
   for (int k = 0; k < degree; ++k) {
@@ -236,7 +242,7 @@ static int cheb_t(pff_level* L, int degree, double lmin, double lmax, const T* d
       PFF_CK(launch_cheb_step<T>(n, x, d, r, Ad, diag, 0.0, 0.0, 1, st));
       break;
     }
-    rc = apply_t<T>(L, d, Ad, 0, st);
+    rc = apply_t<T>(L, d, Ad, 0, st, w16);
     if (rc) return rc;
     const double rho_new = 1.0 / (2.0 * sigma - rho);
     PFF_CK(launch_cheb_step<T>(n, x, d, r, Ad, diag, rho_new * rho, 2.0 * rho_new / delta, 0, st));
@@ -444,7 +450,7 @@ int pff_create_operator(pff_ctx* ctx, pff_basis* fine, pff_restr* restr, pff_op*
 int pff_destroy_operator(pff_op* op) {
   if (!op) return PFF_OK;
   cudaFree(op->hist_c); cudaFree(op->hist_t); cudaFree(op->phase); cudaFree(op->flags);
-  cudaFree(op->lin64); cudaFree(op->lin32); cudaFree(op->io); cudaFree(op->mask);
+  cudaFree(op->lin64); cudaFree(op->lin32); cudaFree(op->lin16); cudaFree(op->io); cudaFree(op->mask);
   cudaFree(op->dvals); cudaFree(op->status);
   cudaFree(op->fint); cudaFree(op->sums); cudaFree(op->geo);
   free_tables(op->tab);
@@ -483,6 +489,29 @@ int pff_op_enable_df(pff_op* op, int enable) {
   }
   if (enable) op->f32 = 1;
   op->df = enable ? 1 : 0;  // disabling keeps both planes allocated until pff_op_enable_f32(op, 0)
+  return PFF_OK;
+}
+
+int pff_op_enable_bf16(pff_op* op, int enable) {
+  PFF_REQUIRE(op, "pff_op_enable_bf16: null operator");
+  if (enable && !op->lin16) {
+    const long long nblk = op->lin_len / (kLinWords * stride_of(op->Q));
+    const long long len = nblk * kLin16Words * stride_of(op->Q);
+    PFF_CK(cudaMalloc((void**)&op->lin16, sizeof(uint16_t) * len));
+    const cudaError_t e = cudaMemset(op->lin16, 0, sizeof(uint16_t) * len);
+    if (e != cudaSuccess) {
+      cudaFree(op->lin16);
+      op->lin16 = nullptr;
+    }
+    PFF_CK(e);
+    op->lin16_len = len;
+  }
+  if (!enable && op->lin16) {
+    cudaFree(op->lin16);
+    op->lin16 = nullptr;
+    op->lin16_len = 0;
+  }
+  op->bf16 = enable ? 1 : 0;
   return PFF_OK;
 }
 
@@ -607,6 +636,8 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   if (op->f32 && op->lin32)
     PFF_CK(launch_split_df(op->lin64, op->lin32, op->df ? op->lin32 + op->lin_len : nullptr,
                            op->lin_len / (kLinWords * stride_of(op->Q)), op->Q, st));
+  if (op->bf16 && op->lin16)
+    PFF_CK(launch_split_bf16(op->lin64, op->lin16, op->lin_len / (kLinWords * stride_of(op->Q)), op->Q, st));
   return PFF_OK;
 }
 
@@ -682,6 +713,7 @@ int pff_jacobian_apply(pff_level* L, pff_prec prec, const void* x, void* y, void
   if (prec == PFF_F64) return apply_t<double>(L, (const double*)x, (double*)y, 0, S(stream));
   if (prec == PFF_F32) return apply_t<float>(L, (const float*)x, (float*)y, 0, S(stream));
   if (prec == PFF_DF64) return apply_df(L, (const double*)x, (double*)y, 0, S(stream));
+  if (prec == PFF_F32_BF16) return apply_t<float>(L, (const float*)x, (float*)y, 0, S(stream), true);
   return fail(PFF_ERR_INVALID, "pff_jacobian_apply: unknown precision");
 }
 
@@ -690,13 +722,14 @@ int pff_jacobian_transpose_apply(pff_level* L, pff_prec prec, const void* x, voi
   if (prec == PFF_F64) return apply_t<double>(L, (const double*)x, (double*)y, 1, S(stream));
   if (prec == PFF_F32) return apply_t<float>(L, (const float*)x, (float*)y, 1, S(stream));
   if (prec == PFF_DF64) return apply_df(L, (const double*)x, (double*)y, 1, S(stream));
+  if (prec == PFF_F32_BF16) return apply_t<float>(L, (const float*)x, (float*)y, 1, S(stream), true);
   return fail(PFF_ERR_INVALID, "pff_jacobian_transpose_apply: unknown precision");
 }
 
 int pff_assemble_diagonal(pff_level* L, pff_prec prec, void* diag, void* stream) {
   PFF_REQUIRE(L && diag, "pff_assemble_diagonal: null argument");
   if (prec == PFF_F64) return diag_t<double>(L, (double*)diag, S(stream));
-  if (prec == PFF_F32) return diag_t<float>(L, (float*)diag, S(stream));
+  if (prec == PFF_F32 || prec == PFF_F32_BF16) return diag_t<float>(L, (float*)diag, S(stream));
   return fail(PFF_ERR_INVALID, "pff_assemble_diagonal: unknown precision");
 }
 
@@ -709,7 +742,7 @@ int pff_prolong(pff_level* c, pff_level* f, pff_prec prec, const void* xc, void*
   const uint8_t* mc = level_mask(c);
   const uint8_t* mf = level_mask(f);
   if (prec == PFF_F64) PFF_CK(launch_prolong<double>(c->mesh, f->mesh, c->I64, (const double*)xc, (double*)xf, mc, mf, S(stream)));
-  else if (prec == PFF_F32) PFF_CK(launch_prolong<float>(c->mesh, f->mesh, c->I32, (const float*)xc, (float*)xf, mc, mf, S(stream)));
+  else if (prec == PFF_F32 || prec == PFF_F32_BF16) PFF_CK(launch_prolong<float>(c->mesh, f->mesh, c->I32, (const float*)xc, (float*)xf, mc, mf, S(stream)));
   else return fail(PFF_ERR_INVALID, "pff_prolong: unknown precision");
   return PFF_OK;
 }
@@ -723,7 +756,7 @@ int pff_restrict(pff_level* c, pff_level* f, pff_prec prec, const void* rf, void
   const uint8_t* mc = level_mask(c);
   const uint8_t* mf = level_mask(f);
   if (prec == PFF_F64) PFF_CK(launch_restrict<double>(c->mesh, f->mesh, c->I64, (const double*)rf, (double*)rc_, mc, mf, S(stream)));
-  else if (prec == PFF_F32) PFF_CK(launch_restrict<float>(c->mesh, f->mesh, c->I32, (const float*)rf, (float*)rc_, mc, mf, S(stream)));
+  else if (prec == PFF_F32 || prec == PFF_F32_BF16) PFF_CK(launch_restrict<float>(c->mesh, f->mesh, c->I32, (const float*)rf, (float*)rc_, mc, mf, S(stream)));
   else return fail(PFF_ERR_INVALID, "pff_restrict: unknown precision");
   return PFF_OK;
 }
@@ -735,8 +768,9 @@ int pff_chebyshev_smooth(pff_level* L, pff_prec prec, int degree, double lmin, d
   PFF_REQUIRE(lmax > lmin && lmin > 0.0, "pff_chebyshev_smooth: need 0 < lmin < lmax");
   if (prec == PFF_F64)
     return cheb_t<double>(L, degree, lmin, lmax, (const double*)diag, (const double*)b, (double*)x, (double*)work, S(stream));
-  if (prec == PFF_F32)
-    return cheb_t<float>(L, degree, lmin, lmax, (const float*)diag, (const float*)b, (float*)x, (float*)work, S(stream));
+  if (prec == PFF_F32 || prec == PFF_F32_BF16)
+    return cheb_t<float>(L, degree, lmin, lmax, (const float*)diag, (const float*)b, (float*)x, (float*)work, S(stream),
+                         prec == PFF_F32_BF16);
   return fail(PFF_ERR_INVALID, "pff_chebyshev_smooth: unknown precision");
 }
 

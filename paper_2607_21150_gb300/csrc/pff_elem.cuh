@@ -705,11 +705,20 @@ k_diag(const ElemArgs<T> a) {
   }
 }
 
+}  // namespace pff
+
+#include "pff_elem_w16.cuh"
+
+namespace pff {
+
 template <int P, int Q, typename T>
 cudaError_t launch_elem_pq(int mode, const ElemArgs<T>& a, cudaStream_t st) {
   constexpr int EB = elems_per_block(Q);
   int nblk = (a.mesh.nel + EB - 1) / EB;
   if (nblk == 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4 && sizeof(typename ElemTypes<T>::L) == 4) {  // FP32 action with BF16 words
+    if (a.lin16) return mode == kApply ? launch_elem_w16<P, Q>(a, st) : cudaErrorInvalidValue;
+  }
   size_t smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words<Q>());
   dim3 block(Q * Q * EB);
   if (mode == kApply) smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words_t<Q, T>());

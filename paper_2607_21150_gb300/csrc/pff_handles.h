@@ -56,6 +56,9 @@ struct pff_op {
   int f32 = 0;
   int df = 0;                 // maintain the double-float planes of the stored linearisation
   int lin32_planes = 0;       // FP32 planes allocated at lin32 (0, 1 or 2)
+  uint16_t* lin16 = nullptr;  // BF16 words (lin16_word layout), written by pff_residual when bf16 = 1
+  long long lin16_len = 0;    // uint16 entries at lin16
+  int bf16 = 0;
   double* geo = nullptr;      // mapped mesh: [10][nq] d xi / dX and w det J (null: the affine box)
   double* fint = nullptr;     // internal force work vector of pff_reaction (allocated on first use)
   double* sums = nullptr;     // 4 doubles

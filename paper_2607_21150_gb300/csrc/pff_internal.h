@@ -25,6 +25,20 @@ __host__ __device__ constexpr long long lin32_word(int w, int k, int t, long lon
                            : (long long)w * q3eb + (long long)k * q2eb + t;
 }
 
+// BF16 words of the stored linearisation (the level actions of PFF_F32_BF16):
+// per block a region of kLin16Words * Q^3 EB uint16, words [0, 64) of a point
+// grouped by eight (one 16-byte load), words [64, 68) and [68, 72) in two
+// planes of four per point (8 bytes; the second is read on mapped meshes
+// only, its words 70 and 71 are zero).  Slice k of a block is one contiguous
+// run per plane: 8 Q^2 EB words of each octet plane, 4 Q^2 EB of each tail
+// plane, so that a slice moves as ten 1D bulk copies.
+constexpr int kLin16Words = 72;
+__host__ __device__ constexpr long long lin16_word(int w, int k, int t, long long q3eb, long long q2eb) {
+  return w < 64 ? (long long)(w >> 3) * 8 * q3eb + (long long)k * 8 * q2eb + 8LL * t + (w & 7)
+       : w < 68 ? 64 * q3eb + (long long)k * 4 * q2eb + 4LL * t + (w - 64)
+                : 68 * q3eb + (long long)k * 4 * q2eb + 4LL * t + (w - 68);
+}
+
 // Elements handled by one thread block of the element kernels: Q*Q threads per element.
 __host__ __device__ constexpr int elems_per_block(int Q) { return 256 / (Q * Q); }
 // 128-bit alignment of the FP32 quad planes needs an even Q^3 EB for every Q
@@ -153,6 +167,8 @@ struct ElemArgs {
   int transpose;
   int kx;                 // 1: add the off-diagonal phase-gradient words (mapped meshes)
   long long lo;           // df64: offset (in words) from the hi plane to the lo plane
+  const uint16_t* lin16;  // FP32 action only: read the BF16 words (lin16_word layout) instead of lin
+  int* status;            // device status word (BF16-word action: bit 32 when a staging wait gave up)
 };
 
 // One translation unit per quadrature size Q (pff_elem_q<Q>.cu); each covers
@@ -177,6 +193,8 @@ cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* u
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
 // hi[i] = fl32(a[i]) and, when lo is not null, lo[i] = fl32(a[i] - hi[i]).
 cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nblk, int Q, cudaStream_t st);
+// out = the BF16 words (round to nearest even) of the FP64 words a, lin16_word layout.
+cudaError_t launch_split_bf16(const double* a, uint16_t* out, long long nblk, int Q, cudaStream_t st);
 cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st);
 cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st);
 cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st);

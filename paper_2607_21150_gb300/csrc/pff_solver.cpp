@@ -350,7 +350,7 @@ int arnoldi_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
       S_CK(launch_dscale<double>(wv, wv, (const double*)w.diag, n, st));
     } else {
       S_CK(launch_d2f((float*)w.x, vj, n, st));
-      S_RC(pff_jacobian_apply(w.L, PFF_F32, w.x, w.tmp, st));
+      S_RC(pff_jacobian_apply(w.L, (pff_prec)w.prec, w.x, w.tmp, st));
       S_CK(launch_dscale<float>((float*)w.tmp, (const float*)w.tmp, (const float*)w.diag, n, st));
       S_CK(launch_f2d(wv, (const float*)w.tmp, n, st));
     }
@@ -641,6 +641,7 @@ int pff_solver_default_params(pff_solver_params* p) {
   p->outer_prec = PFF_F64;
   p->newton_stall = 0;
   p->eig_every = 1;
+  p->level_words = 32;
   return PFF_OK;
 }
 
@@ -662,6 +663,10 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     return sfail(PFF_ERR_INVALID, "pff_create_solver: outer_prec must be PFF_F64 or PFF_DF64");
   if (prm->outer_prec == PFF_DF64 && !op->df)
     return sfail(PFF_ERR_INVALID, "pff_create_solver: outer_prec PFF_DF64 needs pff_op_enable_df");
+  if (prm->level_words != 32 && prm->level_words != 16)
+    return sfail(PFF_ERR_INVALID, "pff_create_solver: level_words must be 32 or 16");
+  if (prm->mixed && prm->level_words == 16 && !(op->bf16 && op->lin16))
+    return sfail(PFF_ERR_INVALID, "pff_create_solver: level_words 16 needs pff_op_enable_bf16");
   pff_solver* s = new pff_solver();
   s->op = op;
   s->prm = *prm;
@@ -672,7 +677,7 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
     LevelWork w;
     w.L = levels[l];
     w.p = levels[l]->p;
-    w.prec = prm->mixed ? PFF_F32 : PFF_F64;
+    w.prec = prm->mixed ? (prm->level_words == 16 ? PFF_F32_BF16 : PFF_F32) : PFF_F64;
     w.esz = (w.prec == PFF_F64) ? 8 : 4;
     w.n = 4 * levels[l]->mesh.nn;
     if (e == cudaSuccess) e = cudaMalloc(&w.diag, w.esz * w.n);

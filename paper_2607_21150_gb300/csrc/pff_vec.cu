@@ -2,6 +2,8 @@
 // planes of the stored linearisation, the p-multigrid transfer operators, the
 // Chebyshev smoother updates, the export of the linearisation, reaction sums
 // and the geometric factors of mapped meshes.
+#include <cuda_bf16.h>
+
 #include "pff_internal.h"
 
 namespace pff {
@@ -84,6 +86,51 @@ cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nbl
   const long long q3eb = (long long)Q * Q * Q * elems_per_block(Q);
   const long long n = nblk * ((kLinQuadWords / 4) + (kLinWords - kLinQuadWords)) * q3eb;
   k_split_df<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, nblk, q3eb); note_launch();
+  return cudaGetLastError();
+}
+
+// BF16 words of the stored linearisation (lin16_word layout): one thread per
+// output unit, eight words of an octet plane (eight coalesced FP64 reads, one
+// 128-bit write) or four of a tail plane (one 64-bit write; words 70 and 71
+// are zero).  Round to nearest even from FP64.
+__global__ void k_split_bf16(const double* __restrict__ a, uint16_t* __restrict__ out, long long nblk,
+                             long long q3eb) {
+  const long long bw = (long long)kLinWords * q3eb, ow = (long long)kLin16Words * q3eb;
+  const long long opb = 8 * q3eb, tpb = 2 * q3eb;  // octet / tail units per block
+  const long long no = nblk * opb, n = no + nblk * tpb;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
+    if (u < no) {
+      const long long b = u / opb, rem = u % opb;
+      const long long oc = rem / q3eb, r2 = rem % q3eb;
+      const double* src = a + b * bw + 8 * oc * q3eb + r2;
+      unsigned v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const unsigned lo = __bfloat16_as_ushort(__double2bfloat16(src[(2 * c) * q3eb]));
+        const unsigned hi = __bfloat16_as_ushort(__double2bfloat16(src[(2 * c + 1) * q3eb]));
+        v[c] = lo | (hi << 16);
+      }
+      *reinterpret_cast<uint4*>(out + b * ow + oc * 8 * q3eb + 8 * r2) = make_uint4(v[0], v[1], v[2], v[3]);
+    } else {
+      const long long w = u - no, b = w / tpb, rem = w % tpb;
+      const long long tp = rem / q3eb, r2 = rem % q3eb;
+      unsigned v[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int w0 = 64 + 4 * (int)tp + 2 * c, w1 = w0 + 1;
+        const unsigned lo = w0 < kLinWords ? __bfloat16_as_ushort(__double2bfloat16(a[b * bw + w0 * q3eb + r2])) : 0u;
+        const unsigned hi = w1 < kLinWords ? __bfloat16_as_ushort(__double2bfloat16(a[b * bw + w1 * q3eb + r2])) : 0u;
+        v[c] = lo | (hi << 16);
+      }
+      *reinterpret_cast<uint2*>(out + b * ow + (64 + 4 * tp) * q3eb + 4 * r2) = make_uint2(v[0], v[1]);
+    }
+  }
+}
+cudaError_t launch_split_bf16(const double* a, uint16_t* out, long long nblk, int Q, cudaStream_t st) {
+  if (nblk == 0) return cudaSuccess;
+  const long long q3eb = (long long)Q * Q * Q * elems_per_block(Q);
+  const long long n = nblk * 10 * q3eb;
+  k_split_bf16<<<grid_for(n), kVecThreads, 0, st>>>(a, out, nblk, q3eb); note_launch();
   return cudaGetLastError();
 }
 

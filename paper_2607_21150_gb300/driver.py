@@ -62,14 +62,16 @@ class LoadStepper:
         (PFF_DF64) instead of FP64; by default on with mixed precision (same
         converged fields to ~1e-15, half the time of the FP64 action).
         max_cuts: consecutive halvings of a failing load increment before
-        `advance` gives up."""
+        `advance` gives up.  solver_params: fields of pff_solver_params, e.g.
+        level_words=16 for BF16 words in the FP32 levels."""
         if df is None:
             df = mixed
         m = w.mesh
         if levels is None:
             levels = {4: [4, 2, 1], 3: [3, 1], 2: [2, 1], 1: [1]}[m.p]
         self.levels = list(levels)
-        self.s = session or Session(w, levels=[p for p in self.levels if p != m.p], f32=mixed, df=df)
+        bf16 = mixed and solver_params.get("level_words", 32) == 16
+        self.s = session or Session(w, levels=[p for p in self.levels if p != m.p], f32=mixed, df=df, bf16=bf16)
         if df:
             solver_params.setdefault("outer_prec", pff.PFF_DF64)
         solver_params.setdefault("newton_stall", 6)  # a stagnating solve hands over to the cut-back early

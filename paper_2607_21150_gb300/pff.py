@@ -15,6 +15,7 @@ from . import build as _build
 PFF_F64 = 0
 PFF_F32 = 1
 PFF_DF64 = 2
+PFF_F32_BF16 = 3
 PFF_PROBE_DFMA, PFF_PROBE_FFMA, PFF_PROBE_DMMA = 0, 1, 2
 STATUS_EIGEN, STATUS_DETF, STATUS_NONFINITE = 1, 2, 4
 
@@ -52,7 +53,7 @@ class pff_solver_params(ctypes.Structure):
                 ("krylov_rtol", ctypes.c_double), ("newton_maxit", ctypes.c_int), ("newton_rtol", ctypes.c_double),
                 ("line_search_max", ctypes.c_int), ("coarse_solver", ctypes.c_int), ("coarse_rtol", ctypes.c_double),
                 ("coarse_maxit", ctypes.c_int), ("verbose", ctypes.c_int), ("outer_prec", ctypes.c_int),
-                ("newton_stall", ctypes.c_int), ("eig_every", ctypes.c_int)]
+                ("newton_stall", ctypes.c_int), ("eig_every", ctypes.c_int), ("level_words", ctypes.c_int)]
 
 
 class pff_newton_stats(ctypes.Structure):
@@ -92,6 +93,7 @@ _SIGS = {
     "pff_destroy_operator": ([_VP], _I),
     "pff_op_enable_f32": ([_VP, _I], _I),
     "pff_op_enable_df": ([_VP, _I], _I),
+    "pff_op_enable_bf16": ([_VP, _I], _I),
     "pff_op_set_geometry": ([_VP, _VP, _VP], _I),
     "pff_op_num_qpoints": ([_VP], _I64),
     "pff_op_num_nodes": ([_VP], _I64),
@@ -266,6 +268,10 @@ def pff_op_enable_f32(op, enable=True):
 
 def pff_op_enable_df(op, enable=True):
     _call("pff_op_enable_df", op, 1 if enable else 0)
+
+
+def pff_op_enable_bf16(op, enable=True):
+    _call("pff_op_enable_bf16", op, 1 if enable else 0)
 
 
 def pff_op_set_geometry(op, X, stream=None):

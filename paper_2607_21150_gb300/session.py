@@ -11,7 +11,7 @@ from .inputs import Workload, coarsen_mask, element_offsets
 
 class Session:
     def __init__(self, w: Workload, levels=(), f32: bool = False, offsets: bool = False,
-                 device: str = "cuda", stream=None, df: bool = False):
+                 device: str = "cuda", stream=None, df: bool = False, bf16: bool = False):
         self.w = w
         self.dev = torch.device(device)
         self.stream = stream
@@ -31,6 +31,8 @@ class Session:
             pff.pff_op_enable_f32(self.op, True)
         if df:
             pff.pff_op_enable_df(self.op, True)
+        if bf16:
+            pff.pff_op_enable_bf16(self.op, True)
         self.phase = torch.from_numpy(np.ascontiguousarray(w.phase, dtype=np.uint8)).to(self.dev)
         self.set_history(w.hist)
         self.mask = None

@@ -140,15 +140,17 @@ def test_fgmres_linear_solve(orc):
     pff.pff_destroy_solver(solver)
 
 
-@pytest.mark.parametrize("mixed,outer,eig_every", [(0, 0, 1), (1, 0, 1), (1, 2, 1), (1, 0, 0)])
-def test_newton_solution_matches_oracle(orc, mixed, outer, eig_every):
+@pytest.mark.parametrize("mixed,outer,eig_every,words", [(0, 0, 1, 32), (1, 0, 1, 32), (1, 2, 1, 32), (1, 0, 0, 32),
+                                                         (1, 2, 1, 16)])
+def test_newton_solution_matches_oracle(orc, mixed, outer, eig_every, words):
     """outer = 2: the FGMRES operator is the double-float action (PFF_DF64);
-    eig_every = 0: eigenvalue bounds estimated on the first Newton iteration only."""
+    eig_every = 0: eigenvalue bounds estimated on the first Newton iteration only;
+    words = 16: BF16 stored words in the FP32 levels and smoothers."""
     w = _box(2, 2, 3, 2, 11, state=False)
     z_ref, hist_ref, _ = orc.newton(w, rtol=1e-13)
-    s = Session(w, levels=(1,), f32=bool(mixed), df=(outer == pff.PFF_DF64))
+    s = Session(w, levels=(1,), f32=bool(mixed), df=(outer == pff.PFF_DF64), bf16=(words == 16))
     solver = s.solver([2, 1], mixed=mixed, newton_rtol=1e-11, krylov_rtol=1e-6, outer_prec=outer,
-                      eig_every=eig_every)
+                      eig_every=eig_every, level_words=words)
     z = torch.from_numpy(w.z.ravel().copy()).cuda()
     st = pff.pff_newton_solve(solver, z)
     assert st["converged"] == 1, st
