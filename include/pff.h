@@ -393,6 +393,14 @@ int pff_get_linearization(pff_op* op, double* out, void* stream);
 /* Synchronises `stream`, returns the kernel status bits accumulated since the
  * last call in *status and clears them. */
 int pff_get_status(pff_op* op, void* stream, int* status);
+/* Summary of the state for a load-step log (Sec. 5 reports reaction curves,
+ * plastic strain and damage fields): out8 (HOST, 8 doubles) = numbers of
+ * quadrature points whose flags of the last residual have the yield, history
+ * active and theta >= 0 bits; largest and smallest nodal phase field of z
+ * (device FP64 [4][N_n]); nodes with phi > 0.9; largest accumulated plastic
+ * strain and largest history field H of the committed history.  Synchronises
+ * the stream. */
+int pff_state_summary(pff_op* op, const double* z, double* out8, void* stream);
 
 /* Pipe-rate probe (measurement aid; the paper has no counterpart): launches
  * `blocks` x `threads` threads that each run 8 independent dependent chains of

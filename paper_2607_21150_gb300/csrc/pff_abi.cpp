@@ -652,7 +652,7 @@ int pff_reaction(pff_op* op, const uint8_t* sel, double* out4, void* stream) {
   cudaStream_t st = S(stream);
   const long long n = 4 * op->mesh.nn;
   if (!op->fint) PFF_CK(cudaMalloc((void**)&op->fint, sizeof(double) * n));
-  if (!op->sums) PFF_CK(cudaMalloc((void**)&op->sums, sizeof(double) * 4));
+  if (!op->sums) PFF_CK(cudaMalloc((void**)&op->sums, sizeof(double) * 8));
   PFF_CK(cudaMemsetAsync(op->fint, 0, sizeof(double) * n, st));
   ElemArgs<double> a;
   std::memset(&a, 0, sizeof(a));
@@ -784,6 +784,16 @@ int pff_get_history(pff_op* op, int which, double* hist, void* stream) {
   PFF_REQUIRE(op && hist && (which == 0 || which == 1), "pff_get_history: bad argument");
   PFF_CK(cudaMemcpyAsync(hist, which ? op->hist_t : op->hist_c, sizeof(double) * 15 * op->nq,
                          cudaMemcpyDeviceToDevice, S(stream)));
+  return PFF_OK;
+}
+
+int pff_state_summary(pff_op* op, const double* z, double* out8, void* stream) {
+  PFF_REQUIRE(op && z && out8, "pff_state_summary: null argument");
+  cudaStream_t st = S(stream);
+  if (!op->sums) PFF_CK(cudaMalloc((void**)&op->sums, sizeof(double) * 8));
+  PFF_CK(launch_state_summary(op->flags, op->hist_c, op->nq, z + 3 * op->mesh.nn, op->mesh.nn, op->sums, st));
+  PFF_CK(cudaMemcpyAsync(out8, op->sums, sizeof(double) * 8, cudaMemcpyDeviceToHost, st));
+  PFF_CK(cudaStreamSynchronize(st));
   return PFF_OK;
 }
 

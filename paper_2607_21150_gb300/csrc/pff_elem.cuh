@@ -367,7 +367,7 @@ template <int Q, typename T>
 __device__ __forceinline__ void jac_at(const ElemArgs<T>& a, int k, int t, const T g[4][3], T phi, T o[4][3], T& o0) {
   constexpr long long EB = elems_per_block(Q);
   constexpr long long run = (long long)Q * Q * EB, stride = run * Q;
-  const long long blk = blockIdx.x * (long long)kLinWords * stride;
+  const long long blk = (a.blk0 + blockIdx.x) * (long long)kLinWords * stride;
   if constexpr (sizeof(typename ElemTypes<T>::L) == 4) {
     const float* q = a.lin + blk + lin32_word(0, k, t, stride, run);
     const float* tl = a.lin + blk + lin32_word(kLinQuadWords, k, t, stride, run);
@@ -408,7 +408,7 @@ __device__ __forceinline__ void prefetch_slice(const ElemArgs<T>& a, int k, int 
     if (t >= NQ + (a.kx ? kLinWords - kLinQuadWords : kWKX - kLinQuadWords) || k >= Q) return;
     const long long nblk = (a.mesh.nel + EB - 1) / EB;
     const long long plane = nblk * kLinWords * Q * Q * Q * EB;
-    const long long blk = blockIdx.x * kLinWords * Q * run;
+    const long long blk = (a.blk0 + blockIdx.x) * kLinWords * Q * run;
     const uintptr_t base = reinterpret_cast<uintptr_t>(a.lin);
     if (t < NQ) prefetch_run(base, blk + lin32_word(4 * t, k, 0, Q * run, run), 4 * run, plane);
     else prefetch_run(base, blk + lin32_word(kLinQuadWords + t - NQ, k, 0, Q * run, run), run, plane);
@@ -431,7 +431,7 @@ k_elem(const ElemArgs<T> a) {
   const int t = threadIdx.x;
   const int el = t / Q2, ij = t % Q2;
   const int i = ij % Q, j = ij / Q;
-  const int e = blockIdx.x * EB + el;
+  const int e = (a.blk0 + blockIdx.x) * EB + el;
   const bool valid = e < a.mesh.nel;
 
   T* mats = sm;
@@ -604,7 +604,7 @@ k_diag(const ElemArgs<T> a) {
   const int t = threadIdx.x;
   const int el = t / Q2, ij = t % Q2;
   const int i = ij % Q, j = ij / Q;
-  const int e = blockIdx.x * EB + el;
+  const int e = (a.blk0 + blockIdx.x) * EB + el;
   const bool valid = e < a.mesh.nel;
   T* M = sm;  // [3][Q][P]: BB, BD, DD
   for (int idx = t; idx < Q * P; idx += blockDim.x) {
@@ -662,7 +662,7 @@ k_diag(const ElemArgs<T> a) {
     T col[Q];
 #pragma unroll
     for (int k = 0; k < Q; ++k) {
-      const long long off = blockIdx.x * blk_words + (sizeof(T) == 4 ? lin32_word(word, k, t, stride, Q2 * EB)
+      const long long off = (a.blk0 + blockIdx.x) * blk_words + (sizeof(T) == 4 ? lin32_word(word, k, t, stride, Q2 * EB)
                                                                     : (long long)word * stride + (long long)k * Q2 * EB + t);
       col[k] = valid ? ldg(a.lin + off) * wgt : T(0);
     }
@@ -714,7 +714,7 @@ namespace pff {
 template <int P, int Q, typename T>
 cudaError_t launch_elem_pq(int mode, const ElemArgs<T>& a, cudaStream_t st) {
   constexpr int EB = elems_per_block(Q);
-  int nblk = (a.mesh.nel + EB - 1) / EB;
+  int nblk = a.nblk > 0 ? a.nblk : (a.mesh.nel + EB - 1) / EB;
   if (nblk == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4 && sizeof(typename ElemTypes<T>::L) == 4) {  // FP32 action with BF16 words
     if (a.lin16) return mode == kApply ? launch_elem_w16<P, Q>(a, st) : cudaErrorInvalidValue;

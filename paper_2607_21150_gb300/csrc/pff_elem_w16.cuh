@@ -180,10 +180,10 @@ k_elem_w16(const ElemArgs<float> a) {
   const int t = threadIdx.x;
   const int el = t / Q2, ij = t % Q2;
   const int i = ij % Q, j = ij / Q;
-  const int e = blockIdx.x * EB + el;
+  const int e = (a.blk0 + blockIdx.x) * EB + el;
   const bool valid = e < a.mesh.nel;
   const unsigned char* gblk =
-      reinterpret_cast<const unsigned char*>(a.lin16) + (unsigned long long)blockIdx.x * 2 * kLin16Words * Q3 * EB;
+      reinterpret_cast<const unsigned char*>(a.lin16) + (unsigned long long)(a.blk0 + blockIdx.x) * 2 * kLin16Words * Q3 * EB;
 
   float* Bs = sm;
   float* Dcs = Bs + Q * P;
@@ -276,7 +276,7 @@ k_elem_w16(const ElemArgs<float> a) {
 template <int P, int Q>
 cudaError_t launch_elem_w16(const ElemArgs<float>& a, cudaStream_t st) {
   constexpr int EB = elems_per_block(Q);
-  const int nblk = (a.mesh.nel + EB - 1) / EB;
+  const int nblk = a.nblk > 0 ? a.nblk : (a.mesh.nel + EB - 1) / EB;
   if (nblk == 0) return cudaSuccess;
   const size_t smem = w16_slot_bytes<Q>() + 16 +
                       sizeof(float) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words_t<Q, float>());

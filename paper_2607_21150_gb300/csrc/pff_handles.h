@@ -61,7 +61,7 @@ struct pff_op {
   int bf16 = 0;
   double* geo = nullptr;      // mapped mesh: [10][nq] d xi / dX and w det J (null: the affine box)
   double* fint = nullptr;     // internal force work vector of pff_reaction (allocated on first use)
-  double* sums = nullptr;     // 4 doubles
+  double* sums = nullptr;     // 8 doubles (reaction sums, state summary)
 };
 
 struct pff_level {

@@ -169,6 +169,8 @@ struct ElemArgs {
   long long lo;           // df64: offset (in words) from the hi plane to the lo plane
   const uint16_t* lin16;  // FP32 action only: read the BF16 words (lin16_word layout) instead of lin
   int* status;            // device status word (BF16-word action: bit 32 when a staging wait gave up)
+  int blk0;               // first element block of the launch (actions; 0 = from the first)
+  int nblk;               // element blocks of the launch (actions; 0 = all blocks from blk0 = 0)
 };
 
 // One translation unit per quadrature size Q (pff_elem_q<Q>.cu); each covers
@@ -197,6 +199,10 @@ cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nbl
 cudaError_t launch_split_bf16(const double* a, uint16_t* out, long long nblk, int Q, cudaStream_t st);
 cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st);
 cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st);
+// out[8]: flag counts (yield, history active, theta >= 0), phi max / min, nodes
+// with phi > 0.9, max eps_p and max H of hist (device memory).
+cudaError_t launch_state_summary(const uint8_t* flags, const double* hist, long long nq, const double* phi,
+                                 long long nn, double* out, cudaStream_t st);
 cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, cudaStream_t st);
 template <typename T>
 cudaError_t launch_prolong(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* xc, T* xf,

@@ -345,6 +345,75 @@ cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long l
   return cudaGetLastError();
 }
 
+// State summary of a load step (the per-step log): out[0..2] = points whose
+// flags have bit 0 (Prandtl yield), bit 1 (history active), bit 2 (theta >=
+// 0); out[3], out[4] = largest and smallest nodal phase field; out[5] = nodes
+// with phi > 0.9; out[6], out[7] = largest accumulated plastic strain and
+// history field of the given history.  One block-reduced pass per quantity.
+__device__ __forceinline__ void atomic_max_d(double* a, double v) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(a);
+  unsigned long long old = *p;
+  while (v > __longlong_as_double((long long)old)) {
+    const unsigned long long prev = atomicCAS(p, old, (unsigned long long)__double_as_longlong(v));
+    if (prev == old) break;
+    old = prev;
+  }
+}
+__device__ __forceinline__ void atomic_min_d(double* a, double v) {
+  unsigned long long* p = reinterpret_cast<unsigned long long*>(a);
+  unsigned long long old = *p;
+  while (v < __longlong_as_double((long long)old)) {
+    const unsigned long long prev = atomicCAS(p, old, (unsigned long long)__double_as_longlong(v));
+    if (prev == old) break;
+    old = prev;
+  }
+}
+__global__ void k_state_summary(const uint8_t* __restrict__ flags, const double* __restrict__ hist, long long nq,
+                                const double* __restrict__ phi, long long nn, double* __restrict__ out) {
+  double cnt[3] = {0.0, 0.0, 0.0}, hi = -INFINITY, lo = INFINITY, n9 = 0.0, ep = -INFINITY, H = -INFINITY;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq; q += stride) {
+    const unsigned f = flags[q];
+    cnt[0] += (f & 1u) ? 1.0 : 0.0;
+    cnt[1] += (f & 2u) ? 1.0 : 0.0;
+    cnt[2] += (f & 4u) ? 1.0 : 0.0;
+    ep = fmax(ep, hist[12 * nq + q]);
+    H = fmax(H, hist[13 * nq + q]);
+  }
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < nn; n += stride) {
+    const double v = phi[n];
+    hi = fmax(hi, v);
+    lo = fmin(lo, v);
+    n9 += (v > 0.9) ? 1.0 : 0.0;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    for (int c = 0; c < 3; ++c) cnt[c] += __shfl_down_sync(0xffffffffu, cnt[c], off);
+    hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, off));
+    lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, off));
+    n9 += __shfl_down_sync(0xffffffffu, n9, off);
+    ep = fmax(ep, __shfl_down_sync(0xffffffffu, ep, off));
+    H = fmax(H, __shfl_down_sync(0xffffffffu, H, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    for (int c = 0; c < 3; ++c) atomicAdd(out + c, cnt[c]);
+    atomic_max_d(out + 3, hi);
+    atomic_min_d(out + 4, lo);
+    atomicAdd(out + 5, n9);
+    atomic_max_d(out + 6, ep);
+    atomic_max_d(out + 7, H);
+  }
+}
+__global__ void k_state_summary_init(double* out) {
+  if (threadIdx.x < 8) out[threadIdx.x] = (threadIdx.x == 3 || threadIdx.x >= 6) ? -INFINITY
+                                          : (threadIdx.x == 4 ? INFINITY : 0.0);
+}
+cudaError_t launch_state_summary(const uint8_t* flags, const double* hist, long long nq, const double* phi,
+                                 long long nn, double* out, cudaStream_t st) {
+  k_state_summary_init<<<1, 32, 0, st>>>(out); note_launch();
+  k_state_summary<<<grid_for(nq > nn ? nq : nn), kVecThreads, 0, st>>>(flags, hist, nq, phi, nn, out); note_launch();
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_prolong<double>(const MeshDev&, const MeshDev&, const double*, const double*, double*,
                                             const uint8_t*, const uint8_t*, cudaStream_t);
 template cudaError_t launch_prolong<float>(const MeshDev&, const MeshDev&, const float*, const float*, float*,

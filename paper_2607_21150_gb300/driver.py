@@ -21,6 +21,19 @@ class StepFailed(RuntimeError):
     pass
 
 
+def _jsonable(x):
+    """Plain Python numbers, lists and dicts of x (numpy scalars and arrays converted)."""
+    if isinstance(x, dict):
+        return {str(k): _jsonable(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [_jsonable(v) for v in x]
+    if isinstance(x, np.ndarray):
+        return x.tolist()
+    if isinstance(x, (np.floating, np.integer)):
+        return x.item()
+    return x
+
+
 class StepController:
     """Adaptive sub-stepping of the load factor from `start` to `target`.
 
@@ -94,6 +107,10 @@ class LoadStepper:
         self.loaded = 0.0
         # callback(f_from, f_to, dt, hist_before, stats) after every converged sub-step of `advance`
         self.on_substep = None
+        # per committed sub-step: state summary (flag counts, phi extremes, ...) and the
+        # lambda_max estimates of the levels
+        self.diagnostics = False
+        self.failures = []   # sub-steps that did not converge (undone), with their solver stats
 
     def set_load(self, factor: float):
         vals = torch.from_numpy((self.unit * factor).ravel()).to(self.s.dev)
@@ -112,11 +129,70 @@ class LoadStepper:
     def _commit(self, factor: float, stats, t0: float):
         pff.pff_commit_history(self.s.op, self.s.stream)
         stats["reaction"] = pff.pff_reaction(self.s.op, self.top, self.s.stream)[2]
+        if self.diagnostics:
+            stats["state"] = pff.pff_state_summary(self.s.op, self.z, self.s.stream)
+            stats["lambda_max"] = [pff.pff_solver_level_lambda(self.solver, l) for l in range(len(self.levels))]
         stats["wall_s"] = time.perf_counter() - t0
         stats["load"] = factor
         self.loaded = factor
         self.history.append(stats)
         return stats
+
+    # ------------------------------------------------------------ checkpoints
+    def state_dict(self):
+        """Everything a later run needs to continue from the last committed
+        load factor: the state z, the committed quadrature-point history, the
+        phase map (to check that a resume uses the same microstructure), the
+        load factor and the nominal time step (host arrays)."""
+        if self.z.is_cuda:
+            torch.cuda.synchronize()
+        return {"z": self.z.cpu().numpy().copy(), "hist": self.s.history(0).cpu().numpy().copy(),
+                "phase": np.ascontiguousarray(self.w.phase, dtype=np.uint8).copy(),
+                "loaded": float(self.loaded), "dt": float(self.dt)}
+
+    def load_state_dict(self, d):
+        """Continue from a state_dict: z, committed history, load factor (and
+        its Dirichlet values); refuses a different mesh or phase map."""
+        if d["z"].size != self.z.numel() or d["hist"].shape != (15, self.w.mesh.nq):
+            raise ValueError("checkpoint of a different mesh")
+        if not np.array_equal(d["phase"], np.asarray(self.w.phase, dtype=np.uint8)):
+            raise ValueError("checkpoint of a different microstructure (phase map)")
+        self.dt = float(d["dt"])
+        self.s.set_history(d["hist"])
+        self.z.copy_(torch.from_numpy(np.ascontiguousarray(d["z"], dtype=np.float64).ravel()))
+        self.loaded = float(d["loaded"])
+        self.set_load(self.loaded)
+        if self.z.is_cuda:
+            torch.cuda.synchronize()
+
+    def save_checkpoint(self, path: str, meta: dict | None = None):
+        """Writes state_dict() to directory `path` (z.npy, hist.npy, phase.npy,
+        meta.json with the load factor, time step, per-step log and `meta`);
+        files are written under temporary names and renamed, so that an
+        interrupted save leaves the previous checkpoint intact."""
+        import json
+        import os
+        d = self.state_dict()
+        os.makedirs(path, exist_ok=True)
+        for k in ("z", "hist", "phase"):
+            np.save(os.path.join(path, k + ".tmp.npy"), d[k])
+        info = {"loaded": d["loaded"], "dt": d["dt"], "log": _jsonable(self.history), **(meta or {})}
+        with open(os.path.join(path, "meta.tmp.json"), "w") as f:
+            json.dump(info, f)
+        for k in ("z", "hist", "phase"):
+            os.replace(os.path.join(path, k + ".tmp.npy"), os.path.join(path, k + ".npy"))
+        os.replace(os.path.join(path, "meta.tmp.json"), os.path.join(path, "meta.json"))
+
+    def load_checkpoint(self, path: str) -> dict:
+        """Continues from a checkpoint written by save_checkpoint; returns its meta."""
+        import json
+        import os
+        with open(os.path.join(path, "meta.json")) as f:
+            info = json.load(f)
+        d = {k: np.load(os.path.join(path, k + ".npy")) for k in ("z", "hist", "phase")}
+        d.update(loaded=info["loaded"], dt=info["dt"])
+        self.load_state_dict(d)
+        return info
 
     def step(self, k: float):
         """One Newton solve to load factor k from the current one, the time step
@@ -151,6 +227,7 @@ class LoadStepper:
                 # the committed history is untouched until a sub-step converges
                 self.z.copy_(z_prev)
                 self.loaded = f0
+                self.failures.append({"from": f0, "to": f1, **{k: v for k, v in stats.items() if k != "res_history"}})
                 return False
             stats["step"] = k
             stats["dt"] = dt

@@ -133,6 +133,7 @@ _SIGS = {
     "pff_get_flags": ([_VP, _VP, _VP], _I),
     "pff_get_linearization": ([_VP, _VP, _VP], _I),
     "pff_get_status": ([_VP, _VP, ctypes.POINTER(_I)], _I),
+    "pff_state_summary": ([_VP, _VP, ctypes.POINTER(_D), _VP], _I),
     "pff_probe_pipe": ([_I, _I64, _I, _I, _VP, ctypes.POINTER(_D), _VP], _I),
 }
 
@@ -476,3 +477,14 @@ def pff_probe_pipe(kind, iters, blocks, threads, sink, stream=None):
 def pff_kernel_launches():
     """Kernels libpff has launched in this process so far."""
     return int(lib().pff_kernel_launches())
+
+
+STATE_SUMMARY_KEYS = ("n_yield", "n_active", "n_tension", "phi_max", "phi_min", "n_phi_above_0.9", "eps_p_max",
+                      "H_max")
+
+
+def pff_state_summary(op, z, stream=None):
+    """Per-step state summary (dict with STATE_SUMMARY_KEYS)."""
+    out = (_D * 8)()
+    _call("pff_state_summary", op, _ptr(z), out, _stream(stream))
+    return dict(zip(STATE_SUMMARY_KEYS, [float(v) for v in out]))

@@ -175,3 +175,40 @@ def test_replayed_schedule_must_converge_and_end_at_the_target(monkeypatch):
     lsp2, _, _ = _stepper(monkeypatch, limit=1.0)
     with pytest.raises(StepFailed, match="schedule ends"):
         lsp2.advance(1, schedule=[0.5])
+
+
+def test_checkpoint_round_trip(monkeypatch, tmp_path):
+    """save_checkpoint writes z, the committed history, the phase map, the load
+    factor and the log; load_checkpoint on a fresh stepper restores them (the
+    history through the session, the Dirichlet values of the load factor) and
+    refuses a checkpoint of another microstructure."""
+    import torch
+    lsp, log, w = _stepper(monkeypatch, limit=1.0)
+    lsp.s.hist = torch.arange(15 * w.mesh.nq, dtype=torch.float64).view(15, -1)
+    lsp.advance(1)
+    lsp.advance(2)
+    lsp.save_checkpoint(str(tmp_path / "ck"), {"step": 2})
+    lsp2, log2, _ = _stepper(monkeypatch, limit=1.0)
+    got = {}
+    lsp2.s.set_history = lambda h: got.update(hist=np.array(h))
+    loads = []
+    lsp2.set_load = lambda f: loads.append(f)
+    info = lsp2.load_checkpoint(str(tmp_path / "ck"))
+    assert info["step"] == 2 and info["loaded"] == 2.0 and len(info["log"]) == 2
+    assert lsp2.loaded == 2.0 and loads == [2.0]
+    assert torch.equal(lsp2.z, lsp.z)
+    assert np.array_equal(got["hist"], lsp.s.hist.numpy())
+    lsp3, _, _ = _stepper(monkeypatch, limit=1.0)
+    lsp3.w.phase = lsp3.w.phase.copy()
+    lsp3.w.phase[0] ^= 1
+    with pytest.raises(ValueError, match="microstructure"):
+        lsp3.load_checkpoint(str(tmp_path / "ck"))
+
+
+def test_failed_substeps_are_recorded(monkeypatch):
+    lsp, log, w = _stepper(monkeypatch, limit=0.3)
+    lsp.advance(1)
+    fails = [(f["from"], f["to"]) for f in lsp.failures]
+    assert fails[:2] == [(0.0, 1.0), (0.0, 0.5)]
+    assert all(b - a > 0.3 for a, b in fails) and all(f["converged"] == 0 for f in lsp.failures)
+    assert len(fails) + len(lsp.history) == len(log["solves"])

@@ -32,7 +32,7 @@ def _tension_box(at=2):
     hist = inputs.zero_history(m.nq)
     if at == 1:
         for pid, d in ((0, inputs.EX3_MATRIX), (1, inputs.EX3_PARTICLE)):
-            hist[13, phase == pid] = 3 * d["Gc"] / (16 * d["l0"])
+            hist[13, phase == pid] = d["psi_c"]
     return inputs.Workload("tension", m, phases, glob, phase, np.zeros((4, m.nn)), hist, mask, dv)
 
 
@@ -110,3 +110,44 @@ def test_substeps_match_oracle(orc):
     assert np.linalg.norm(zg - z) <= 1e-9 * np.linalg.norm(z)
     assert np.linalg.norm(lsp.s.history(0).cpu().numpy() - hist) <= 1e-9 * np.linalg.norm(hist)
     lsp.close()
+
+
+def test_state_summary_and_checkpoint_resume(orc, tmp_path):
+    """Per-step diagnostics and checkpoint/resume of the load stepper.
+
+    The state summary's flag counts equal the counts of the oracle's flags at
+    the converged state (up to points whose decision margin is below 1e-10);
+    its extremes equal those of the state and history it summarises.  A
+    stepper resumed from the checkpoint after step 1 reproduces step 2 of the
+    uninterrupted run (fields and reaction to 1e-9, the trajectory tolerance:
+    both runs stop Newton at 1e-11 and the atomic scatter orders sums
+    differently from run to run)."""
+    w = _tension_box(1)
+    lsp = LoadStepper(w, levels=[2, 1], mixed=False, newton_rtol=1e-11, krylov_rtol=1e-8)
+    lsp.diagnostics = True
+    h0 = w.hist.copy()
+    st1 = lsp.advance(1)[-1]
+    z1 = lsp.z.cpu().numpy().reshape(4, -1)
+    summ = st1["state"]
+    ref = orc.assemble(w, z=z1, hist=h0, matrix=False)
+    margins = ref["margins"]
+    unsafe = int(np.sum(np.any(np.abs(margins) <= 1e-10, axis=1)))
+    for bit, key in ((1, "n_yield"), (2, "n_active"), (4, "n_tension")):
+        assert abs(summ[key] - np.count_nonzero(ref["flags"] & bit)) <= unsafe, key
+    assert summ["phi_max"] == z1[3].max() and summ["phi_min"] == z1[3].min()
+    assert summ["n_phi_above_0.9"] == np.count_nonzero(z1[3] > 0.9)
+    hc = lsp.s.history(0).cpu().numpy()
+    assert summ["eps_p_max"] == hc[12].max() and summ["H_max"] == hc[13].max()
+    assert len(st1["lambda_max"]) == 2 and all(v > 0 for v in st1["lambda_max"])
+    lsp.save_checkpoint(str(tmp_path / "ck"), {"step": 1})
+    st2 = lsp.advance(2)[-1]
+    z2 = lsp.z.cpu().numpy()
+    lsp.close()
+    lsp2 = LoadStepper(w, levels=[2, 1], mixed=False, newton_rtol=1e-11, krylov_rtol=1e-8)
+    info = lsp2.load_checkpoint(str(tmp_path / "ck"))
+    assert info["step"] == 1 and lsp2.loaded == 1.0
+    st2b = lsp2.advance(2)[-1]
+    z2b = lsp2.z.cpu().numpy()
+    lsp2.close()
+    assert np.linalg.norm(z2b - z2) <= 1e-9 * np.linalg.norm(z2)
+    assert abs(st2b["reaction"] - st2["reaction"]) <= 1e-9 * abs(st2["reaction"])

@@ -17,6 +17,7 @@ class _Fake:
     def __init__(self, w, mixed=True, max_cuts=6, **kw):
         self.mixed, self.max_cuts, self.kw = mixed, max_cuts, kw
         self.history = []
+        self.failures = []
         _Fake.made.append(self)
 
     def advance(self, k):
