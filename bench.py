@@ -213,11 +213,12 @@ def newton_compare(name: str, steps: int = 1, variants=("mixed", "mixed_df", "fp
     from paper_2607_21150_gb300.driver import LoadStepper
     out = {"workload": name, "load_steps": steps}
     fields = {}
-    for label, mixed, df in (("mixed", True, False), ("mixed_df", True, True), ("fp64", False, False)):
+    for label, mixed, df, extra in (("mixed", True, False, {}), ("mixed_df", True, True, {}),
+                                    ("mixed_bf16", True, True, {"level_words": 16}), ("fp64", False, False, {})):
         if label not in variants:
             continue
         w = getattr(inputs, name)()
-        lsp = LoadStepper(w, mixed=mixed, df=df, verbose=1)
+        lsp = LoadStepper(w, mixed=mixed, df=df, verbose=1, **extra)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         its = kr = 0
@@ -244,9 +245,9 @@ def newton_compare(name: str, steps: int = 1, variants=("mixed", "mixed_df", "fp
         torch.cuda.empty_cache()
     if "fp64" in fields:
         a = fields["fp64"]
-        for label in ("mixed", "mixed_df"):
+        for label in ("mixed", "mixed_df", "mixed_bf16"):
             if label in fields:
-                sfx = "" if label == "mixed" else "_df"
+                sfx = "" if label == "mixed" else label[len("mixed"):]
                 out["field_rel_diff" + sfx] = float(np.linalg.norm(a - fields[label]) / np.linalg.norm(a))
                 out[f"speedup_{label}_vs_fp64"] = out["fp64"]["wall_s"] / out[label]["wall_s"]
     return out
@@ -428,7 +429,7 @@ def run_native(args):
 
     w = make_workload(args.config, seed=rank)
     m = w.mesh
-    s = Session(w, levels=(2, 1) if m.p == 4 else (), f32=True, df=True)
+    s = Session(w, levels=(2, 1) if m.p == 4 else (), f32=True, df=True, bf16=True)
     stream = torch.cuda.current_stream()
     z = torch.from_numpy(w.z.ravel()).cuda()
     t0 = torch.cuda.Event(enable_timing=True)
@@ -495,18 +496,25 @@ def run_native(args):
     totdf, _, _ = timed(applydf, args.steps, args.warmup)
     df_rel = float(torch.linalg.norm(ydf - y64) / torch.linalg.norm(y64))
 
-    # end to end through the C ABI with host buffers: pinned x -> device, apply, y -> pinned host
+    # end to end through the C ABI with host buffers: pff_jacobian_apply_host
+    # uploads x from pinned host memory, applies and downloads y, the copies of
+    # one chunk of node layers overlapping the computation of another
     xh = x64.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(x64)
-    yd = torch.empty_like(x64)
 
     def e2e_step():
-        xd.copy_(xh, non_blocking=True)
-        pff.pff_jacobian_apply(L, pff.PFF_F64, xd, yd, stream)
-        yh.copy_(yd, non_blocking=True)
+        pff.pff_jacobian_apply_host(L, pff.PFF_F64, xh, yh, args.e2e_chunks, stream)
 
     tot_e2e, _, _ = timed(e2e_step, args.steps, 3, "e2e")
+    apply64()
+    torch.cuda.synchronize()
+    e2e_rel = float(torch.linalg.norm(yh.cuda() - y64) / torch.linalg.norm(y64))
+
+    # level action with BF16 stored words (FP32 vectors and arithmetic)
+    y16 = torch.empty_like(x32)
+    tot16, _, _ = timed(lambda: pff.pff_jacobian_apply(L, pff.PFF_F32_BF16, x32, y16, stream), args.steps,
+                        args.warmup)
+    bf16_rel = float(torch.linalg.norm(y16.double() - y64) / torch.linalg.norm(y64))
 
     # p-multigrid level actions on the same quadrature points (Galerkin levels)
     levels = {}
@@ -519,9 +527,16 @@ def run_native(args):
         t64l, _, _ = timed(lambda: pff.pff_jacobian_apply(Ll, pff.PFF_F64, xl, yl, stream), args.steps, args.warmup)
         t32l, _, _ = timed(lambda: pff.pff_jacobian_apply(Ll, pff.PFF_F32, xl32, yl32, stream), args.steps,
                            args.warmup)
+        t16l, _, _ = timed(lambda: pff.pff_jacobian_apply(Ll, pff.PFF_F32_BF16, xl32, yl32, stream), args.steps,
+                           args.warmup)
+        b32 = 4 * nl * 2 + nl + 67 * 4 * m.nq
+        b16 = 4 * nl * 2 + nl + 67 * 2 * m.nq
         levels[f"Q{pl}"] = {"ndof": nl, "fp64_ms": t64l / args.steps, "fp32_ms": t32l / args.steps,
+                            "bf16_words_ms": t16l / args.steps,
                             "fp64_gdofs": nl / (t64l / args.steps / 1e3) / 1e9,
-                            "fp32_gdofs": nl / (t32l / args.steps / 1e3) / 1e9}
+                            "fp32_gdofs": nl / (t32l / args.steps / 1e3) / 1e9,
+                            "fp32_hbm_frac": b32 / (t32l / args.steps / 1e3) / 1e9 / peaks()[0],
+                            "bf16_words_hbm_frac": b16 / (t16l / args.steps / 1e3) / 1e9 / peaks()[0]}
 
     # every timed leg: the slowest rank's time
     tot64, tot32, totdf, tot_e2e = max_over_ranks([tot64, tot32, totdf, tot_e2e], world)
@@ -538,6 +553,7 @@ def run_native(args):
     hbm_peak, src = peaks()
     bytes64 = 8 * ndof * 2 + ndof + 67 * 8 * m.nq
     bytes32 = 4 * ndof * 2 + ndof + 67 * 4 * m.nq
+    bytes16 = 4 * ndof * 2 + ndof + 67 * 2 * m.nq
     t32 = tot32 / args.steps / 1e3
     q4 = (P, Q) == (5, 5)
     traffic64 = TRAFFIC_PER_ELEMENT["f64"] * m.nel if q4 else None
@@ -580,6 +596,12 @@ def run_native(args):
                              "algorithmic_bytes": bytes32,
                              "achieved_gbs": bytes32 / t32 / 1e9, "hbm_frac": bytes32 / t32 / 1e9 / hbm_peak,
                              "bound": "hbm", "peak_gbs": hbm_peak, "peak_source": src},
+        "bf16_words_level_apply": {"gdofs": ndof / (tot16 / args.steps / 1e3) / 1e9, "ms": tot16 / args.steps,
+                                   "algorithmic_bytes": bytes16, "achieved_gbs": bytes16 / (tot16 / args.steps / 1e3) / 1e9,
+                                   "hbm_frac": bytes16 / (tot16 / args.steps / 1e3) / 1e9 / hbm_peak,
+                                   "rel_l2_vs_fp64": bf16_rel,
+                                   "note": "FP32 vectors and arithmetic, stored words as BF16 staged through shared "
+                                           "memory by bulk copies (the p-multigrid level precision PFF_F32_BF16)"},
         "df64_apply": {"gdofs": ndof / (totdf / args.steps / 1e3) / 1e9, "ms": totdf / args.steps,
                        "rel_l2_vs_fp64": df_rel,
                        "note": "double-float action (FP32-pair arithmetic, FP64 vectors); not the headline"},
@@ -591,7 +613,9 @@ def run_native(args):
         "apply_mapped_mesh": apply_mapped,
         "adjoint": adjoint,
         "e2e": {"value": whole_job_rate(world, ndof, args.steps, tot_e2e), "unit": "GDoF/s",
-                "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof},
+                "h2d_bytes_per_step": 8 * ndof, "d2h_bytes_per_step": 8 * ndof,
+                "call": f"pff_jacobian_apply_host(PFF_F64, pinned x, pinned y, {args.e2e_chunks} chunks)",
+                "rel_l2_vs_device_buffers": e2e_rel},
         "gpu_launches": launches["fp64"],
         "gpu_launches_note": "libpff kernels launched inside the timed FP64-action region (pff_kernel_launches "
                              "before and after it); per action: the y initialisation and the fused element kernel",
@@ -622,8 +646,11 @@ def main():
                     help="comma list of workloads (compress_q4, tension_q4, notched_q3) of the FP64-vs-mixed "
                          "Newton comparison, the first one reported as newton_step; or none")
     ap.add_argument("--newton-steps", type=int, default=1, help="load steps of the first --newton workload")
-    ap.add_argument("--newton-variants", default="mixed,mixed_df,fp64",
-                    help="comma list of mixed, mixed_df (double-float outer action), fp64")
+    ap.add_argument("--newton-variants", default="mixed,mixed_df,mixed_bf16,fp64",
+                    help="comma list of mixed, mixed_df (double-float outer action), mixed_bf16 (double-float "
+                         "outer action, BF16 level words), fp64")
+    ap.add_argument("--e2e-chunks", type=int, default=8,
+                    help="chunks of the end-to-end action through host buffers (pff_jacobian_apply_host)")
     ap.add_argument("--adjoint-steps", type=int, default=10, help="load steps of the adjoint timing (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":

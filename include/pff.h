@@ -219,6 +219,20 @@ int pff_level_set_mask(pff_level* level, const uint8_t* mask, void* stream);
 int pff_jacobian_apply(pff_level* level, pff_prec prec, const void* x, void* y, void* stream);
 /* Transposed action y = J^T x (same Dirichlet treatment). */
 int pff_jacobian_transpose_apply(pff_level* level, pff_prec prec, const void* x, void* y, void* stream);
+/* The Jacobian action y = J x of pff_jacobian_apply with x and y in HOST
+ * memory (4 N_n entries each, FP64 for PFF_F64 / PFF_DF64, FP32 for PFF_F32 /
+ * PFF_F32_BF16; page-locked memory, e.g. cudaHostAlloc or cudaHostRegister,
+ * lets the copies overlap the computation, pageable memory serialises them).
+ * The element blocks run in `nchunks` chunks in element order (rounded to whole
+ * waves of the element kernel); each chunk's node layers are uploaded ahead of
+ * it on a second stream and the node layers no later chunk touches are
+ * downloaded on a third while later chunks compute.  Asynchronous on
+ * `stream`: x_host must stay unchanged and y_host unread until the stream has
+ * passed this call.  The first call on a level allocates its device staging
+ * (two vectors of 8 bytes per entry), two streams and four events, freed by
+ * pff_destroy_level.  Needs the structured restriction (no explicit offsets). */
+int pff_jacobian_apply_host(pff_level* level, pff_prec prec, const void* x_host, void* y_host, int nchunks,
+                            void* stream);
 /* Diagonal of J (1 on Dirichlet DoFs). */
 int pff_assemble_diagonal(pff_level* level, pff_prec prec, void* diag, void* stream);
 

@@ -15,7 +15,7 @@ LIB = os.path.join(HERE, "libpff.so")
 SOURCES = [
     "pff_elem_q5.cu", "pff_elem_q4.cu", "pff_elem_q3.cu", "pff_elem_q2.cu",
     "pff_point.cu", "pff_vec.cu", "pff_abi.cpp", "pff_basis.cpp", "pff_noalloc.cu", "pff_krylov.cu", "pff_solver.cpp", "pff_adjoint.cu",
-    "pff_probe.cu",
+    "pff_probe.cu", "pff_hostio.cpp",
 ]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

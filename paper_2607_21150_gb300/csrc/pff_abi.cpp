@@ -144,13 +144,18 @@ ElemArgs<T> level_args(const pff_level* L) {
 }
 
 // w16: FP32 action reading the BF16 words (PFF_F32_BF16) instead of the FP32 copy.
+// blk0, nblk: element blocks [blk0, blk0 + nblk) only (nblk = 0: all) and, with
+// init = false, no initialisation of y (the caller has initialised the rows).
 template <typename T>
-int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool w16 = false) {
+int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool w16 = false, int blk0 = 0,
+            int nblk = 0, bool init = true) {
   pff_op* op = L->op;
   if (w16) PFF_REQUIRE(op->bf16 && op->lin16, "PFF_F32_BF16 apply needs pff_op_enable_bf16 before pff_residual");
   else PFF_REQUIRE(linOf<T>(op) != nullptr, "FP32 apply needs pff_op_enable_f32 before pff_residual");
-  PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
+  if (init) PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
   ElemArgs<T> a = level_args<T>(L);
+  a.blk0 = blk0;
+  a.nblk = nblk;
   if (w16) {
     a.lin16 = op->lin16;
     a.status = op->status;
@@ -168,12 +173,15 @@ int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool
 
 // Double-float action: FP64 vectors, contractions on the FP32 pipes with
 // pairs of floats, stored linearisation read from its hi/lo planes.
-int apply_df(pff_level* L, const double* x, double* y, int transpose, cudaStream_t st) {
+int apply_df(pff_level* L, const double* x, double* y, int transpose, cudaStream_t st, int blk0 = 0, int nblk = 0,
+             bool init = true) {
   pff_op* op = L->op;
   PFF_REQUIRE(op->df && op->lin32, "PFF_DF64 apply needs pff_op_enable_df before pff_residual");
-  PFF_CK(launch_init_masked(0, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
+  if (init) PFF_CK(launch_init_masked(0, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
   ElemArgs<df64> a;
   std::memset(&a, 0, sizeof(a));
+  a.blk0 = blk0;
+  a.nblk = nblk;
   a.mesh = L->mesh;
   a.mask = level_mask(L);
   a.B = L->tab.B64;
@@ -252,6 +260,14 @@ static int cheb_t(pff_level* L, int degree, double lmin, double lmax, const T* d
 }
 
 namespace pff {
+int apply_blocks(pff_level* L, int prec, const void* x, void* y, int transpose, int blk0, int nblk, cudaStream_t st) {
+  if (prec == PFF_F64) return apply_t<double>(L, (const double*)x, (double*)y, transpose, st, false, blk0, nblk, false);
+  if (prec == PFF_F32 || prec == PFF_F32_BF16)
+    return apply_t<float>(L, (const float*)x, (float*)y, transpose, st, prec == PFF_F32_BF16, blk0, nblk, false);
+  if (prec == PFF_DF64) return apply_df(L, (const double*)x, (double*)y, transpose, st, blk0, nblk, false);
+  return fail(PFF_ERR_INVALID, "unknown precision");
+}
+const uint8_t* level_rows_mask(const pff_level* L) { return level_mask(L); }
 int set_last_error(int code, const char* msg) { return fail(code, msg); }
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace pff
@@ -689,6 +705,7 @@ int pff_create_level(pff_op* fine, int p, pff_level** out) {
 
 int pff_destroy_level(pff_level* L) {
   if (!L) return PFF_OK;
+  pff::free_host_io(L);
   free_tables(L->tab);
   cudaFree(L->mask);
   cudaFree(L->I64); cudaFree(L->I32);

@@ -64,7 +64,10 @@ struct pff_op {
   double* sums = nullptr;     // 8 doubles (reaction sums, state summary)
 };
 
+namespace pff { struct HostIO; }
+
 struct pff_level {
+  pff::HostIO* hio = nullptr;  // device staging and streams of pff_jacobian_apply_host (created on first use)
   pff_op* op;
   int p;
   MeshDev mesh;
@@ -77,3 +80,14 @@ struct pff_level {
   float* I32 = nullptr;
 };
 
+
+namespace pff {
+// Element blocks [blk0, blk0 + nblk) of a level action (nblk = 0: all), without
+// the initialisation of y; prec PFF_F64, PFF_F32, PFF_DF64 or PFF_F32_BF16
+// (pff_abi.cpp).
+int apply_blocks(pff_level* L, int prec, const void* x, void* y, int transpose, int blk0, int nblk, cudaStream_t st);
+// The Dirichlet mask of a level's rows (pff_abi.cpp).
+const uint8_t* level_rows_mask(const pff_level* L);
+// Releases the staging buffers, streams and events of pff_jacobian_apply_host (pff_hostio.cpp).
+void free_host_io(pff_level* L);
+}  // namespace pff

@@ -193,6 +193,9 @@ cudaError_t launch_geometry(const double* J, double* geo, const Geom& g, int Q, 
 // Vector / transfer kernels (pff_vec.cu)
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
+// y = mask ? x : 0 on nodes [n0, n1) of each field (prec 0: FP64, 1: FP32).
+cudaError_t launch_init_rows(int prec, void* y, const void* x, const uint8_t* mask, long long nn, long long n0,
+                             long long n1, cudaStream_t st);
 // hi[i] = fl32(a[i]) and, when lo is not null, lo[i] = fl32(a[i] - hi[i]).
 cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nblk, int Q, cudaStream_t st);
 // out = the BF16 words (round to nearest even) of the FP64 words a, lin16_word layout.

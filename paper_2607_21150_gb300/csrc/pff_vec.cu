@@ -45,6 +45,26 @@ cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* u
   return cudaGetLastError();
 }
 
+// y = mask ? x : 0 on the nodes [n0, n1) of each of the four fields (rows of
+// one range of node layers; the pipelined action through host buffers).
+template <typename T>
+__global__ void k_init_rows(T* __restrict__ y, const T* __restrict__ x, const uint8_t* __restrict__ mask, long long nn,
+                            long long n0, long long cnt) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < 4 * cnt; i += (long long)gridDim.x * blockDim.x) {
+    const long long g = (i / cnt) * nn + n0 + i % cnt;
+    y[g] = (mask && mask[g]) ? x[g] : T(0);
+  }
+}
+cudaError_t launch_init_rows(int prec, void* y, const void* x, const uint8_t* mask, long long nn, long long n0,
+                             long long n1, cudaStream_t st) {
+  const long long cnt = n1 - n0;
+  if (cnt <= 0) return cudaSuccess;
+  if (prec == 0) k_init_rows<double><<<grid_for(4 * cnt), kVecThreads, 0, st>>>((double*)y, (const double*)x, mask, nn, n0, cnt);
+  else k_init_rows<float><<<grid_for(4 * cnt), kVecThreads, 0, st>>>((float*)y, (const float*)x, mask, nn, n0, cnt);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // FP32 planes of the stored linearisation: hi = fl32(a), lo = fl32(a - hi)
 // (lo optional), words [0, 64) of every point regrouped by four (the quad
 // layout of lin32_word), words [64, 70) in place.  One thread per output float4

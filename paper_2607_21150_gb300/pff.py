@@ -108,6 +108,7 @@ _SIGS = {
     "pff_level_set_mask": ([_VP, _VP, _VP], _I),
     "pff_jacobian_apply": ([_VP, _I, _VP, _VP, _VP], _I),
     "pff_jacobian_transpose_apply": ([_VP, _I, _VP, _VP, _VP], _I),
+    "pff_jacobian_apply_host": ([_VP, _I, _VP, _VP, _I, _VP], _I),
     "pff_assemble_diagonal": ([_VP, _I, _VP, _VP], _I),
     "pff_prolong": ([_VP, _VP, _I, _VP, _VP, _VP], _I),
     "pff_restrict": ([_VP, _VP, _I, _VP, _VP, _VP], _I),
@@ -333,6 +334,12 @@ def pff_jacobian_apply(level, prec, x, y, stream=None):
 
 def pff_jacobian_transpose_apply(level, prec, x, y, stream=None):
     _call("pff_jacobian_transpose_apply", level, int(prec), _ptr(x), _ptr(y), _stream(stream))
+
+
+def pff_jacobian_apply_host(level, prec, x_host, y_host, nchunks=8, stream=None):
+    """y = J x with x, y in (page-locked) host memory, the copies overlapped
+    with the computation; asynchronous on the stream."""
+    _call("pff_jacobian_apply_host", level, int(prec), _ptr(x_host), _ptr(y_host), int(nchunks), _stream(stream))
 
 
 def pff_assemble_diagonal(level, prec, diag, stream=None):
