@@ -126,6 +126,7 @@ template <> const double* linOf<double>(const pff_op* op) { return op->lin64; }
 template <> const float* linOf<float>(const pff_op* op) { return op->lin32; }
 
 const uint8_t* level_mask(const pff_level* L) { return L->is_fine ? L->op->mask : L->mask; }
+const uint8_t* level_emask(const pff_level* L) { return L->is_fine ? L->op->emask : L->emask; }
 
 template <typename T>
 ElemArgs<T> level_args(const pff_level* L) {
@@ -133,6 +134,7 @@ ElemArgs<T> level_args(const pff_level* L) {
   std::memset(&a, 0, sizeof(a));
   a.mesh = L->mesh;
   a.mask = level_mask(L);
+  a.emask = a.mask ? level_emask(L) : nullptr;
   a.B = tabB<T>(L->tab);
   a.Dc = tabDc<T>(L->tab);
   a.Dt = tabDt<T>(L->tab);
@@ -184,6 +186,7 @@ int apply_df(pff_level* L, const double* x, double* y, int transpose, cudaStream
   a.nblk = nblk;
   a.mesh = L->mesh;
   a.mask = level_mask(L);
+  a.emask = a.mask ? level_emask(L) : nullptr;
   a.B = L->tab.B64;
   a.Dc = L->tab.Dc64;
   a.Dt = L->tab.Dt64;
@@ -467,6 +470,7 @@ int pff_destroy_operator(pff_op* op) {
   if (!op) return PFF_OK;
   cudaFree(op->hist_c); cudaFree(op->hist_t); cudaFree(op->phase); cudaFree(op->flags);
   cudaFree(op->lin64); cudaFree(op->lin32); cudaFree(op->lin16); cudaFree(op->io); cudaFree(op->mask);
+  cudaFree(op->emask);
   cudaFree(op->dvals); cudaFree(op->status);
   cudaFree(op->fint); cudaFree(op->sums); cudaFree(op->geo);
   free_tables(op->tab);
@@ -546,11 +550,14 @@ int pff_set_dirichlet(pff_op* op, const uint8_t* mask, const double* values, voi
   long long n = 4 * op->mesh.nn;
   if (!mask) {
     cudaFree(op->mask); op->mask = nullptr;
+    cudaFree(op->emask); op->emask = nullptr;
     cudaFree(op->dvals); op->dvals = nullptr;
     return PFF_OK;
   }
   if (!op->mask) PFF_CK(cudaMalloc((void**)&op->mask, n));
+  if (!op->emask) PFF_CK(cudaMalloc((void**)&op->emask, op->mesh.nel > 0 ? op->mesh.nel : 1));
   PFF_CK(cudaMemcpyAsync(op->mask, mask, n, cudaMemcpyDeviceToDevice, S(stream)));
+  PFF_CK(launch_elem_mask(op->mesh, op->mask, op->emask, S(stream)));
   if (values) {
     if (!op->dvals) PFF_CK(cudaMalloc((void**)&op->dvals, sizeof(double) * n));
     PFF_CK(cudaMemcpyAsync(op->dvals, values, sizeof(double) * n, cudaMemcpyDeviceToDevice, S(stream)));
@@ -648,6 +655,7 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   PFF_CK(launch_pointwise(pa, st));
   a.y = r;
   a.mask = op->mask;
+  a.emask = op->mask ? op->emask : nullptr;
   PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
   if (op->f32 && op->lin32)
     PFF_CK(launch_split_df(op->lin64, op->lin32, op->df ? op->lin32 + op->lin_len : nullptr,
@@ -708,6 +716,7 @@ int pff_destroy_level(pff_level* L) {
   pff::free_host_io(L);
   free_tables(L->tab);
   cudaFree(L->mask);
+  cudaFree(L->emask);
   cudaFree(L->I64); cudaFree(L->I32);
   delete L;
   return PFF_OK;
@@ -719,9 +728,15 @@ int pff_level_set_mask(pff_level* L, const uint8_t* mask, void* stream) {
   PFF_REQUIRE(L, "pff_level_set_mask: null level");
   PFF_REQUIRE(!L->is_fine, "pff_level_set_mask: the fine level uses pff_set_dirichlet");
   long long n = 4 * L->mesh.nn;
-  if (!mask) { cudaFree(L->mask); L->mask = nullptr; return PFF_OK; }
+  if (!mask) {
+    cudaFree(L->mask); L->mask = nullptr;
+    cudaFree(L->emask); L->emask = nullptr;
+    return PFF_OK;
+  }
   if (!L->mask) PFF_CK(cudaMalloc((void**)&L->mask, n));
+  if (!L->emask) PFF_CK(cudaMalloc((void**)&L->emask, L->mesh.nel > 0 ? L->mesh.nel : 1));
   PFF_CK(cudaMemcpyAsync(L->mask, mask, n, cudaMemcpyDeviceToDevice, S(stream)));
+  PFF_CK(launch_elem_mask(L->mesh, L->mask, L->emask, S(stream)));
   return PFF_OK;
 }
 

@@ -111,6 +111,8 @@ template <int P, int Q, typename T>
 __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, Q, T>& s, int e, bool valid, int ij) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   const long long nn = a.mesh.nn;
+  // the node mask is read only for elements flagged as having masked nodes
+  const bool masked = a.mask && valid && (!a.emask || a.emask[e]);
   // every thread's gather loads (values and mask bytes) are independent and
   // issued together: one memory round trip instead of one per node and a
   // second one behind each mask byte
@@ -126,7 +128,7 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
       if (valid) {
         long long g = f * nn + n;
         const auto xv = ldg(a.x + g);
-        const bool fixed = a.mask && ldg(a.mask + g);
+        const bool fixed = masked && ldg(a.mask + g);
         if (!fixed) v = from_store<T>(xv);
       }
       s.bufA[f * Q3 + idx] = v;
@@ -244,6 +246,7 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
   __syncthreads();
   if (!valid) return;
   const long long nn = a.mesh.nn;
+  const bool masked = a.mask && (!a.emask || a.emask[e]);
 #pragma unroll
   for (int r = 0; r < (P3 + Q2 - 1) / Q2; ++r) {
     const int idx = ij + r * Q2;
@@ -253,7 +256,7 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
       long long g = f * nn + n;
-      if (a.mask && ldg(a.mask + g)) continue;
+      if (masked && ldg(a.mask + g)) continue;
       atomicAdd(a.y + g, to_vec(s.bufA[f * Q3 + idx]));
     }
   }

@@ -51,6 +51,7 @@ struct pff_op {
   long long lin_len = 0;
   double* io = nullptr;
   uint8_t* mask = nullptr;
+  uint8_t* emask = nullptr;   // [nel] elements with masked nodes (fine level), from pff_set_dirichlet
   double* dvals = nullptr;
   int* status = nullptr;
   int f32 = 0;
@@ -73,6 +74,7 @@ struct pff_level {
   MeshDev mesh;
   Tables tab;
   uint8_t* mask = nullptr;   // owned copy (coarse levels) ; fine level uses op->mask
+  uint8_t* emask = nullptr;  // [nel] elements with masked nodes (coarse levels; the fine level uses op->emask)
   bool is_fine = false;
   // prolongation table towards the finer level with order I_pf
   int I_pf = -1;

@@ -169,6 +169,7 @@ struct ElemArgs {
   long long lo;           // df64: offset (in words) from the hi plane to the lo plane
   const uint16_t* lin16;  // FP32 action only: read the BF16 words (lin16_word layout) instead of lin
   int* status;            // device status word (BF16-word action: bit 32 when a staging wait gave up)
+  const uint8_t* emask;   // [nel] 1 = the element has masked nodes (null: check the mask everywhere)
   int blk0;               // first element block of the launch (actions; 0 = from the first)
   int nblk;               // element blocks of the launch (actions; 0 = all blocks from blk0 = 0)
 };
@@ -193,6 +194,8 @@ cudaError_t launch_geometry(const double* J, double* geo, const Geom& g, int Q, 
 // Vector / transfer kernels (pff_vec.cu)
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
+// emask[e] = 1 where element e has a masked node (any field), 0 elsewhere.
+cudaError_t launch_elem_mask(const MeshDev& m, const uint8_t* mask, uint8_t* emask, cudaStream_t st);
 // y = mask ? x : 0 on nodes [n0, n1) of each field (prec 0: FP64, 1: FP32).
 cudaError_t launch_init_rows(int prec, void* y, const void* x, const uint8_t* mask, long long nn, long long n0,
                              long long n1, cudaStream_t st);

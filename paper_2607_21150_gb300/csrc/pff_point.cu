@@ -6,7 +6,10 @@
 // takes eps_i = log1p(x_i) / 2 (the log1p form of Sec. 2.2), corrects the
 // deviatoric principal strains with the branch factor a_k (Box 1 step 2 and
 // Eq. principal-directions-format-1 with the degraded mu and q_tr of Sec. 3),
-// and rebuilds tau_d,k = N diag(2 mu a eps_d) N^T.  The volumetric strain
+// and rebuilds tau_d,k = N diag(2 mu a eps_d) N^T.  The Maxwell and Prandtl
+// branches are diagonalised in the Hooke branch's principal frame (their b_tr
+// differ from it by the inelastic strains, so Jacobi starts nearly
+// converged).  The volumetric strain
 // theta = ln J is shared by all branches and decides the Amor split
 // (Eqs. linear-Psi-plus, linear-degraded-stress).
 //
@@ -117,6 +120,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
   double hist_new[12];
   for (int v = 0; v < 12; ++v) hist_new[v] = a.hist[v * nq + q];
 
+  double N0[3][3];  // principal frame of the Hooke branch (always present): warm start of the others
   for (int br = 0; br < 3; ++br) {
     if (!ph.has[br]) continue;
     const double mu = ph.mu[br];
@@ -143,7 +147,27 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
         }
     }
     double N[3][3], x[3];
-    if (!jacobi3(X, N, x)) status |= 1;
+    if (br == 0) {
+      if (!jacobi3(X, N, x)) status |= 1;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) N0[r][c] = N[r][c];
+    } else {
+      // the inelastic branches' b_tr differ from the elastic one by the
+      // (small) inelastic strains, so in the Hooke frame X is nearly
+      // diagonal: Jacobi on N0^T X N0 needs fewer sweeps, N = N0 N~
+      double T1[3][3], Xt[3][3], Nt[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) T1[r][c] = X[r][0] * N0[0][c] + X[r][1] * N0[1][c] + X[r][2] * N0[2][c];
+      for (int r = 0; r < 3; ++r)
+        for (int c = r; c < 3; ++c) {
+          const double v = N0[0][r] * T1[0][c] + N0[1][r] * T1[1][c] + N0[2][r] * T1[2][c];
+          Xt[r][c] = v;
+          Xt[c][r] = v;
+        }
+      if (!jacobi3(Xt, Nt, x)) status |= 1;
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) N[r][c] = N0[r][0] * Nt[0][c] + N0[r][1] * Nt[1][c] + N0[r][2] * Nt[2][c];
+    }
     double eps[3], ed[3];
     for (int p = 0; p < 3; ++p) eps[p] = 0.5 * log1p(x[p]);
     const double tr = eps[0] + eps[1] + eps[2];

@@ -45,6 +45,32 @@ cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* u
   return cudaGetLastError();
 }
 
+// emask[e] = 1 if any of element e's nodes has a prescribed (masked) DoF in
+// any field, else 0: the element kernels read the node mask only for flagged
+// elements (on a box with Dirichlet faces, a few percent of them).
+__global__ void k_elem_mask(MeshDev m, const uint8_t* __restrict__ mask, uint8_t* __restrict__ emask) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= m.nel) return;
+  const int P = m.p + 1;
+  const int ex = (int)(e % m.nx), t = (int)(e / m.nx), ey = t % m.ny, ez = t / m.ny;
+  uint8_t any = 0;
+  for (int c = 0; c < P && !any; ++c)
+    for (int b = 0; b < P && !any; ++b)
+      for (int a = 0; a < P; ++a) {
+        const long long n = m.offsets ? (long long)m.offsets[e * P * P * P + a + P * (b + P * c)]
+                                      : (long long)(m.p * ex + a) +
+                                            (long long)m.nnx * ((long long)(m.p * ey + b) + (long long)m.nny * (m.p * ez + c));
+        for (int f = 0; f < 4; ++f) any |= mask[f * m.nn + n];
+        if (any) break;
+      }
+  emask[e] = any ? 1 : 0;
+}
+cudaError_t launch_elem_mask(const MeshDev& m, const uint8_t* mask, uint8_t* emask, cudaStream_t st) {
+  if (m.nel == 0) return cudaSuccess;
+  k_elem_mask<<<(unsigned)((m.nel + 255) / 256), 256, 0, st>>>(m, mask, emask); note_launch();
+  return cudaGetLastError();
+}
+
 // y = mask ? x : 0 on the nodes [n0, n1) of each of the four fields (rows of
 // one range of node layers; the pipelined action through host buffers).
 template <typename T>
