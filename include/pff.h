@@ -166,6 +166,16 @@ int pff_op_enable_df(pff_op* op, int enable);
  * written by pff_residual, round to nearest even from FP64), needed by
  * PFF_F32_BF16 applies.  Disabling frees them. */
 int pff_op_enable_bf16(pff_op* op, int enable);
+/* Deterministic transposed contractions (race-free reruns): with enable = 1
+ * the element kernels of pff_residual, the actions of every level of op (all
+ * precisions, pff_jacobian_apply_host included), pff_assemble_diagonal and
+ * pff_restrict leave their element values in a buffer ([nel][4][(p+1)^3] doubles, allocated
+ * here), and one thread per node sums its incident elements' values in a
+ * fixed order instead of the atomic scatter-add, so repeated calls give
+ * bitwise identical results.  Calls on op must then not overlap on the GPU
+ * (they share the buffer).  Needs the structured element numbering.  The
+ * reaction and the adjoint keep the atomic scatter. */
+int pff_op_set_deterministic(pff_op* op, int enable);
 int64_t pff_op_num_qpoints(const pff_op* op);
 int64_t pff_op_num_nodes(const pff_op* op);
 

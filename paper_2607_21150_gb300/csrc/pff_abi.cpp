@@ -154,10 +154,12 @@ int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool
   pff_op* op = L->op;
   if (w16) PFF_REQUIRE(op->bf16 && op->lin16, "PFF_F32_BF16 apply needs pff_op_enable_bf16 before pff_residual");
   else PFF_REQUIRE(linOf<T>(op) != nullptr, "FP32 apply needs pff_op_enable_f32 before pff_residual");
-  if (init) PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
+  const bool det = op->det && op->evec;
+  if (init && !det) PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
   ElemArgs<T> a = level_args<T>(L);
   a.blk0 = blk0;
   a.nblk = nblk;
+  if (det) a.evec = op->evec;
   if (w16) {
     a.lin16 = op->lin16;
     a.status = op->status;
@@ -170,6 +172,9 @@ int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool
   a.linC = lin + (transpose ? kWP : kWC) * stride;
   a.transpose = transpose;
   PFF_CK(elem_dispatch<T>(op->Q, L->p + 1, kApply, a, st));
+  if (det && init)
+    PFF_CK(launch_node_gather(sizeof(T) == 8 ? 0 : 1, L->mesh, op->evec, level_mask(L), 0, x, nullptr, y, 0,
+                              L->mesh.nn, st));
   return PFF_OK;
 }
 
@@ -179,11 +184,13 @@ int apply_df(pff_level* L, const double* x, double* y, int transpose, cudaStream
              bool init = true) {
   pff_op* op = L->op;
   PFF_REQUIRE(op->df && op->lin32, "PFF_DF64 apply needs pff_op_enable_df before pff_residual");
-  if (init) PFF_CK(launch_init_masked(0, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
+  const bool det = op->det && op->evec;
+  if (init && !det) PFF_CK(launch_init_masked(0, y, x, nullptr, level_mask(L), 4 * L->mesh.nn, 0, st));
   ElemArgs<df64> a;
   std::memset(&a, 0, sizeof(a));
   a.blk0 = blk0;
   a.nblk = nblk;
+  if (det) a.evec = op->evec;
   a.mesh = L->mesh;
   a.mask = level_mask(L);
   a.emask = a.mask ? level_emask(L) : nullptr;
@@ -201,6 +208,8 @@ int apply_df(pff_level* L, const double* x, double* y, int transpose, cudaStream
   a.lo = op->lin_len;
   a.transpose = transpose;
   PFF_CK(elem_dispatch<df64>(op->Q, L->p + 1, kApply, a, st));
+  if (det && init)
+    PFF_CK(launch_node_gather(0, L->mesh, op->evec, level_mask(L), 0, x, nullptr, y, 0, L->mesh.nn, st));
   return PFF_OK;
 }
 
@@ -208,10 +217,16 @@ template <typename T>
 int diag_t(pff_level* L, T* diag, cudaStream_t st) {
   pff_op* op = L->op;
   PFF_REQUIRE(linOf<T>(op) != nullptr, "FP32 diagonal needs pff_op_enable_f32 before pff_residual");
-  PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, diag, nullptr, nullptr, level_mask(L), 4 * L->mesh.nn, 2, st));
+  const bool det = op->det && op->evec;
+  if (!det)
+    PFF_CK(launch_init_masked(sizeof(T) == 8 ? 0 : 1, diag, nullptr, nullptr, level_mask(L), 4 * L->mesh.nn, 2, st));
   ElemArgs<T> a = level_args<T>(L);
   a.y = diag;
+  if (det) a.evec = op->evec;
   PFF_CK(diag_dispatch<T>(op->Q, L->p + 1, a, st));
+  if (det)
+    PFF_CK(launch_node_gather(sizeof(T) == 8 ? 0 : 1, L->mesh, op->evec, level_mask(L), 2, nullptr, nullptr, diag, 0,
+                              L->mesh.nn, st));
   return PFF_OK;
 }
 
@@ -471,6 +486,7 @@ int pff_destroy_operator(pff_op* op) {
   cudaFree(op->hist_c); cudaFree(op->hist_t); cudaFree(op->phase); cudaFree(op->flags);
   cudaFree(op->lin64); cudaFree(op->lin32); cudaFree(op->lin16); cudaFree(op->io); cudaFree(op->mask);
   cudaFree(op->emask);
+  cudaFree(op->evec);
   cudaFree(op->dvals); cudaFree(op->status);
   cudaFree(op->fint); cudaFree(op->sums); cudaFree(op->geo);
   free_tables(op->tab);
@@ -512,6 +528,23 @@ int pff_op_enable_df(pff_op* op, int enable) {
   return PFF_OK;
 }
 
+int pff_op_set_deterministic(pff_op* op, int enable) {
+  PFF_REQUIRE(op, "pff_op_set_deterministic: null operator");
+  if (enable) {
+    PFF_REQUIRE(op->mesh.offsets == nullptr, "pff_op_set_deterministic: needs the structured element numbering");
+    if (!op->evec) {
+      const long long P = op->p + 1;
+      const size_t bytes = sizeof(double) * 4 * (size_t)P * P * P * (size_t)(op->mesh.nel > 0 ? op->mesh.nel : 1);
+      PFF_CK(cudaMalloc(&op->evec, bytes));
+    }
+  } else {
+    cudaFree(op->evec);
+    op->evec = nullptr;
+  }
+  op->det = enable ? 1 : 0;
+  return PFF_OK;
+}
+
 int pff_op_enable_bf16(pff_op* op, int enable) {
   PFF_REQUIRE(op, "pff_op_enable_bf16: null operator");
   if (enable && !op->lin16) {
@@ -550,7 +583,8 @@ int pff_set_dirichlet(pff_op* op, const uint8_t* mask, const double* values, voi
   long long n = 4 * op->mesh.nn;
   if (!mask) {
     cudaFree(op->mask); op->mask = nullptr;
-    cudaFree(op->emask); op->emask = nullptr;
+    cudaFree(op->emask);
+  cudaFree(op->evec); op->emask = nullptr;
     cudaFree(op->dvals); op->dvals = nullptr;
     return PFF_OK;
   }
@@ -620,7 +654,8 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   PFF_REQUIRE(op && z && r, "pff_residual: null argument");
   cudaStream_t st = S(stream);
   const long long n = 4 * op->mesh.nn;
-  PFF_CK(launch_init_masked(0, r, z, op->dvals, op->mask, n, 1, st));
+  const bool det = op->det && op->evec;
+  if (!det) PFF_CK(launch_init_masked(0, r, z, op->dvals, op->mask, n, 1, st));
   ElemArgs<double> a;
   std::memset(&a, 0, sizeof(a));
   a.mesh = op->mesh;
@@ -656,7 +691,9 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   a.y = r;
   a.mask = op->mask;
   a.emask = op->mask ? op->emask : nullptr;
+  if (det) a.evec = op->evec;
   PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
+  if (det) PFF_CK(launch_node_gather(0, op->mesh, op->evec, op->mask, 1, z, op->dvals, r, 0, op->mesh.nn, st));
   if (op->f32 && op->lin32)
     PFF_CK(launch_split_df(op->lin64, op->lin32, op->df ? op->lin32 + op->lin_len : nullptr,
                            op->lin_len / (kLinWords * stride_of(op->Q)), op->Q, st));
@@ -787,8 +824,9 @@ int pff_restrict(pff_level* c, pff_level* f, pff_prec prec, const void* rf, void
   if (rc) return rc;
   const uint8_t* mc = level_mask(c);
   const uint8_t* mf = level_mask(f);
-  if (prec == PFF_F64) PFF_CK(launch_restrict<double>(c->mesh, f->mesh, c->I64, (const double*)rf, (double*)rc_, mc, mf, S(stream)));
-  else if (prec == PFF_F32 || prec == PFF_F32_BF16) PFF_CK(launch_restrict<float>(c->mesh, f->mesh, c->I32, (const float*)rf, (float*)rc_, mc, mf, S(stream)));
+  void* ev = (c->op->det && c->op->evec) ? c->op->evec : nullptr;
+  if (prec == PFF_F64) PFF_CK(launch_restrict<double>(c->mesh, f->mesh, c->I64, (const double*)rf, (double*)rc_, mc, mf, S(stream), ev));
+  else if (prec == PFF_F32 || prec == PFF_F32_BF16) PFF_CK(launch_restrict<float>(c->mesh, f->mesh, c->I32, (const float*)rf, (float*)rc_, mc, mf, S(stream), ev));
   else return fail(PFF_ERR_INVALID, "pff_restrict: unknown precision");
   return PFF_OK;
 }

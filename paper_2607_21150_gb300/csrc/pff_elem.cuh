@@ -245,6 +245,14 @@ __device__ __forceinline__ void backward(const ElemArgs<T>& a, const ElemSmem<P,
   }
   __syncthreads();
   if (!valid) return;
+  if (a.evec) {  // deterministic transpose: element-local values, summed per node by k_node_gather
+    using V = typename ElemTypes<T>::V;
+    V* ev = static_cast<V*>(a.evec) + (long long)e * 4 * P3;
+    for (int idx = ij; idx < P3; idx += Q2)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) ev[f * P3 + idx] = to_vec(s.bufA[f * Q3 + idx]);
+    return;
+  }
   const long long nn = a.mesh.nn;
   const bool masked = a.mask && (!a.emask || a.emask[e]);
 #pragma unroll
@@ -695,6 +703,13 @@ k_diag(const ElemArgs<T> a) {
     __syncthreads();
   }
   if (!valid) return;
+  if (a.evec) {  // deterministic: element-local values, summed per node by k_node_gather
+    T* ev = static_cast<T*>(a.evec) + (long long)e * 4 * P3;
+    for (int idx = ij; idx < P3; idx += Q2)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) ev[f * P3 + idx] = acc[f * P3 + idx];
+    return;
+  }
   const long long nn = a.mesh.nn;
   for (int idx = ij; idx < P3; idx += Q2) {
     int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);

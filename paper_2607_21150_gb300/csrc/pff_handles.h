@@ -57,6 +57,8 @@ struct pff_op {
   int f32 = 0;
   int df = 0;                 // maintain the double-float planes of the stored linearisation
   int lin32_planes = 0;       // FP32 planes allocated at lin32 (0, 1 or 2)
+  int det = 0;                // deterministic transpose (pff_op_set_deterministic)
+  void* evec = nullptr;       // its element values, [nel][4][P^3] doubles of the fine order
   uint16_t* lin16 = nullptr;  // BF16 words (lin16_word layout), written by pff_residual when bf16 = 1
   long long lin16_len = 0;    // uint16 entries at lin16
   int bf16 = 0;

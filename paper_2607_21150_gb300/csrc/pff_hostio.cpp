@@ -129,6 +129,7 @@ extern "C" int pff_jacobian_apply_host(pff_level* L, pff_prec prec, const void* 
   const char* xh = static_cast<const char*>(x_host);
   char* yh = static_cast<char*>(y_host);
   const uint8_t* mask = level_rows_mask(L);
+  const bool det = L->op->det && L->op->evec;  // deterministic transpose (pff_op_set_deterministic)
   const int vprec = esz == 8 ? 0 : 1;
   const long long per_layer_el = (long long)m.nx * m.ny;
   // the staging buffers are free once the caller's earlier work is done
@@ -144,13 +145,15 @@ extern "C" int pff_jacobian_apply_host(pff_level* L, pff_prec prec, const void* 
     if (rc) return rc;
     HIO_CK(cudaEventRecord(h->ev_in, h->s_in));
     HIO_CK(cudaStreamWaitEvent(st, h->ev_in, 0));
-    HIO_CK(launch_init_rows(vprec, yd, xd, mask, nn, have * layer, need * layer, st));
+    if (!det) HIO_CK(launch_init_rows(vprec, yd, xd, mask, nn, have * layer, need * layer, st));
     have = std::max(have, need);
     rc = apply_blocks(L, prec, xd, yd, 0, (int)b0, (int)(b1 - b0), st);
     if (rc) return rc;
     // layers below the first node layer of the next chunk's first element are final
     const long long fin = (b1 == nblk) ? nlay : (long long)m.p * ((b1 * EB) / per_layer_el);
     if (fin > done) {
+      if (det)  // their rows: the fixed-order sums of the element values
+        HIO_CK(launch_node_gather(vprec, m, L->op->evec, mask, 0, xd, nullptr, yd, done * layer, fin * layer, st));
       HIO_CK(cudaEventRecord(h->ev_out, st));
       HIO_CK(cudaStreamWaitEvent(h->s_out, h->ev_out, 0));
       rc = copy_layers(yh, yd, nn, layer, done, fin, esz, cudaMemcpyDeviceToHost, h->s_out);

@@ -170,6 +170,7 @@ struct ElemArgs {
   const uint16_t* lin16;  // FP32 action only: read the BF16 words (lin16_word layout) instead of lin
   int* status;            // device status word (BF16-word action: bit 32 when a staging wait gave up)
   const uint8_t* emask;   // [nel] 1 = the element has masked nodes (null: check the mask everywhere)
+  void* evec;             // deterministic transpose: element values [nel][4][P^3] (type V) instead of atomics
   int blk0;               // first element block of the launch (actions; 0 = from the first)
   int nblk;               // element blocks of the launch (actions; 0 = all blocks from blk0 = 0)
 };
@@ -194,6 +195,14 @@ cudaError_t launch_geometry(const double* J, double* geo, const Geom& g, int Q, 
 // Vector / transfer kernels (pff_vec.cu)
 cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* ubar,
                                const uint8_t* mask, long long n, int mode, cudaStream_t st);
+// Deterministic transpose: for nodes [n0, n1) of each field, y = mask ? init :
+// the sum of the element values evec[e][f][local] of the node's incident
+// elements (up to eight, in ascending element order; structured numbering).
+// init as launch_init_masked's mode: 0 x, 1 x - ubar, 2 one; 3 zero.  prec 0: FP64
+// values and vectors, 1: FP32.
+cudaError_t launch_node_gather(int prec, const MeshDev& m, const void* evec, const uint8_t* mask, int mode,
+                               const void* x, const double* ubar, void* y, long long n0, long long n1,
+                               cudaStream_t st);
 // emask[e] = 1 where element e has a masked node (any field), 0 elsewhere.
 cudaError_t launch_elem_mask(const MeshDev& m, const uint8_t* mask, uint8_t* emask, cudaStream_t st);
 // y = mask ? x : 0 on nodes [n0, n1) of each field (prec 0: FP64, 1: FP32).
@@ -213,9 +222,10 @@ cudaError_t launch_untile(const double* lin, double* out, long long nq, int Q, c
 template <typename T>
 cudaError_t launch_prolong(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* xc, T* xf,
                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st);
+// evec (deterministic mode): element values and a node gather instead of atomics.
 template <typename T>
 cudaError_t launch_restrict(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* rf, T* rc,
-                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st);
+                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st, void* evec = nullptr);
 template <typename T>
 cudaError_t launch_cheb_init(long long n, const T* b, const T* Ax, const T* diag, T* r, T* d,
                              double inv_theta, cudaStream_t st);

@@ -45,6 +45,57 @@ cudaError_t launch_init_masked(int prec, void* y, const void* x, const double* u
   return cudaGetLastError();
 }
 
+// Deterministic transpose E^T: every node sums the values its incident
+// elements left in evec, always in the same order (elements ascending), so
+// reruns are bitwise identical.  Node (I, J, K) lies in elements
+// ex = I / p (local a = I mod p) and, on an element boundary (I mod p = 0),
+// also ex - 1 (local a = p); likewise in y and z.
+template <typename T>
+__global__ void k_node_gather(MeshDev m, const T* __restrict__ evec, const uint8_t* __restrict__ mask, int mode,
+                              const T* __restrict__ x, const double* __restrict__ ubar, T* __restrict__ y, long long n0,
+                              long long n1) {
+  const long long n = n0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= n1) return;
+  const int p = m.p, P = p + 1, P3 = P * P * P;
+  const int I = (int)(n % m.nnx), J = (int)((n / m.nnx) % m.nny), K = (int)(n / ((long long)m.nnx * m.nny));
+  int ex[2], ax[2], nxc = 0, ey[2], ay[2], nyc = 0, ez[2], az[2], nzc = 0;
+  if (I % p == 0 && I > 0) { ex[nxc] = I / p - 1; ax[nxc++] = p; }
+  if (I / p < m.nx) { ex[nxc] = I / p; ax[nxc++] = I % p; }
+  if (J % p == 0 && J > 0) { ey[nyc] = J / p - 1; ay[nyc++] = p; }
+  if (J / p < m.ny) { ey[nyc] = J / p; ay[nyc++] = J % p; }
+  if (K % p == 0 && K > 0) { ez[nzc] = K / p - 1; az[nzc++] = p; }
+  if (K / p < m.nz) { ez[nzc] = K / p; az[nzc++] = K % p; }
+  for (int f = 0; f < 4; ++f) {
+    const long long g = f * m.nn + n;
+    T v = T(0);
+    if (mask && mask[g]) {
+      v = (mode == 0) ? x[g] : (mode == 1) ? x[g] - (ubar ? (T)ubar[g] : T(0)) : (mode == 2) ? T(1) : T(0);
+    } else {
+      for (int cz = 0; cz < nzc; ++cz)
+        for (int cy = 0; cy < nyc; ++cy)
+          for (int cx = 0; cx < nxc; ++cx) {
+            const long long e = ex[cx] + (long long)m.nx * (ey[cy] + (long long)m.ny * ez[cz]);
+            v += evec[(e * 4 + f) * P3 + ax[cx] + P * (ay[cy] + P * az[cz])];
+          }
+    }
+    y[g] = v;
+  }
+}
+cudaError_t launch_node_gather(int prec, const MeshDev& m, const void* evec, const uint8_t* mask, int mode,
+                               const void* x, const double* ubar, void* y, long long n0, long long n1,
+                               cudaStream_t st) {
+  if (n1 <= n0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n1 - n0 + 255) / 256);
+  if (prec == 0)
+    k_node_gather<double><<<blocks, 256, 0, st>>>(m, (const double*)evec, mask, mode, (const double*)x, ubar,
+                                                  (double*)y, n0, n1);
+  else
+    k_node_gather<float><<<blocks, 256, 0, st>>>(m, (const float*)evec, mask, mode, (const float*)x, ubar,
+                                                 (float*)y, n0, n1);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // emask[e] = 1 if any of element e's nodes has a prescribed (masked) DoF in
 // any field, else 0: the element kernels read the node mask only for flagged
 // elements (on a box with Dirichlet faces, a few percent of them).
@@ -238,7 +289,8 @@ cudaError_t launch_prolong(const MeshDev& mc, const MeshDev& mf, const T* I1, co
 // per (element, coarse local node).
 template <typename T>
 __global__ void k_restrict(MeshDev mc, MeshDev mf, const T* __restrict__ I1, const T* __restrict__ rf,
-                           T* __restrict__ rc, const uint8_t* __restrict__ maskc, const uint8_t* __restrict__ maskf) {
+                           T* __restrict__ rc, const uint8_t* __restrict__ maskc, const uint8_t* __restrict__ maskf,
+                           T* __restrict__ evec) {
   const int Pc = mc.p + 1, Pf = mf.p + 1;
   const int Pc3 = Pc * Pc * Pc;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -270,6 +322,10 @@ __global__ void k_restrict(MeshDev mc, MeshDev mf, const T* __restrict__ I1, con
       }
     }
   }
+  if (evec) {  // deterministic: element values, summed per coarse node by k_node_gather
+    for (int f = 0; f < 4; ++f) evec[((long long)e * 4 + f) * Pc3 + lb] = acc[f];
+    return;
+  }
   for (int f = 0; f < 4; ++f) {
     long long gc = f * mc.nn + nc;
     if (maskc && maskc[gc]) continue;
@@ -279,12 +335,16 @@ __global__ void k_restrict(MeshDev mc, MeshDev mf, const T* __restrict__ I1, con
 
 template <typename T>
 cudaError_t launch_restrict(const MeshDev& mc, const MeshDev& mf, const T* I1, const T* rf, T* rc,
-                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st) {
+                            const uint8_t* maskc, const uint8_t* maskf, cudaStream_t st, void* evec) {
   long long n = (long long)mc.nel * (mc.p + 1) * (mc.p + 1) * (mc.p + 1);
-  cudaError_t err = cudaMemsetAsync(rc, 0, sizeof(T) * 4 * mc.nn, st);
-  if (err != cudaSuccess) return err;
+  if (!evec) {
+    cudaError_t err = cudaMemsetAsync(rc, 0, sizeof(T) * 4 * mc.nn, st);
+    if (err != cudaSuccess) return err;
+  }
   if (n == 0) return cudaSuccess;
-  k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mc, mf, I1, rf, rc, maskc, maskf); note_launch();
+  k_restrict<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(mc, mf, I1, rf, rc, maskc, maskf, (T*)evec);
+  note_launch();
+  if (evec) return launch_node_gather(sizeof(T) == 8 ? 0 : 1, mc, evec, maskc, 3, nullptr, nullptr, rc, 0, mc.nn, st);
   return cudaGetLastError();
 }
 
@@ -465,9 +525,9 @@ template cudaError_t launch_prolong<double>(const MeshDev&, const MeshDev&, cons
 template cudaError_t launch_prolong<float>(const MeshDev&, const MeshDev&, const float*, const float*, float*,
                                            const uint8_t*, const uint8_t*, cudaStream_t);
 template cudaError_t launch_restrict<double>(const MeshDev&, const MeshDev&, const double*, const double*, double*,
-                                             const uint8_t*, const uint8_t*, cudaStream_t);
+                                             const uint8_t*, const uint8_t*, cudaStream_t, void*);
 template cudaError_t launch_restrict<float>(const MeshDev&, const MeshDev&, const float*, const float*, float*,
-                                            const uint8_t*, const uint8_t*, cudaStream_t);
+                                            const uint8_t*, const uint8_t*, cudaStream_t, void*);
 template cudaError_t launch_cheb_init<double>(long long, const double*, const double*, const double*, double*, double*,
                                               double, cudaStream_t);
 template cudaError_t launch_cheb_init<float>(long long, const float*, const float*, const float*, float*, float*,

@@ -94,6 +94,7 @@ _SIGS = {
     "pff_op_enable_f32": ([_VP, _I], _I),
     "pff_op_enable_df": ([_VP, _I], _I),
     "pff_op_enable_bf16": ([_VP, _I], _I),
+    "pff_op_set_deterministic": ([_VP, _I], _I),
     "pff_op_set_geometry": ([_VP, _VP, _VP], _I),
     "pff_op_num_qpoints": ([_VP], _I64),
     "pff_op_num_nodes": ([_VP], _I64),
@@ -274,6 +275,10 @@ def pff_op_enable_df(op, enable=True):
 
 def pff_op_enable_bf16(op, enable=True):
     _call("pff_op_enable_bf16", op, 1 if enable else 0)
+
+
+def pff_op_set_deterministic(op, enable=True):
+    _call("pff_op_set_deterministic", op, 1 if enable else 0)
 
 
 def pff_op_set_geometry(op, X, stream=None):
