@@ -67,9 +67,9 @@ def pipe_rates(stream, iters: int = 20000):
     return out
 
 
-def make_workload(name: str, seed: int = 0):
+def make_workload(name: str, seed: int = 0, n: int | None = None):
     from paper_2607_21150_gb300 import inputs
-    w = getattr(inputs, name)()
+    w = getattr(inputs, name)() if n is None else getattr(inputs, name)(n=n)
     rng = np.random.default_rng(seed + 100)
     m = w.mesh
     h = min(m.h) / m.p
@@ -427,7 +427,7 @@ def run_native(args):
     from paper_2607_21150_gb300 import pff
     from paper_2607_21150_gb300.session import Session
 
-    w = make_workload(args.config, seed=rank)
+    w = make_workload(args.config, seed=rank, n=args.n)
     m = w.mesh
     s = Session(w, levels=(2, 1) if m.p == 4 else (), f32=True, df=True, bf16=True)
     stream = torch.cuda.current_stream()
@@ -642,6 +642,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--config", default="compress_q4", choices=["compress_q4", "tension_q4"])
+    ap.add_argument("--n", type=int, default=None,
+                    help="elements per direction of the --config workload (its default size if omitted; smaller "
+                         "sizes serve ncu captures, the bench line is for the default)")
     ap.add_argument("--newton", default="compress_q4,tension_q4,notched_q3",
                     help="comma list of workloads (compress_q4, tension_q4, notched_q3) of the FP64-vs-mixed "
                          "Newton comparison, the first one reported as newton_step; or none")

@@ -40,18 +40,23 @@ class StepController:
     attempt(f_from, f_to) -> bool runs one sub-step (load factor and time both
     advance by f_to - f_from in units of the nominal step) and reports whether
     it converged; a failed attempt must leave the state at f_from.  After a
-    failure the increment is halved (at most `max_cuts` failures in a row),
-    after a success it grows by `grow`, never past `target`.  Increments are
-    dyadic fractions of the nominal step, so the sub-step ends are exact."""
+    failure the increment is halved (at most `max_cuts` failures in a row);
+    after `grow_after` successes in a row at the same increment it grows by
+    `grow`, never past `target` (grow_after = 1: after every success; 2 keeps
+    a halved increment for two sub-steps, which saves the attempts that fail
+    when the softening regime needs the smaller increment for a while).
+    Increments are dyadic fractions of the nominal step, so the sub-step ends
+    are exact."""
 
-    def __init__(self, max_cuts: int = 6, grow: float = 2.0):
+    def __init__(self, max_cuts: int = 6, grow: float = 2.0, grow_after: int = 1):
         self.max_cuts = max_cuts
         self.grow = grow
+        self.grow_after = max(1, int(grow_after))
 
     def run(self, start: float, target: float, attempt, first: float | None = None):
         f = float(start)
         inc = float(target - start) if first is None else float(first)
-        done, cuts = [], 0
+        done, cuts, wins = [], 0, 0
         while f < target:
             inc = min(inc, target - f)
             f_to = target if f + inc >= target else f + inc
@@ -59,9 +64,13 @@ class StepController:
                 done.append((f, f_to))
                 f = f_to
                 cuts = 0
-                inc *= self.grow
+                wins += 1
+                if wins >= self.grow_after:
+                    inc *= self.grow
+                    wins = 0
             else:
                 cuts += 1
+                wins = 0
                 if cuts > self.max_cuts:
                     raise StepFailed(f"no convergence from load factor {f} after {self.max_cuts} cuts")
                 inc *= 0.5
@@ -70,12 +79,13 @@ class StepController:
 
 class LoadStepper:
     def __init__(self, w: Workload, levels=None, mixed: bool = True, session: Session | None = None,
-                 df: bool | None = None, max_cuts: int = 6, **solver_params):
+                 df: bool | None = None, max_cuts: int = 6, grow_after: int = 1, **solver_params):
         """df: the fine-level action inside FGMRES in double-float arithmetic
         (PFF_DF64) instead of FP64; by default on with mixed precision (same
         converged fields to ~1e-15, half the time of the FP64 action).
         max_cuts: consecutive halvings of a failing load increment before
-        `advance` gives up.  solver_params: fields of pff_solver_params, e.g.
+        `advance` gives up; grow_after: successes in a row before a cut
+        increment grows again (StepController).  solver_params: fields of pff_solver_params, e.g.
         level_words=16 for BF16 words in the FP32 levels."""
         if df is None:
             df = mixed
@@ -91,7 +101,7 @@ class LoadStepper:
         self.solver = self.s.solver(self.levels, mixed=int(mixed), **solver_params)
         self.w = w
         self.dt = float(w.glob[3])
-        self.controller = StepController(max_cuts=max_cuts)
+        self.controller = StepController(max_cuts=max_cuts, grow_after=grow_after)
         self.z = torch.from_numpy(np.ascontiguousarray(w.z, dtype=np.float64).ravel()).to(self.s.dev)
         self.unit = np.ascontiguousarray(w.dvals if w.dvals is not None else np.zeros((4, m.nn)), dtype=np.float64)
         self.top = torch.from_numpy(top_face_mask(m).ravel()).to(self.s.dev)

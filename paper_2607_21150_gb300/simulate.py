@@ -28,6 +28,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=None, help="load steps (workload default if omitted)")
     ap.add_argument("--fp64", action="store_true", help="FP64 multigrid levels instead of FP32")
     ap.add_argument("--max-cuts", type=int, default=6)
+    ap.add_argument("--grow-after", type=int, default=2,
+                    help="converged sub-steps in a row before a cut load increment doubles again")
     ap.add_argument("--verbose", action="store_true", help="the solver's per-iteration log on stderr")
     ap.add_argument("--param", action="append", default=[], metavar="NAME=VALUE",
                     help="solver parameter, a field of pff_solver_params (repeatable)")
@@ -53,7 +55,7 @@ def main(argv=None):
     w = make() if args.n is None else make(n=args.n)
     steps = args.steps or int(w.meta.get("steps", 10))
     t0 = time.perf_counter()
-    lsp = LoadStepper(w, mixed=not args.fp64, max_cuts=args.max_cuts, **params)
+    lsp = LoadStepper(w, mixed=not args.fp64, max_cuts=args.max_cuts, grow_after=args.grow_after, **params)
     lsp.diagnostics = True
     first = 1
     if args.resume:

@@ -212,3 +212,28 @@ def test_failed_substeps_are_recorded(monkeypatch):
     assert fails[:2] == [(0.0, 1.0), (0.0, 0.5)]
     assert all(b - a > 0.3 for a, b in fails) and all(f["converged"] == 0 for f in lsp.failures)
     assert len(fails) + len(lsp.history) == len(log["solves"])
+
+
+def test_controller_grows_only_after_repeated_successes():
+    """grow_after = 2: after a cut the increment stays at its halved size for
+    two converged sub-steps before it doubles; with grow_after = 1 (the
+    default) it doubles after every success."""
+    from paper_2607_21150_gb300.driver import StepController
+
+    def run(grow_after):
+        tried = []
+
+        def attempt(f0, f1):
+            tried.append((f0, f1))
+            return f1 - f0 <= 0.25
+        done = StepController(grow_after=grow_after).run(0.0, 2.0, attempt)
+        return tried, done
+
+    t1, d1 = run(1)
+    t2, d2 = run(2)
+    assert [b for _, b in d1] == [b for _, b in d2] == [0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75, 2.0]
+    fails1 = [x for x in t1 if x[1] - x[0] > 0.25]
+    fails2 = [x for x in t2 if x[1] - x[0] > 0.25]
+    assert len(fails2) < len(fails1)
+    assert t2[:5] == [(0.0, 2.0), (0.0, 1.0), (0.0, 0.5), (0.0, 0.25), (0.25, 0.5)]
+    assert t2[5] == (0.5, 1.0)        # grows only after the second success

@@ -14,8 +14,8 @@ from paper_2607_21150_gb300 import driver, simulate  # noqa: E402
 class _Fake:
     made = []
 
-    def __init__(self, w, mixed=True, max_cuts=6, **kw):
-        self.mixed, self.max_cuts, self.kw = mixed, max_cuts, kw
+    def __init__(self, w, mixed=True, max_cuts=6, grow_after=1, **kw):
+        self.mixed, self.max_cuts, self.grow_after, self.kw = mixed, max_cuts, grow_after, kw
         self.history = []
         self.failures = []
         _Fake.made.append(self)
