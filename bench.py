@@ -29,10 +29,12 @@ sys.path.insert(0, ROOT)
 METRIC = "Q4 Jacobian-apply GDoF/s & %HBM roofline; Newton step time FP64 vs mixed p-MG"
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x max SM clock
 # DRAM bytes (read + write) per element of one Jacobian action, Q4 (P = Q = 5),
-# from one ncu capture of the same kernels at 16^3 elements (4096 elements:
-# FP64 297.09 + 7.55 MB, FP32 151.00 + 4.23 MB), scaled to a launch by the
-# element count.
-TRAFFIC_PER_ELEMENT = {"f64": (297.09e6 + 7.55e6) / 4096, "f32": (151.00e6 + 4.23e6) / 4096}
+# from one ncu capture of the same kernels on the 24^3 tension workload
+# (python bench.py --config tension_q4 --n 24 ...): FP64 220.06 + 5.48 MB over
+# a 3 040-element launch, FP32 521.86 + 24.02 MB and BF16 words 265.11 + 4.50 MB
+# over 13 824 elements; scaled to a launch by the element count.
+TRAFFIC_PER_ELEMENT = {"f64": (220.06e6 + 5.48e6) / 3040, "f32": (521.86e6 + 24.02e6) / 13824,
+                       "bf16": (265.11e6 + 4.50e6) / 13824}
 
 
 def peaks():
@@ -558,6 +560,7 @@ def run_native(args):
     q4 = (P, Q) == (5, 5)
     traffic64 = TRAFFIC_PER_ELEMENT["f64"] * m.nel if q4 else None
     traffic32 = TRAFFIC_PER_ELEMENT["f32"] * m.nel if q4 else None
+    traffic16 = TRAFFIC_PER_ELEMENT["bf16"] * m.nel if q4 else None
     s.close()
     del s
     torch.cuda.empty_cache()
@@ -584,7 +587,7 @@ def run_native(args):
                    "microstructure": w.meta},
         "roofline": {"bound": "alu", "achieved": achieved_flops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": achieved_flops / FP64_PEAK_TFLOPS, "traffic": traffic64,
-                     "traffic_source": "ncu dram bytes per element at 16^3 Q4 x elements" if traffic64 else None,
+                     "traffic_source": "ncu dram bytes per element at 24^3 Q4 x elements" if traffic64 else None,
                      "algorithmic_bytes": bytes64,
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (derived from unit "
                                     "counts and the maximum clock; pipe_rates has the live probe)",
@@ -597,7 +600,7 @@ def run_native(args):
                              "achieved_gbs": bytes32 / t32 / 1e9, "hbm_frac": bytes32 / t32 / 1e9 / hbm_peak,
                              "bound": "hbm", "peak_gbs": hbm_peak, "peak_source": src},
         "bf16_words_level_apply": {"gdofs": ndof / (tot16 / args.steps / 1e3) / 1e9, "ms": tot16 / args.steps,
-                                   "algorithmic_bytes": bytes16, "achieved_gbs": bytes16 / (tot16 / args.steps / 1e3) / 1e9,
+                                   "algorithmic_bytes": bytes16, "traffic": traffic16, "achieved_gbs": bytes16 / (tot16 / args.steps / 1e3) / 1e9,
                                    "hbm_frac": bytes16 / (tot16 / args.steps / 1e3) / 1e9 / hbm_peak,
                                    "rel_l2_vs_fp64": bf16_rel,
                                    "note": "FP32 vectors and arithmetic, stored words as BF16 staged through shared "

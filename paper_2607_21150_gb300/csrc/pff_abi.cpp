@@ -125,6 +125,18 @@ template <typename T> const T* linOf(const pff_op* op);
 template <> const double* linOf<double>(const pff_op* op) { return op->lin64; }
 template <> const float* linOf<float>(const pff_op* op) { return op->lin32; }
 
+// Multiprocessors of the current device (cached per device).
+int sm_count() {
+  static thread_local int dev_cached = -1, sms = 0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (dev != dev_cached) {
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
+    dev_cached = dev;
+  }
+  return sms;
+}
+
 const uint8_t* level_mask(const pff_level* L) { return L->is_fine ? L->op->mask : L->mask; }
 const uint8_t* level_emask(const pff_level* L) { return L->is_fine ? L->op->emask : L->emask; }
 
@@ -163,6 +175,7 @@ int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool
   if (w16) {
     a.lin16 = op->lin16;
     a.status = op->status;
+    a.pf_ahead = 2 * sm_count();  // one wave of the kernel's two resident blocks per SM
   }
   a.x = x;
   a.y = y;

@@ -172,6 +172,7 @@ struct ElemArgs {
   const uint8_t* emask;   // [nel] 1 = the element has masked nodes (null: check the mask everywhere)
   void* evec;             // deterministic transpose: element values [nel][4][P^3] (type V) instead of atomics
   int blk0;               // first element block of the launch (actions; 0 = from the first)
+  int pf_ahead;           // BF16-word action: prefetch the x rows of the block this many ahead (0 = off)
   int nblk;               // element blocks of the launch (actions; 0 = all blocks from blk0 = 0)
 };
 
