@@ -31,10 +31,9 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x m
 # DRAM bytes (read + write) per element of one Jacobian action, Q4 (P = Q = 5),
 # from one ncu capture of the same kernels on the 24^3 tension workload
 # (python bench.py --config tension_q4 --n 24 ...): FP64 220.06 + 5.48 MB over
-# a 3 040-element launch, FP32 521.86 + 24.02 MB and BF16 words 265.11 + 4.50 MB
-# over 13 824 elements; scaled to a launch by the element count.
-TRAFFIC_PER_ELEMENT = {"f64": (220.06e6 + 5.48e6) / 3040, "f32": (521.86e6 + 24.02e6) / 13824,
-                       "bf16": (265.11e6 + 4.50e6) / 13824}
+# a 3 040-element launch; scaled to a launch by the element count.  None where
+# the kernel has changed since its counters were taken.
+TRAFFIC_PER_ELEMENT = {"f64": (220.06e6 + 5.48e6) / 3040, "f32": None, "bf16": None}
 
 
 def peaks():
@@ -559,8 +558,8 @@ def run_native(args):
     t32 = tot32 / args.steps / 1e3
     q4 = (P, Q) == (5, 5)
     traffic64 = TRAFFIC_PER_ELEMENT["f64"] * m.nel if q4 else None
-    traffic32 = TRAFFIC_PER_ELEMENT["f32"] * m.nel if q4 else None
-    traffic16 = TRAFFIC_PER_ELEMENT["bf16"] * m.nel if q4 else None
+    traffic32 = TRAFFIC_PER_ELEMENT["f32"] * m.nel if q4 and TRAFFIC_PER_ELEMENT["f32"] else None
+    traffic16 = TRAFFIC_PER_ELEMENT["bf16"] * m.nel if q4 and TRAFFIC_PER_ELEMENT["bf16"] else None
     s.close()
     del s
     torch.cuda.empty_cache()

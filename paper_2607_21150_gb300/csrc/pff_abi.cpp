@@ -63,6 +63,8 @@ int make_tables(int p, int Q, Tables& t) {
     }
   for (int i = 0; i < Q; ++i)
     for (int k = 0; k < Q; ++k) Dc[i * Q + k] = lagrange_deriv(xq.data(), Q, k, xq[i]);
+  for (int i = 0; i < Q * P; ++i) t.hB32[i] = (float)B[i];
+  for (int i = 0; i < Q * Q; ++i) t.hDc32[i] = (float)Dc[i];
   int rc;
   if ((rc = upload(B, &t.B64))) return rc;
   if ((rc = upload(B, &t.B32))) return rc;
@@ -154,6 +156,8 @@ ElemArgs<T> level_args(const pff_level* L) {
   a.nq = L->op->nq;
   a.kx = L->op->geo != nullptr;
   for (int d = 0; d < 3; ++d) a.s[d] = L->op->geom.s[d];
+  std::memcpy(a.cB, L->tab.hB32, sizeof(a.cB));
+  std::memcpy(a.cDc, L->tab.hDc32, sizeof(a.cDc));
   return a;
 }
 
@@ -172,10 +176,10 @@ int apply_t(pff_level* L, const T* x, T* y, int transpose, cudaStream_t st, bool
   a.blk0 = blk0;
   a.nblk = nblk;
   if (det) a.evec = op->evec;
-  if (w16) {
-    a.lin16 = op->lin16;
+  if (w16) a.lin16 = op->lin16;
+  if (sizeof(T) == 4) {  // the persistent FP32-arithmetic kernel: two resident blocks per SM
     a.status = op->status;
-    a.pf_ahead = 2 * sm_count();  // one wave of the kernel's two resident blocks per SM
+    a.ctas = 2 * sm_count();
   }
   a.x = x;
   a.y = y;
@@ -510,8 +514,8 @@ int pff_destroy_operator(pff_op* op) {
 int pff_op_enable_f32(pff_op* op, int enable) {
   PFF_REQUIRE(op, "pff_op_enable_f32: null operator");
   if (enable && !op->lin32) {
-    PFF_CK(cudaMalloc((void**)&op->lin32, sizeof(float) * op->lin_len));
-    PFF_CK(cudaMemset(op->lin32, 0, sizeof(float) * op->lin_len));
+    PFF_CK(cudaMalloc((void**)&op->lin32, sizeof(float) * (op->lin_len + kLin32Pad)));
+    PFF_CK(cudaMemset(op->lin32, 0, sizeof(float) * (op->lin_len + kLin32Pad)));
     op->lin32_planes = 1;
   }
   if (!enable && op->lin32) {
@@ -528,8 +532,8 @@ int pff_op_enable_df(pff_op* op, int enable) {
   PFF_REQUIRE(op, "pff_op_enable_df: null operator");
   if (enable && op->lin32_planes < 2) {
     float* planes = nullptr;
-    PFF_CK(cudaMalloc((void**)&planes, sizeof(float) * 2 * op->lin_len));
-    const cudaError_t e = cudaMemset(planes, 0, sizeof(float) * 2 * op->lin_len);
+    PFF_CK(cudaMalloc((void**)&planes, sizeof(float) * (2 * op->lin_len + kLin32Pad)));
+    const cudaError_t e = cudaMemset(planes, 0, sizeof(float) * (2 * op->lin_len + kLin32Pad));
     if (e != cudaSuccess) cudaFree(planes);  // keep the operator as it was
     PFF_CK(e);
     cudaFree(op->lin32);

@@ -725,7 +725,7 @@ k_diag(const ElemArgs<T> a) {
 
 }  // namespace pff
 
-#include "pff_elem_w16.cuh"
+#include "pff_elem_pipe.cuh"
 
 namespace pff {
 
@@ -734,8 +734,12 @@ cudaError_t launch_elem_pq(int mode, const ElemArgs<T>& a, cudaStream_t st) {
   constexpr int EB = elems_per_block(Q);
   int nblk = a.nblk > 0 ? a.nblk : (a.mesh.nel + EB - 1) / EB;
   if (nblk == 0) return cudaSuccess;
-  if constexpr (sizeof(T) == 4 && sizeof(typename ElemTypes<T>::L) == 4) {  // FP32 action with BF16 words
-    if (a.lin16) return mode == kApply ? launch_elem_w16<P, Q>(a, st) : cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4 && sizeof(typename ElemTypes<T>::L) == 4) {  // FP32 arithmetic: persistent kernel
+    if (a.lin16 && mode != kApply) return cudaErrorInvalidValue;
+    if (mode == kApply) {
+      cudaError_t err = cudaSuccess;
+      if (launch_level_pipe<P, Q>(a, nblk, st, &err)) return err;
+    }
   }
   size_t smem = sizeof(T) * (size_t)(mat_smem_words<P, Q>() + EB * elem_smem_words<Q>());
   dim3 block(Q * Q * EB);

@@ -32,6 +32,7 @@ struct pff_restr {
 struct Tables {  // per-level device copies of the 1D matrices, both precisions
   double *B64 = nullptr, *Dc64 = nullptr, *Dt64 = nullptr;
   float *B32 = nullptr, *Dc32 = nullptr, *Dt32 = nullptr;
+  float hB32[pff::kMaxQ * pff::kMaxQ] = {}, hDc32[pff::kMaxQ * pff::kMaxQ] = {};  // host copies (kernel parameters)
 };
 
 struct pff_op {

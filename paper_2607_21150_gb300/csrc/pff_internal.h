@@ -24,6 +24,9 @@ __host__ __device__ constexpr long long lin32_word(int w, int k, int t, long lon
   return w < kLinQuadWords ? (long long)(w >> 2) * 4 * q3eb + (long long)k * 4 * q2eb + 4LL * t + (w & 3)
                            : (long long)w * q3eb + (long long)k * q2eb + t;
 }
+// Floats allocated past the FP32 planes: the persistent level kernel copies
+// each tail-word run widened to 16-byte boundaries, up to 12 bytes past it.
+constexpr long long kLin32Pad = 16;
 
 // BF16 words of the stored linearisation (the level actions of PFF_F32_BF16):
 // per block a region of kLin16Words * Q^3 EB uint16, words [0, 64) of a point
@@ -172,8 +175,12 @@ struct ElemArgs {
   const uint8_t* emask;   // [nel] 1 = the element has masked nodes (null: check the mask everywhere)
   void* evec;             // deterministic transpose: element values [nel][4][P^3] (type V) instead of atomics
   int blk0;               // first element block of the launch (actions; 0 = from the first)
-  int pf_ahead;           // BF16-word action: prefetch the x rows of the block this many ahead (0 = off)
+  int ctas;               // FP32-arithmetic actions: resident blocks of the persistent kernel (0 = one per element block)
   int nblk;               // element blocks of the launch (actions; 0 = all blocks from blk0 = 0)
+  // FP32-arithmetic actions: the 1D matrices B [Q][P] and Dc [Q][Q] as kernel
+  // parameters, read as constant-bank operands where the index is fixed at compile time
+  float cB[kMaxQ * kMaxQ];
+  float cDc[kMaxQ * kMaxQ];
 };
 
 // One translation unit per quadrature size Q (pff_elem_q<Q>.cu); each covers
