@@ -43,13 +43,15 @@ __device__ __forceinline__ df64 add(df64 a, df64 b) { return df_add(a, b); }
 
 template <typename T> __device__ __forceinline__ T zero() { return T(0); }
 template <> __device__ __forceinline__ df64 zero<df64>() { return df_make(0.0f, 0.0f); }
-// storage value (vector entry or basis matrix) -> arithmetic type
+// storage value (vector entry or basis matrix) -> arithmetic type; FP64 ->
+// double-float by integer operations (the conversion instructions run at the
+// FP64 rate on GB300)
 template <typename T, typename S> __device__ __forceinline__ T from_store(S x) { return (T)x; }
-template <> __device__ __forceinline__ df64 from_store<df64, double>(double x) { return df_from(x); }
+template <> __device__ __forceinline__ df64 from_store<df64, double>(double x) { return df_split(x); }
 // arithmetic type -> vector entry
 __device__ __forceinline__ double to_vec(double v) { return v; }
 __device__ __forceinline__ float to_vec(float v) { return v; }
-__device__ __forceinline__ double to_vec(df64 v) { return df_to(v); }
+__device__ __forceinline__ double to_vec(df64 v) { return df_join(v); }
 // stored linearisation word (df64: hi plane at p, lo plane at p + lo)
 template <typename T>
 __device__ __forceinline__ T ld_lin(const typename ElemTypes<T>::L* p, long long lo) {
@@ -464,33 +466,36 @@ k_elem(const ElemArgs<T> a) {
 
   if constexpr (MODE == kEval) {
     if (valid) {
+      T sd[3];  // d xi / dX of the box
+#pragma unroll
+      for (int al = 0; al < 3; ++al) sd[al] = from_store<T>(a.s[al]);
 #pragma unroll 1
       for (int k = 0; k < Q; ++k) {
         T g[4][3], phi;
         grad_at<P, Q, T>(s, i, j, k, g, phi);
         long long q = (long long)e * Q3 + k * Q2 + j * Q + i;
         if (a.geo) {  // mapped mesh: reference gradient = parent gradient x d xi / dX
-          double G[3][3];
+          T G[3][3];
 #pragma unroll
           for (int al = 0; al < 3; ++al)
 #pragma unroll
-            for (int A = 0; A < 3; ++A) G[al][A] = a.geo[(3 * al + A) * a.nq + q];
+            for (int A = 0; A < 3; ++A) G[al][A] = from_store<T>(a.geo[(3 * al + A) * a.nq + q]);
 #pragma unroll
           for (int f = 0; f < 4; ++f)
 #pragma unroll
             for (int A = 0; A < 3; ++A) {
-              const double v = (double)g[f][0] * G[0][A] + (double)g[f][1] * G[1][A] + (double)g[f][2] * G[2][A];
-              a.scratch[((f < 3) ? 3 * f + A : 10 + A) * a.nq + q] = v;
+              const T v = madd(madd(mul(g[f][0], G[0][A]), g[f][1], G[1][A]), g[f][2], G[2][A]);
+              a.scratch[((f < 3) ? 3 * f + A : 10 + A) * a.nq + q] = to_vec(v);
             }
         } else {
 #pragma unroll
           for (int f = 0; f < 3; ++f)
 #pragma unroll
-            for (int al = 0; al < 3; ++al) a.scratch[(3 * f + al) * a.nq + q] = (double)g[f][al] * a.s[al];
+            for (int al = 0; al < 3; ++al) a.scratch[(3 * f + al) * a.nq + q] = to_vec(mul(g[f][al], sd[al]));
 #pragma unroll
-          for (int al = 0; al < 3; ++al) a.scratch[(10 + al) * a.nq + q] = (double)g[3][al] * a.s[al];
+          for (int al = 0; al < 3; ++al) a.scratch[(10 + al) * a.nq + q] = to_vec(mul(g[3][al], sd[al]));
         }
-        a.scratch[9 * a.nq + q] = (double)phi;
+        a.scratch[9 * a.nq + q] = to_vec(phi);
       }
     }
     return;
@@ -564,10 +569,10 @@ k_elem(const ElemArgs<T> a) {
 #pragma unroll
         for (int f = 0; f < 3; ++f)
 #pragma unroll
-          for (int al = 0; al < 3; ++al) o[f][al] = (T)a.scratch[(3 * f + al) * a.nq + q];
-        o0 = (T)a.scratch[9 * a.nq + q];
+          for (int al = 0; al < 3; ++al) o[f][al] = from_store<T>(a.scratch[(3 * f + al) * a.nq + q]);
+        o0 = from_store<T>(a.scratch[9 * a.nq + q]);
 #pragma unroll
-        for (int al = 0; al < 3; ++al) o[3][al] = (T)a.scratch[(10 + al) * a.nq + q];
+        for (int al = 0; al < 3; ++al) o[3][al] = from_store<T>(a.scratch[(10 + al) * a.nq + q]);
       } else {
 #pragma unroll
         for (int f = 0; f < 4; ++f) o[f][0] = o[f][1] = o[f][2] = zero<T>();

@@ -30,9 +30,13 @@
 // coefficient matrix M_v per branch; then the direction phi.  The words are
 // scaled by the quadrature weight and the parent-to-reference factors (mapped
 // meshes: transformed to the parent frame with d xi / dX) and stored in the
-// tiled layout of kLinWords words.
+// tiled layout of kLinWords words.  The tangent's
+// products and sums run in double-float on the FP32 pipes (about 2^-46
+// relative per operation), converted to and from FP64 by integer operations:
+// on GB300 the FP64 pipe, not memory, bounds this kernel.
 #include <cmath>
 
+#include "pff_df.cuh"
 #include "pff_internal.h"
 #include "pff_point.cuh"
 
@@ -109,12 +113,19 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
 
   double taud[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   double psid = 0.0;
-  double dtau[10][6];
-  double dpsi[10];
+  // the tangent's products and sums run in double-float on the FP32 pipes
+  // (the FP64 pipe is this kernel's bound), converted by integer operations
+  df64 dtau[10][6];
+  df64 dpsi[10];
+  df64 Fid[3][3];
+  const df64 dz = df_make(0.0f, 0.0f);
   for (int d = 0; d < 10; ++d) {
-    dpsi[d] = 0.0;
-    for (int v = 0; v < 6; ++v) dtau[d][v] = 0.0;
+    dpsi[d] = dz;
+    for (int v = 0; v < 6; ++v) dtau[d][v] = dz;
   }
+  if (a.want_tangent)
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) Fid[r][c] = df_split(Fi[r][c]);
   uint8_t flag = 0;
   double dgam = 0.0;
   double hist_new[12];
@@ -218,27 +229,41 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
     }
 
     if (a.want_tangent) {
-      double V[3][3];  // F^-1 N : ell_hat for ell = e_a (x) F^-T e_B is N[a][p] V[B][q]
+      df64 Nd[3][3], Vd[3][3];  // N and V = F^-1 N: ell_hat for ell = e_a (x) F^-T e_B is N[a][p] V[B][q]
       for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) V[r][c] = Fi[r][0] * N[0][c] + Fi[r][1] * N[1][c] + Fi[r][2] * N[2][c];
+        for (int c = 0; c < 3; ++c) Nd[r][c] = df_split(N[r][c]);
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          Vd[r][c] = df_madd(df_madd(df_mul(Fid[r][0], Nd[0][c]), Fid[r][1], Nd[1][c]), Fid[r][2], Nd[2][c]);
       const double rho01 = log_ratio(x[0], x[1]);
       const double rho02 = log_ratio(x[0], x[2]);
       const double rho12 = log_ratio(x[1], x[2]);
-      const double b[3] = {1.0 + x[0], 1.0 + x[1], 1.0 + x[2]};
+      const df64 one = df_make(1.0f, 0.0f);
+      df64 bd[3], edd[3];
+      for (int p = 0; p < 3; ++p) {
+        bd[p] = df_add(one, df_split(x[p]));
+        edd[p] = df_split(ed[p]);
+      }
       // symmetric basis of the principal frame in Voigt order: N dh N^T =
       // sum_p dh_pp n_p n_p^T + sum_{p<t} dh_pt (n_p n_t^T + n_t n_p^T)
-      double E[6][6];
+      df64 E[6][6];
       for (int v = 0; v < 6; ++v) {
         int r, c;
         vo_idx(v, r, c);
-        E[0][v] = N[r][0] * N[c][0];
-        E[1][v] = N[r][1] * N[c][1];
-        E[2][v] = N[r][2] * N[c][2];
-        E[3][v] = N[r][1] * N[c][2] + N[r][2] * N[c][1];
-        E[4][v] = N[r][0] * N[c][2] + N[r][2] * N[c][0];
-        E[5][v] = N[r][0] * N[c][1] + N[r][1] * N[c][0];
+        E[0][v] = df_mul(Nd[r][0], Nd[c][0]);
+        E[1][v] = df_mul(Nd[r][1], Nd[c][1]);
+        E[2][v] = df_mul(Nd[r][2], Nd[c][2]);
+        E[3][v] = df_madd(df_mul(Nd[r][1], Nd[c][2]), Nd[r][2], Nd[c][1]);
+        E[4][v] = df_madd(df_mul(Nd[r][0], Nd[c][2]), Nd[r][2], Nd[c][0]);
+        E[5][v] = df_madd(df_mul(Nd[r][0], Nd[c][1]), Nd[r][1], Nd[c][0]);
       }
-      const double k01 = mu * af * rho01, k02 = mu * af * rho02, k12 = mu * af * rho12;
+      const df64 mud = df_split(mu), afd = df_split(af);
+      const df64 mua = df_mul(mud, afd);
+      const df64 k01 = df_mul(mua, df_split(rho01)), k02 = df_mul(mua, df_split(rho02)),
+                 k12 = df_mul(mua, df_split(rho12));
+      // off-diagonal coefficients of M_v per unit E entry
+      const df64 c12 = df_mul(k12, bd[2]), c21 = df_mul(k12, bd[1]), c02 = df_mul(k02, bd[2]),
+                 c20 = df_mul(k02, bd[0]), c01 = df_mul(k01, bd[1]), c10 = df_mul(k01, bd[0]);
       const double cq_s2 = plastic ? cq / s2 : 0.0;  // d a / d(eps_d . d eps_d) = cq / s2 (dq / q = edde / s2)
       // The nine F-directions ell = e_a (x) F^-T e_B have ell_hat = n_a v_B^T
       // (rows of N and V), and every term of the branch tangent is bilinear in
@@ -247,35 +272,52 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
       // divided differences off the diagonal), and dpsi(a, B) = c (N diag(ed) V^T)[a][B].
       //   dh_q (diagonal) = sum_p ell_pp [2 mu a (delta_qp - 1/3) + 2 mu cq_s2 ed_q ed_p]
       //   dh_12 = k12 (b_2 ell_12 + b_1 ell_21), dh_02, dh_01 alike.
-      double cdiag[3][3];  // cdiag[q][p]: coefficient of ell_pp in dh_q
+      const df64 two_mua = df_add(mua, mua);
+      const df64 c2 = df_mul(df_add(mud, mud), df_split(cq_s2));
+      const df64 third = df_split(1.0 / 3.0);
+      df64 cdiag[3][3];  // cdiag[q][p]: coefficient of ell_pp in dh_q
       for (int qq = 0; qq < 3; ++qq)
-        for (int p = 0; p < 3; ++p)
-          cdiag[qq][p] = 2.0 * mu * (af * ((qq == p ? 1.0 : 0.0) - 1.0 / 3.0) + cq_s2 * ed[qq] * ed[p]);
+        for (int p = 0; p < 3; ++p) {
+          const df64 dq = qq == p ? df_sub(one, third) : df_neg(third);
+          cdiag[qq][p] = df_madd(df_mul(two_mua, dq), df_mul(c2, edd[qq]), edd[p]);
+        }
+      const df64 cphi = df_mul(df_add(mud, mud), df_split(da_dphi));  // phi direction: dh_q = 2 mu da_dphi ed_q
 #pragma unroll 1
       for (int v = 0; v < 6; ++v) {
-        double M[3][3];
-        for (int p = 0; p < 3; ++p) M[p][p] = cdiag[0][p] * E[0][v] + cdiag[1][p] * E[1][v] + cdiag[2][p] * E[2][v];
-        M[1][2] = k12 * b[2] * E[3][v];
-        M[2][1] = k12 * b[1] * E[3][v];
-        M[0][2] = k02 * b[2] * E[4][v];
-        M[2][0] = k02 * b[0] * E[4][v];
-        M[0][1] = k01 * b[1] * E[5][v];
-        M[1][0] = k01 * b[0] * E[5][v];
-        double T[3][3];  // N M
+        df64 M[3][3];
+        for (int p = 0; p < 3; ++p)
+          M[p][p] = df_madd(df_madd(df_mul(cdiag[0][p], E[0][v]), cdiag[1][p], E[1][v]), cdiag[2][p], E[2][v]);
+        M[1][2] = df_mul(c12, E[3][v]);
+        M[2][1] = df_mul(c21, E[3][v]);
+        M[0][2] = df_mul(c02, E[4][v]);
+        M[2][0] = df_mul(c20, E[4][v]);
+        M[0][1] = df_mul(c01, E[5][v]);
+        M[1][0] = df_mul(c10, E[5][v]);
+        df64 T[3][3];  // N M
         for (int r = 0; r < 3; ++r)
-          for (int c = 0; c < 3; ++c) T[r][c] = N[r][0] * M[0][c] + N[r][1] * M[1][c] + N[r][2] * M[2][c];
+          for (int c = 0; c < 3; ++c)
+            T[r][c] = df_madd(df_madd(df_mul(Nd[r][0], M[0][c]), Nd[r][1], M[1][c]), Nd[r][2], M[2][c]);
         for (int aa = 0; aa < 3; ++aa)
-          for (int BB = 0; BB < 3; ++BB)
-            dtau[3 * aa + BB][v] += T[aa][0] * V[BB][0] + T[aa][1] * V[BB][1] + T[aa][2] * V[BB][2];
-        // phi direction: dh_q = 2 mu da_dphi ed_q
-        dtau[9][v] += 2.0 * mu * da_dphi * (ed[0] * E[0][v] + ed[1] * E[1][v] + ed[2] * E[2][v]);
+          for (int BB = 0; BB < 3; ++BB) {
+            df64 acc = dtau[3 * aa + BB][v];
+            acc = df_madd(acc, T[aa][0], Vd[BB][0]);
+            acc = df_madd(acc, T[aa][1], Vd[BB][1]);
+            dtau[3 * aa + BB][v] = df_madd(acc, T[aa][2], Vd[BB][2]);
+          }
+        const df64 edE = df_madd(df_madd(df_mul(edd[0], E[0][v]), edd[1], E[1][v]), edd[2], E[2][v]);
+        dtau[9][v] = df_madd(dtau[9][v], cphi, edE);
       }
       // energy: dpsi = 2 mu a^2 edde + 2 mu a s2 da = 2 mu a (a + cq) edde in the F-directions
-      const double cpsi = 2.0 * mu * af * (af + (plastic ? cq : 0.0));
+      const df64 cpsi = df_mul(two_mua, df_add(afd, df_split(plastic ? cq : 0.0)));
+      df64 Ne[3][3];  // N diag(ed)
+      for (int r = 0; r < 3; ++r)
+        for (int p = 0; p < 3; ++p) Ne[r][p] = df_mul(Nd[r][p], edd[p]);
       for (int aa = 0; aa < 3; ++aa)
-        for (int BB = 0; BB < 3; ++BB)
-          dpsi[3 * aa + BB] += cpsi * (N[aa][0] * ed[0] * V[BB][0] + N[aa][1] * ed[1] * V[BB][1] + N[aa][2] * ed[2] * V[BB][2]);
-      dpsi[9] += 2.0 * mu * af * s2 * da_dphi;
+        for (int BB = 0; BB < 3; ++BB) {
+          const df64 t = df_madd(df_madd(df_mul(Ne[aa][0], Vd[BB][0]), Ne[aa][1], Vd[BB][1]), Ne[aa][2], Vd[BB][2]);
+          dpsi[3 * aa + BB] = df_madd(dpsi[3 * aa + BB], cpsi, t);
+        }
+      dpsi[9] = df_madd(dpsi[9], df_mul(two_mua, df_split(s2)), df_split(da_dphi));
     }
   }
 
@@ -342,47 +384,78 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
     const double cL = 2.0 * Hh + ph.gc_c0l0 * app + gl.zeta / gl.dt;
     // mapped mesh: reference-frame columns kept, transformed to the parent frame below
     double Dm[9][9], Pv[9], Lv[9], Lphi = 0.0;
+    // double-float copies of the point's scalars and matrices
+    const df64 gd = df_split(g), gpd = df_split(gp), tvd = df_split(tv), kapd = df_split(ph.kap_tot);
+    const df64 kth = df_mul(kapd, df_split(theta)), cLd = df_split(cL);
+    df64 taudd[6];
+    for (int v = 0; v < 6; ++v) {
+      int r, c;
+      vo_idx(v, r, c);
+      taudd[v] = df_split(taud[r][c]);
+    }
+    df64 TF[3][3];  // tau_degr F^-T: the geometric term of direction (aa, BB) is column BB, placed in column aa
+    {
+      df64 td[3][3];
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) td[r][c] = df_split(tdeg[r][c]);
+      for (int r = 0; r < 3; ++r)
+        for (int B = 0; B < 3; ++B)
+          TF[r][B] = df_madd(df_madd(df_mul(td[r][0], Fid[B][0]), td[r][1], Fid[B][1]), td[r][2], Fid[B][2]);
+    }
+    // scale of the stored words: w det J, d xi / dX per direction, s_phi
+    df64 wsc[3], wsc2[3][3];
+    const df64 wd = df_split(wdet), sphi = df_split(gl.s_phi);
+    for (int A = 0; A < 3; ++A) wsc[A] = df_mul(wd, df_split(sg[A]));
+    for (int A = 0; A < 3; ++A)
+      for (int B = 0; B < 3; ++B) wsc2[A][B] = df_mul(wsc[A], df_split(sg[B]));
     for (int d = 0; d < 10; ++d) {
-      const double dphi = (d == 9) ? 1.0 : 0.0;
+      const bool dphi = d == 9;
       const int aa = (d < 9) ? d / 3 : 0, BB = (d < 9) ? d % 3 : 0;
-      const double trl = (d < 9) ? Fi[BB][aa] : 0.0;
-      const double dtv = ph.kap_tot * trl;
-      double M[3][3];
-      double dpsip;
+      const df64 trl = (d < 9) ? Fid[BB][aa] : df_make(0.0f, 0.0f);
+      const df64 dtv = df_mul(kapd, trl);
+      df64 M[3][3];
       for (int v = 0; v < 6; ++v) {
         int r, c;
         vo_idx(v, r, c);
-        double val;
-        if (tens) val = g * dtau[d][v] + gp * dphi * taud[r][c] + (r == c ? g * dtv + gp * dphi * tv : 0.0);
-        else val = g * dtau[d][v] + gp * dphi * taud[r][c] + (r == c ? dtv : 0.0);
+        df64 val = df_mul(gd, dtau[d][v]);
+        if (dphi) val = df_madd(val, gpd, taudd[v]);
+        if (r == c) {
+          if (tens) {
+            val = df_madd(val, gd, dtv);
+            if (dphi) val = df_madd(val, gpd, tvd);
+          } else {
+            val = df_add(val, dtv);
+          }
+        }
         M[r][c] = val; M[c][r] = val;
       }
-      dpsip = tens ? dpsi[d] + ph.kap_tot * theta * trl : dpsi[d];
-      if (d < 9) {  // geometric term: - tau_degr ell^T, (tau ell^T)_{i aa} = (tau F^-T e_BB)_i
-        for (int r = 0; r < 3; ++r) M[r][aa] -= tdeg[r][0] * Fi[BB][0] + tdeg[r][1] * Fi[BB][1] + tdeg[r][2] * Fi[BB][2];
-      }
-      double dP[3][3];
+      const df64 dpsip = tens ? df_madd(dpsi[d], kth, trl) : dpsi[d];
+      if (d < 9)  // geometric term: - tau_degr ell^T, (tau ell^T)_{i aa} = (tau F^-T e_BB)_i
+        for (int r = 0; r < 3; ++r) M[r][aa] = df_sub(M[r][aa], TF[r][BB]);
+      df64 dP[3][3];
       for (int r = 0; r < 3; ++r)
-        for (int A = 0; A < 3; ++A) dP[r][A] = M[r][0] * Fi[A][0] + M[r][1] * Fi[A][1] + M[r][2] * Fi[A][2];
-      const double dL = cL * dphi + gp * (active ? dpsip : 0.0);
+        for (int A = 0; A < 3; ++A)
+          dP[r][A] = df_madd(df_madd(df_mul(M[r][0], Fid[A][0]), M[r][1], Fid[A][1]), M[r][2], Fid[A][2]);
+      df64 dL = active ? df_mul(gpd, dpsip) : df_make(0.0f, 0.0f);
+      if (dphi) dL = df_add(dL, cLd);
       if (mapped) {
         if (d < 9) {
-          for (int m = 0; m < 9; ++m) Dm[m][d] = dP[m / 3][m % 3];
-          Lv[d] = dL;
+          for (int m = 0; m < 9; ++m) Dm[m][d] = df_join(dP[m / 3][m % 3]);
+          Lv[d] = df_join(dL);
         } else {
-          for (int m = 0; m < 9; ++m) Pv[m] = dP[m / 3][m % 3];
-          Lphi = dL;
+          for (int m = 0; m < 9; ++m) Pv[m] = df_join(dP[m / 3][m % 3]);
+          Lphi = df_join(dL);
         }
       } else if (d < 9) {
         const int n = 3 * aa + BB;
         for (int m = 0; m <= n; ++m) {
           const int r = m / 3, A = m % 3;
-          lin[(long long)(kWA + sym9(m, n)) * stride] = wdet * sg[A] * sg[BB] * dP[r][A];
+          lin[(long long)(kWA + sym9(m, n)) * stride] = df_join(df_mul(wsc2[A][BB], dP[r][A]));
         }
-        lin[(long long)(kWC + n) * stride] = wdet * sg[BB] * gl.s_phi * dL;
+        lin[(long long)(kWC + n) * stride] = df_join(df_mul(df_mul(wsc[BB], sphi), dL));
       } else {
-        for (int m = 0; m < 9; ++m) lin[(long long)(kWP + m) * stride] = wdet * sg[m % 3] * dP[m / 3][m % 3];
-        lin[(long long)kWD * stride] = wdet * gl.s_phi * dL;
+        for (int m = 0; m < 9; ++m) lin[(long long)(kWP + m) * stride] = df_join(df_mul(wsc[m % 3], dP[m / 3][m % 3]));
+        lin[(long long)kWD * stride] = df_join(df_mul(df_mul(wd, sphi), dL));
       }
     }
     if (!mapped) {

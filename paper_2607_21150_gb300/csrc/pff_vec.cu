@@ -4,6 +4,7 @@
 // and the geometric factors of mapped meshes.
 #include <cuda_bf16.h>
 
+#include "pff_df.cuh"
 #include "pff_internal.h"
 
 namespace pff {
@@ -142,11 +143,15 @@ cudaError_t launch_init_rows(int prec, void* y, const void* x, const uint8_t* ma
   return cudaGetLastError();
 }
 
-// FP32 planes of the stored linearisation: hi = fl32(a), lo = fl32(a - hi)
-// (lo optional), words [0, 64) of every point regrouped by four (the quad
-// layout of lin32_word), words [64, 70) in place.  One thread per output float4
-// of the quad region (four coalesced FP64 reads, one 128-bit write), then one
-// per tail word.
+// FP32 planes of the stored linearisation: hi = fl32(a) (round to nearest
+// even), lo = a - hi to 23 bits (lo optional; df_split_rn, integer operations,
+// so that the kernel runs at HBM speed rather than at the FP64 rate of the
+// conversion instructions), words [0, 64) of every point regrouped by four
+// (the quad layout of lin32_word), words [64, 70) in place.  Writing these
+// copies from the pointwise kernel instead measured slower (64^3 Q4 residual
+// 154 -> 176 ms): its scattered narrow stores cost more than this pass.  One
+// thread per output float4 of the quad region (four coalesced FP64 reads, one
+// 128-bit write), then one per tail word.
 __global__ void k_split_df(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo,
                            long long nblk, long long q3eb) {
   const long long bw = (long long)kLinWords * q3eb;
@@ -161,9 +166,9 @@ __global__ void k_split_df(const double* __restrict__ a, float* __restrict__ hi,
       float h[4], l[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        const double v = src[c * q3eb];
-        h[c] = __double2float_rn(v);
-        l[c] = __double2float_rn(v - (double)h[c]);
+        const df64 v = df_split_rn(src[c * q3eb]);
+        h[c] = v.hi;
+        l[c] = v.lo;
       }
       const long long o = b * bw + quad * 4 * q3eb + 4 * r2;
       *reinterpret_cast<float4*>(hi + o) = make_float4(h[0], h[1], h[2], h[3]);
@@ -171,10 +176,9 @@ __global__ void k_split_df(const double* __restrict__ a, float* __restrict__ hi,
     } else {
       const long long v = u - nq4, b = v / tpb;
       const long long i = b * bw + (long long)kLinQuadWords * q3eb + v % tpb;
-      const double x = a[i];
-      const float h = __double2float_rn(x);
-      hi[i] = h;
-      if (lo) lo[i] = __double2float_rn(x - (double)h);
+      const df64 sv = df_split_rn(a[i]);
+      hi[i] = sv.hi;
+      if (lo) lo[i] = sv.lo;
     }
   }
 }
