@@ -711,11 +711,10 @@ int pff_residual(pff_op* op, const double* z, double* r, void* stream) {
   if (det) a.evec = op->evec;
   PFF_CK(elem_dispatch<double>(op->Q, op->p + 1, kBack, a, st));
   if (det) PFF_CK(launch_node_gather(0, op->mesh, op->evec, op->mask, 1, z, op->dvals, r, 0, op->mesh.nn, st));
-  if (op->f32 && op->lin32)
-    PFF_CK(launch_split_df(op->lin64, op->lin32, op->df ? op->lin32 + op->lin_len : nullptr,
-                           op->lin_len / (kLinWords * stride_of(op->Q)), op->Q, st));
-  if (op->bf16 && op->lin16)
-    PFF_CK(launch_split_bf16(op->lin64, op->lin16, op->lin_len / (kLinWords * stride_of(op->Q)), op->Q, st));
+  float* w32 = (op->f32 && op->lin32) ? op->lin32 : nullptr;
+  PFF_CK(launch_split_words(op->lin64, w32, w32 && op->df ? op->lin32 + op->lin_len : nullptr,
+                            (op->bf16 && op->lin16) ? op->lin16 : nullptr,
+                            op->lin_len / (kLinWords * stride_of(op->Q)), op->Q, st));
   return PFF_OK;
 }
 

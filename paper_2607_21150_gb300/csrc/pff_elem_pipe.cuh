@@ -14,8 +14,10 @@
 // stage s into registers, whether it belongs to this element block or the
 // next, so that the first two stages of block b + 1 stream in while block b
 // runs its transposed contractions and scatter and block b + 1 its gather and
-// forward contractions.  The x rows of the block's next element block are
-// requested into L2 (cp.async.bulk.prefetch.L2) one element block ahead.
+// forward contractions.  The nodal values of the next element block are
+// loaded into registers while the present one runs its transposed contractions
+// and scatter (an additional L2 prefetch of those x rows, one element block
+// ahead, measured slower: 64^3 Q4 FP32 words 2.33 -> 2.19 ms without it).
 //
 // The x- and y-derivative outputs of slice k go through a double-buffered
 // slice buffer and are contracted at the next slice, after the barrier that
@@ -91,38 +93,6 @@ __device__ __forceinline__ unsigned long long l2_evict_first_policy() {
   unsigned long long p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
-}
-// L2 prefetch of the x rows that element block `blk` will gather (structured
-// numbering): thread t < 4 P^2 takes field f and node row (b, c) and requests
-// the row segment of each element row the block covers (16-byte rounded).
-template <int P, int Q>
-__device__ __forceinline__ void prefetch_x_rows(const MeshDev& m, const float* x, long long blk, int t) {
-  constexpr int EB = elems_per_block(Q);
-  if (m.offsets || t >= 4 * P * P || !x) return;
-  const long long e0 = blk * EB;
-  if (e0 >= m.nel) return;
-  const long long e1 = (e0 + EB < (long long)m.nel ? e0 + EB : (long long)m.nel) - 1;
-  const int f = t / (P * P), bb = t % P, cc = (t / P) % P;
-  const uintptr_t end = reinterpret_cast<uintptr_t>(x + 4 * m.nn) & ~uintptr_t(15);
-  for (long long es = e0; es <= e1;) {
-    const int ex = (int)(es % m.nx);
-    const long long row = es / m.nx;
-    const int ey = (int)(row % m.ny), ez = (int)(row / m.ny);
-    long long last = es + (m.nx - 1 - ex);
-    if (last > e1) last = e1;
-    const long long node0 =
-        (long long)m.p * ex + (long long)m.nnx * ((long long)(m.p * ey + bb) + (long long)m.nny * (m.p * ez + cc));
-    const long long cnt = (long long)m.p * (last - es) + m.p + 1;
-    const uintptr_t base = reinterpret_cast<uintptr_t>(x + f * m.nn + node0);
-    const uintptr_t lo = base & ~uintptr_t(15);
-    uintptr_t hi = (base + cnt * sizeof(float) + 15) & ~uintptr_t(15);
-    if (hi > end) hi = end;
-    if (hi > lo)
-      asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tcp.async.bulk.prefetch.L2.global [ga], %1;\n\t}" ::"l"(lo),
-                   "r"((unsigned)(hi - lo))
-                   : "memory");
-    es = last + 1;
-  }
 }
 // Orders this thread's earlier generic-proxy shared-memory accesses (and, after
 // a barrier, the block's) before later async-proxy writes to the same bytes.
@@ -585,8 +555,6 @@ k_level_pipe(const ElemArgs<float> a) {
 
   for (int it = 0; it < nmine; ++it) {
     const long long blk = blk_first + (long long)it * G;
-    if constexpr (P == Q)
-      if (it + 1 < nmine) prefetch_x_rows<P, Q>(a.mesh, a.x, blk + G, t);
     pipe_gather_store<P, Q>(s.bufA, ij, xv);
     fwd_lines<P, Q>(a, s.bufA, s.bufB, ij);
 

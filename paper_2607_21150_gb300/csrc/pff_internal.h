@@ -216,10 +216,11 @@ cudaError_t launch_elem_mask(const MeshDev& m, const uint8_t* mask, uint8_t* ema
 // y = mask ? x : 0 on nodes [n0, n1) of each field (prec 0: FP64, 1: FP32).
 cudaError_t launch_init_rows(int prec, void* y, const void* x, const uint8_t* mask, long long nn, long long n0,
                              long long n1, cudaStream_t st);
-// hi[i] = fl32(a[i]) and, when lo is not null, lo[i] = fl32(a[i] - hi[i]).
-cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nblk, int Q, cudaStream_t st);
-// out = the BF16 words (round to nearest even) of the FP64 words a, lin16_word layout.
-cudaError_t launch_split_bf16(const double* a, uint16_t* out, long long nblk, int Q, cudaStream_t st);
+// Level copies of the FP64 words a in one pass, each optional: FP32 planes hi
+// (round to nearest even) and lo = a - hi (lin32_word layout), BF16 words b16
+// (round to nearest even, lin16_word layout).
+cudaError_t launch_split_words(const double* a, float* hi, float* lo, uint16_t* b16, long long nblk, int Q,
+                               cudaStream_t st);
 cudaError_t launch_apply_dirichlet(double* z, const double* ubar, const uint8_t* mask, long long n, cudaStream_t st);
 cudaError_t launch_masked_field_sums(const double* v, const uint8_t* sel, long long nn, double* out, cudaStream_t st);
 // out[8]: flag counts (yield, history active, theta >= 0), phi max / min, nodes

@@ -235,9 +235,9 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
       for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c)
           Vd[r][c] = df_madd(df_madd(df_mul(Fid[r][0], Nd[0][c]), Fid[r][1], Nd[1][c]), Fid[r][2], Nd[2][c]);
-      const double rho01 = log_ratio(x[0], x[1]);
-      const double rho02 = log_ratio(x[0], x[2]);
-      const double rho12 = log_ratio(x[1], x[2]);
+      const df64 rho01 = log_ratio_df(x[0], x[1]);
+      const df64 rho02 = log_ratio_df(x[0], x[2]);
+      const df64 rho12 = log_ratio_df(x[1], x[2]);
       const df64 one = df_make(1.0f, 0.0f);
       df64 bd[3], edd[3];
       for (int p = 0; p < 3; ++p) {
@@ -259,8 +259,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
       }
       const df64 mud = df_split(mu), afd = df_split(af);
       const df64 mua = df_mul(mud, afd);
-      const df64 k01 = df_mul(mua, df_split(rho01)), k02 = df_mul(mua, df_split(rho02)),
-                 k12 = df_mul(mua, df_split(rho12));
+      const df64 k01 = df_mul(mua, rho01), k02 = df_mul(mua, rho02), k12 = df_mul(mua, rho12);
       // off-diagonal coefficients of M_v per unit E entry
       const df64 c12 = df_mul(k12, bd[2]), c21 = df_mul(k12, bd[1]), c02 = df_mul(k02, bd[2]),
                  c20 = df_mul(k02, bd[0]), c01 = df_mul(k01, bd[1]), c10 = df_mul(k01, bd[0]);

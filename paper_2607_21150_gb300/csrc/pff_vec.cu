@@ -143,59 +143,35 @@ cudaError_t launch_init_rows(int prec, void* y, const void* x, const uint8_t* ma
   return cudaGetLastError();
 }
 
-// FP32 planes of the stored linearisation: hi = fl32(a) (round to nearest
-// even), lo = a - hi to 23 bits (lo optional; df_split_rn, integer operations,
-// so that the kernel runs at HBM speed rather than at the FP64 rate of the
-// conversion instructions), words [0, 64) of every point regrouped by four
-// (the quad layout of lin32_word), words [64, 70) in place.  Writing these
-// copies from the pointwise kernel instead measured slower (64^3 Q4 residual
-// 154 -> 176 ms): its scattered narrow stores cost more than this pass.  One
-// thread per output float4 of the quad region (four coalesced FP64 reads, one
-// 128-bit write), then one per tail word.
-__global__ void k_split_df(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo,
-                           long long nblk, long long q3eb) {
-  const long long bw = (long long)kLinWords * q3eb;
-  const long long qpb = (kLinQuadWords / 4) * q3eb;                // float4 per block
-  const long long tpb = (long long)(kLinWords - kLinQuadWords) * q3eb;
-  const long long nq4 = nblk * qpb, n = nq4 + nblk * tpb;
-  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < n; u += (long long)gridDim.x * blockDim.x) {
-    if (u < nq4) {
-      const long long b = u / qpb, rem = u % qpb;
-      const long long quad = rem / q3eb, r2 = rem % q3eb;
-      const double* src = a + b * bw + 4 * quad * q3eb + r2;
-      float h[4], l[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const df64 v = df_split_rn(src[c * q3eb]);
-        h[c] = v.hi;
-        l[c] = v.lo;
-      }
-      const long long o = b * bw + quad * 4 * q3eb + 4 * r2;
-      *reinterpret_cast<float4*>(hi + o) = make_float4(h[0], h[1], h[2], h[3]);
-      if (lo) *reinterpret_cast<float4*>(lo + o) = make_float4(l[0], l[1], l[2], l[3]);
-    } else {
-      const long long v = u - nq4, b = v / tpb;
-      const long long i = b * bw + (long long)kLinQuadWords * q3eb + v % tpb;
-      const df64 sv = df_split_rn(a[i]);
-      hi[i] = sv.hi;
-      if (lo) lo[i] = sv.lo;
-    }
-  }
-}
-cudaError_t launch_split_df(const double* a, float* hi, float* lo, long long nblk, int Q, cudaStream_t st) {
-  if (nblk == 0) return cudaSuccess;
-  const long long q3eb = (long long)Q * Q * Q * elems_per_block(Q);
-  const long long n = nblk * ((kLinQuadWords / 4) + (kLinWords - kLinQuadWords)) * q3eb;
-  k_split_df<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, nblk, q3eb); note_launch();
-  return cudaGetLastError();
+// BF16 word of x, round to nearest even, by integer operations on the FP64
+// bit pattern (zero and FP64 subnormals give signed zero; the rare |x| outside
+// the normal FP32 range goes through the library conversion).
+__device__ __forceinline__ unsigned bf16_rne(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x), lw = (unsigned)__double2loint(x);
+  const unsigned sgn = (hw >> 16) & 0x8000u;
+  const int e = (int)((hw >> 20) & 0x7ffu);
+  if (e == 0) return sgn;
+  const int ef = e - 896;
+  if (ef <= 0 || ef >= 255) return __bfloat16_as_ushort(__double2bfloat16(x));
+  const unsigned top = ((unsigned)ef << 7) | ((hw & 0xfffffu) >> 13);  // exponent and 7 significand bits
+  const unsigned r = hw & 0x1fffu;                                      // significand bits 44..32 (44: half)
+  const unsigned inc = (r > 0x1000u || (r == 0x1000u && (lw != 0u || (top & 1u)))) ? 1u : 0u;
+  return sgn | (top + inc);  // a carry moves into the exponent
 }
 
-// BF16 words of the stored linearisation (lin16_word layout): one thread per
-// output unit, eight words of an octet plane (eight coalesced FP64 reads, one
-// 128-bit write) or four of a tail plane (one 64-bit write; words 70 and 71
-// are zero).  Round to nearest even from FP64.
-__global__ void k_split_bf16(const double* __restrict__ a, uint16_t* __restrict__ out, long long nblk,
-                             long long q3eb) {
+// The level copies of the stored linearisation in one pass over the FP64
+// words: the FP32 planes (lin32_word layout; hi = fl32(a), round to nearest
+// even, and lo = a - hi to 23 bits, df_split_rn) and the BF16 words
+// (lin16_word layout; words 70 and 71 zero), each optional.  All conversions
+// are integer operations, so that the pass runs at HBM speed rather than at
+// the FP64 rate of the conversion instructions.  One thread per octet of a
+// point's words [0, 64) (eight coalesced FP64 reads; two 128-bit writes per
+// FP32 plane, one for the BF16 octet), then one per tail plane of four words.
+// Writing these copies from the pointwise kernel instead measured slower
+// (64^3 Q4 residual 154 -> 176 ms): its scattered narrow stores cost more than
+// this pass.
+__global__ void k_split_words(const double* __restrict__ a, float* __restrict__ hi, float* __restrict__ lo,
+                              uint16_t* __restrict__ b16, long long nblk, long long q3eb) {
   const long long bw = (long long)kLinWords * q3eb, ow = (long long)kLin16Words * q3eb;
   const long long opb = 8 * q3eb, tpb = 2 * q3eb;  // octet / tail units per block
   const long long no = nblk * opb, n = no + nblk * tpb;
@@ -204,34 +180,61 @@ __global__ void k_split_bf16(const double* __restrict__ a, uint16_t* __restrict_
       const long long b = u / opb, rem = u % opb;
       const long long oc = rem / q3eb, r2 = rem % q3eb;
       const double* src = a + b * bw + 8 * oc * q3eb + r2;
-      unsigned v[4];
+      double x[8];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const unsigned lo = __bfloat16_as_ushort(__double2bfloat16(src[(2 * c) * q3eb]));
-        const unsigned hi = __bfloat16_as_ushort(__double2bfloat16(src[(2 * c + 1) * q3eb]));
-        v[c] = lo | (hi << 16);
+      for (int c = 0; c < 8; ++c) x[c] = src[c * q3eb];
+      if (hi) {
+        float h[8], l[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const df64 v = df_split_rn(x[c]);
+          h[c] = v.hi;
+          l[c] = v.lo;
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const long long o = b * bw + (2 * oc + g) * 4 * q3eb + 4 * r2;
+          *reinterpret_cast<float4*>(hi + o) = make_float4(h[4 * g], h[4 * g + 1], h[4 * g + 2], h[4 * g + 3]);
+          if (lo) *reinterpret_cast<float4*>(lo + o) = make_float4(l[4 * g], l[4 * g + 1], l[4 * g + 2], l[4 * g + 3]);
+        }
       }
-      *reinterpret_cast<uint4*>(out + b * ow + oc * 8 * q3eb + 8 * r2) = make_uint4(v[0], v[1], v[2], v[3]);
+      if (b16) {
+        unsigned v[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = bf16_rne(x[2 * c]) | (bf16_rne(x[2 * c + 1]) << 16);
+        *reinterpret_cast<uint4*>(b16 + b * ow + oc * 8 * q3eb + 8 * r2) = make_uint4(v[0], v[1], v[2], v[3]);
+      }
     } else {
       const long long w = u - no, b = w / tpb, rem = w % tpb;
       const long long tp = rem / q3eb, r2 = rem % q3eb;
-      unsigned v[2];
+      unsigned v[4];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int w0 = 64 + 4 * (int)tp + 2 * c, w1 = w0 + 1;
-        const unsigned lo = w0 < kLinWords ? __bfloat16_as_ushort(__double2bfloat16(a[b * bw + w0 * q3eb + r2])) : 0u;
-        const unsigned hi = w1 < kLinWords ? __bfloat16_as_ushort(__double2bfloat16(a[b * bw + w1 * q3eb + r2])) : 0u;
-        v[c] = lo | (hi << 16);
+      for (int c = 0; c < 4; ++c) {
+        const int wd = 64 + 4 * (int)tp + c;
+        v[c] = 0u;
+        if (wd < kLinWords) {
+          const long long i = b * bw + wd * q3eb + r2;
+          const double x = a[i];
+          if (hi) {
+            const df64 sv = df_split_rn(x);
+            hi[i] = sv.hi;
+            if (lo) lo[i] = sv.lo;
+          }
+          v[c] = bf16_rne(x);
+        }
       }
-      *reinterpret_cast<uint2*>(out + b * ow + (64 + 4 * tp) * q3eb + 4 * r2) = make_uint2(v[0], v[1]);
+      if (b16)
+        *reinterpret_cast<uint2*>(b16 + b * ow + (64 + 4 * tp) * q3eb + 4 * r2) =
+            make_uint2(v[0] | (v[1] << 16), v[2] | (v[3] << 16));
     }
   }
 }
-cudaError_t launch_split_bf16(const double* a, uint16_t* out, long long nblk, int Q, cudaStream_t st) {
-  if (nblk == 0) return cudaSuccess;
+cudaError_t launch_split_words(const double* a, float* hi, float* lo, uint16_t* b16, long long nblk, int Q,
+                               cudaStream_t st) {
+  if (nblk == 0 || (!hi && !b16)) return cudaSuccess;
   const long long q3eb = (long long)Q * Q * Q * elems_per_block(Q);
   const long long n = nblk * 10 * q3eb;
-  k_split_bf16<<<grid_for(n), kVecThreads, 0, st>>>(a, out, nblk, q3eb); note_launch();
+  k_split_words<<<grid_for(n), kVecThreads, 0, st>>>(a, hi, lo, b16, nblk, q3eb); note_launch();
   return cudaGetLastError();
 }
 
