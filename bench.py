@@ -46,15 +46,16 @@ def peaks():
 
 def pipe_rates(stream, iters: int = 20000):
     """FP64 FMA, FP64 tensor-core (mma.sync m8n8k4) and FP32 FMA throughput of
-    this GPU at its current clocks, by the library's pipe-rate probe: best of
-    three launches of 8 blocks of 256 threads per SM, CUDA events."""
+    this GPU at its current clocks, and the rate of the FP64 <-> FP32
+    conversion instructions (G conversions/s), by the library's pipe-rate
+    probe: best of three launches of 8 blocks of 256 threads per SM, CUDA events."""
     import torch
     from paper_2607_21150_gb300 import pff
     out = {}
     blocks, threads = 152 * 8, 256
     sink = torch.zeros(blocks * threads, dtype=torch.float64, device="cuda")
     for name, kind, it in (("dfma", pff.PFF_PROBE_DFMA, iters), ("dmma", pff.PFF_PROBE_DMMA, iters // 4),
-                           ("ffma", pff.PFF_PROBE_FFMA, 8 * iters)):
+                           ("ffma", pff.PFF_PROBE_FFMA, 8 * iters), ("cvt", pff.PFF_PROBE_CVT, iters // 2)):
         pff.pff_probe_pipe(kind, 64, blocks, threads, sink, stream)
         best = 0.0
         for _ in range(3):
@@ -64,7 +65,10 @@ def pipe_rates(stream, iters: int = 20000):
             b.record(stream)
             torch.cuda.synchronize()
             best = max(best, fl / (a.elapsed_time(b) / 1e3) / 1e12)
-        out[name + "_tflops"] = best
+        if name == "cvt":
+            out["cvt_gops"] = best * 1e3
+        else:
+            out[name + "_tflops"] = best
     return out
 
 
@@ -443,6 +447,22 @@ def run_native(args):
     t1.record(stream)
     torch.cuda.synchronize()
     t_res = t0.elapsed_time(t1)
+    # the residual alone, without the level copies of the words (FP32 / double-
+    # float planes, BF16) that the mixed-precision solvers read; then restored
+    pff.pff_op_enable_bf16(s.op, False)
+    pff.pff_op_enable_f32(s.op, False)
+    s.residual(z)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    s.residual(z)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    t_res64 = t0.elapsed_time(t1)
+    pff.pff_op_enable_f32(s.op, True)
+    pff.pff_op_enable_df(s.op, True)
+    pff.pff_op_enable_bf16(s.op, True)
+    r = s.residual(z)
+    torch.cuda.synchronize()
     status = s.status()
     ndof = m.ndof
     L = s.levels[m.p]
@@ -607,7 +627,7 @@ def run_native(args):
         "df64_apply": {"gdofs": ndof / (totdf / args.steps / 1e3) / 1e9, "ms": totdf / args.steps,
                        "rel_l2_vs_fp64": df_rel,
                        "note": "double-float action (FP32-pair arithmetic, FP64 vectors); not the headline"},
-        "residual_ms": t_res, "kernel_status": status,
+        "residual_ms": t_res, "residual_without_level_copies_ms": t_res64, "kernel_status": status,
         "newton_step": newton,
         "newton_configs": newton_configs,
         "level_applies": levels,

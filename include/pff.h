@@ -432,13 +432,16 @@ int pff_state_summary(pff_op* op, const double* z, double* out8, void* stream);
  * floating-point operations that launch performs, so that flops / (launch
  * time) is the pipe's throughput on this GPU at its current clocks:
  *   PFF_PROBE_DFMA  FP64 FMA (2 flop each), PFF_PROBE_FFMA  FP32 FMA,
- *   PFF_PROBE_DMMA  FP64 tensor-core mma.sync m8n8k4 (512 flop per warp op).
+ *   PFF_PROBE_DMMA  FP64 tensor-core mma.sync m8n8k4 (512 flop per warp op),
+ *   PFF_PROBE_CVT   FP64 -> FP32 -> FP64 conversion instructions (*flops then
+ *                   counts conversions, two per chain step).
  * sink: device FP64 [blocks * threads] receiving the chains' final sums
  * (keeps them live).  Asynchronous on the stream; iters a multiple of 4,
  * threads a multiple of 32 in [32, 1024]; PFF_ERR_INVALID otherwise. */
 #define PFF_PROBE_DFMA 0
 #define PFF_PROBE_FFMA 1
 #define PFF_PROBE_DMMA 2
+#define PFF_PROBE_CVT 3
 int pff_probe_pipe(int kind, int64_t iters, int blocks, int threads, double* sink, double* flops, void* stream);
 
 #ifdef __cplusplus

@@ -8,6 +8,10 @@
 //   PFF_PROBE_DMMA  FP64 warp matrix multiply-accumulate mma.sync m8n8k4
 //                   (the only FP64 tensor-core instruction; tcgen05 has no
 //                   FP64 kind), 2 * 8 * 8 * 4 = 512 flop per warp instruction
+//   PFF_PROBE_CVT   double -> float -> double conversion instructions (two
+//                   per step; counted as operations): on GB300 they run at
+//                   the FP64 rate, which is why the kernels that move FP64
+//                   work onto the FP32 pipes convert by integer operations
 //
 // Every thread (warp, for DMMA) runs kChains independent chains of `iters`
 // steps, so the pipe sees kChains operations in flight per thread; the FMA
@@ -85,6 +89,22 @@ __global__ void k_probe_dmma(long long iters, double a, double b, double* sink) 
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+__global__ void k_probe_cvt(long long iters, double a, double b, double* sink) {
+  double acc[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc[c] = a + b * (threadIdx.x + c);
+  for (long long it = 0; it < iters; it += kUnroll) {
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+      for (int c = 0; c < kChains; ++c) acc[c] = (double)__double2float_rn(acc[c]);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += acc[c];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace
 }  // namespace pff
 
@@ -113,6 +133,10 @@ extern "C" int pff_probe_pipe(int kind, int64_t iters, int blocks, int threads, 
     case PFF_PROBE_DMMA:
       k_probe_dmma<<<blocks, threads, 0, st>>>(iters, a, b, sink); note_launch();
       *flops = 512.0 * per_thread * (nthreads / 32.0);
+      break;
+    case PFF_PROBE_CVT:
+      k_probe_cvt<<<blocks, threads, 0, st>>>(iters, a, b, sink); note_launch();
+      *flops = 2.0 * per_thread * nthreads;
       break;
     default:
       return set_last_error(PFF_ERR_INVALID, "pff_probe_pipe: unknown probe kind");

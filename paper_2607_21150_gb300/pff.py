@@ -16,7 +16,7 @@ PFF_F64 = 0
 PFF_F32 = 1
 PFF_DF64 = 2
 PFF_F32_BF16 = 3
-PFF_PROBE_DFMA, PFF_PROBE_FFMA, PFF_PROBE_DMMA = 0, 1, 2
+PFF_PROBE_DFMA, PFF_PROBE_FFMA, PFF_PROBE_DMMA, PFF_PROBE_CVT = 0, 1, 2, 3
 STATUS_EIGEN, STATUS_DETF, STATUS_NONFINITE = 1, 2, 4
 
 _lib = None

@@ -1,5 +1,6 @@
 """The C-ABI library loads and exports every entry point include/pff.h declares;
 host-only calls (argument checks, basis tables) work without a GPU."""
+import ctypes
 import os
 import re
 import subprocess
@@ -46,6 +47,13 @@ def test_argument_errors_without_gpu(libpff):
     with pytest.raises(pff.PffError, match="nnodes"):
         pff.pff_create_restriction(ctx, (2, 2, 2, 0.1, 0.1, 0.1), 2, None, 7)
     pff.pff_destroy_context(ctx)
+    # the pipe-rate probe checks its arguments before any launch (the sink
+    # address is never dereferenced on the host)
+    sink = ctypes.c_void_p(16)
+    with pytest.raises(pff.PffError, match="multiple of 4"):
+        pff.pff_probe_pipe(pff.PFF_PROBE_CVT, 3, 1, 32, sink, 0)
+    with pytest.raises(pff.PffError, match="unknown probe kind"):
+        pff.pff_probe_pipe(7, 4, 1, 32, sink, 0)
 
 
 def test_degenerate_arguments_rejected_without_gpu(libpff):
