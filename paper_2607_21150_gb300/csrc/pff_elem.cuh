@@ -108,9 +108,9 @@ struct ElemSmem {
   const T* Dt;
 };
 
-// Forward: gather x into bufA, interpolate to Gauss points into bufB.
+// Gather x into bufA [4][c][b][a] (masked entries zero).
 template <int P, int Q, typename T>
-__device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, Q, T>& s, int e, bool valid, int ij) {
+__device__ __forceinline__ void gather(const ElemArgs<T>& a, T* bufA, int e, bool valid, int ij) {
   constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
   const long long nn = a.mesh.nn;
   // the node mask is read only for elements flagged as having masked nodes
@@ -133,9 +133,16 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
         const bool fixed = masked && ldg(a.mask + g);
         if (!fixed) v = from_store<T>(xv);
       }
-      s.bufA[f * Q3 + idx] = v;
+      bufA[f * Q3 + idx] = v;
     }
   }
+}
+
+// Forward: gather x into bufA, interpolate to Gauss points into bufB.
+template <int P, int Q, typename T>
+__device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, Q, T>& s, int e, bool valid, int ij) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
+  gather<P, Q, T>(a, s.bufA, e, valid, ij);
   __syncthreads();
   // x: [c][b][a] -> [c][b][i]
   for (int idx = ij; idx < P * P * Q; idx += Q2) {
@@ -181,6 +188,160 @@ __device__ __forceinline__ void forward(const ElemArgs<T>& a, const ElemSmem<P, 
     }
   }
   __syncthreads();
+}
+
+// The 1D interpolation matrix B [Q][P] as kernel parameters, read as
+// constant-bank operands where the index is fixed at compile time.
+__device__ __forceinline__ float basis_b(const ElemArgs<float>& a, int idx) { return a.cB[idx]; }
+
+// Interpolation to the Gauss points as line transforms (the persistent FP32
+// kernel; the double-float action measured slower with them, 9.7 -> 9.9 ms at
+// 64^3 Q4, its registers being the tighter limit): each thread takes whole
+// lines (P inputs in registers, Q outputs),
+// with the 1D matrix as kernel-parameter operands, so that a stage costs P
+// loads and Q stores of shared memory per line instead of two loads per
+// multiply-add, and a line's Q outputs are independent chains.  From bufA
+// [4][c][b][a] (gathered); x: -> bufB [4][c][b][i]; y: -> bufA [4][c][j][i];
+// z: -> bufB [4][k][j][i].
+template <int P, int Q, typename T>
+__device__ __forceinline__ void fwd_lines(const ElemArgs<T>& a, T* bufA, T* bufB, int ij) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < (4 * P * P + Q2 - 1) / Q2; ++r) {  // x: lines (f, c, b)
+    const int L = ij + r * Q2;
+    if (L >= 4 * P * P) break;
+    const int f = L / (P * P), cb = L % (P * P);
+    const T* in = bufA + f * Q3 + cb * P;
+    T v[P];
+#pragma unroll
+    for (int aa = 0; aa < P; ++aa) v[aa] = in[aa];
+    T* out = bufB + f * Q3 + cb * Q;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      T acc = zero<T>();
+#pragma unroll
+      for (int aa = 0; aa < P; ++aa) acc = madd(acc, basis_b(a, i * P + aa), v[aa]);
+      out[i] = acc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < (4 * P * Q + Q2 - 1) / Q2; ++r) {  // y: lines (f, c, i)
+    const int L = ij + r * Q2;
+    if (L >= 4 * P * Q) break;
+    const int f = L / (P * Q), ci = L % (P * Q), c = ci / Q, i = ci % Q;
+    const T* in = bufB + f * Q3 + c * (P * Q) + i;
+    T v[P];
+#pragma unroll
+    for (int b = 0; b < P; ++b) v[b] = in[b * Q];
+    T* out = bufA + f * Q3 + c * Q2 + i;
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {
+      T acc = zero<T>();
+#pragma unroll
+      for (int b = 0; b < P; ++b) acc = madd(acc, basis_b(a, j * P + b), v[b]);
+      out[j * Q] = acc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {  // z: the thread's own column (j, i) of every field
+    T v[P];
+#pragma unroll
+    for (int c = 0; c < P; ++c) v[c] = bufA[f * Q3 + c * Q2 + ij];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      T acc = zero<T>();
+#pragma unroll
+      for (int c = 0; c < P; ++c) acc = madd(acc, basis_b(a, k * P + c), v[c]);
+      bufB[f * Q3 + k * Q2 + ij] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// Transposed interpolation as line transforms, from the accumulated column
+// values Y[f][k] of the thread's own column, then the scatter-add (or the
+// element values of the deterministic transpose): z (registers) -> bufA
+// [4][c][j][i]; y: -> bufB [4][c][b][i]; x: -> bufA [4][c][b][a].  em: the
+// element has masked nodes.
+template <int P, int Q, typename T>
+__device__ __forceinline__ void bwd_lines(const ElemArgs<T>& a, T* bufA, T* bufB, int e, bool valid, bool em, int ij,
+                                          const T Y[4][Q]) {
+  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
+#pragma unroll
+  for (int f = 0; f < 4; ++f)
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      T acc = zero<T>();
+#pragma unroll
+      for (int k = 0; k < Q; ++k) acc = madd(acc, basis_b(a, k * P + c), Y[f][k]);
+      bufA[f * Q3 + c * Q2 + ij] = acc;
+    }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < (4 * P * Q + Q2 - 1) / Q2; ++r) {  // y: lines (f, c, i)
+    const int L = ij + r * Q2;
+    if (L >= 4 * P * Q) break;
+    const int f = L / (P * Q), ci = L % (P * Q), c = ci / Q, i = ci % Q;
+    const T* in = bufA + f * Q3 + c * Q2 + i;
+    T v[Q];
+#pragma unroll
+    for (int j = 0; j < Q; ++j) v[j] = in[j * Q];
+    T* out = bufB + f * Q3 + c * (P * Q) + i;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      T acc = zero<T>();
+#pragma unroll
+      for (int j = 0; j < Q; ++j) acc = madd(acc, basis_b(a, j * P + b), v[j]);
+      out[b * Q] = acc;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < (4 * P * P + Q2 - 1) / Q2; ++r) {  // x: lines (f, c, b)
+    const int L = ij + r * Q2;
+    if (L >= 4 * P * P) break;
+    const int f = L / (P * P), cb = L % (P * P);
+    const T* in = bufB + f * Q3 + cb * Q;
+    T v[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = in[i];
+    T* out = bufA + f * Q3 + cb * P;
+#pragma unroll
+    for (int aa = 0; aa < P; ++aa) {
+      T acc = zero<T>();
+#pragma unroll
+      for (int i = 0; i < Q; ++i) acc = madd(acc, basis_b(a, i * P + aa), v[i]);
+      out[aa] = acc;
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  if (a.evec) {  // deterministic transpose: element-local values, summed per node by k_node_gather
+    using V = typename ElemTypes<T>::V;
+    V* ev = static_cast<V*>(a.evec) + (long long)e * 4 * P3;
+    for (int idx = ij; idx < P3; idx += Q2)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) ev[f * P3 + idx] = to_vec(bufA[f * Q3 + idx]);
+    return;
+  }
+  const long long nn = a.mesh.nn;
+  const bool masked = a.mask && em;
+#pragma unroll
+  for (int r = 0; r < (P3 + Q2 - 1) / Q2; ++r) {
+    const int idx = ij + r * Q2;
+    if (idx >= P3) break;
+    const int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);
+    const long long n = node_of<P, Q>(a.mesh, e, aa, bb, cc);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const long long g = f * nn + n;
+      if (masked && __ldg(a.mask + g)) continue;
+      atomicAdd(a.y + g, to_vec(bufA[f * Q3 + idx]));
+    }
+  }
 }
 
 // Parent-frame gradients of the four fields at point (i, j, k) from bufB.

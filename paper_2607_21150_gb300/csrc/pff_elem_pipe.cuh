@@ -315,70 +315,6 @@ __device__ __forceinline__ void pipe_gather_store(float* bufA, int ij, const flo
   }
 }
 
-// Interpolation to the Gauss points as line transforms: each thread takes
-// whole lines (P inputs in registers, Q outputs), with the 1D matrix as
-// kernel-parameter operands, so that a stage costs P loads and Q stores of
-// shared memory per line instead of two loads per multiply-add.  From bufA
-// [4][c][b][a] (gathered); x: -> bufB [4][c][b][i]; y: -> bufA [4][c][j][i];
-// z: -> bufB [4][k][j][i].
-template <int P, int Q>
-__device__ __forceinline__ void fwd_lines(const ElemArgs<float>& a, float* bufA, float* bufB, int ij) {
-  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q;
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < (4 * P * P + Q2 - 1) / Q2; ++r) {  // x: lines (f, c, b)
-    const int L = ij + r * Q2;
-    if (L >= 4 * P * P) break;
-    const int f = L / (P * P), cb = L % (P * P);
-    const float* in = bufA + f * Q3 + cb * P;
-    float v[P];
-#pragma unroll
-    for (int aa = 0; aa < P; ++aa) v[aa] = in[aa];
-    float* out = bufB + f * Q3 + cb * Q;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int aa = 0; aa < P; ++aa) acc = fmaf(a.cB[i * P + aa], v[aa], acc);
-      out[i] = acc;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < (4 * P * Q + Q2 - 1) / Q2; ++r) {  // y: lines (f, c, i)
-    const int L = ij + r * Q2;
-    if (L >= 4 * P * Q) break;
-    const int f = L / (P * Q), ci = L % (P * Q), c = ci / Q, i = ci % Q;
-    const float* in = bufB + f * Q3 + c * (P * Q) + i;
-    float v[P];
-#pragma unroll
-    for (int b = 0; b < P; ++b) v[b] = in[b * Q];
-    float* out = bufA + f * Q3 + c * Q2 + i;
-#pragma unroll
-    for (int j = 0; j < Q; ++j) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int b = 0; b < P; ++b) acc = fmaf(a.cB[j * P + b], v[b], acc);
-      out[j * Q] = acc;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int f = 0; f < 4; ++f) {  // z: the thread's own column (j, i) of every field
-    float v[P];
-#pragma unroll
-    for (int c = 0; c < P; ++c) v[c] = bufA[f * Q3 + c * Q2 + ij];
-#pragma unroll
-    for (int k = 0; k < Q; ++k) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int c = 0; c < P; ++c) acc = fmaf(a.cB[k * P + c], v[c], acc);
-      bufB[f * Q3 + k * Q2 + ij] = acc;
-    }
-  }
-  __syncthreads();
-}
-
 // Gradients of the four fields at point (i, j, k) from the Gauss-point values
 // V = bufB; the z-derivative row Dc[k][.] as kernel-parameter operands (k is
 // fixed at compile time), the x- and y-rows from shared memory.
@@ -407,87 +343,6 @@ __device__ __forceinline__ void grad_at_c(const ElemArgs<float>& a, const float*
   phi = V0[3 * Q3 + k * Q2 + j * Q + i];
 }
 
-// Transposed interpolation as line transforms, from the accumulated column
-// values Y[f][k] of the thread's own column, then the scatter-add (or the
-// element values of the deterministic transpose): z (registers) -> bufA
-// [4][c][j][i]; y: -> bufB [4][c][b][i]; x: -> bufA [4][c][b][a].
-template <int P, int Q>
-__device__ __forceinline__ void bwd_lines(const ElemArgs<float>& a, float* bufA, float* bufB, int e, bool valid,
-                                          bool em, int ij, const float Y[4][Q]) {
-  constexpr int Q2 = Q * Q, Q3 = Q * Q * Q, P3 = P * P * P;
-#pragma unroll
-  for (int f = 0; f < 4; ++f)
-#pragma unroll
-    for (int c = 0; c < P; ++c) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int k = 0; k < Q; ++k) acc = fmaf(a.cB[k * P + c], Y[f][k], acc);
-      bufA[f * Q3 + c * Q2 + ij] = acc;
-    }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < (4 * P * Q + Q2 - 1) / Q2; ++r) {  // y: lines (f, c, i)
-    const int L = ij + r * Q2;
-    if (L >= 4 * P * Q) break;
-    const int f = L / (P * Q), ci = L % (P * Q), c = ci / Q, i = ci % Q;
-    const float* in = bufA + f * Q3 + c * Q2 + i;
-    float v[Q];
-#pragma unroll
-    for (int j = 0; j < Q; ++j) v[j] = in[j * Q];
-    float* out = bufB + f * Q3 + c * (P * Q) + i;
-#pragma unroll
-    for (int b = 0; b < P; ++b) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int j = 0; j < Q; ++j) acc = fmaf(a.cB[j * P + b], v[j], acc);
-      out[b * Q] = acc;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int r = 0; r < (4 * P * P + Q2 - 1) / Q2; ++r) {  // x: lines (f, c, b)
-    const int L = ij + r * Q2;
-    if (L >= 4 * P * P) break;
-    const int f = L / (P * P), cb = L % (P * P);
-    const float* in = bufB + f * Q3 + cb * Q;
-    float v[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = in[i];
-    float* out = bufA + f * Q3 + cb * P;
-#pragma unroll
-    for (int aa = 0; aa < P; ++aa) {
-      float acc = 0.0f;
-#pragma unroll
-      for (int i = 0; i < Q; ++i) acc = fmaf(a.cB[i * P + aa], v[i], acc);
-      out[aa] = acc;
-    }
-  }
-  __syncthreads();
-  if (!valid) return;
-  if (a.evec) {  // deterministic transpose: element-local values, summed per node by k_node_gather
-    float* ev = static_cast<float*>(a.evec) + (long long)e * 4 * P3;
-    for (int idx = ij; idx < P3; idx += Q2)
-#pragma unroll
-      for (int f = 0; f < 4; ++f) ev[f * P3 + idx] = bufA[f * Q3 + idx];
-    return;
-  }
-  const long long nn = a.mesh.nn;
-  const bool masked = a.mask && em;
-#pragma unroll
-  for (int r = 0; r < (P3 + Q2 - 1) / Q2; ++r) {
-    const int idx = ij + r * Q2;
-    if (idx >= P3) break;
-    const int aa = idx % P, bb = (idx / P) % P, cc = idx / (P * P);
-    const long long n = node_of<P, Q>(a.mesh, e, aa, bb, cc);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-      const long long g = f * nn + n;
-      if (masked && __ldg(a.mask + g)) continue;
-      atomicAdd(a.y + g, bufA[f * Q3 + idx]);
-    }
-  }
-}
-
 // Transposed x- and y-derivatives of slice kc: Y[f][kc] += sum_m Dc[m, i] ox(m, j)
 // + Dc[m, j] oy(i, m), from the slice buffer sb = [8][Q^2] (ox, oy per field).
 template <int Q>
@@ -504,6 +359,31 @@ __device__ __forceinline__ void pipe_contract_xy(const float* Dc, const float* s
     }
     Y[f][kc] = acc;
   }
+}
+
+// The same contraction returned as the contribution c[f] to Y[f][kc], and its
+// addition at a slice index known only at run time (the rolled slice loop).
+template <int Q>
+__device__ __forceinline__ void pipe_contract_c(const float* Dc, const float* sb, int i, int j, float c[4]) {
+  constexpr int Q2 = Q * Q;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    float acc = 0.0f;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      acc = fmaf(Dc[m * Q + i], sb[(2 * f) * Q2 + j * Q + m], acc);
+      acc = fmaf(Dc[m * Q + j], sb[(2 * f + 1) * Q2 + m * Q + i], acc);
+    }
+    c[f] = acc;
+  }
+}
+template <int Q>
+__device__ __forceinline__ void add_at(float Y[4][Q], int kc, const float c[4]) {
+#pragma unroll
+  for (int kk = 0; kk < Q; ++kk)
+    if (kk == kc)
+#pragma unroll
+      for (int f = 0; f < 4; ++f) Y[f][kk] += c[f];
 }
 
 template <int P, int Q, bool BF, bool KX, bool TR>
@@ -564,9 +444,13 @@ k_level_pipe(const ElemArgs<float> a) {
 #pragma unroll
       for (int k = 0; k < Q; ++k) Y[f][k] = 0.0f;
     float g[4][3], phi = 0.0f, ou[9], s0 = 0.0f, o3[3] = {0.0f, 0.0f, 0.0f};
+    // the slice loop stays rolled (smaller code: at 64^3 Q4 1 % faster with
+    // FP32 words, 3 % with BF16 words) except on the order-1 level, whose
+    // short contractions leave the loop overhead exposed (5 % slower rolled)
+#pragma unroll(P >= 3 ? 1 : Q)
+    for (int k = 0; k < Q; ++k) {
 #pragma unroll
-    for (int st = 0; st < NS; ++st) {
-      const int k = st / SPS, h = st % SPS;
+    for (int h = 0; h < SPS; ++h) {
       const int sl = (int)(seq & 1);
       const bool ok = mbar_wait(bar + sl, (unsigned)((seq >> 1) & 1), a.status);
       unsigned r[38];
@@ -586,7 +470,11 @@ k_level_pipe(const ElemArgs<float> a) {
       }
       ++seq;
       if (h == 0) {
-        if (k > 0) pipe_contract_xy<Q>(s.Dc, sbuf + ((k - 1) & 1) * 8 * Q2, i, j, Y, k - 1);
+        if (k > 0) {
+          float c[4];
+          pipe_contract_c<Q>(s.Dc, sbuf + ((k - 1) & 1) * 8 * Q2, i, j, c);
+          add_at<Q>(Y, k - 1, c);
+        }
         grad_at_c<Q>(a, s.bufB, s.Dc, i, j, k, g, phi);
 #pragma unroll
         for (int m = 0; m < 9; ++m) ou[m] = 0.0f;
@@ -615,8 +503,12 @@ k_level_pipe(const ElemArgs<float> a) {
           sb[(2 * f) * Q2 + ij] = ox;
           sb[(2 * f + 1) * Q2 + ij] = oy;
         }
-        Y[3][k] += s0;
+#pragma unroll
+        for (int kk = 0; kk < Q; ++kk)
+          if (kk == k) Y[3][kk] += s0;
       }
+    }
+    if (!staged) break;
     }
     if (!staged) break;
     __syncthreads();
