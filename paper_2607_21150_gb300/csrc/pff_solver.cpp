@@ -319,15 +319,24 @@ int arnoldi_lmax(pff_solver* s, long long n, Op&& op, double* out, cudaStream_t 
     double* vj = V + (long long)j * n;
     double* wv = V + (long long)(j + 1) * n;
     S_RC(op(vj, wv));
+    // classical Gram-Schmidt with the second pass only when the first removed
+    // more than half of ||w||^2 (the criterion of the outer FGMRES); the dots
+    // include w . w itself (wv is V_{j+1})
+    double ww2 = 0.0;
     for (int pass = 0; pass < 2; ++pass) {
-      S_RC(dev_dots(s, V, n, j + 1, wv, n, h.data(), st));
+      S_RC(dev_dots(s, V, n, j + 2, wv, n, h.data(), st));
+      const double ww = h[j + 1];
       S_CK(cudaMemcpyAsync(s->hdev, h.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, st));
       S_CK(launch_maxpy(wv, V, n, j + 1, s->hdev, -1.0, n, st));
-      for (int i = 0; i <= j; ++i) H[i * k + j] += h[i];
+      double hsq = 0.0;
+      for (int i = 0; i <= j; ++i) {
+        H[i * k + j] += h[i];
+        hsq += h[i] * h[i];
+      }
+      ww2 = std::max(ww - hsq, 0.0);
+      if (ww2 >= 0.5 * ww) break;
     }
-    double ww;
-    S_RC(dev_dots(s, wv, 0, 1, wv, n, &ww, st));
-    const double hn = std::sqrt(ww);
+    const double hn = std::sqrt(ww2);
     if (!std::isfinite(hn)) return sfail(PFF_ERR_DEVICE, "Arnoldi eigenvalue estimate: non-finite vector");
     H[(j + 1) * k + j] = hn;
     if (hn <= 1e-14 * std::fabs(H[j * k + j]) + 1e-300) { kk = j + 1; break; }
