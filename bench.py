@@ -31,11 +31,11 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12  # 152 SMs x 2 DFMA/clk x 2 flop x m
 # DRAM bytes (read + write) per element of one Jacobian action, Q4 (P = Q = 5),
 # from one ncu capture of the same kernels on the 24^3 tension workload
 # (python bench.py --config tension_q4 --n 24 ...): FP64 220.06 + 5.48 MB over
-# a 3 040-element launch, FP32 words 495.65 + 4.05 MB and BF16 words 265.18 +
-# 3.82 MB over 13 824 elements; scaled to a launch by the element count.  None
+# a 3 040-element launch, FP32 words 495.72 + 3.87 MB and BF16 words 265.13 +
+# 3.72 MB over 13 824 elements; scaled to a launch by the element count.  None
 # where the kernel has changed since its counters were taken.
-TRAFFIC_PER_ELEMENT = {"f64": (220.06e6 + 5.48e6) / 3040, "f32": (495.65e6 + 4.05e6) / 13824,
-                       "bf16": (265.18e6 + 3.82e6) / 13824}
+TRAFFIC_PER_ELEMENT = {"f64": (220.06e6 + 5.48e6) / 3040, "f32": (495.72e6 + 3.87e6) / 13824,
+                       "bf16": (265.13e6 + 3.72e6) / 13824}
 
 
 def peaks():
