@@ -261,6 +261,8 @@ cudaError_t launch_dscale(T* y, const T* x, const T* d, long long n, cudaStream_
 cudaError_t launch_d2f(float* y, const double* x, long long n, cudaStream_t st);
 cudaError_t launch_f2d(double* y, const float* x, long long n, cudaStream_t st);
 cudaError_t launch_q1_spmv(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
+// The same with an FP32 copy of the stencil and FP32 arithmetic (FP64 vectors).
+cudaError_t launch_q1_spmv32(const MeshDev& mc, const float* A, const double* x, double* y, cudaStream_t st);
 cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st);
 // Sum-factorised element matrices (Ke: [nel][32][32] work space) and a
 // deterministic gather into the stencil storage.

@@ -2,6 +2,7 @@
 // assembled coarse (Q1) operator of the p-multigrid hierarchy (element
 // matrices, stencil gather, SpMV and diagonal) and the geometric h-multigrid
 // below it (Galerkin coarsening, masks, prolongation and restriction).
+#include "pff_df.cuh"
 #include "pff_internal.h"
 
 namespace pff {
@@ -186,6 +187,30 @@ __global__ void k_q1_spmv(MeshDev mc, const double* __restrict__ A, const double
   }
   for (int f = 0; f < 4; ++f) y[f * mc.nn + n] = acc[f];
 }
+// The same product with an FP32 copy of the stencil, FP32 arithmetic, FP64
+// vectors in and out (the mixed solver's coarse level: a preconditioner, whose
+// FP64 product is bound by the FP64 pipe at 432 multiply-adds per node).  x is
+// taken to FP32 by truncation of its significand (integer operations: the
+// conversion instructions run at the FP64 rate).
+__global__ void k_q1_spmv32(MeshDev mc, const float* __restrict__ A, const double* __restrict__ x,
+                            double* __restrict__ y) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= mc.nn) return;
+  const int nnz_ = (int)(mc.nn / ((long long)mc.nnx * mc.nny));
+  const int I = (int)(n % mc.nnx), J = (int)((n / mc.nnx) % mc.nny), K = (int)(n / ((long long)mc.nnx * mc.nny));
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int slot = 0; slot < 27; ++slot) {
+    const int dx = slot % 3 - 1, dy = (slot / 3) % 3 - 1, dz = slot / 9 - 1;
+    const int I2 = I + dx, J2 = J + dy, K2 = K + dz;
+    if (I2 < 0 || J2 < 0 || K2 < 0 || I2 >= mc.nnx || J2 >= mc.nny || K2 >= nnz_) continue;
+    const long long m = I2 + (long long)mc.nnx * (J2 + (long long)mc.nny * K2);
+    float xv[4];
+    for (int g = 0; g < 4; ++g) xv[g] = df_split(x[g * mc.nn + m]).hi;
+    for (int f = 0; f < 4; ++f)
+      for (int g = 0; g < 4; ++g) acc[f] = fmaf(A[(long long)(slot * 16 + f * 4 + g) * mc.nn + n], xv[g], acc[f]);
+  }
+  for (int f = 0; f < 4; ++f) y[f * mc.nn + n] = df_f2d(acc[f]);
+}
 // y = A^T x with the stencil storage: row (g, m) of A^T gathers the entries
 // A[(f, n), (g, m)] of the nodes n = m - offset(slot).
 __global__ void k_q1_spmv_t(MeshDev mc, const double* __restrict__ A, const double* __restrict__ x,
@@ -238,6 +263,10 @@ __global__ void k_q1_diag(MeshDev mc, const double* __restrict__ A, double* __re
 }
 cudaError_t launch_q1_spmv(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st) {
   k_q1_spmv<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, x, y); note_launch();
+  return cudaGetLastError();
+}
+cudaError_t launch_q1_spmv32(const MeshDev& mc, const float* A, const double* x, double* y, cudaStream_t st) {
+  k_q1_spmv32<<<(unsigned)((mc.nn + 255) / 256), 256, 0, st>>>(mc, A, x, y); note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st) {

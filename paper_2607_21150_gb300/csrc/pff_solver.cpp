@@ -61,6 +61,7 @@ struct HLevel {
   MeshDev mesh;
   long long n = 0;
   double *Ke = nullptr, *A = nullptr, *diag = nullptr;
+  float* A32 = nullptr;  // mixed solver: FP32 copy of A for the preconditioner's products
   const uint8_t* mask = nullptr;
   uint8_t* own_mask = nullptr;
   double *b = nullptr, *x = nullptr, *r = nullptr, *work = nullptr;
@@ -80,6 +81,7 @@ struct pff_solver {
   std::vector<LevelWork> lv;
   bool assembled = false;
   double *A = nullptr, *cdiag = nullptr, *cb = nullptr, *cx = nullptr, *cwork = nullptr;
+  float* A32 = nullptr;                 // mixed solver: FP32 copy of the coarse stencil
   double *cV = nullptr, *cZ = nullptr;  // coarse GMRES basis
   double* Ke = nullptr;                 // coarse element matrices [nel][32][32]
   std::vector<HLevel> hl;               // geometric h-hierarchy (coarse_solver 2)
@@ -161,8 +163,12 @@ int cheb_level(pff_solver* s, LevelWork& w, int degree, double lmin, double lmax
   return PFF_OK;
 }
 
+// Products with the assembled coarse level: FP64, or with the mixed solver
+// the FP32 copy of the stencil (the coarse level only preconditions; the
+// transposed product of the adjoint stays FP64).
 int coarse_spmv(pff_solver* s, const MeshDev& mc, const double* x, double* y, cudaStream_t st) {
   if (s->transpose) S_CK(launch_q1_spmv_t(mc, s->A, x, y, st));
+  else if (s->A32) S_CK(launch_q1_spmv32(mc, s->A32, x, y, st));
   else S_CK(launch_q1_spmv(mc, s->A, x, y, st));
   return PFF_OK;
 }
@@ -225,6 +231,7 @@ int vcycle(pff_solver* s, int l, cudaStream_t st) {
 // ---- geometric h-multigrid on the assembled order-1 grid ------------------
 int h_spmv(pff_solver* s, const HLevel& h, const double* x, double* y, cudaStream_t st) {
   if (s->transpose) S_CK(launch_q1_spmv_t(h.mesh, h.A, x, y, st));
+  else if (h.A32) S_CK(launch_q1_spmv32(h.mesh, h.A32, x, y, st));
   else S_CK(launch_q1_spmv(h.mesh, h.A, x, y, st));
   return PFF_OK;
 }
@@ -370,7 +377,7 @@ int arnoldi_level(pff_solver* s, LevelWork& w, cudaStream_t st) {
 
 int arnoldi_hlevel(pff_solver* s, HLevel& h, cudaStream_t st) {
   auto op = [&](const double* vj, double* wv) -> int {
-    S_CK(launch_q1_spmv(h.mesh, h.A, vj, wv, st));
+    S_RC(h_spmv(s, h, vj, wv, st));
     S_CK(launch_dscale<double>(wv, wv, h.diag, h.n, st));
     return PFF_OK;
   };
@@ -388,7 +395,7 @@ int power_coarse(pff_solver* s, cudaStream_t st) {
   S_CK(launch_axpby<double>(v, v, 1.0 / std::sqrt(h), 0.0, n, st));
   double lam = 1.0;
   for (int it = 0; it < s->prm.power_iters; ++it) {
-    S_CK(launch_q1_spmv(c.L->mesh, s->A, v, y, st));
+    S_RC(coarse_spmv(s, c.L->mesh, v, y, st));
     S_CK(launch_dscale<double>(y, y, s->cdiag, n, st));
     S_RC(dev_dots(s, y, 0, 1, y, n, &h, st));
     lam = std::sqrt(h);
@@ -586,6 +593,7 @@ int setup(pff_solver* s, cudaStream_t st, bool eig = true) {
     S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->Ke, s->A,
                                op->geo != nullptr, st));
     S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
+    if (s->A32) S_CK(launch_d2f(s->A32, s->A, 27LL * 16 * c.L->mesh.nn, st));
     if (s->prm.coarse_solver == 0 && eig) S_RC(power_coarse(s, st));
     if (s->prm.coarse_solver == 2) {
       for (size_t l = 1; l < s->hl.size(); ++l) {
@@ -595,6 +603,7 @@ int setup(pff_solver* s, cudaStream_t st, bool eig = true) {
         S_CK(launch_q1_coarsen(f.mesh, h.mesh, f.mask, f.Ke, h.Ke, st));
         S_CK(launch_q1_gather(h.mesh, h.Ke, h.mask, h.A, st));
         S_CK(launch_q1_diag(h.mesh, h.A, h.diag, st));
+        if (h.A32) S_CK(launch_d2f(h.A32, h.A, 27LL * 16 * h.mesh.nn, st));
       }
       if (eig)
         for (HLevel& h : s->hl) S_RC(arnoldi_hlevel(s, h, st));
@@ -611,10 +620,10 @@ void free_solver(pff_solver* s) {
   for (auto& w : s->lv) {
     cudaFree(w.diag); cudaFree(w.b); cudaFree(w.x); cudaFree(w.tmp); cudaFree(w.work);
   }
-  cudaFree(s->A); cudaFree(s->cdiag); cudaFree(s->cb); cudaFree(s->cx); cudaFree(s->cwork);
+  cudaFree(s->A); cudaFree(s->A32); cudaFree(s->cdiag); cudaFree(s->cb); cudaFree(s->cx); cudaFree(s->cwork);
   cudaFree(s->cV); cudaFree(s->cZ); cudaFree(s->Ke);
   for (HLevel& h : s->hl) {
-    if (h.owns) { cudaFree(h.Ke); cudaFree(h.A); cudaFree(h.diag); cudaFree(h.own_mask); }
+    if (h.owns) { cudaFree(h.Ke); cudaFree(h.A); cudaFree(h.A32); cudaFree(h.diag); cudaFree(h.own_mask); }
     cudaFree(h.b); cudaFree(h.x); cudaFree(h.r); cudaFree(h.work);
   }
   cudaFree(s->V); cudaFree(s->Z); cudaFree(s->r); cudaFree(s->dz); cudaFree(s->zold);
@@ -699,6 +708,7 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
   if (s->assembled) {
     const long long nc = s->lv.back().n;
     if (e == cudaSuccess) e = cudaMalloc(&s->A, sizeof(double) * 27 * 16 * (nc / 4));
+    if (e == cudaSuccess && prm->mixed) e = cudaMalloc(&s->A32, sizeof(float) * 27 * 16 * (nc / 4));
     if (e == cudaSuccess) e = cudaMalloc(&s->cdiag, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->cb, sizeof(double) * nc);
     if (e == cudaSuccess) e = cudaMalloc(&s->cx, sizeof(double) * nc);
@@ -715,6 +725,7 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
       h0.n = nc;
       h0.Ke = s->Ke;
       h0.A = s->A;
+      h0.A32 = s->A32;
       h0.diag = s->cdiag;
       h0.mask = Lc->is_fine ? op->mask : Lc->mask;
       s->hl.push_back(h0);
@@ -732,6 +743,7 @@ int pff_create_solver(pff_op* op, int nlevels, pff_level* const* levels, const p
         h.owns = true;
         if (e == cudaSuccess) e = cudaMalloc(&h.Ke, sizeof(double) * 1024 * (size_t)h.mesh.nel);
         if (e == cudaSuccess) e = cudaMalloc(&h.A, sizeof(double) * 27 * 16 * (size_t)h.mesh.nn);
+        if (e == cudaSuccess && prm->mixed) e = cudaMalloc(&h.A32, sizeof(float) * 27 * 16 * (size_t)h.mesh.nn);
         if (e == cudaSuccess) e = cudaMalloc(&h.diag, sizeof(double) * h.n);
         if (e == cudaSuccess) e = cudaMalloc(&h.own_mask, h.n);
         h.mask = h.own_mask;
