@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
   const double g = omp * omp + gl.eta;
   const double gp = -2.0 * omp;
 
-  double taud[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double tau6[6] = {0, 0, 0, 0, 0, 0};  // deviatoric Kirchhoff stress of all branches, Voigt order
   double psid = 0.0;
   // the tangent's products and sums run in double-float on the FP32 pipes
   // (the FP64 pipe is this kernel's bound), converted by integer operations
@@ -208,10 +208,16 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
         flag |= 1;
       }
     }
-    double ti[3];
-    for (int p = 0; p < 3; ++p) ti[p] = 2.0 * mu * af * ed[p];
+    // tau_d += N diag(ti) N^T: the six entries of the symmetric sum (Voigt order)
+    const double tma = 2.0 * mu * af;
+    double Nt[3][3];  // N diag(ti), ti = 2 mu a ed
     for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c) taud[r][c] += N[r][0] * ti[0] * N[c][0] + N[r][1] * ti[1] * N[c][1] + N[r][2] * ti[2] * N[c][2];
+      for (int p = 0; p < 3; ++p) Nt[r][p] = N[r][p] * (tma * ed[p]);
+    for (int v = 0; v < 6; ++v) {
+      int r, c;
+      vo_idx(v, r, c);
+      tau6[v] += Nt[r][0] * N[c][0] + Nt[r][1] * N[c][1] + Nt[r][2] * N[c][2];
+    }
     psid += mu * af * af * s2;
 
     if (br > 0) {  // trial history: C = F^-1 N diag(exp(2 eps_e)) N^T F^-T
@@ -221,10 +227,13 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
       for (int r = 0; r < 3; ++r)
         for (int c = 0; c < 3; ++c) W[r][c] = Fi[r][0] * N[0][c] + Fi[r][1] * N[1][c] + Fi[r][2] * N[2][c];
       const int off = (br == 1) ? 0 : 6;
+      double We[3][3];  // W diag(ee)
+      for (int r = 0; r < 3; ++r)
+        for (int p = 0; p < 3; ++p) We[r][p] = W[r][p] * ee[p];
       for (int v = 0; v < 6; ++v) {
         int r, c;
         vo_idx(v, r, c);
-        hist_new[off + v] = W[r][0] * ee[0] * W[c][0] + W[r][1] * ee[1] * W[c][1] + W[r][2] * ee[2] * W[c][2];
+        hist_new[off + v] = We[r][0] * W[c][0] + We[r][1] * W[c][1] + We[r][2] * W[c][2];
       }
     }
 
@@ -318,6 +327,14 @@ __global__ void __launch_bounds__(128) k_pointwise(const PointArgs a) {
         }
       dpsi[9] = df_madd(dpsi[9], df_mul(two_mua, df_split(s2)), df_split(da_dphi));
     }
+  }
+
+  double taud[3][3];
+  for (int v = 0; v < 6; ++v) {
+    int r, c;
+    vo_idx(v, r, c);
+    taud[r][c] = tau6[v];
+    taud[c][r] = tau6[v];
   }
 
   // volumetric part and the Amor split
