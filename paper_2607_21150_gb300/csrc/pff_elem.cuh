@@ -96,7 +96,6 @@ template <typename T> __host__ __device__ constexpr bool elem_split() { return s
 template <int Q, typename T> __host__ __device__ constexpr int elem_smem_words_t() {
   return elem_split<T>() ? 12 * Q * Q * Q : elem_smem_words<Q>();
 }
-template <int P, int Q> __host__ __device__ constexpr int mat_smem_words() { return 3 * Q * P + Q * Q; }
 
 template <int P, int Q, typename T>
 struct ElemSmem {

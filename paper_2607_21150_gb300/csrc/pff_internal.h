@@ -49,6 +49,42 @@ static_assert((2 * 2 * 2 * elems_per_block(2)) % 2 == 0 && (3 * 3 * 3 * elems_pe
               (4 * 4 * 4 * elems_per_block(4)) % 2 == 0 && (5 * 5 * 5 * elems_per_block(5)) % 2 == 0,
               "FP32 quad layout needs Q^3 EB even");
 
+// Shared-memory words of the 1D matrices in an element kernel (B, D_t, and
+// the collocated derivative D_c; the persistent kernel keeps B and D_c).
+template <int P, int Q> __host__ __device__ constexpr int mat_smem_words() { return 3 * Q * P + Q * Q; }
+
+// Geometry of the persistent FP32-arithmetic level kernel (pff_elem_pipe.cuh);
+// here so that the host tests can check the bulk copies it issues.
+// Stage geometry.  q2eb = points of one Gauss slice of an element block.
+template <int Q> __host__ __device__ constexpr int pipe_q2eb() { return Q * Q * elems_per_block(Q); }
+// Region of one FP32 tail-word run in a slot: the run of 4 q2eb bytes widened
+// to 16-byte boundaries (it starts 0, 4, 8 or 12 bytes into the region).
+template <int Q> __host__ __device__ constexpr int pipe_tail_bytes() { return (4 * pipe_q2eb<Q>() + 12 + 15) / 16 * 16; }
+template <bool BF, bool KX> __host__ __device__ constexpr int pipe_tails() { return BF ? (KX ? 2 : 1) : (KX ? 6 : 3); }
+template <int Q, bool BF, bool KX> __host__ __device__ constexpr int pipe_slot_bytes() {
+  return BF ? (KX ? 144 : 136) * pipe_q2eb<Q>() : 128 * pipe_q2eb<Q>() + pipe_tails<BF, KX>() * pipe_tail_bytes<Q>();
+}
+// Per element: the values at the Gauss points (4 Q^3), then the ping-pong
+// buffer of the contractions, which holds the two slice buffers (2 x 8 Q^2)
+// during the slice loop.
+template <int Q> __host__ __device__ constexpr int pipe_elem_words() {
+  return 4 * Q * Q * Q + (4 * Q * Q * Q > 16 * Q * Q ? 4 * Q * Q * Q : 16 * Q * Q);
+}
+// Element stride in shared memory: the element's words, padded to Q^2 mod 32,
+// so that the Q^2 threads of consecutive elements fall on consecutive banks
+// (Q = 5: 1017 instead of 1000 words cuts the wavefronts of the contraction
+// stages by a fifth, counted over every access pattern of the kernel).
+template <int Q> __host__ __device__ constexpr int pipe_elem_stride() {
+  return pipe_elem_words<Q>() + ((Q * Q - pipe_elem_words<Q>()) % 32 + 32) % 32;
+}
+template <int P, int Q, bool BF, bool KX> __host__ __device__ constexpr int pipe_smem_bytes() {
+  return 2 * pipe_slot_bytes<Q, BF, KX>() + 16 +
+         4 * (mat_smem_words<P, Q>() + elems_per_block(Q) * pipe_elem_stride<Q>());
+}
+// Two resident blocks per SM: 228 KB of shared memory per SM, 1 KB reserved per block.
+template <int P, int Q, bool BF, bool KX> __host__ __device__ constexpr bool pipe_fits() {
+  return pipe_smem_bytes<P, Q, BF, KX>() <= 113 * 1024;
+}
 __host__ __device__ constexpr int sym9(int m, int n) {  // m <= n
   return m * 9 - (m * (m - 1)) / 2 + (n - m);
 }
