@@ -22,7 +22,9 @@
 // The x- and y-derivative outputs of slice k go through a double-buffered
 // slice buffer and are contracted at the next slice, after the barrier that
 // frees the slot; shared memory per element is then 8 Q^3 values (Q = 5), so
-// that two slots and two blocks fit on an SM.
+// that two slots and two blocks fit on an SM.  The interpolation and its
+// transpose are line transforms (fwd_lines / bwd_lines, pff_elem.cuh) with the
+// 1D matrices as kernel parameters; the slice loop stays rolled for P >= 3.
 //
 // Every wait on an mbarrier is bounded (about one second of clock cycles); a
 // wait that runs out sets status bit 32 (the result is then invalid).  A wait
