@@ -302,14 +302,18 @@ cudaError_t launch_q1_spmv32(const MeshDev& mc, const float* A, const double* x,
 cudaError_t launch_q1_diag(const MeshDev& mc, const double* A, double* d, cudaStream_t st);
 // Sum-factorised element matrices (Ke: [nel][32][32] work space) and a
 // deterministic gather into the stencil storage.
-cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
-                                  const uint8_t* maskc, double* Ke, double* A, int kx, cudaStream_t st);
+// lin32 not null: from the FP32 words (quad layout) in FP32 arithmetic (the
+// mixed solver's preconditioner); Ke and A stay FP64.
+cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const float* lin32, const double* B1,
+                                  const double* D1, const uint8_t* maskc, double* Ke, double* A, int kx,
+                                  cudaStream_t st);
 cudaError_t launch_q1_spmv_t(const MeshDev& mc, const double* A, const double* x, double* y, cudaStream_t st);
 // Geometric h-hierarchy on the order-1 grid (full coarsening, trilinear
 // transfers): Galerkin element matrices of the coarse grid, their gather into
 // the stencil storage, the coarse mask, and the transfers.
+// f32: Galerkin products in FP32 arithmetic (the mixed solver), FP64 storage.
 cudaError_t launch_q1_coarsen(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, const double* Kef,
-                              double* Kec, cudaStream_t st);
+                              double* Kec, bool f32, cudaStream_t st);
 cudaError_t launch_q1_gather(const MeshDev& mc, const double* Ke, const uint8_t* maskc, double* A, cudaStream_t st);
 cudaError_t launch_hmask(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, uint8_t* maskc, cudaStream_t st);
 cudaError_t launch_hprolong_add(const MeshDev& mc, const MeshDev& mf, const double* xc, double* xf,

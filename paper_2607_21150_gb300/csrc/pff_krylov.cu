@@ -318,18 +318,30 @@ __device__ __forceinline__ void q1_combo(int c, int& word, int& rk, int& ck) {
 // (D[Q^3] -> T1[4][Q^2] -> T2[16][Q] -> R[c][64]) with the 1D products
 // X[(fa, fb)][i][(a, b)] = F_fa(i, a) F_fb(i, b) tabulated once per block; the
 // block then sums the combinations of each (f, g) block of Ke.
-template <int Q>
+// T = double: FP64 words (planar layout), FP64 arithmetic; T = float (the
+// mixed solver, whose coarse level only preconditions): the FP32 words (quad
+// layout) and FP32 arithmetic, about sixty times the FP64 rate on GB300.
+// Ke is FP64 either way.
+__device__ __forceinline__ double q1_out(double v) { return v; }
+__device__ __forceinline__ double q1_out(float v) { return df_f2d(v); }
+template <int Q, typename T>
+__device__ __forceinline__ T q1_word(const T* lin, long long blockbase, int word, int k, int t, long long stride) {
+  constexpr long long q2eb = (long long)Q * Q * elems_per_block(Q);
+  if constexpr (sizeof(T) == 8) return lin[blockbase + (long long)word * stride + (long long)k * q2eb + t];
+  else return lin[blockbase + lin32_word(word, k, t, stride, q2eb)];
+}
+template <int Q, typename T>
 __global__ void __launch_bounds__(kQ1Threads)
-k_q1_elem(int nel, int ncombo, const double* __restrict__ lin, const double* __restrict__ B1,
+k_q1_elem(int nel, int ncombo, const T* __restrict__ lin, const double* __restrict__ B1,
           const double* __restrict__ D1, double* __restrict__ Ke) {
   constexpr int Q2 = Q * Q, Q3 = Q2 * Q;
   constexpr int EB = elems_per_block(Q);
   constexpr int kWarps = kQ1Threads / 32;
   constexpr int kScratch = Q3 + 4 * Q2 + 16 * Q;
-  extern __shared__ double sm[];
-  double* R = sm;                                   // [67][64]
-  double* X = R + kQ1Combos * 64;                   // [4][Q][4]
-  double* W = X + 16 * Q;                           // [warps][kScratch]
+  extern __shared__ __align__(16) unsigned char q1_smem[];
+  T* R = reinterpret_cast<T*>(q1_smem);             // [67][64]
+  T* X = R + kQ1Combos * 64;                        // [4][Q][4]
+  T* W = X + 16 * Q;                                // [warps][kScratch]
   int* ctab = reinterpret_cast<int*>(W + kWarps * kScratch);  // [67][3]: word, rk, ck
   const int e = blockIdx.x;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -338,52 +350,53 @@ k_q1_elem(int nel, int ncombo, const double* __restrict__ lin, const double* __r
     const int fa = p >> 1, fb = p & 1, a = ab >> 1, b = ab & 1;
     const double Fa = fa ? D1[i * 2 + a] : B1[i * 2 + a];
     const double Fb = fb ? D1[i * 2 + b] : B1[i * 2 + b];
-    X[idx] = Fa * Fb;
+    X[idx] = (T)(Fa * Fb);
   }
   for (int c = t; c < ncombo; c += kQ1Threads) q1_combo(c, ctab[3 * c], ctab[3 * c + 1], ctab[3 * c + 2]);
   __syncthreads();
   const long long stride = (long long)Q3 * EB;
-  const long long base = (long long)(e / EB) * kLinWords * stride + (e % EB) * Q2;
-  double* D = W + warp * kScratch;
-  double* T1 = D + Q3;
-  double* T2 = T1 + 4 * Q2;
+  const long long blockbase = (long long)(e / EB) * kLinWords * stride;
+  const int t0 = (e % EB) * Q2;
+  T* D = W + warp * kScratch;
+  T* T1 = D + Q3;
+  T* T2 = T1 + 4 * Q2;
   for (int c = warp; c < ncombo; c += kWarps) {
     const int word = ctab[3 * c], rk = ctab[3 * c + 1], ck = ctab[3 * c + 2];
     for (int q = lane; q < Q3; q += 32) {
       const int k = q / Q2, jq = q % Q2;
-      D[q] = lin[base + (long long)word * stride + (long long)k * Q2 * EB + jq];
+      D[q] = q1_word<Q, T>(lin, blockbase, word, k, t0 + jq, stride);
     }
     __syncwarp();
     // direction 0 (i): T1[a0 b0][j + Q k]
-    const double* X0 = X + ((rk == 1) * 2 + (ck == 1)) * 4 * Q;
+    const T* X0 = X + ((rk == 1) * 2 + (ck == 1)) * 4 * Q;
     for (int idx = lane; idx < 4 * Q2; idx += 32) {
       const int ab = idx / Q2, jk = idx % Q2;
-      double s = 0.0;
+      T s = 0;
 #pragma unroll
       for (int i = 0; i < Q; ++i) s += X0[i * 4 + ab] * D[jk * Q + i];
       T1[idx] = s;
     }
     __syncwarp();
     // direction 1 (j): T2[(a0 b0) 4 + (a1 b1)][k]
-    const double* X1 = X + ((rk == 2) * 2 + (ck == 2)) * 4 * Q;
+    const T* X1 = X + ((rk == 2) * 2 + (ck == 2)) * 4 * Q;
     for (int idx = lane; idx < 16 * Q; idx += 32) {
       const int abab = idx / Q, k = idx % Q;
       const int ab0 = abab >> 2, ab1 = abab & 3;
-      const double* Tc = T1 + ab0 * Q2 + k * Q;
-      double s = 0.0;
+      const T* Tc = T1 + ab0 * Q2 + k * Q;
+      T s = 0;
 #pragma unroll
       for (int j = 0; j < Q; ++j) s += X1[j * 4 + ab1] * Tc[j];
       T2[idx] = s;
     }
     __syncwarp();
     // direction 2 (k): R[c][a][b], a = a0 + 2 a1 + 4 a2
-    const double* X2 = X + ((rk == 3) * 2 + (ck == 3)) * 4 * Q;
+    const T* X2 = X + ((rk == 3) * 2 + (ck == 3)) * 4 * Q;
     for (int r = lane; r < 64; r += 32) {
       const int a = r / 8, b = r % 8;
       const int a0 = a & 1, a1 = (a >> 1) & 1, a2 = a >> 2;
       const int b0 = b & 1, b1 = (b >> 1) & 1, b2 = b >> 2;
-      const double* Tc = T2 + ((a0 * 2 + b0) * 4 + (a1 * 2 + b1)) * Q;
-      double s = 0.0;
+      const T* Tc = T2 + ((a0 * 2 + b0) * 4 + (a1 * 2 + b1)) * Q;
+      T s = 0;
 #pragma unroll
       for (int k = 0; k < Q; ++k) s += X2[k * 4 + a2 * 2 + b2] * Tc[k];
       R[c * 64 + r] = s;
@@ -396,7 +409,7 @@ k_q1_elem(int nel, int ncombo, const double* __restrict__ lin, const double* __r
   for (int idx = t; idx < 1024; idx += kQ1Threads) {
     const int row = idx / 32, col = idx % 32;
     const int f = row / 8, a = row % 8, g = col / 8, b = col % 8;
-    double v = 0.0;
+    T v = 0;
     if (f < 3 && g < 3) {
       for (int al = 0; al < 3; ++al)
         for (int be = 0; be < 3; ++be) {
@@ -413,7 +426,7 @@ k_q1_elem(int nel, int ncombo, const double* __restrict__ lin, const double* __r
       for (int c = 63; c < 67; ++c) v += R[c * 64 + a * 8 + b];
       for (int c = 67; c < ncombo; ++c) v += R[c * 64 + a * 8 + b] + R[c * 64 + b * 8 + a];
     }
-    out[idx] = v;
+    out[idx] = q1_out(v);
   }
 }
 
@@ -466,24 +479,29 @@ __global__ void k_q1_gather(MeshDev mc, const double* __restrict__ Ke, const uin
 // W_c[(f, a), (f, A)] = prod_d w((c_d + a_d) / 2, A_d), w(x, 0) = 1 - x,
 // w(x, 1) = x, M the fine Dirichlet mask (prescribed DoFs take no correction).
 // One block per coarse element, the two contractions through shared memory.
-__device__ __forceinline__ double q1_weight(int c, int a, int A) {
-  double w = 1.0;
+// The weights are products of 0, 1/2 and 1: exact in FP32 and FP64.  T =
+// float for the mixed solver (FP32 arithmetic, FP64 storage of Ke).
+template <typename T> __device__ __forceinline__ T q1_weight(int c, int a, int A) {
+  T w = 1;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int cd = (c >> d) & 1, ad = (a >> d) & 1, Ad = (A >> d) & 1;
-    const double x = 0.5 * (cd + ad);
-    w *= Ad ? x : 1.0 - x;
+    const T x = (T)0.5 * (T)(cd + ad);
+    w *= Ad ? x : (T)1 - x;
   }
   return w;
 }
+__device__ __forceinline__ double q1_in(double v, double) { return v; }
+__device__ __forceinline__ float q1_in(double v, float) { return df_split(v).hi; }
 
+template <typename T>
 __global__ void __launch_bounds__(256) k_q1_coarsen(MeshDev mf, MeshDev mc, const uint8_t* __restrict__ maskf,
                                                     const double* __restrict__ Kef, double* __restrict__ Kec) {
-  __shared__ double Kf[1024], Y[1024], Kc[1024];
+  __shared__ T Kf[1024], Y[1024], Kc[1024];
   __shared__ int fnode[8];
   const int E = blockIdx.x, t = threadIdx.x;
   const int Ex = E % mc.nx, Ey = (E / mc.nx) % mc.ny, Ez = E / (mc.nx * mc.ny);
-  for (int idx = t; idx < 1024; idx += blockDim.x) Kc[idx] = 0.0;
+  for (int idx = t; idx < 1024; idx += blockDim.x) Kc[idx] = 0;
   for (int c = 0; c < 8; ++c) {
     const int ex = 2 * Ex + (c & 1), ey = 2 * Ey + ((c >> 1) & 1), ez = 2 * Ez + (c >> 2);
     const long long e = ex + (long long)mf.nx * (ey + (long long)mf.ny * ez);
@@ -493,31 +511,31 @@ __global__ void __launch_bounds__(256) k_q1_coarsen(MeshDev mf, MeshDev mc, cons
     __syncthreads();
     for (int idx = t; idx < 1024; idx += blockDim.x) {
       const int row = idx >> 5, col = idx & 31;
-      double v = Kef[e * 1024 + idx];
-      if (maskf && (maskf[(row >> 3) * mf.nn + fnode[row & 7]] || maskf[(col >> 3) * mf.nn + fnode[col & 7]])) v = 0.0;
+      T v = q1_in(Kef[e * 1024 + idx], T(0));
+      if (maskf && (maskf[(row >> 3) * mf.nn + fnode[row & 7]] || maskf[(col >> 3) * mf.nn + fnode[col & 7]])) v = 0;
       Kf[idx] = v;
     }
     __syncthreads();
     // Y[(f, a)][(g, B)] = sum_b Kf[(f, a)][(g, b)] W_c[b][B]
     for (int idx = t; idx < 1024; idx += blockDim.x) {
       const int row = idx >> 5, g = (idx >> 3) & 3, B = idx & 7;
-      double acc = 0.0;
+      T acc = 0;
 #pragma unroll
-      for (int b = 0; b < 8; ++b) acc += Kf[row * 32 + g * 8 + b] * q1_weight(c, b, B);
+      for (int b = 0; b < 8; ++b) acc += Kf[row * 32 + g * 8 + b] * q1_weight<T>(c, b, B);
       Y[idx] = acc;
     }
     __syncthreads();
     // Kc[(f, A)][(g, B)] += sum_a W_c[a][A] Y[(f, a)][(g, B)]
     for (int idx = t; idx < 1024; idx += blockDim.x) {
       const int f = idx >> 8, A = (idx >> 5) & 7, col = idx & 31;
-      double acc = 0.0;
+      T acc = 0;
 #pragma unroll
-      for (int a = 0; a < 8; ++a) acc += q1_weight(c, a, A) * Y[(f * 8 + a) * 32 + col];
+      for (int a = 0; a < 8; ++a) acc += q1_weight<T>(c, a, A) * Y[(f * 8 + a) * 32 + col];
       Kc[idx] += acc;
     }
   }
   __syncthreads();
-  for (int idx = t; idx < 1024; idx += blockDim.x) Kec[(long long)E * 1024 + idx] = Kc[idx];
+  for (int idx = t; idx < 1024; idx += blockDim.x) Kec[(long long)E * 1024 + idx] = q1_out(Kc[idx]);
 }
 
 // Coarse Dirichlet mask: a coarse vertex is prescribed where the coincident
@@ -588,9 +606,11 @@ __global__ void k_hrestrict(MeshDev mc, MeshDev mf, const double* __restrict__ r
 }
 
 cudaError_t launch_q1_coarsen(const MeshDev& mf, const MeshDev& mc, const uint8_t* maskf, const double* Kef,
-                              double* Kec, cudaStream_t st) {
+                              double* Kec, bool f32, cudaStream_t st) {
   if (mc.nel == 0) return cudaSuccess;
-  k_q1_coarsen<<<mc.nel, 256, 0, st>>>(mf, mc, maskf, Kef, Kec); note_launch();
+  if (f32) k_q1_coarsen<float><<<mc.nel, 256, 0, st>>>(mf, mc, maskf, Kef, Kec);
+  else k_q1_coarsen<double><<<mc.nel, 256, 0, st>>>(mf, mc, maskf, Kef, Kec);
+  note_launch();
   return cudaGetLastError();
 }
 cudaError_t launch_q1_gather(const MeshDev& mc, const double* Ke, const uint8_t* maskc, double* A, cudaStream_t st) {
@@ -613,21 +633,34 @@ cudaError_t launch_hrestrict(const MeshDev& mc, const MeshDev& mf, const double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const double* B1, const double* D1,
-                                  const uint8_t* maskc, double* Ke, double* A, int kx, cudaStream_t st) {
-  const size_t smem = sizeof(double) * (size_t)(kQ1Combos * 64 + 16 * Q + (kQ1Threads / 32) * (Q * Q * Q + 4 * Q * Q + 16 * Q)) +
+template <int Q, typename T>
+void q1_elem_launch(const MeshDev& mc, const T* lin, const double* B1, const double* D1, double* Ke, int ncombo,
+                    cudaStream_t st) {
+  const size_t smem = sizeof(T) * (size_t)(kQ1Combos * 64 + 16 * Q + (kQ1Threads / 32) * (Q * Q * Q + 4 * Q * Q + 16 * Q)) +
                       sizeof(int) * 3 * kQ1Combos;
+  cudaFuncSetAttribute(k_q1_elem<Q, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_q1_elem<Q, T><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, ncombo, lin, B1, D1, Ke); note_launch();
+}
+template <typename T>
+cudaError_t q1_elem_dispatch(const MeshDev& mc, int Q, const T* lin, const double* B1, const double* D1, double* Ke,
+                             int ncombo, cudaStream_t st) {
   switch (Q) {
-    case 2: cudaFuncSetAttribute(k_q1_elem<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<2><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
-    case 3: cudaFuncSetAttribute(k_q1_elem<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<3><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
-    case 4: cudaFuncSetAttribute(k_q1_elem<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<4><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
-    case 5: cudaFuncSetAttribute(k_q1_elem<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_q1_elem<5><<<mc.nel, kQ1Threads, smem, st>>>(mc.nel, kx ? kQ1Combos : 67, lin, B1, D1, Ke); note_launch(); break;
+    case 2: q1_elem_launch<2, T>(mc, lin, B1, D1, Ke, ncombo, st); break;
+    case 3: q1_elem_launch<3, T>(mc, lin, B1, D1, Ke, ncombo, st); break;
+    case 4: q1_elem_launch<4, T>(mc, lin, B1, D1, Ke, ncombo, st); break;
+    case 5: q1_elem_launch<5, T>(mc, lin, B1, D1, Ke, ncombo, st); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_q1_assemble_sf(const MeshDev& mc, int Q, const double* lin, const float* lin32, const double* B1,
+                                  const double* D1, const uint8_t* maskc, double* Ke, double* A, int kx,
+                                  cudaStream_t st) {
+  const int ncombo = kx ? kQ1Combos : 67;
+  const cudaError_t d = lin32 ? q1_elem_dispatch<float>(mc, Q, lin32, B1, D1, Ke, ncombo, st)
+                              : q1_elem_dispatch<double>(mc, Q, lin, B1, D1, Ke, ncombo, st);
+  if (d != cudaSuccess) return d;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const long long nt = mc.nn * 16;

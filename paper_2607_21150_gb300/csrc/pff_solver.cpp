@@ -590,7 +590,10 @@ int setup(pff_solver* s, cudaStream_t st, bool eig = true) {
   if (s->assembled) {
     LevelWork& c = s->lv.back();
     pff_op* op = s->op;
-    S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, c.L->tab.B64, c.L->tab.Dt64, c.L->mask, s->Ke, s->A,
+    // the mixed solver assembles its (preconditioning) coarse level from the
+    // FP32 words in FP32 arithmetic, the FP64 solver from the FP64 words
+    S_CK(launch_q1_assemble_sf(c.L->mesh, op->Q, op->lin64, s->prm.mixed ? op->lin32 : nullptr, c.L->tab.B64,
+                               c.L->tab.Dt64, c.L->mask, s->Ke, s->A,
                                op->geo != nullptr, st));
     S_CK(launch_q1_diag(c.L->mesh, s->A, s->cdiag, st));
     if (s->A32) S_CK(launch_d2f(s->A32, s->A, 27LL * 16 * c.L->mesh.nn, st));
@@ -600,7 +603,7 @@ int setup(pff_solver* s, cudaStream_t st, bool eig = true) {
         HLevel& f = s->hl[l - 1];
         HLevel& h = s->hl[l];
         S_CK(launch_hmask(f.mesh, h.mesh, f.mask, h.own_mask, st));
-        S_CK(launch_q1_coarsen(f.mesh, h.mesh, f.mask, f.Ke, h.Ke, st));
+        S_CK(launch_q1_coarsen(f.mesh, h.mesh, f.mask, f.Ke, h.Ke, s->prm.mixed != 0, st));
         S_CK(launch_q1_gather(h.mesh, h.Ke, h.mask, h.A, st));
         S_CK(launch_q1_diag(h.mesh, h.A, h.diag, st));
         if (h.A32) S_CK(launch_d2f(h.A32, h.A, 27LL * 16 * h.mesh.nn, st));
