@@ -283,8 +283,10 @@ int pff_chebyshev_smooth_noalloc(pff_level* level, pff_prec prec, int degree, do
  * on its structured grid (coarse_solver 2, the default; Jacobi-preconditioned
  * GMRES and Chebyshev-Jacobi remain as 1 and 0)).  Outer iterations, Krylov vectors and
  * inner products are FP64; with mixed = 1 the level operators and smoothers run
- * in FP32 (stored tangent copied by pff_op_enable_f32), the coarsest assembled
- * solve stays FP64.
+ * in FP32 (stored tangent copied by pff_op_enable_f32), and the assembled
+ * coarsest level is built and applied in FP32 arithmetic (element matrices from
+ * the FP32 words, FP32 copy of the stencil for its products; FP64 storage, FP64
+ * vectors and FP64 GMRES); the adjoint's transposed coarse products stay FP64.
  * ------------------------------------------------------------------------- */
 typedef struct pff_solver pff_solver;
 
