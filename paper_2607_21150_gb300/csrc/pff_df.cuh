@@ -4,7 +4,7 @@
 // exact product (p + e = a * b exactly, e = fma(a, b, -p)).  On GB300 the FP32
 // pipes are 61 times wider than the FP64 pipe, so a contraction carried this
 // way can outrun FP64 although it takes about a dozen FP32 instructions per
-// multiply-add (the Q4 Jacobian action: 9.75 ms against 20.1 ms at 64^3), at
+// multiply-add (the Q4 Jacobian action: 8.94 ms against 20.1 ms at 64^3), at
 // an error of about 2^-47 of the magnitudes involved per operation (FP64:
 // 2^-53).
 //

@@ -588,6 +588,24 @@ __device__ __forceinline__ void prefetch_slice(const ElemArgs<T>& a, int k, int 
   }
 }
 
+// Entry k of a thread's column accumulators when k is not a compile-time
+// constant: selects over the unrolled entries, so the column stays in
+// registers.
+template <int Q, typename T>
+__device__ __forceinline__ T column_at(const T (&y)[Q], int k) {
+  T v = y[0];
+#pragma unroll
+  for (int kk = 1; kk < Q; ++kk)
+    if (kk == k) v = y[kk];
+  return v;
+}
+template <int Q, typename T>
+__device__ __forceinline__ void set_column_at(T (&y)[Q], int k, T v) {
+#pragma unroll
+  for (int kk = 0; kk < Q; ++kk)
+    if (kk == k) y[kk] = v;
+}
+
 // Resident blocks per SM the register allocation is held to (Q = 5: 250
 // threads per block, 97 KB of shared memory at 8-byte words): two for FP64 and
 // double-float (<= 128 registers), three for FP32 (<= 85 registers).  With a
@@ -711,7 +729,14 @@ k_elem(const ElemArgs<T> a) {
     backward<P, Q, T>(a, s, e, valid, ij, Y);
     return;
   }
-#pragma unroll
+  // The double-float action keeps this loop rolled: its pointwise map takes
+  // about ten times the instructions of the FP64 one, and five unrolled
+  // slices, each with both orientations of the map, overflow the instruction
+  // cache.  Y[f][k] is then selected and written back by column_at /
+  // set_column_at; o0 joins Y[3][k] after the barrier, in the same order of
+  // operations as the FP64 loop.
+  constexpr bool kRollSlices = sizeof(T) != sizeof(typename ElemTypes<T>::L);
+#pragma unroll(kRollSlices ? 1 : Q)
   for (int k = 0; k < Q; ++k) {
     T o[4][3], o0 = zero<T>();
     if constexpr (MODE == kApply) {
@@ -743,7 +768,7 @@ k_elem(const ElemArgs<T> a) {
     for (int f = 0; f < 4; ++f)
 #pragma unroll
       for (int kk = 0; kk < Q; ++kk) Y[f][kk] = madd(Y[f][kk], s.Dc[k * Q + kk], o[f][2]);
-    Y[3][k] = add(Y[3][k], o0);
+    if constexpr (!kRollSlices) Y[3][k] = add(Y[3][k], o0);
     // x- and y-derivative outputs of this slice through shared memory
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
@@ -753,13 +778,20 @@ k_elem(const ElemArgs<T> a) {
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      T acc = Y[f][k];
+      T acc;
+      if constexpr (kRollSlices) {
+        acc = column_at<Q>(Y[f], k);
+        if (f == 3) acc = add(acc, o0);
+      } else {
+        acc = Y[f][k];
+      }
 #pragma unroll
       for (int m = 0; m < Q; ++m) {
         acc = madd(acc, s.Dc[m * Q + i], s.slice[(2 * f) * Q2 + j * Q + m]);
         acc = madd(acc, s.Dc[m * Q + j], s.slice[(2 * f + 1) * Q2 + m * Q + i]);
       }
-      Y[f][k] = acc;
+      if constexpr (kRollSlices) set_column_at<Q>(Y[f], k, acc);
+      else Y[f][k] = acc;
     }
     __syncthreads();
   }
