@@ -63,7 +63,7 @@ extern "C" {
 #define PFF_STATUS_NONFINITE 4   /* non-finite residual integrand */
 #define PFF_STATUS_PHASE 8       /* phase id >= nphase (phase 0 used) */
 #define PFF_STATUS_RETURN 16     /* hardening return map: local Newton hit its cap (50) */
-#define PFF_STATUS_PIPE 32       /* PFF_F32_BF16 action: a wait for staged words gave up (result invalid) */
+#define PFF_STATUS_PIPE 32       /* FP32-arithmetic level action (PFF_F32 or PFF_F32_BF16 words): a wait for staged words gave up (result invalid) */
 
 /* PFF_DF64: FP64 vectors, the Jacobian action's contractions carried in
  * double-float arithmetic (pairs of FP32 words on the FP32 pipes, error about
